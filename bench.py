@@ -1,0 +1,341 @@
+"""Benchmark: Lloyd iterations/s of accelerated spherical k-means on one GB300.
+
+Workload (default): the RCV-1-like sparse TF-IDF set -- n = 100,000 rows,
+d = 50,000 terms, nnz/row lognormal(mean 120, sigma 0.8) clipped to
+[5, 2000], Zipf(1.1) terms, unit FP32 rows + int32 indices, k = 100 seeded
+initial rows, run to convergence (at most 100 iterations).
+
+One step = one complete clustering run from the seeded initial centers
+(restart, then assign + update until no label changes).  value = Lloyd
+iterations per second over the K timed steps (the variant given, Elkan by
+default); the plain standard variant is timed on the same workload, its label
+sequence must be identical, and its rate is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--variant elkan]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "Lloyd iterations/sec and point·center sims/sec vs plain FP32 standard (same GB300, same labels)"
+K_CLUSTERS = 100
+MAX_ITERS = 100
+INIT_SEED = 2
+
+
+def workload_cfg():
+    return synth.CSR_RCV1_LIKE
+
+
+def config_block(cfg, variant, l2_note):
+    return {"workload": f"rcv1-like sparse TF-IDF n={cfg.n} d={cfg.d} nnz/row~lognormal(120,0.8) Zipf(1.1) "
+                        f"k={K_CLUSTERS} to convergence (max {MAX_ITERS})",
+            "variant": variant, "n": cfg.n, "d": cfg.d, "k": K_CLUSTERS, "seed": cfg.seed,
+            "step": "one full clustering run from the seeded initial rows", "l2": l2_note,
+            "parallelism": "replicas"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------ roofline helpers
+
+def algorithmic_bytes(name, n, d, k, nnz, w1=None):
+    """Compulsory bytes of one launch (the minimum any implementation moves)."""
+    if name == "k_rows_top2":  # CSR + centers once + labels r/w + row scalars + Elkan bound row writes
+        return 8 * (n + 1) + 8 * nnz + 4 * d * k + 8 * n + 8 * n + 4 * n * k + 4 * n
+    if name == "k_elk_bounds":  # u(i,j) read + write, l r/w, a and delta read
+        return 8 * n * k + 8 * n + 4 * n + 4 * n
+    if name == "k_center_sum":  # term-major entries + the sums written + label / norm per row
+        return 8 * nnz + 4 * d * k + 8 * n
+    if name == "k_normalize_drift":
+        return 12 * d * k
+    if name == "k_colnorm_part":
+        return 4 * d * k
+    return None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2107_04074_gb300 import skm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = workload_cfg()
+    csr = synth.tfidf(cfg)
+    init = synth.init_rows(csr.n, K_CLUSTERS, INIT_SEED)
+    n, d, k, nnz = csr.n, csr.d, K_CLUSTERS, csr.nnz
+    rp = torch.from_numpy(csr.row_ptr).to(dev)
+    col = torch.from_numpy(csr.col).to(dev)
+    val = torch.from_numpy(csr.val).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def make(variant):
+        return skm.KMeans(n, d, rp, col, val, k, variant=variant, init_rows=init, stream=stream.cuda_stream)
+
+    def timed_runs(km, steps, warmup):
+        for _ in range(warmup):
+            km.reset(init)
+            km.run(MAX_ITERS)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        total_ms, iters, sims = 0.0, 0, 0
+        l0 = skm.kernel_launches()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            km.reset(init)
+            it, J = km.run(MAX_ITERS)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            iters += it
+            sims += km.stats().total_sims
+        launches = skm.kernel_launches() - l0
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return total_ms, iters, sims, launches, J
+
+    variant = args.variant
+    km = make(variant)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms, iters, sims, launches, J = timed_runs(km, args.steps, args.warmup)
+    clocks = sampler.stop()
+    lab_v = km.labels()
+    # whole-job time = max over ranks
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    it_per_step = iters / args.steps
+    value = world * iters / (ms / 1e3)
+
+    # the plain FP32 standard variant at identical labels
+    std_steps = max(1, min(args.steps, 3))
+    km_std = make("standard")
+    ms_s, iters_s, sims_s, _, J_s = timed_runs(km_std, std_steps, 1)
+    lab_s = km_std.labels()
+    labels_identical = bool(np.array_equal(lab_v, lab_s)) and iters_s / std_steps == it_per_step
+    std_rate = iters_s / (ms_s / 1e3)
+    km_std.close()
+
+    # per-kernel CUDA-event profile of one more run (not part of the timed value)
+    flush.fill_(1.0)
+    km.profile(True)
+    km.reset(init)
+    km.run(MAX_ITERS)
+    prof = km.profile_read()
+    km.profile(False)
+    km.close()
+    tot_prof = sum(v[0] for v in prof.values()) or 1.0
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    top_name, (top_ms, top_n) = top
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, peak_src = 6800.0, "fallback"
+    ab = algorithmic_bytes(top_name, n, d, k, nnz)
+    roof = None
+    if ab is not None:
+        avg_s = top_ms / 1e3 / top_n
+        ach = ab / avg_s / 1e9
+        roof = {"kernel": top_name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
+                "avg_launch_us": round(avg_s * 1e6, 2), "launches": top_n,
+                "algorithmic_bytes_per_launch": ab}
+    kernel_share = {nm: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot_prof, 4)}
+                    for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    pin = [torch.from_numpy(a).pin_memory() for a in (csr.row_ptr, csr.col, csr.val)]
+    host = [t.numpy() for t in pin]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(e2e_steps):
+        kh = skm.KMeans(n, d, host[0], host[1], host[2], k, variant=variant, init_rows=init,
+                        stream=stream.cuda_stream)
+        it, _ = kh.run(MAX_ITERS)
+        lab_h = kh.labels()
+        kh.close()
+        e2e_iters += it
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    assert np.array_equal(lab_h, lab_v)
+    h2d = int(csr.row_ptr.nbytes + csr.col.nbytes + csr.val.nbytes + init.nbytes)
+    d2h = int(4 * n + 8 + 8 * 8)
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Lloyd iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_block(cfg, variant, "L2 flushed (256 MB write) before every step"),
+        "iterations_per_run": it_per_step,
+        "sims_per_s_effective": round(world * n * k * iters / (ms / 1e3), 1),
+        "sims_per_s_evaluated": round(world * sims / (ms / 1e3), 1),
+        "standard_iters_per_s": round(std_rate, 3),
+        "speedup_vs_standard": round(value / world / std_rate, 3),
+        "labels_identical_to_standard": labels_identical,
+        "objective": J,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": roof,
+        "kernel_time_share": kernel_share,
+        "e2e": {"value": round(e2e_iters / e2e_s, 3), "unit": "Lloyd iterations/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "note": "skm_init with host CSR (H2D copy, row norms, term-major copy) + run + labels to host"},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(csr, init, variant)
+    return out
+
+
+def cpu_baseline(csr, init, variant, iters=3):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
+    first `iters` iterations of the same run on the full data."""
+    import oracle
+    X = oracle.Data.from_csr(csr)
+    C0 = oracle.unit_rows(X, init)
+    t0 = time.perf_counter()
+    tr = oracle.run(X, C0, variant, max_iters=iters)
+    dt = time.perf_counter() - t0
+    return {"value": round(tr.iters / dt, 4), "unit": "Lloyd iterations/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {tr.iters} {variant} iterations of the same run on the full data "
+                      f"(early iterations prune least), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: each step = the first 2 iterations of the run (FP64, one
+    host core)."""
+    import oracle
+    cfg = workload_cfg()
+    csr = synth.tfidf(cfg)
+    init = synth.init_rows(csr.n, K_CLUSTERS, INIT_SEED)
+    X = oracle.Data.from_csr(csr)
+    C0 = oracle.unit_rows(X, init)
+    ri = oracle.rinv(X)
+    per_step = 2
+    for _ in range(args.warmup):
+        oracle.run(X, C0, args.variant, max_iters=1, ri=ri)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        its += oracle.run(X, C0, args.variant, max_iters=per_step, ri=ri).iters
+    dt = time.perf_counter() - t0
+    v = its / dt
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "Lloyd iterations/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_block(cfg, args.variant, "n/a (CPU)"),
+            "cpu_baseline": {"value": round(v, 4), "unit": "Lloyd iterations/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step = the first {per_step} {args.variant} iterations, full data"},
+            "e2e": {"value": round(v, 4), "unit": "Lloyd iterations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="elkan", choices=["standard", "hamerly", "elkan", "simp_hamerly",
+                                                            "simp_elkan"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * skm.h -- C ABI of the GB300 spherical k-means library (libskm.so).
+ *
+ * Implements one Lloyd iteration of spherical k-means and its accelerated
+ * variants from "Accelerating Spherical k-Means" (Schubert, Lang, Feher,
+ * arXiv 2107.04074):
+ *   - assignment a(i) = argmax_j <x(i), c(j)> on unit vectors (Section 5),
+ *     pruned with cosine bounds kept directly on similarities (Section 4:
+ *     Eq. eqn:l-bound, Eq. eqn:u-elkan; Section 5.3: Eq. eqn:u-hamerly-2);
+ *   - center update c(j) = sum_{a(i)=j} x(i) / |sum| (Section 5).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns an int status: SKM_OK (0) or a negative SKM_E*
+ *     code (skm_strerror names it).  No call aborts the process.
+ *   - Work is enqueued on the CUDA stream given to skm_init (passed as a
+ *     plain pointer, NULL = legacy default stream).  A call synchronises
+ *     that stream only when it returns a host scalar (non-NULL host output).
+ *   - Device pointers given to skm_init with memspace SKM_DEVICE are
+ *     BORROWED: the caller keeps them alive and unchanged until
+ *     skm_destroy.  With SKM_HOST the library copies them to device memory it
+ *     owns.  All other device memory is allocated by the library
+ *     (cudaMallocAsync on the context's stream) and released by skm_destroy.
+ *   - Rows are normalised by the library (Section 5: all samples normalised
+ *     at initialisation): stored rows need not be exactly unit length, but a
+ *     row may not be all zero.
+ *   - Ties follow one rule everywhere: the current label wins; among the
+ *     other centers the lowest index wins (a point moves only on a strict
+ *     improvement).  All variants therefore produce the label sequence of the
+ *     standard variant.
+ */
+#ifndef SKM_H
+#define SKM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SKM_OK 0
+#define SKM_EINVAL (-1)       /* bad argument or malformed input data */
+#define SKM_ENOMEM (-2)       /* device or host allocation failed */
+#define SKM_ECUDA (-3)        /* a CUDA runtime call or a kernel launch failed */
+#define SKM_ETIMEOUT (-4)     /* a bounded device-side wait expired */
+#define SKM_EUNSUPPORTED (-5) /* valid request this build does not handle */
+#define SKM_ESTATE (-6)       /* call not valid in the context's current state */
+
+/* ---- enumerations ---- */
+/* Variants (Section 5): standard Lloyd; Hamerly (5.3 + center test 5.4);
+ * Elkan (5.2); Simplified Hamerly (5.4, no center test); Simplified Elkan
+ * (5.1, no center-center tests). */
+typedef enum {
+  SKM_STANDARD = 0,
+  SKM_HAMERLY = 1,
+  SKM_ELKAN = 2,
+  SKM_SIMP_HAMERLY = 3,
+  SKM_SIMP_ELKAN = 4
+} skm_variant;
+
+typedef enum { SKM_F32 = 0, SKM_F16 = 1, SKM_BF16 = 2 } skm_dtype;
+typedef enum { SKM_CSR = 0, SKM_DENSE = 1 } skm_layout;
+typedef enum { SKM_DEVICE = 0, SKM_HOST = 1 } skm_memspace;
+
+/* Input vectors x(1..n) in R^d (Section 2: sparse rows stored as sorted
+ * (index, value) pairs; dense rows as plain arrays).
+ *   CSR:   row_ptr int64[n+1] (row_ptr[0] = 0, non-decreasing), col_idx
+ *          int32[nnz] strictly increasing within each row and in [0, d),
+ *          values[nnz] of type dtype.
+ *   DENSE: values[n*d] row-major of type dtype; row_ptr, col_idx unused.
+ * memspace says where all three pointers live. */
+typedef struct {
+  int64_t n;
+  int64_t d;
+  int32_t layout;   /* skm_layout */
+  int32_t dtype;    /* skm_dtype */
+  int32_t memspace; /* skm_memspace */
+  int32_t reserved; /* must be 0 */
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const void* values;
+} skm_data;
+
+/* Options; skm_default_options fills the defaults. */
+typedef struct {
+  int32_t hamerly_tight;   /* 0: Eq. eqn:u-hamerly-2 as in the paper (guarded);
+                              1: the clamped single-center update with p' */
+  int32_t validate;        /* 1 (default): check the CSR structure at init */
+  int64_t pair_capacity;   /* Elkan (point, center) worklist entries; 0 = auto */
+  int32_t row_threshold;   /* Elkan: a point with more candidate centers than
+                              this is recomputed as a whole row; 0 = k/8 */
+  int32_t reserved[7];
+} skm_options;
+
+/* Counters of the last assignment and of the run so far. */
+typedef struct {
+  int64_t iterations;     /* assignments performed since init / reset */
+  int64_t last_changed;   /* labels changed by the last assignment */
+  int64_t last_sims;      /* exact similarities computed by the last assignment */
+  int64_t total_sims;     /* ... summed over all assignments */
+  int64_t last_survivors; /* points that failed the first bound test */
+  int64_t last_rechecks;  /* points still failing after l was tightened (Hamerly)
+                             or (point, center) pairs computed (Elkan) */
+  double objective;       /* J = sum_j |S_j| after the last center update */
+} skm_stats;
+
+typedef struct skm_ctx skm_ctx;
+
+void skm_default_options(skm_options* opt);
+
+/* Create a clustering context for data x with k clusters and the given
+ * variant.  init_rows (HOST, k distinct row ids in [0,n)) picks the initial
+ * centers c(j) = x(init_rows[j]) (Section 6: uniform random rows); NULL draws
+ * them from seed.  Prepares everything the iterations need (row norms, the
+ * term-major copy of the data, work buffers).  stream: a cudaStream_t.
+ * Errors: SKM_EINVAL (k < 1, k > n, malformed CSR, zero or non-finite row,
+ * duplicate init rows), SKM_EUNSUPPORTED (Elkan with k > 4096), SKM_ENOMEM,
+ * SKM_ECUDA.  On error *out is NULL. */
+int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant,
+             const int64_t* init_rows, uint64_t seed, const skm_options* opt,
+             void* stream);
+
+/* Restart from new initial rows (HOST, k ids; NULL = draw from seed) without
+ * repeating the data preparation. */
+int skm_reset(skm_ctx* ctx, const int64_t* init_rows, uint64_t seed);
+
+/* The assignment step (Section 5), pruned per the variant (Sections 5.1-5.4).
+ * The first call after init/reset (or after skm_set_centers/labels) computes
+ * all n*k similarities and initialises the bounds.  n_changed (HOST, may be
+ * NULL): labels changed; non-NULL synchronises the stream. */
+int skm_assign(skm_ctx* ctx, int64_t* n_changed);
+
+/* The center update (Section 5): c(j) = normalised member sum; a cluster with
+ * a zero sum keeps its center.  Also computes the center drift
+ * p(j) = <c(j), c'(j)> (Section 4) and, for Elkan and Hamerly, the
+ * center-center bounds cc and s (Section 5.2).  objective (HOST, may be NULL):
+ * J = sum_j |S_j|; non-NULL synchronises. */
+int skm_update_centers(skm_ctx* ctx, double* objective);
+
+/* Iterate assign + update until an assignment changes no label or max_iters
+ * assignments were done.  Outputs (HOST, may be NULL): iterations done and the
+ * final objective.  Synchronises. */
+int skm_run(skm_ctx* ctx, int32_t max_iters, int32_t* iters_done, double* objective);
+
+/* Copy out the labels a(i) (int32[n]) or the centers (float[k*d], row-major
+ * c(j)) to memory in memspace out_space. */
+int skm_get_labels(skm_ctx* ctx, int32_t* out, int32_t out_space);
+int skm_get_centers(skm_ctx* ctx, float* out, int32_t out_space);
+
+/* Overwrite the centers (float[k*d] row-major, in memspace) or the labels
+ * (int32[n], each in [0,k) ).  Invalidates the bounds: the next assignment
+ * recomputes everything.  Used to resume from a checkpoint. */
+int skm_set_centers(skm_ctx* ctx, const float* C, int32_t space);
+int skm_set_labels(skm_ctx* ctx, const int32_t* a, int32_t space);
+
+/* Copy out the bounds for inspection: l (float[n]); u is float[n] for the
+ * Hamerly variants and float[n*k] (row-major u(i,j)) for the Elkan variants;
+ * either pointer may be NULL.  SKM_ESTATE before the first assignment or for
+ * the standard variant. */
+int skm_get_bounds(skm_ctx* ctx, float* l, float* u, int32_t out_space);
+
+int skm_get_stats(skm_ctx* ctx, skm_stats* out);
+
+/* Bytes of bound state a variant keeps for n points and k centers (labels
+ * excluded): standard 0; Hamerly 8n (two FP32 bounds); Elkan 4n + 4nk. */
+int skm_bound_bytes(int32_t variant, int64_t n, int32_t k, int64_t* bytes);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t skm_kernel_launches(void);
+
+/* Per-kernel timing for profiling.  skm_profile(ctx, 1) starts bracketing
+ * every kernel the context launches with two CUDA events on its stream (this
+ * adds a little launch overhead); skm_profile(ctx, 0) stops; either call
+ * drops what was recorded.  skm_profile_read reports kernel number idx (in
+ * order of first launch): its name (NUL-terminated, truncated to name_len),
+ * the summed event time in ms and the number of launches.  SKM_EINVAL once
+ * idx is past the last kernel.  Both synchronise the stream. */
+int skm_profile(skm_ctx* ctx, int32_t enable);
+int skm_profile_read(skm_ctx* ctx, int32_t idx, char* name, int32_t name_len, double* total_ms,
+                     int64_t* launches);
+
+void skm_destroy(skm_ctx* ctx);
+const char* skm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKM_H */

@@ -1,0 +1,516 @@
+// The C ABI of libskm (declared in include/skm.h): argument checks, device
+// memory of a context, and the order of the kernels of one Lloyd iteration.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <unordered_set>
+#include <vector>
+
+#include "skm_internal.cuh"
+
+namespace skm {
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t reduction_blocks(int64_t d);
+
+struct ProfRec {
+  const char* name;
+  cudaEvent_t b, e;
+};
+using ProfList = std::vector<ProfRec>;
+
+void prof_begin(skm_ctx* c, const char* name) {
+  if (!c->prof_on) return;
+  ProfRec r{name, nullptr, nullptr};
+  if (cudaEventCreate(&r.b) != cudaSuccess || cudaEventCreate(&r.e) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return;
+  }
+  cudaEventRecord(r.b, c->st);
+  static_cast<ProfList*>(c->prof)->push_back(r);
+}
+
+void prof_end(skm_ctx* c) {
+  if (!c->prof_on) return;
+  ProfList* L = static_cast<ProfList*>(c->prof);
+  if (!L->empty()) cudaEventRecord(L->back().e, c->st);
+}
+
+static void prof_clear(skm_ctx* c) {
+  if (!c->prof) return;
+  ProfList* L = static_cast<ProfList*>(c->prof);
+  for (auto& r : *L) {
+    cudaEventDestroy(r.b);
+    cudaEventDestroy(r.e);
+  }
+  L->clear();
+}
+
+}  // namespace skm
+
+using namespace skm;
+
+namespace {
+
+template <typename T>
+int dalloc(skm_ctx* c, T** p, size_t count) {
+  if (count == 0) count = 1;
+  if (cudaMallocAsync((void**)p, sizeof(T) * count, c->st) != cudaSuccess) {
+    (void)cudaGetLastError();
+    *p = nullptr;
+    return SKM_ENOMEM;
+  }
+  return SKM_OK;
+}
+
+#define TRY(x)                   \
+  do {                           \
+    int r__ = (x);               \
+    if (r__ != SKM_OK) return r__; \
+  } while (0)
+
+size_t dtype_size(int dt) { return dt == SKM_F32 ? 4 : 2; }
+
+uint64_t mix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// k distinct rows from a seed (used when the caller gives no init rows).
+void seeded_rows(int64_t n, int32_t k, uint64_t seed, std::vector<int64_t>& out) {
+  std::unordered_set<int64_t> seen;
+  out.clear();
+  uint64_t ctr = 0;
+  while ((int32_t)out.size() < k) {
+    const int64_t r = (int64_t)(mix64(seed * 0x9E3779B97F4A7C15ull + (ctr++)) % (uint64_t)n);
+    if (seen.insert(r).second) out.push_back(r);
+  }
+}
+
+int set_init(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
+  std::vector<int64_t> rows;
+  if (init_rows) {
+    std::unordered_set<int64_t> seen;
+    for (int32_t j = 0; j < c->k; ++j) {
+      if (init_rows[j] < 0 || init_rows[j] >= c->n || !seen.insert(init_rows[j]).second) return SKM_EINVAL;
+      rows.push_back(init_rows[j]);
+    }
+  } else {
+    seeded_rows(c->n, c->k, seed, rows);
+  }
+  int64_t* drows = nullptr;
+  TRY(dalloc(c, &drows, (size_t)c->k));
+  SKM_CUDA_TRY(cudaMemcpyAsync(drows, rows.data(), sizeof(int64_t) * c->k, cudaMemcpyHostToDevice, c->st));
+  const int rc = init_centers(c, drows);
+  cudaFreeAsync(drows, c->st);
+  // the host vector must outlive the copy
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (rc) return rc;
+  SKM_CUDA_TRY(cudaMemsetAsync(c->a, 0xff, sizeof(int32_t) * c->n, c->st));
+  c->have_bounds = 0;
+  c->moved = 0;
+  std::memset(&c->stats, 0, sizeof(c->stats));
+  return SKM_OK;
+}
+
+void release(skm_ctx* c) {
+  if (!c) return;
+  if (c->prof) {
+    skm::prof_clear(c);
+    delete static_cast<ProfList*>(c->prof);
+    c->prof = nullptr;
+  }
+  void* ptrs[] = {c->own[0], c->own[1], c->own[2], c->rinv,  c->dlt,   c->t_ptr, c->t_row, c->t_val,
+                  c->ch_term, c->ch_idx, c->ch_part, c->multi_term, c->multi_base, c->multi_cnt, c->part64,
+                  c->Ct,     c->S,      c->nrm,    c->red,   c->obj,   c->pdn,   c->pup,   c->qup,
+                  c->hsel,   c->cc,     c->sc,     c->gpart, c->a,     c->lb,    c->ub,    c->w1,
+                  c->w2,     c->w1s,    c->poff,   c->pnum,  c->pslot, c->pj,    c->psim,  c->cnt};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, c->st);
+  cudaStreamSynchronize(c->st);
+  if (c->hcnt) cudaFreeHost(c->hcnt);
+  if (c->hobj) cudaFreeHost(c->hobj);
+  (void)cudaGetLastError();
+  delete c;
+}
+
+int read_counters(skm_ctx* c) {
+  SKM_CUDA_TRY(cudaMemcpyAsync(c->hcnt, c->cnt, sizeof(unsigned long long) * C_NUM, cudaMemcpyDeviceToHost, c->st));
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  c->stats.last_changed = (int64_t)c->hcnt[C_CHANGED];
+  c->stats.last_sims = (int64_t)c->hcnt[C_SIMS];
+  c->stats.last_survivors = (int64_t)c->hcnt[C_W1];
+  const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
+  c->stats.last_rechecks = elk ? (int64_t)c->hcnt[C_PAIRS] : (int64_t)c->hcnt[C_W2];
+  return SKM_OK;
+}
+
+int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t seed) {
+  SKM_CUDA_TRY(cudaGetDevice(&c->dev));
+  SKM_CUDA_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev));
+  const int64_t n = c->n, d = c->d;
+  // ---- data
+  if (x->layout == SKM_CSR) {
+    int64_t nnz = 0;
+    if (x->memspace == SKM_HOST) {
+      nnz = x->row_ptr[n];
+      if (x->row_ptr[0] != 0 || nnz < 0) return SKM_EINVAL;
+    } else {
+      SKM_CUDA_TRY(cudaMemcpyAsync(&nnz, x->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->st));
+      SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+      if (nnz < 0) return SKM_EINVAL;
+    }
+    c->nnz = nnz;
+    if (x->memspace == SKM_HOST) {
+      int64_t* rp = nullptr;
+      int32_t* col = nullptr;
+      char* val = nullptr;
+      TRY(dalloc(c, &rp, (size_t)(n + 1)));
+      c->own[0] = rp;
+      TRY(dalloc(c, &col, (size_t)nnz));
+      c->own[1] = col;
+      TRY(dalloc(c, &val, (size_t)nnz * dtype_size(c->dtype)));
+      c->own[2] = val;
+      SKM_CUDA_TRY(cudaMemcpyAsync(rp, x->row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->st));
+      SKM_CUDA_TRY(cudaMemcpyAsync(col, x->col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->st));
+      SKM_CUDA_TRY(cudaMemcpyAsync(val, x->values, nnz * dtype_size(c->dtype), cudaMemcpyHostToDevice, c->st));
+      c->rp = rp;
+      c->col = col;
+      c->val = val;
+    } else {
+      c->rp = x->row_ptr;
+      c->col = x->col_idx;
+      c->val = x->values;
+    }
+  } else {
+    return SKM_EUNSUPPORTED;
+  }
+  // ---- counters and per-row data
+  TRY(dalloc(c, &c->cnt, C_NUM));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_NUM, c->st));
+  SKM_CUDA_TRY(cudaMallocHost((void**)&c->hcnt, sizeof(unsigned long long) * C_NUM));
+  SKM_CUDA_TRY(cudaMallocHost((void**)&c->hobj, sizeof(double)));
+  TRY(dalloc(c, &c->rinv, (size_t)n));
+  TRY(dalloc(c, &c->dlt, (size_t)n));
+  TRY(prep_rows(c));
+  TRY(read_counters(c));
+  if (c->hcnt[C_ERR]) return SKM_EINVAL;
+  TRY(prep_transpose(c));
+  // ---- centers
+  const int64_t kst = c->kst, k = c->k;
+  TRY(dalloc(c, &c->Ct, (size_t)(d * kst)));
+  TRY(dalloc(c, &c->S, (size_t)(d * kst)));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->S, 0, sizeof(float) * d * kst, c->st));
+  TRY(dalloc(c, &c->nrm, (size_t)(2 * kst)));
+  c->red_blocks = reduction_blocks(d);
+  TRY(dalloc(c, &c->red, (size_t)(c->red_blocks * kst * 3)));
+  TRY(dalloc(c, &c->obj, 1));
+  TRY(dalloc(c, &c->pdn, (size_t)kst));
+  TRY(dalloc(c, &c->pup, (size_t)kst));
+  TRY(dalloc(c, &c->qup, (size_t)kst));
+  TRY(dalloc(c, &c->hsel, HSEL_N));
+  const bool full = (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY);
+  const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
+  const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
+  if (full) {
+    int64_t sp = (d + 4095) / 4096;
+    c->gsplit = (int32_t)(sp < 1 ? 1 : (sp > 64 ? 64 : sp));
+    TRY(dalloc(c, &c->cc, (size_t)(k * kst)));
+    TRY(dalloc(c, &c->sc, (size_t)k));
+    TRY(dalloc(c, &c->gpart, (size_t)(c->gsplit * k * k)));
+  }
+  // ---- labels, bounds, worklists
+  TRY(dalloc(c, &c->a, (size_t)n));
+  if (ham || elk) {
+    TRY(dalloc(c, &c->lb, (size_t)n));
+    TRY(dalloc(c, &c->ub, (size_t)(elk ? n * kst : n)));
+    TRY(dalloc(c, &c->w1, (size_t)n));
+    TRY(dalloc(c, &c->w2, (size_t)n));
+    TRY(dalloc(c, &c->w1s, (size_t)n));
+  }
+  if (elk) {
+    TRY(dalloc(c, &c->poff, (size_t)n));
+    TRY(dalloc(c, &c->pnum, (size_t)n));
+    int64_t cap = c->opt.pair_capacity;
+    if (cap <= 0) {
+      cap = n * k;
+      if (cap > (int64_t(1) << 28)) cap = int64_t(1) << 28;
+    }
+    c->pcap = cap;
+    TRY(dalloc(c, &c->pslot, (size_t)cap));
+    TRY(dalloc(c, &c->pj, (size_t)cap));
+    TRY(dalloc(c, &c->psim, (size_t)cap));
+  }
+  // fixed-point scale of the center sums: |sum| <= n, keep 1 bit of headroom
+  int bits = 1;
+  while ((int64_t(1) << bits) <= n) ++bits;
+  c->fx_scale = std::ldexp(1.0f, 62 - bits);
+  c->fx_inv = std::ldexp(1.0f, -(62 - bits));
+  TRY(set_init(c, init_rows, seed));
+  return SKM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void skm_default_options(skm_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->validate = 1;
+}
+
+int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const int64_t* init_rows, uint64_t seed,
+             const skm_options* opt, void* stream) {
+  if (!out) return SKM_EINVAL;
+  *out = nullptr;
+  if (!x || x->n < 1 || x->d < 1 || k < 1 || k > x->n || x->reserved != 0) return SKM_EINVAL;
+  if (variant < SKM_STANDARD || variant > SKM_SIMP_ELKAN) return SKM_EINVAL;
+  if (x->dtype < SKM_F32 || x->dtype > SKM_BF16) return SKM_EINVAL;
+  if (x->layout != SKM_CSR && x->layout != SKM_DENSE) return SKM_EINVAL;
+  if (x->memspace != SKM_DEVICE && x->memspace != SKM_HOST) return SKM_EINVAL;
+  if (!x->values || (x->layout == SKM_CSR && (!x->row_ptr || !x->col_idx))) return SKM_EINVAL;
+  if (x->d > INT32_MAX || x->n > INT32_MAX) return SKM_EUNSUPPORTED;
+  if ((variant == SKM_ELKAN || variant == SKM_SIMP_ELKAN) && k > 4096) return SKM_EUNSUPPORTED;
+  skm_ctx* c = new (std::nothrow) skm_ctx();
+  if (!c) return SKM_ENOMEM;
+  std::memset(c, 0, sizeof(*c));
+  c->st = (cudaStream_t)stream;
+  c->n = x->n;
+  c->d = x->d;
+  c->k = k;
+  c->kst = (k + 7) / 8 * 8;
+  c->variant = variant;
+  c->layout = x->layout;
+  c->dtype = x->dtype;
+  if (opt) c->opt = *opt;
+  else skm_default_options(&c->opt);
+  c->prof = new (std::nothrow) ProfList();
+  if (!c->prof) {
+    delete c;
+    return SKM_ENOMEM;
+  }
+  const int rc = build_ctx(c, x, init_rows, seed);
+  if (rc != SKM_OK) {
+    release(c);
+    return rc;
+  }
+  *out = c;
+  return SKM_OK;
+}
+
+int skm_reset(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
+  if (!c) return SKM_EINVAL;
+  return set_init(c, init_rows, seed);
+}
+
+int skm_assign(skm_ctx* c, int64_t* n_changed) {
+  if (!c) return SKM_EINVAL;
+  SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_ERR, c->st));
+  int rc;
+  if (!c->have_bounds || c->variant == SKM_STANDARD) {
+    const int mode = (c->variant == SKM_STANDARD) ? 0
+                     : (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) ? 1
+                                                                                      : 2;
+    rc = assign_full(c, mode, nullptr, nullptr, c->n);
+    if (rc == SKM_OK) c->have_bounds = (c->variant != SKM_STANDARD);
+  } else if (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) {
+    rc = hamerly_step(c);
+  } else {
+    rc = elkan_step(c);
+  }
+  if (rc) return rc;
+  c->moved = 0;
+  c->stats.iterations++;
+  if (n_changed) {
+    TRY(read_counters(c));
+    c->stats.total_sims += c->stats.last_sims;
+    *n_changed = c->stats.last_changed;
+  } else {
+    c->stats.last_changed = -1;
+  }
+  return SKM_OK;
+}
+
+int skm_update_centers(skm_ctx* c, double* objective) {
+  if (!c) return SKM_EINVAL;
+  TRY(update_centers(c));
+  c->moved = 1;
+  if (objective) {
+    SKM_CUDA_TRY(cudaMemcpyAsync(c->hobj, c->obj, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    *objective = *c->hobj;
+    c->stats.objective = *c->hobj;
+  }
+  return SKM_OK;
+}
+
+int skm_run(skm_ctx* c, int32_t max_iters, int32_t* iters_done, double* objective) {
+  if (!c || max_iters < 0) return SKM_EINVAL;
+  int32_t it = 0;
+  for (; it < max_iters; ++it) {
+    int64_t ch = 0;
+    TRY(skm_assign(c, &ch));
+    if (ch == 0) {
+      ++it;
+      break;
+    }
+    TRY(skm_update_centers(c, nullptr));
+  }
+  SKM_CUDA_TRY(cudaMemcpyAsync(c->hobj, c->obj, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  c->stats.objective = *c->hobj;
+  if (iters_done) *iters_done = it;
+  if (objective) *objective = *c->hobj;
+  return SKM_OK;
+}
+
+int skm_get_labels(skm_ctx* c, int32_t* out, int32_t space) {
+  if (!c || !out) return SKM_EINVAL;
+  SKM_CUDA_TRY(cudaMemcpyAsync(out, c->a, sizeof(int32_t) * c->n,
+                               space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+  if (space == SKM_HOST) SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  return SKM_OK;
+}
+
+int skm_get_centers(skm_ctx* c, float* out, int32_t space) {
+  if (!c || !out) return SKM_EINVAL;
+  if (space == SKM_DEVICE) return centers_to_rows(c, out);
+  float* tmp = nullptr;
+  TRY(dalloc(c, &tmp, (size_t)(c->k * c->d)));
+  int rc = centers_to_rows(c, tmp);
+  if (rc == SKM_OK && cudaMemcpyAsync(out, tmp, sizeof(float) * c->k * c->d, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+    rc = SKM_ECUDA;
+  cudaFreeAsync(tmp, c->st);
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) rc = SKM_ECUDA;
+  return rc;
+}
+
+int skm_set_centers(skm_ctx* c, const float* C, int32_t space) {
+  if (!c || !C) return SKM_EINVAL;
+  int rc;
+  if (space == SKM_DEVICE) {
+    rc = rows_to_centers(c, C);
+  } else {
+    float* tmp = nullptr;
+    TRY(dalloc(c, &tmp, (size_t)(c->k * c->d)));
+    SKM_CUDA_TRY(cudaMemcpyAsync(tmp, C, sizeof(float) * c->k * c->d, cudaMemcpyHostToDevice, c->st));
+    rc = rows_to_centers(c, tmp);
+    cudaFreeAsync(tmp, c->st);
+    SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  }
+  c->have_bounds = 0;
+  c->moved = 0;
+  return rc;
+}
+
+int skm_set_labels(skm_ctx* c, const int32_t* lab, int32_t space) {
+  if (!c || !lab) return SKM_EINVAL;
+  if (space == SKM_HOST)
+    for (int64_t i = 0; i < c->n; ++i)
+      if (lab[i] < 0 || lab[i] >= c->k) return SKM_EINVAL;
+  SKM_CUDA_TRY(cudaMemcpyAsync(c->a, lab, sizeof(int32_t) * c->n,
+                               space == SKM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->st));
+  if (space == SKM_HOST) SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  c->have_bounds = 0;
+  return SKM_OK;
+}
+
+int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
+  if (!c) return SKM_EINVAL;
+  if (c->variant == SKM_STANDARD || !c->have_bounds) return SKM_ESTATE;
+  const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
+  const cudaMemcpyKind kind = space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (l) SKM_CUDA_TRY(cudaMemcpyAsync(l, c->lb, sizeof(float) * c->n, kind, c->st));
+  if (u) {
+    if (elk)
+      SKM_CUDA_TRY(cudaMemcpy2DAsync(u, sizeof(float) * c->k, c->ub, sizeof(float) * c->kst, sizeof(float) * c->k,
+                                     (size_t)c->n, kind, c->st));
+    else
+      SKM_CUDA_TRY(cudaMemcpyAsync(u, c->ub, sizeof(float) * c->n, kind, c->st));
+  }
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  return SKM_OK;
+}
+
+int skm_get_stats(skm_ctx* c, skm_stats* out) {
+  if (!c || !out) return SKM_EINVAL;
+  *out = c->stats;
+  return SKM_OK;
+}
+
+int skm_bound_bytes(int32_t variant, int64_t n, int32_t k, int64_t* bytes) {
+  if (!bytes || n < 0 || k < 1) return SKM_EINVAL;
+  switch (variant) {
+    case SKM_STANDARD: *bytes = 0; return SKM_OK;
+    case SKM_HAMERLY:
+    case SKM_SIMP_HAMERLY: *bytes = 8 * n; return SKM_OK;
+    case SKM_ELKAN:
+    case SKM_SIMP_ELKAN: *bytes = 4 * n + 4 * n * (int64_t)k; return SKM_OK;
+  }
+  return SKM_EINVAL;
+}
+
+int64_t skm_kernel_launches(void) { return (int64_t)g_launches.load(); }
+
+int skm_profile(skm_ctx* c, int32_t enable) {
+  if (!c) return SKM_EINVAL;
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  prof_clear(c);
+  c->prof_on = enable ? 1 : 0;
+  return SKM_OK;
+}
+
+int skm_profile_read(skm_ctx* c, int32_t idx, char* name, int32_t name_len, double* total_ms, int64_t* launches) {
+  if (!c || idx < 0) return SKM_EINVAL;
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  ProfList* L = static_cast<ProfList*>(c->prof);
+  // distinct kernel names in order of first launch
+  std::vector<const char*> names;
+  for (auto& r : *L) {
+    bool seen = false;
+    for (const char* q : names) seen = seen || std::strcmp(q, r.name) == 0;
+    if (!seen) names.push_back(r.name);
+  }
+  if (idx >= (int32_t)names.size()) return SKM_EINVAL;
+  double tot = 0.0;
+  int64_t cntl = 0;
+  for (auto& r : *L) {
+    if (std::strcmp(r.name, names[idx]) != 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.b, r.e) == cudaSuccess) {
+      tot += ms;
+      ++cntl;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
+  if (name && name_len > 0) {
+    std::strncpy(name, names[idx], (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (total_ms) *total_ms = tot;
+  if (launches) *launches = cntl;
+  return SKM_OK;
+}
+
+void skm_destroy(skm_ctx* c) { release(c); }
+
+const char* skm_strerror(int s) {
+  switch (s) {
+    case SKM_OK: return "ok";
+    case SKM_EINVAL: return "invalid argument or malformed input";
+    case SKM_ENOMEM: return "out of memory";
+    case SKM_ECUDA: return "CUDA error";
+    case SKM_ETIMEOUT: return "device wait timed out";
+    case SKM_EUNSUPPORTED: return "unsupported configuration";
+    case SKM_ESTATE: return "invalid state for this call";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

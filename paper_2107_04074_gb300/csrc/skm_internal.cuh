@@ -1,0 +1,227 @@
+// Internal declarations of libskm: the context, device helpers shared by the
+// kernels, and the host-side launch wrappers each kernel file exports.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/skm.h"
+
+#define SKM_FULL_MASK 0xffffffffu
+
+namespace skm {
+
+// ---------------------------------------------------------------- counters
+// Device counters of one assignment (reset at its start).
+enum Counter {
+  C_CHANGED = 0,  // labels changed
+  C_SIMS = 1,     // exact similarities computed
+  C_W1 = 2,       // points failing the first bound test
+  C_W2 = 3,       // points needing a full row of similarities
+  C_PAIRS = 4,    // Elkan (point, center) pairs reserved (may exceed capacity)
+  C_ERR = 5,      // error flags (bit field)
+  C_NUM = 8
+};
+
+// Data-preparation error bits (C_ERR).
+enum ErrBits { E_COLIDX = 1, E_ORDER = 2, E_ZERO_ROW = 4, E_NONFINITE = 8, E_ROWPTR = 16 };
+
+// Hamerly drift summary (Section 5.3): for the worst-moving center over all
+// j != a(i) we keep, for "a(i) is the argmin/argmax" and "it is not":
+//   [0] argmin p_dn   [1] min p_dn    [2] second min p_dn
+//   [3] argmin p_up   [4] min p_up    [5] second min p_up
+//   [6] argmax q_up   [7] max q_up    [8] second max q_up
+constexpr int HSEL_N = 9;
+
+// --------------------------------------------------------------- helpers
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Canonical similarity of row i to center j: sequential FMA over the row's
+// stored entries in CSR order, starting from 0, then times 1/|x_i|.  Every
+// kernel that produces a similarity uses exactly this order, so all variants
+// see bit-identical values and take identical decisions.
+template <typename VT>
+__device__ __forceinline__ float dot_row_center(int64_t b, int64_t e, const int32_t* __restrict__ col,
+                                                const VT* __restrict__ val, const float* __restrict__ Ct,
+                                                int64_t kst, int j) {
+  float acc = 0.f;
+  for (int64_t p = b; p < e; ++p) acc = __fmaf_rn(to_f32(val[p]), __ldg(Ct + (int64_t)__ldg(col + p) * kst + j), acc);
+  return acc;
+}
+
+// Eq. (eqn:l-bound) with the clamp of the angle triangle inequality, in FP32
+// rounded towards -inf.  The drift of the center is an interval: its cosine p
+// lies in [pd, pu] and its sine is at most q.
+__device__ __forceinline__ float bound_l(float l, float pd, float pu, float q) {
+  if (l < -pd) return -1.f;  // arccos l + arccos p may exceed pi
+  const float lp = (l >= 0.f) ? __fmul_rd(l, pd) : __fmul_rd(l, pu);
+  const float om = __fmul_ru(__fsub_ru(1.f, l), __fadd_ru(1.f, l));
+  const float v = __fsub_rd(lp, __fmul_ru(__fsqrt_ru(om), q));
+  return fmaxf(v, -1.f);
+}
+
+// Eq. (eqn:u-elkan) with the clamp, rounded towards +inf.
+__device__ __forceinline__ float bound_u(float u, float pd, float pu, float q) {
+  if (u > pd) return 1.f;  // arccos u may be below arccos p: the angle can close
+  const float up = (u >= 0.f) ? __fmul_ru(u, pu) : __fmul_ru(u, pd);
+  const float om = __fmul_ru(__fsub_ru(1.f, u), __fadd_ru(1.f, u));
+  const float v = __fadd_ru(up, __fmul_ru(__fsqrt_ru(om), q));
+  return fminf(v, 1.f);
+}
+
+// Hamerly's single upper bound, Eq. (eqn:u-hamerly-2), used when u >= 0 and
+// every other center moved by at most 90 degrees; otherwise (or when tight)
+// the clamped single-center form with the worst drift p' = min_{j != a} p(j).
+__device__ __forceinline__ float bound_u_hamerly(float u, float pd_min, float pu_min, float q_max, int tight) {
+  if (!tight && u >= 0.f && pd_min >= 0.f) {
+    const float om = __fmul_ru(__fsub_ru(1.f, u), __fadd_ru(1.f, u));
+    return fminf(__fadd_ru(u, __fmul_ru(__fsqrt_ru(om), q_max)), 1.f);
+  }
+  return bound_u(u, pd_min, pu_min, q_max);
+}
+
+// Warp-aggregated append of `item` (when take) to list[*count]; returns nothing.
+__device__ __forceinline__ void warp_push(bool take, int32_t item, int32_t* __restrict__ list,
+                                          unsigned long long* __restrict__ count) {
+  const unsigned m = __ballot_sync(SKM_FULL_MASK, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+  base = __shfl_sync(SKM_FULL_MASK, base, leader);
+  if (take) list[base + __popc(m & ((1u << lane) - 1u))] = item;
+}
+
+// ---------------------------------------------------------------- context
+}  // namespace skm
+
+struct skm_ctx {
+  cudaStream_t st;
+  int dev;
+  int nsm;
+  // problem
+  int64_t n, d, nnz;
+  int32_t k, kst;  // kst = row stride of the term-major center arrays (k rounded up to 8)
+  int32_t variant, layout, dtype;
+  skm_options opt;
+  // data (borrowed, or owned copies when given in host memory)
+  const int64_t* rp;
+  const int32_t* col;
+  const void* val;
+  void* own[3];
+  // preparation
+  float* rinv;         // [n] 1/|x_i| (FP32 of the FP64 value)
+  float* dlt;          // [n] delta_i: bound on the FP32 error of a similarity of row i
+  int64_t* t_ptr;      // [d+1] term-major (CSC) offsets
+  int32_t* t_row;      // [nnz]
+  void* t_val;         // [nnz] dtype
+  int64_t nchunks;     // center-sum work items
+  int32_t* ch_term;    // [nchunks]
+  int32_t* ch_idx;     // [nchunks] chunk number within its term
+  int64_t* ch_part;    // [nchunks] partial slot (-1: the term has a single chunk)
+  int64_t nparts;      // number of partial slots
+  int64_t nmulti;      // terms with several chunks
+  int32_t* multi_term; // [nmulti]
+  int64_t* multi_base; // [nmulti] first partial slot of the term
+  int32_t* multi_cnt;  // [nmulti] chunks of the term
+  long long* part64;   // [nparts * k] fixed-point partial sums
+  float fx_scale, fx_inv;
+  // centers (term-major, d x kst)
+  float* Ct;    // current centers
+  float* S;     // work: sums, then the next centers
+  double* nrm;  // [k] |S_j|
+  double* red;  // reduction partials
+  int64_t red_blocks;
+  double* obj;  // [1] objective
+  float* pdn;   // [kst] drift cosine lower bound
+  float* pup;   // [kst] drift cosine upper bound
+  float* qup;   // [kst] drift sine upper bound
+  float* hsel;  // [HSEL_N] Hamerly drift summary
+  float* cc;    // [k * kst] center-center bounds (full variants)
+  float* sc;    // [k] s(j)
+  double* gpart;  // Gram partials
+  int32_t gsplit;
+  // labels and bounds
+  int32_t* a;
+  float* lb;  // [n]
+  float* ub;  // [n] (Hamerly) or [n * kst] (Elkan)
+  // worklists
+  int32_t* w1;
+  int32_t* w2;
+  float* w1s;       // [n] tightened similarity to the current center (Elkan)
+  int64_t* poff;    // [n] pair offset per W1 slot
+  int32_t* pnum;    // [n] pair count per W1 slot
+  int32_t* pslot;   // [pcap]
+  int32_t* pj;      // [pcap]
+  float* psim;      // [pcap]
+  int64_t pcap;
+  // counters
+  unsigned long long* cnt;   // device [C_NUM]
+  unsigned long long* hcnt;  // pinned host mirror [C_NUM]
+  double* hobj;              // pinned host [1]
+  // per-kernel CUDA-event timing (skm_profile)
+  int prof_on;
+  void* prof;  // std::vector of (name, start event, end event)
+  // state
+  int have_bounds;
+  int moved;  // centers changed since the last assignment (drift valid)
+  skm_stats stats;
+};
+
+namespace skm {
+
+// Library-wide kernel launch counter (host side).
+void note_launch(int n = 1);
+
+// Per-kernel timing: when enabled on the context, the launch between
+// prof_begin and prof_end is bracketed by two CUDA events on its stream.
+void prof_begin(skm_ctx* c, const char* name);
+void prof_end(skm_ctx* c);
+
+// ------------------------------------------------------- kernel wrappers
+// prep (k_prep.cu)
+int prep_rows(skm_ctx* c);             // validate CSR, rinv, delta
+int prep_transpose(skm_ctx* c);        // CSC copy + center-sum chunks
+int init_centers(skm_ctx* c, const int64_t* rows_dev);
+int scan_i64(cudaStream_t st, const int64_t* in, int64_t* out, int64_t len);  // exclusive, out[len] = total
+int centers_to_rows(skm_ctx* c, float* out /* k x d */);
+int rows_to_centers(skm_ctx* c, const float* in /* k x d */);
+
+// assignment (k_assign.cu)
+int assign_full(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows);
+int hamerly_step(skm_ctx* c);
+int elkan_step(skm_ctx* c);
+
+// update (k_update.cu)
+int update_centers(skm_ctx* c);
+
+}  // namespace skm
+
+#define SKM_CUDA_TRY(x)                      \
+  do {                                       \
+    cudaError_t e__ = (x);                   \
+    if (e__ != cudaSuccess) return SKM_ECUDA; \
+  } while (0)
+
+#define SKM_LAUNCH_CHECK()                                 \
+  do {                                                     \
+    skm::note_launch();                                    \
+    if (cudaPeekAtLastError() != cudaSuccess) {            \
+      (void)cudaGetLastError();                            \
+      return SKM_ECUDA;                                    \
+    }                                                      \
+  } while (0)
+
+// Profiled launch: name the kernel before the launch, close it after.
+#define SKM_PROF_BEGIN(c, name) skm::prof_begin((c), (name))
+#define SKM_LAUNCHED(c)   \
+  do {                    \
+    skm::prof_end(c);     \
+    SKM_LAUNCH_CHECK();   \
+  } while (0)

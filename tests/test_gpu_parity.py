@@ -1,0 +1,277 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Acceptance (per the method: pruning never changes a decision of the standard
+variant):
+  * labels bit-exact, except points whose FP64 top-2 similarity gap is below
+    1e-6 (there the FP32 similarities may legitimately order differently);
+  * centers within 1e-5 (L2 per center; centers are unit vectors) and the
+    objective J within 1e-5 relative;
+  * the GPU variants agree with each other bit for bit (one canonical FP32
+    similarity everywhere).
+Checks are teacher-forced per step: the oracle assigns with the GPU's centers
+and updates with the GPU's labels, so one near-tie cannot derail the rest.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2107_04074_gb300 import skm  # noqa: E402
+
+GAP = 1e-6
+CTOL = 1e-5
+VARIANTS = ["standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan"]
+
+
+def _dev(csr):
+    return (torch.from_numpy(csr.row_ptr).cuda(), torch.from_numpy(csr.col).cuda(),
+            torch.from_numpy(csr.val).cuda())
+
+
+def _km(csr, k, variant, init, dev=None, **kw):
+    rp, col, val = dev if dev is not None else _dev(csr)
+    return skm.KMeans(csr.n, csr.d, rp, col, val, k, variant=variant, init_rows=init, **kw)
+
+
+def _check_assign(X, ri, C_used, prev, got, rows=None):
+    """Oracle assignment with the GPU's centers; returns #labels compared."""
+    if rows is not None:
+        sub = X_rows(X, rows)
+        lab, _, _, _, gap = oracle.assign(sub, oracle.rinv(sub), C_used.astype(np.float64), prev[rows])
+        got = got[rows]
+    else:
+        lab, _, _, _, gap = oracle.assign(X, ri, C_used.astype(np.float64), prev)
+    ok = (lab == got) | (gap < GAP)
+    bad = np.flatnonzero(~ok)
+    assert bad.size == 0, f"{bad.size} label mismatches, e.g. rows {bad[:5]}"
+    return int(np.sum(gap >= GAP))
+
+
+_CSR_CACHE = {}
+
+
+def X_rows(X, rows):
+    key = id(X)
+    csr = _CSR_CACHE[key]
+    return oracle.Data.from_csr(csr.rows(rows))
+
+
+def _teacher_forced(csr, k, variant, init, iters, sample=None, seed=0):
+    X = oracle.Data.from_csr(csr)
+    _CSR_CACHE[id(X)] = csr
+    ri = oracle.rinv(X)
+    km = _km(csr, k, variant, init)
+    prev = np.full(csr.n, -1, dtype=np.int32)
+    rng = np.random.default_rng(seed)
+    seq = []
+    for it in range(iters):
+        C = km.centers()
+        ch = km.assign()
+        lab = km.labels()
+        assert ch == int(np.sum(lab != prev))
+        rows = None if sample is None else np.sort(rng.choice(csr.n, size=min(sample, csr.n), replace=False))
+        _check_assign(X, ri, C, prev, lab, rows)
+        seq.append(lab.copy())
+        if ch == 0:
+            break
+        J = km.update_centers()
+        Cn = km.centers()
+        Co, _, Jo = oracle.update(X, ri, lab, C.astype(np.float64))
+        assert np.max(np.linalg.norm(Cn - Co, axis=1)) < CTOL
+        assert abs(J - Jo) <= CTOL * abs(Jo)
+        prev = lab
+    km.close()
+    return seq
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return synth.tfidf(synth.CSR_TINY)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    # the RCV-1-like recipe at 20k rows: several SpMM tiles, ragged rows
+    return synth.tfidf(synth.scaled(synth.CSR_RCV1_LIKE, n=20000, d=20000, seed=12))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_tiny_teacher_forced(tiny, variant):
+    init = synth.init_rows(tiny.n, 20, 1)
+    _teacher_forced(tiny, 20, variant, init, 20)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_mid_teacher_forced(mid, variant):
+    init = synth.init_rows(mid.n, 100, 2)
+    _teacher_forced(mid, 100, variant, init, 12, sample=3000)
+
+
+def test_variants_bit_identical_and_match_oracle_trajectory(tiny):
+    """All GPU variants give the same label sequence, equal to the oracle's
+    full (untouched) trajectory wherever no near-tie occurred."""
+    init = synth.init_rows(tiny.n, 20, 1)
+    X = oracle.Data.from_csr(tiny)
+    tr = oracle.run(X, oracle.unit_rows(X, init), "standard", max_iters=20)
+    dev = _dev(tiny)
+    seqs = {}
+    for v in VARIANTS:
+        km = _km(tiny, 20, v, init, dev)
+        labs, Js = [], []
+        for _ in range(20):
+            ch = km.assign()
+            labs.append(km.labels())
+            if ch == 0:
+                break
+            Js.append(km.update_centers())
+        seqs[v] = (labs, Js)
+        km.close()
+    ref = seqs["standard"][0]
+    for v, (labs, Js) in seqs.items():
+        assert len(labs) == len(ref), v
+        for a, b in zip(labs, ref):
+            np.testing.assert_array_equal(a, b)
+    assert len(ref) == tr.iters
+    for t in range(tr.iters):
+        np.testing.assert_array_equal(ref[t], tr.labels[t])
+    np.testing.assert_allclose(seqs["standard"][1], tr.J[:len(seqs["standard"][1])], rtol=CTOL)
+
+
+@pytest.mark.parametrize("variant", ["hamerly", "elkan", "simp_hamerly", "simp_elkan"])
+def test_bounds_hold_against_exact_similarities(mid, variant):
+    """Section 4 invariants after every assignment: l(i) <= <x,c_a>,
+    u(i,j) >= <x,c_j> (Elkan), u(i) >= max_{j != a} <x,c_j> (Hamerly)."""
+    k = 100
+    init = synth.init_rows(mid.n, k, 3)
+    X = oracle.Data.from_csr(mid)
+    ri = oracle.rinv(X)
+    Xd = None
+    km = _km(mid, k, variant, init)
+    rows = np.random.default_rng(5).choice(mid.n, 1500, replace=False)
+    sub = mid.rows(rows)
+    Xs = sub.dense() * oracle.rinv(oracle.Data.from_csr(sub))[:, None]
+    for it in range(8):
+        km.assign()
+        C = km.centers().astype(np.float64)
+        l, u = km.bounds()
+        lab = km.labels()
+        S = Xs @ C.T
+        s_a = S[np.arange(len(rows)), lab[rows]]
+        assert np.all(l[rows] <= s_a + 1e-12)
+        if u.ndim == 2:
+            uu = u[rows]
+            mask = np.ones_like(S, dtype=bool)
+            mask[np.arange(len(rows)), lab[rows]] = False
+            assert np.all(uu[mask] >= S[mask] - 1e-12)
+        else:
+            S2 = S.copy()
+            S2[np.arange(len(rows)), lab[rows]] = -np.inf
+            assert np.all(u[rows] >= S2.max(axis=1) - 1e-12)
+        km.update_centers()
+    km.close()
+    del Xd, ri
+
+
+def test_pruning_saves_similarities(mid):
+    init = synth.init_rows(mid.n, 100, 2)
+    dev = _dev(mid)
+    tot = {}
+    for v in ["standard", "hamerly", "elkan"]:
+        km = _km(mid, 100, v, init, dev)
+        s = 0
+        for _ in range(15):
+            ch = km.assign()
+            s += km.stats().last_sims
+            if ch == 0:
+                break
+            km.update_centers()
+        tot[v] = s
+        km.close()
+    assert tot["elkan"] < tot["standard"] and tot["hamerly"] < tot["standard"]
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_half_precision_values(dtype):
+    """FP16 / BF16 stored values: the oracle promotes the same stored values."""
+    base = synth.tfidf(synth.scaled(synth.CSR_TINY, n=1500, seed=7))
+    if dtype == "f16":
+        val = base.val.astype(np.float16)
+        tval = torch.from_numpy(val).cuda()
+        oval = val.astype(np.float64)
+    else:
+        tval = torch.from_numpy(base.val).to(torch.bfloat16).cuda()
+        oval = tval.float().cpu().numpy().astype(np.float64)
+    csr = synth.CSR(base.n, base.d, base.row_ptr, base.col, oval.astype(np.float32))
+    init = synth.init_rows(csr.n, 16, 4)
+    dev = (torch.from_numpy(base.row_ptr).cuda(), torch.from_numpy(base.col).cuda(), tval)
+    X = oracle.Data(csr.n, csr.d, False, csr.row_ptr, csr.col, oval)
+    ri = oracle.rinv(X)
+    km = _km(csr, 16, "elkan", init, dev)
+    prev = np.full(csr.n, -1, np.int32)
+    for _ in range(6):
+        C = km.centers()
+        ch = km.assign()
+        lab = km.labels()
+        _check_assign(X, ri, C, prev, lab)
+        if ch == 0:
+            break
+        km.update_centers()
+        Co, _, _ = oracle.update(X, ri, lab, C.astype(np.float64))
+        assert np.max(np.linalg.norm(km.centers() - Co, axis=1)) < CTOL
+        prev = lab
+    km.close()
+
+
+def test_host_input_matches_device_input(tiny):
+    init = synth.init_rows(tiny.n, 20, 1)
+    a = _km(tiny, 20, "elkan", init)
+    b = skm.KMeans(tiny.n, tiny.d, tiny.row_ptr, tiny.col, tiny.val, 20, variant="elkan", init_rows=init)
+    ia, Ja = a.run(20)
+    ib, Jb = b.run(20)
+    assert ia == ib and Ja == Jb
+    np.testing.assert_array_equal(a.labels(), b.labels())
+    np.testing.assert_array_equal(a.centers(), b.centers())
+
+
+def test_edge_cases():
+    rng = np.random.default_rng(0)
+    # rows of 1 nnz, rows longer than one 32-entry chunk, a term used by no row
+    n, d = 300, 400
+    dense = np.zeros((n, d), dtype=np.float32)
+    for i in range(n):
+        m = 1 if i % 7 == 0 else (70 if i % 11 == 0 else int(rng.integers(2, 20)))
+        cols = rng.choice(d - 1, size=m, replace=False)
+        dense[i, cols] = rng.uniform(0.1, 1.0, size=m)
+    csr = synth.csr_from_dense(dense)
+    X = oracle.Data.from_csr(csr)
+    for k in (1, 2, 33, n):
+        init = synth.init_rows(n, k, 9)
+        for v in ["standard", "hamerly", "elkan"]:
+            tr = oracle.run(X, oracle.unit_rows(X, init), v, max_iters=10)
+            km = _km(csr, k, v, init)
+            it, J = km.run(10)
+            assert it == tr.iters
+            lab = km.labels()
+            np.testing.assert_array_equal(lab, tr.labels[-1])
+            assert abs(J - tr.J[-1]) <= CTOL * abs(tr.J[-1])
+            km.close()
+
+
+def test_invalid_inputs_rejected():
+    csr = synth.csr_from_dense(np.eye(6, dtype=np.float32))
+    bad_col = csr.col.copy()
+    bad_col[3] = 99
+    with pytest.raises(skm.SkmError):
+        skm.KMeans(6, 6, torch.from_numpy(csr.row_ptr).cuda(), torch.from_numpy(bad_col).cuda(),
+                   torch.from_numpy(csr.val).cuda(), 2)
+    zero = csr.val.copy()
+    zero[2] = 0.0
+    with pytest.raises(skm.SkmError):
+        skm.KMeans(6, 6, torch.from_numpy(csr.row_ptr).cuda(), torch.from_numpy(csr.col).cuda(),
+                   torch.from_numpy(zero).cuda(), 2)
+    with pytest.raises(skm.SkmError):
+        _km(csr, 2, "standard", [1, 1])
