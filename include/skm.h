@@ -45,6 +45,7 @@ extern "C" {
 #define SKM_ETIMEOUT (-4)     /* a bounded device-side wait expired */
 #define SKM_EUNSUPPORTED (-5) /* valid request this build does not handle */
 #define SKM_ESTATE (-6)       /* call not valid in the context's current state */
+#define SKM_ETOOBIG (-7)      /* problem larger than a fixed-size limit of the call */
 
 /* ---- enumerations ---- */
 /* Variants (Section 5): standard Lloyd; Hamerly (5.3 + center test 5.4);
@@ -181,6 +182,30 @@ int skm_profile_read(skm_ctx* ctx, int32_t idx, char* name, int32_t name_len, do
 
 void skm_destroy(skm_ctx* ctx);
 const char* skm_strerror(int status);
+
+/* One standard assignment step that allocates no device memory (the paper has
+ * no counterpart: this exists for callers that cannot call cudaMalloc, e.g.
+ * code running inside another framework's memory pool or under a fixed
+ * memory budget, or a service that must not allocate after start-up).
+ *   x:        CSR data in DEVICE memory (not checked beyond what the kernel
+ *             can see: a row with a column index outside [0,d) or a zero norm
+ *             gets label -1).
+ *   centers:  DEVICE float[k*d], row-major unit centers c(j).
+ *   labels:   DEVICE int32[n], in: current labels (-1 = none), out: the new
+ *             labels a(i) = argmax_j <x(i), c(j)> under the library's tie rule
+ *             -- identical to skm_assign of a standard context holding the
+ *             same centers and labels.
+ *   n_changed: HOST, may be NULL; non-NULL synchronises the stream, returns
+ *             the number of changed labels, and makes the call return
+ *             SKM_EINVAL if some row was malformed.
+ * Scratch lives in a static device array of 16 MiB (plus 16 bytes) that every
+ * GPU loading the library holds until exit: d * round_up(k, 8) must not
+ * exceed 4,194,304, else SKM_ETOOBIG.  The first call on a device looks up the
+ * array's address (cudaGetSymbolAddress); make it before any stream capture.
+ * All calls on a device share the array: calls that overlap on the GPU race
+ * and must be serialised by the caller. */
+int skm_assign_noalloc(const skm_data* x, int32_t k, const float* centers, int32_t* labels,
+                       int64_t* n_changed, void* stream);
 
 #ifdef __cplusplus
 }

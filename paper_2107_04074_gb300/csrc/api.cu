@@ -509,6 +509,7 @@ const char* skm_strerror(int s) {
     case SKM_ETIMEOUT: return "device wait timed out";
     case SKM_EUNSUPPORTED: return "unsupported configuration";
     case SKM_ESTATE: return "invalid state for this call";
+    case SKM_ETOOBIG: return "problem exceeds the fixed-size limit of this call";
   }
   return "unknown status";
 }

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 STANDARD, HAMERLY, ELKAN, SIMP_HAMERLY, SIMP_ELKAN = 0, 1, 2, 3, 4
 VARIANTS = {"standard": STANDARD, "hamerly": HAMERLY, "elkan": ELKAN, "simp_hamerly": SIMP_HAMERLY,
             "simp_elkan": SIMP_ELKAN}
@@ -27,7 +27,7 @@ DEVICE, HOST = 0, 1
 EXPORTS = ["skm_default_options", "skm_init", "skm_reset", "skm_assign", "skm_update_centers", "skm_run",
            "skm_get_labels", "skm_get_centers", "skm_set_centers", "skm_set_labels", "skm_get_bounds",
            "skm_get_stats", "skm_bound_bytes", "skm_kernel_launches", "skm_profile", "skm_profile_read",
-           "skm_destroy", "skm_strerror"]
+           "skm_destroy", "skm_strerror", "skm_assign_noalloc"]
 
 
 class SkmError(RuntimeError):
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = True):
         "skm_profile_read": (ctypes.c_int, [P, i32, P, i32, P, P]),
         "skm_destroy": (None, [P]),
         "skm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "skm_assign_noalloc": (ctypes.c_int, [P, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -120,6 +121,22 @@ def bound_bytes(variant, n: int, k: int) -> int:
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     out = ctypes.c_int64(0)
     _check(load().skm_bound_bytes(v, n, k, ctypes.byref(out)), "skm_bound_bytes")
+    return out.value
+
+
+def assign_noalloc(n: int, d: int, row_ptr, col_idx, values, k: int, centers, labels, stream=None) -> int:
+    """Standard assignment without device allocation (skm_assign_noalloc).
+
+    All arrays are torch CUDA tensors; labels (int32[n]) is updated in place.
+    Returns the number of changed labels (synchronises)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    data = skm_data(n=n, d=d, layout=CSR, dtype=_dtype_code(values.dtype), memspace=DEVICE, reserved=0,
+                    row_ptr=_ptr(row_ptr), col_idx=_ptr(col_idx), values=_ptr(values))
+    out = ctypes.c_int64(0)
+    _check(load().skm_assign_noalloc(ctypes.byref(data), int(k), _ptr(centers), _ptr(labels), ctypes.byref(out),
+                                     ctypes.c_void_p(stream)), "skm_assign_noalloc")
     return out.value
 
 
