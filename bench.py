@@ -171,11 +171,17 @@ def run_ours(args, rank, world, local):
 
     variant = args.variant
     km = make(variant)
+    if args.trace:
+        return trace_run(km, init, n, k)
     sampler = ClockSampler(local)
     sampler.start()
     ms, iters, sims, launches, J = timed_runs(km, args.steps, args.warmup)
     clocks = sampler.stop()
     lab_v = km.labels()
+    if args.quick:
+        km.close()
+        return {"metric": METRIC, "value": round(world * iters / (ms / 1e3), 3), "unit": "Lloyd iterations/s",
+                "quick": True, "ms_per_step": round(ms / args.steps, 4), "iterations_per_run": iters / args.steps}
     # whole-job time = max over ranks
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -267,6 +273,30 @@ def run_ours(args, rank, world, local):
     return out
 
 
+def trace_run(km, init, n, k):
+    """One run, assign and update timed per iteration with per-kernel events."""
+    km.reset(init)
+    rows = []
+    for it in range(MAX_ITERS):
+        km.profile(True)
+        ch = km.assign()
+        st = km.stats()
+        pa = km.profile_read()
+        km.profile(True)
+        if ch:
+            km.update_centers()
+        pu = km.profile_read()
+        km.profile(False)
+        rows.append({"it": it + 1, "changed": ch, "sims": st.last_sims, "survivors": st.last_survivors,
+                     "rows": st.last_rechecks,
+                     "assign_ms": round(sum(v[0] for v in pa.values()), 4),
+                     "update_ms": round(sum(v[0] for v in pu.values()), 4),
+                     "assign_kernels": {kk: round(v[0], 4) for kk, v in pa.items()}})
+        if ch == 0:
+            break
+    return {"trace": rows, "n": n, "k": k}
+
+
 def cpu_baseline(csr, init, variant, iters=3):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
     first `iters` iterations of the same run on the full data."""
@@ -320,6 +350,10 @@ def main():
     ap.add_argument("--variant", default="elkan", choices=["standard", "hamerly", "elkan", "simp_hamerly",
                                                             "simp_elkan"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the timed runs of the chosen variant (for profiler captures)")
+    ap.add_argument("--trace", action="store_true",
+                    help="print a per-iteration table (labels changed, similarities, survivors, kernel ms) and exit")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -87,10 +87,10 @@ typedef struct {
   int32_t hamerly_tight;   /* 0: Eq. eqn:u-hamerly-2 as in the paper (guarded);
                               1: the clamped single-center update with p' */
   int32_t validate;        /* 1 (default): check the CSR structure at init */
-  int64_t pair_capacity;   /* Elkan (point, center) worklist entries; 0 = auto */
   int32_t row_threshold;   /* Elkan: a point with more candidate centers than
-                              this is recomputed as a whole row; 0 = k/8 */
-  int32_t reserved[7];
+                              this (capped at 7) is recomputed as a whole row;
+                              0 = min(k/8, 7) */
+  int32_t reserved[9];
 } skm_options;
 
 /* Counters of the last assignment and of the run so far. */
@@ -100,8 +100,9 @@ typedef struct {
   int64_t last_sims;      /* exact similarities computed by the last assignment */
   int64_t total_sims;     /* ... summed over all assignments */
   int64_t last_survivors; /* points that failed the first bound test */
-  int64_t last_rechecks;  /* points still failing after l was tightened (Hamerly)
-                             or (point, center) pairs computed (Elkan) */
+  int64_t last_rechecks;  /* points recomputed as a whole row of k similarities
+                             (Hamerly: still failing after l was tightened;
+                             Elkan: too many candidate centers) */
   double objective;       /* J = sum_j |S_j| after the last center update */
 } skm_stats;
 

@@ -113,6 +113,8 @@ int set_init(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
   SKM_CUDA_TRY(cudaMemsetAsync(c->a, 0xff, sizeof(int32_t) * c->n, c->st));
   c->have_bounds = 0;
   c->moved = 0;
+  c->s64_valid = 0;
+  c->chg_fresh = 0;
   std::memset(&c->stats, 0, sizeof(c->stats));
   return SKM_OK;
 }
@@ -126,9 +128,10 @@ void release(skm_ctx* c) {
   }
   void* ptrs[] = {c->own[0], c->own[1], c->own[2], c->rinv,  c->dlt,   c->t_ptr, c->t_row, c->t_val,
                   c->ch_term, c->ch_idx, c->ch_part, c->multi_term, c->multi_base, c->multi_cnt, c->part64,
-                  c->Ct,     c->S,      c->nrm,    c->red,   c->obj,   c->pdn,   c->pup,   c->qup,
+                  c->Ct,     c->S64,    c->nrm,    c->red,   c->obj,   c->pdn,   c->pup,   c->qup,
                   c->hsel,   c->cc,     c->sc,     c->gpart, c->a,     c->lb,    c->ub,    c->w1,
-                  c->w2,     c->w1s,    c->poff,   c->pnum,  c->pslot, c->pj,    c->psim,  c->cnt};
+                  c->w2,     c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark, c->dpos, c->dlist,
+                  c->G,      c->rpart};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -144,8 +147,7 @@ int read_counters(skm_ctx* c) {
   c->stats.last_changed = (int64_t)c->hcnt[C_CHANGED];
   c->stats.last_sims = (int64_t)c->hcnt[C_SIMS];
   c->stats.last_survivors = (int64_t)c->hcnt[C_W1];
-  const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
-  c->stats.last_rechecks = elk ? (int64_t)c->hcnt[C_PAIRS] : (int64_t)c->hcnt[C_W2];
+  c->stats.last_rechecks = (int64_t)c->hcnt[C_W2];
   return SKM_OK;
 }
 
@@ -203,8 +205,15 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   // ---- centers
   const int64_t kst = c->kst, k = c->k;
   TRY(dalloc(c, &c->Ct, (size_t)(d * kst)));
-  TRY(dalloc(c, &c->S, (size_t)(d * kst)));
-  SKM_CUDA_TRY(cudaMemsetAsync(c->S, 0, sizeof(float) * d * kst, c->st));
+  TRY(dalloc(c, &c->S64, (size_t)(d * kst)));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->S64, 0, sizeof(long long) * d * kst, c->st));
+  TRY(dalloc(c, &c->chg_i, (size_t)n));
+  TRY(dalloc(c, &c->chg_old, (size_t)n));
+  TRY(dalloc(c, &c->dflag, (size_t)k));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->dflag, 0, sizeof(int32_t) * k, c->st));
+  TRY(dalloc(c, &c->dmark, (size_t)k));
+  TRY(dalloc(c, &c->dpos, (size_t)k));
+  TRY(dalloc(c, &c->dlist, (size_t)k));
   TRY(dalloc(c, &c->nrm, (size_t)(2 * kst)));
   c->red_blocks = reduction_blocks(d);
   TRY(dalloc(c, &c->red, (size_t)(c->red_blocks * kst * 3)));
@@ -217,11 +226,22 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
   const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
   if (full) {
-    int64_t sp = (d + 4095) / 4096;
-    c->gsplit = (int32_t)(sp < 1 ? 1 : (sp > 64 ? 64 : sp));
+    // enough d-splits of the Gram (64 x 64 tiles) for ~4 blocks per SM, each
+    // split >= 256 terms
+    const int64_t tk = (k + 63) / 64, tiles = tk * (tk + 1) / 2;
+    int64_t sp = (4 * c->nsm + tiles - 1) / tiles;
+    if (sp > 128) sp = 128;
+    const int64_t spmax = (d + 255) / 256;
+    if (sp > spmax) sp = spmax;
+    c->gsplit = (int32_t)(sp < 1 ? 1 : sp);
     TRY(dalloc(c, &c->cc, (size_t)(k * kst)));
     TRY(dalloc(c, &c->sc, (size_t)k));
     TRY(dalloc(c, &c->gpart, (size_t)(c->gsplit * k * k)));
+    TRY(dalloc(c, &c->G, (size_t)(k * k)));
+    // Gram rows of at most min(k/4, 64) dirty clusters (same d-splits)
+    c->grow_max = (int32_t)((k + 3) / 4 < 64 ? (k + 3) / 4 : 64);
+    c->rsplit = c->gsplit;
+    TRY(dalloc(c, &c->rpart, (size_t)(c->gsplit * c->grow_max * k)));
   }
   // ---- labels, bounds, worklists
   TRY(dalloc(c, &c->a, (size_t)n));
@@ -230,26 +250,15 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
     TRY(dalloc(c, &c->ub, (size_t)(elk ? n * kst : n)));
     TRY(dalloc(c, &c->w1, (size_t)n));
     TRY(dalloc(c, &c->w2, (size_t)n));
-    TRY(dalloc(c, &c->w1s, (size_t)n));
   }
-  if (elk) {
-    TRY(dalloc(c, &c->poff, (size_t)n));
-    TRY(dalloc(c, &c->pnum, (size_t)n));
-    int64_t cap = c->opt.pair_capacity;
-    if (cap <= 0) {
-      cap = n * k;
-      if (cap > (int64_t(1) << 28)) cap = int64_t(1) << 28;
-    }
-    c->pcap = cap;
-    TRY(dalloc(c, &c->pslot, (size_t)cap));
-    TRY(dalloc(c, &c->pj, (size_t)cap));
-    TRY(dalloc(c, &c->psim, (size_t)cap));
-  }
-  // fixed-point scale of the center sums: |sum| <= n, keep 1 bit of headroom
+  // fixed-point scale of the center sums: an entry |x| <= 1 maps below 2^40
+  // (the 20 + 20 bit split of k_center_sum) and |sum| <= n must stay below
+  // 2^62 in the 64-bit partials
   int bits = 1;
   while ((int64_t(1) << bits) <= n) ++bits;
-  c->fx_scale = std::ldexp(1.0f, 62 - bits);
-  c->fx_inv = std::ldexp(1.0f, -(62 - bits));
+  const int sbits = (62 - bits) < 40 ? (62 - bits) : 40;
+  c->fx_scale = std::ldexp(1.0f, sbits);
+  c->fx_inv = std::ldexp(1.0f, -sbits);
   TRY(set_init(c, init_rows, seed));
   return SKM_OK;
 }
@@ -325,6 +334,7 @@ int skm_assign(skm_ctx* c, int64_t* n_changed) {
   }
   if (rc) return rc;
   c->moved = 0;
+  c->chg_fresh = 1;
   c->stats.iterations++;
   if (n_changed) {
     TRY(read_counters(c));
@@ -338,7 +348,10 @@ int skm_assign(skm_ctx* c, int64_t* n_changed) {
 
 int skm_update_centers(skm_ctx* c, double* objective) {
   if (!c) return SKM_EINVAL;
+  // without an assignment since the last update no label changed
+  if (!c->chg_fresh) SKM_CUDA_TRY(cudaMemsetAsync(c->cnt + C_CHG, 0, sizeof(unsigned long long), c->st));
   TRY(update_centers(c));
+  c->chg_fresh = 0;
   c->moved = 1;
   if (objective) {
     SKM_CUDA_TRY(cudaMemcpyAsync(c->hobj, c->obj, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -405,6 +418,8 @@ int skm_set_centers(skm_ctx* c, const float* C, int32_t space) {
   }
   c->have_bounds = 0;
   c->moved = 0;
+  c->s64_valid = 0;
+  c->chg_fresh = 0;
   return rc;
 }
 
@@ -417,6 +432,8 @@ int skm_set_labels(skm_ctx* c, const int32_t* lab, int32_t space) {
                                space == SKM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, c->st));
   if (space == SKM_HOST) SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
   c->have_bounds = 0;
+  c->s64_valid = 0;
+  c->chg_fresh = 0;
   return SKM_OK;
 }
 

@@ -2,18 +2,18 @@
 // and Elkan (5.1, 5.2) with bounds kept on cosines (Section 4).
 //
 // Kernels:
-//   k_rows_top2     warp per row: all k similarities of a CSR row against the
-//                   term-major centers (an SpMM row fused with a top-2 argmax
-//                   under the tie rule); initialises / refreshes the bounds.
-//   k_ham_bounds    thread per point: Eq. (eqn:l-bound), Eq. (eqn:u-hamerly-2),
-//                   prune test, compaction of the survivors.
-//   k_tighten       thread per survivor: exact <x, c_a> (l made tight), retest.
-//   k_elk_bounds    warp per point: Eq. (eqn:l-bound) and Eq. (eqn:u-elkan) on
-//                   the whole bound row, prune tests, compaction.
-//   k_elk_compact   warp per survivor: retest with the tight l, append the
-//                   surviving (point, center) pairs in ascending center order.
-//   k_pair_sims     thread per pair: the exact similarity, u(i,j) refreshed.
-//   k_elk_merge     thread per survivor: best candidate under the tie rule.
+//   k_rows_top2      warp per row: all k similarities of a CSR row against the
+//                    term-major centers (an SpMM row fused with a top-2 argmax
+//                    under the tie rule); initialises / refreshes the bounds.
+//   k_ham_bounds     thread per point: Eq. (eqn:l-bound), Eq. (eqn:u-hamerly-2),
+//                    prune test, compaction of the survivors into a worklist.
+//   k_ham_tighten    warp per survivor: exact <x, c_a> (l made tight), retest,
+//                    compaction of the points that need a whole row.
+//   k_elk_bounds     warp per point: Eq. (eqn:l-bound) and Eq. (eqn:u-elkan) on
+//                    the whole bound row, prune tests, compaction of survivors.
+//   k_elk_recompute  8-lane group per survivor: its surviving (point, center)
+//                    pairs compacted into lanes, their exact similarities in
+//                    one pass over the row, reassignment under the tie rule.
 #include <climits>
 
 #include "skm_internal.cuh"
@@ -26,17 +26,23 @@ constexpr int kBlock = 256;
 
 // MODE 0: labels only (standard).  MODE 1: also l(i) and Hamerly's u(i).
 // MODE 2: also l(i) and every Elkan bound u(i,j).
-template <typename VT, int NT, int MODE>
+// Lane L owns the centers j = 128 g + 4 L + c (c = 0..3, g = 0..G-1) and
+// gathers them with one 16-byte load per row entry and group; each center's
+// sum runs over the row entries in CSR order (the canonical order).
+template <typename VT, int G, int MODE>
 __global__ void __launch_bounds__(kBlock) k_rows_top2(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
     int64_t kst, const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt, int64_t nrows,
-    int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, unsigned long long* __restrict__ cnt) {
-  constexpr int KT = 32 * NT;
+    int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, int32_t* __restrict__ chg_i,
+    int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
+  constexpr int KT = 128 * G;                     // centers per pass over the row
+  constexpr int NB = G >= 8 ? 1 : 8 / G;          // row entries batched per step
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = list ? (int64_t)(*list_cnt) : nrows;
   unsigned long long my_changed = 0, my_sims = 0;
+  ChangedBuf chb;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
     const int64_t i = list ? (int64_t)list[w] : w;
     const int64_t b = rp[i], e = rp[i + 1];
@@ -46,13 +52,14 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
     float v1 = -INFINITY, v2 = -INFINITY, vcur = -INFINITY;
     int j1 = INT_MAX;
     for (int j0 = 0; j0 < k; j0 += KT) {
-      float acc[NT];
-      bool ok[NT];
+      float4 acc[G];
+      bool ok[G];  // this lane's 4-center slot of group g lies inside the padded row
 #pragma unroll
-      for (int m = 0; m < NT; ++m) {
-        acc[m] = 0.f;
-        ok[m] = (j0 + m * 32 + lane) < k;
+      for (int g = 0; g < G; ++g) {
+        acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ok[g] = (j0 + g * 128 + lane * 4) < k;
       }
+      const float* cbase = Ct + j0 + lane * 4;
       for (int64_t p0 = b; p0 < e; p0 += 32) {
         int tt = 0;
         float vv = 0.f;
@@ -61,29 +68,63 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
           vv = to_f32(val[p0 + lane]);
         }
         const int nq = (int)min((int64_t)32, e - p0);
-#pragma unroll 4
-        for (int q = 0; q < nq; ++q) {
+        int q = 0;
+        for (; q + NB <= nq; q += NB) {
+          int t[NB];
+          float v[NB];
+          float4 cv[NB][G];
+#pragma unroll
+          for (int u = 0; u < NB; ++u) {
+            t[u] = __shfl_sync(SKM_FULL_MASK, tt, q + u);
+            v[u] = __shfl_sync(SKM_FULL_MASK, vv, q + u);
+          }
+#pragma unroll
+          for (int u = 0; u < NB; ++u)
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+              cv[u][g] = ok[g] ? __ldg(reinterpret_cast<const float4*>(cbase + (int64_t)t[u] * kst + g * 128))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < NB; ++u)
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+              acc[g].x = __fmaf_rn(v[u], cv[u][g].x, acc[g].x);
+              acc[g].y = __fmaf_rn(v[u], cv[u][g].y, acc[g].y);
+              acc[g].z = __fmaf_rn(v[u], cv[u][g].z, acc[g].z);
+              acc[g].w = __fmaf_rn(v[u], cv[u][g].w, acc[g].w);
+            }
+        }
+        for (; q < nq; ++q) {
           const int t = __shfl_sync(SKM_FULL_MASK, tt, q);
           const float v = __shfl_sync(SKM_FULL_MASK, vv, q);
-          const float* crow = Ct + (int64_t)t * kst + j0 + lane;
 #pragma unroll
-          for (int m = 0; m < NT; ++m)
-            if (ok[m]) acc[m] = __fmaf_rn(v, __ldg(crow + m * 32), acc[m]);
+          for (int g = 0; g < G; ++g)
+            if (ok[g]) {
+              const float4 c4 = __ldg(reinterpret_cast<const float4*>(cbase + (int64_t)t * kst + g * 128));
+              acc[g].x = __fmaf_rn(v, c4.x, acc[g].x);
+              acc[g].y = __fmaf_rn(v, c4.y, acc[g].y);
+              acc[g].z = __fmaf_rn(v, c4.z, acc[g].z);
+              acc[g].w = __fmaf_rn(v, c4.w, acc[g].w);
+            }
         }
       }
 #pragma unroll
-      for (int m = 0; m < NT; ++m) {
-        const int j = j0 + m * 32 + lane;
-        if (ok[m]) {
-          const float s = __fmul_rn(acc[m], ri);
-          if (MODE == 2) ub[i * kst + j] = __fadd_ru(s, dl);
-          if (j == cur) vcur = s;
-          if (s > v1) {
-            v2 = v1;
-            v1 = s;
-            j1 = j;
-          } else if (s > v2) {
-            v2 = s;
+      for (int g = 0; g < G; ++g) {
+        const float av[4] = {acc[g].x, acc[g].y, acc[g].z, acc[g].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int j = j0 + g * 128 + lane * 4 + c;
+          if (j < k) {
+            const float s = __fmul_rn(av[c], ri);
+            if (MODE == 2) ub[i * kst + j] = __fadd_ru(s, dl);
+            if (j == cur) vcur = s;
+            if (s > v1) {
+              v2 = v1;
+              v1 = s;
+              j1 = j;
+            } else if (s > v2) {
+              v2 = s;
+            }
           }
         }
       }
@@ -118,7 +159,9 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
       if (MODE >= 1) lb[i] = __fsub_rd(v1, dl);
       if (MODE == 1) ub[i] = (k > 1) ? __fadd_ru(ssec, dl) : -1.f;
     }
+    if (nb != cur) chb.push((int32_t)i, cur, chg_i, chg_old, cnt);
   }
+  chb.flush(chg_i, chg_old, cnt);
   if (lane == 0) {
     if (my_changed) atomicAdd(cnt + C_CHANGED, my_changed);
     if (my_sims) atomicAdd(cnt + C_SIMS, my_sims);
@@ -161,43 +204,49 @@ __global__ void __launch_bounds__(kBlock) k_ham_bounds(int64_t n, const int32_t*
   }
 }
 
-// Thread per survivor: l(i) <- <x(i), c(a(i))> (made tight), then the test
-// again; the points still failing go to `out` (Hamerly) -- for Elkan the
-// tight similarity is kept for the merge and no retest is done here.
-template <typename VT, bool FULL, bool HAMERLY>
-__global__ void __launch_bounds__(kBlock) k_tighten(
+// Warp per survivor (Hamerly): l(i) <- <x(i), c(a(i))> (made tight) with the
+// warp-cooperative canonical similarity, then the test again; the points still
+// failing go to `out`.  Each warp walks 8 consecutive survivors and pushes its
+// failures with one atomic.
+template <typename VT, bool FULL>
+__global__ void __launch_bounds__(kBlock) k_ham_tighten(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int64_t kst,
     const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt, const int32_t* __restrict__ a,
-    float* __restrict__ lb, const float* __restrict__ ub, const float* __restrict__ sc, float* __restrict__ w1s,
-    int32_t* __restrict__ out, unsigned long long* __restrict__ cnt) {
+    float* __restrict__ lb, const float* __restrict__ ub, const float* __restrict__ sc, int32_t* __restrict__ out,
+    unsigned long long* __restrict__ cnt) {
+  constexpr int TP = 8;
+  const int lane = threadIdx.x & 31;
   const int64_t total = (int64_t)(*w1_cnt);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long sims = 0;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
-    const int64_t idx = base + threadIdx.x;
-    bool take = false;
-    int32_t i = 0;
-    if (idx < total) {
-      i = w1[idx];
-      const int32_t ai = a[i];
-      const float s = __fmul_rn(dot_row_center<VT>(rp[i], rp[i + 1], col, val, Ct, kst, ai), rinv[i]);
-      ++sims;
-      const float dl = dlt[i];
-      const float l = __fsub_rd(s, dl);
-      lb[i] = l;
-      if (HAMERLY) {
-        const float L = __fsub_rd(l, 2.f * dl);
-        take = !((L >= ub[i]) || (FULL && L >= 0.f && L >= sc[ai]));
-      } else {
-        w1s[idx] = s;
-      }
+  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * TP < total; tile += nw) {
+    const int64_t s0 = tile * TP;
+    const int rows = (int)min((int64_t)TP, total - s0);
+    int32_t my_i = 0, my_a = 0;
+    int64_t my_b = 0, my_e = 0;
+    if (lane < rows) {
+      my_i = w1[s0 + lane];
+      my_a = a[my_i];
+      my_b = rp[my_i];
+      my_e = rp[my_i + 1];
     }
-    if (HAMERLY) warp_push(take, i, out, cnt + C_W2);
+    unsigned keep = 0;
+    for (int r = 0; r < rows; ++r) {
+      const int32_t i = __shfl_sync(SKM_FULL_MASK, my_i, r);
+      const int32_t ai = __shfl_sync(SKM_FULL_MASK, my_a, r);
+      const int64_t b = __shfl_sync(SKM_FULL_MASK, my_b, r), e = __shfl_sync(SKM_FULL_MASK, my_e, r);
+      const float sim = __fmul_rn(warp_dot_one<VT>(b, e, col, val, Ct, kst, ai), rinv[i]);
+      const float dl = dlt[i];
+      const float l = __fsub_rd(sim, dl);
+      const float L = __fsub_rd(l, 2.f * dl);
+      if (lane == 0) lb[i] = l;
+      if (!((L >= ub[i]) || (FULL && L >= 0.f && L >= sc[ai]))) keep |= 1u << r;
+    }
+    sims += (unsigned long long)rows;
+    warp_push((keep >> lane) & 1u, my_i, out, cnt + C_W2);
   }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) sims += __shfl_xor_sync(SKM_FULL_MASK, sims, o);
-  if ((threadIdx.x & 31) == 0 && sims) atomicAdd(cnt + C_SIMS, sims);
+  if (lane == 0 && sims) atomicAdd(cnt + C_SIMS, sims);
 }
 
 // --------------------------------------------------------------- Elkan
@@ -211,32 +260,50 @@ __device__ __forceinline__ bool elk_cand(int j, int32_t ai, float u, float L, co
   return true;
 }
 
-// Warp per point; each warp walks 32 consecutive points and pushes the
-// survivors of the tile with one atomic.
+// Warp per point; each warp walks a tile of kTile consecutive points: lanes
+// 0..kTile-1 first update l and test the point-level rule for one point each
+// (so the scalar loads overlap), then the warp streams each point's bound
+// row and counts its candidate centers.  A point with 1..cap candidates goes
+// to w1 (recomputed pair by pair), one with more to w2 (recomputed as a whole
+// row); each list gets one atomic per tile.
+constexpr int kTile = 8;
+
 template <bool FULL>
 __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int64_t kst, const int32_t* __restrict__ a,
                                                        float* __restrict__ lb, float* __restrict__ ub,
                                                        const float* __restrict__ dlt, const float* __restrict__ pdn,
                                                        const float* __restrict__ pup, const float* __restrict__ qup,
                                                        const float* __restrict__ cc, const float* __restrict__ sc,
-                                                       int moved, int32_t* __restrict__ w1,
-                                                       unsigned long long* __restrict__ cnt) {
+                                                       int moved, int32_t cap, int32_t* __restrict__ w1,
+                                                       int32_t* __restrict__ w2, unsigned long long* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 32 < n; tile += nw) {
-    unsigned surv = 0;
-    const int64_t i0 = tile * 32;
-    const int rows = (int)min((int64_t)32, n - i0);
+  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * kTile < n; tile += nw) {
+    const int64_t i0 = tile * kTile;
+    const int rows = (int)min((int64_t)kTile, n - i0);
+    int32_t my_a = 0;
+    float my_L = 0.f;
+    bool my_skip = true;
+    if (lane < rows) {
+      const int64_t i = i0 + lane;
+      my_a = a[i];
+      float l = lb[i];
+      if (moved) {
+        l = bound_l(l, pdn[my_a], pup[my_a], qup[my_a]);
+        lb[i] = l;
+      }
+      my_L = __fsub_rd(l, 2.f * dlt[i]);
+      my_skip = FULL && my_L >= 0.f && sc[my_a] <= my_L;
+    }
+    unsigned few = 0, many = 0;
     for (int r = 0; r < rows; ++r) {
       const int64_t i = i0 + r;
-      const int32_t ai = a[i];
-      float l = lb[i];
-      if (moved) l = bound_l(l, pdn[ai], pup[ai], qup[ai]);
-      const float L = __fsub_rd(l, 2.f * dlt[i]);
-      const bool skip_pt = FULL && L >= 0.f && sc[ai] <= L;
+      const int32_t ai = __shfl_sync(SKM_FULL_MASK, my_a, r);
+      const float L = __shfl_sync(SKM_FULL_MASK, my_L, r);
+      const bool skip_pt = __shfl_sync(SKM_FULL_MASK, (int)my_skip, r) != 0;
       float* urow = ub + i * kst;
       const float* ccrow = cc + (int64_t)ai * kst;
-      bool any = false;
+      int mine = 0;
       for (int j4 = lane * 4; j4 < k; j4 += 128) {
         float4 u4 = *reinterpret_cast<const float4*>(urow + j4);
         if (moved) {
@@ -250,179 +317,188 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
           *reinterpret_cast<float4*>(urow + j4) = u4;
         }
         if (!skip_pt) {
-          any |= (j4 + 0 < k) && elk_cand<FULL>(j4 + 0, ai, u4.x, L, ccrow);
-          any |= (j4 + 1 < k) && elk_cand<FULL>(j4 + 1, ai, u4.y, L, ccrow);
-          any |= (j4 + 2 < k) && elk_cand<FULL>(j4 + 2, ai, u4.z, L, ccrow);
-          any |= (j4 + 3 < k) && elk_cand<FULL>(j4 + 3, ai, u4.w, L, ccrow);
+          mine += (j4 + 0 < k) && elk_cand<FULL>(j4 + 0, ai, u4.x, L, ccrow);
+          mine += (j4 + 1 < k) && elk_cand<FULL>(j4 + 1, ai, u4.y, L, ccrow);
+          mine += (j4 + 2 < k) && elk_cand<FULL>(j4 + 2, ai, u4.z, L, ccrow);
+          mine += (j4 + 3 < k) && elk_cand<FULL>(j4 + 3, ai, u4.w, L, ccrow);
         }
       }
-      if (__any_sync(SKM_FULL_MASK, any)) surv |= 1u << r;
-      if (moved && lane == 0) lb[i] = l;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(SKM_FULL_MASK, mine, o);
+      if (mine > cap) many |= 1u << r;
+      else if (mine > 0) few |= 1u << r;
     }
-    warp_push((surv >> lane) & 1u, (int32_t)(i0 + lane), w1, cnt + C_W1);
+    warp_push((few >> lane) & 1u, (int32_t)(i0 + lane), w1, cnt + C_W1);
+    warp_push((many >> lane) & 1u, (int32_t)(i0 + lane), w2, cnt + C_W2);
   }
 }
 
-// Warp per survivor: test every center again with the tight l, append the
-// remaining pairs in ascending center order as one contiguous segment.
-template <bool FULL>
-__global__ void __launch_bounds__(kBlock) k_elk_compact(
-    int32_t k, int64_t kst, const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt,
-    const int32_t* __restrict__ a, const float* __restrict__ lb, const float* __restrict__ ub,
-    const float* __restrict__ dlt, const float* __restrict__ cc, const float* __restrict__ sc,
-    int64_t* __restrict__ poff, int32_t* __restrict__ pnum, int32_t* __restrict__ pslot, int32_t* __restrict__ pj,
-    int64_t pcap, int32_t row_thresh, int32_t* __restrict__ w2, unsigned long long* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// Canonical similarity to one center per lane of an 8-lane group (my_j < 0:
+// the lane computes nothing useful).  The group walks the row 16 entries at a
+// time: each lane loads two entries, the group broadcasts them by width-8
+// shuffles, every lane gathers its 16 center values, then accumulates them in
+// CSR order.  The next chunk's entries are loaded ahead.
+template <typename VT>
+__device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t* __restrict__ col,
+                                            const VT* __restrict__ val, const float* __restrict__ Ct, int64_t kst,
+                                            int my_j, unsigned gmask, int gl) {
+  const bool on = my_j >= 0;
+  const float* cbase = Ct + (on ? my_j : 0);
+  float acc = 0.f;
+  int t0 = 0, t1 = 0;
+  float v0 = 0.f, v1 = 0.f;
+  if (b + gl < e) {
+    t0 = __ldg(col + b + gl);
+    v0 = to_f32(val[b + gl]);
+  }
+  if (b + 8 + gl < e) {
+    t1 = __ldg(col + b + 8 + gl);
+    v1 = to_f32(val[b + 8 + gl]);
+  }
+  for (int64_t p0 = b; p0 < e; p0 += 16) {
+    const int ct0 = t0, ct1 = t1;
+    const float cv0 = v0, cv1 = v1;
+    if (p0 + 16 + gl < e) {
+      t0 = __ldg(col + p0 + 16 + gl);
+      v0 = to_f32(val[p0 + 16 + gl]);
+    }
+    if (p0 + 24 + gl < e) {
+      t1 = __ldg(col + p0 + 24 + gl);
+      v1 = to_f32(val[p0 + 24 + gl]);
+    }
+    const int nq = (int)min((int64_t)16, e - p0);
+    float c[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int t = __shfl_sync(gmask, q < 8 ? ct0 : ct1, q & 7, 8);
+      c[q] = (on && q < nq) ? __ldg(cbase + (int64_t)t * kst) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const float v = __shfl_sync(gmask, q < 8 ? cv0 : cv1, q & 7, 8);
+      if (q < nq) acc = __fmaf_rn(v, c[q], acc);
+    }
+  }
+  return acc;
+}
+
+// Elkan survivors, an 8-lane group per point (four points per warp).  The
+// surviving (point, center) pairs of the point -- a(i) itself and every
+// j != a with u(i,j) > L and, for full Elkan, cc(a,j) > L (Section 5.2) --
+// are compacted into the group's lanes in ascending center order (lane 0:
+// a(i)); one pass over the row computes all their canonical similarities.
+// This makes l(i) tight (<x, c_a>, Section 5.1) and gives the exact u(i,j) of
+// every candidate; the best candidate replaces a(i) only on a strict
+// improvement, and among equal maxima the lowest index wins -- the standard
+// variant's rule, because every center left out satisfies sim <= sim(a)
+// (bounds with the 2 delta margin).  The bound kernel only sends points with
+// 1..7 candidates here; anything else is recomputed as a whole row.
+template <typename VT, bool FULL>
+__global__ void __launch_bounds__(kBlock) k_elk_recompute(
+    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
+    const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
+    int64_t kst, const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt,
+    int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, const float* __restrict__ cc,
+    int32_t* __restrict__ w2, int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
+    unsigned long long* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31, gid = lane >> 3, gl = lane & 7;
+  const unsigned gmask = 0xFFu << (8 * gid);
   const int64_t total = (int64_t)(*w1_cnt);
-  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total; slot += nw) {
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  __shared__ int slot_j[kBlock / 8][8];  // per group: center of each compacted lane
+  int* sj = slot_j[threadIdx.x >> 3];
+  unsigned long long sims = 0, changed = 0;
+  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total; slot += ngroups) {
     const int32_t i = w1[slot];
     const int32_t ai = a[i];
-    const float L = __fsub_rd(lb[i], 2.f * dlt[i]);
-    const bool skip_pt = FULL && L >= 0.f && sc[ai] <= L;
-    const float* urow = ub + (int64_t)i * kst;
+    const float dl = dlt[i];
+    const float L = __fsub_rd(lb[i], 2.f * dl);
+    float* urow = ub + (int64_t)i * kst;
     const float* ccrow = cc + (int64_t)ai * kst;
-    int mine = 0;
-    if (!skip_pt) {
-      for (int j4 = lane * 4; j4 < k; j4 += 128) {
-        const float4 u4 = *reinterpret_cast<const float4*>(urow + j4);
-        mine += (j4 + 0 < k) && elk_cand<FULL>(j4 + 0, ai, u4.x, L, ccrow);
-        mine += (j4 + 1 < k) && elk_cand<FULL>(j4 + 1, ai, u4.y, L, ccrow);
-        mine += (j4 + 2 < k) && elk_cand<FULL>(j4 + 2, ai, u4.z, L, ccrow);
-        mine += (j4 + 3 < k) && elk_cand<FULL>(j4 + 3, ai, u4.w, L, ccrow);
+    __syncwarp(gmask);
+    if (gl == 0) sj[0] = ai;
+    // candidates: lane gl scans 4 consecutive centers per step of 32
+    int m = 0;
+    for (int j0 = 0; j0 < k; j0 += 32) {
+      const int jb = j0 + gl * 4;
+      unsigned bits = 0;
+      if (jb < k) {
+        const float4 u4 = *reinterpret_cast<const float4*>(urow + jb);
+        bits |= ((jb + 0 < k) && elk_cand<FULL>(jb + 0, ai, u4.x, L, ccrow)) ? 1u : 0u;
+        bits |= ((jb + 1 < k) && elk_cand<FULL>(jb + 1, ai, u4.y, L, ccrow)) ? 2u : 0u;
+        bits |= ((jb + 2 < k) && elk_cand<FULL>(jb + 2, ai, u4.z, L, ccrow)) ? 4u : 0u;
+        bits |= ((jb + 3 < k) && elk_cand<FULL>(jb + 3, ai, u4.w, L, ccrow)) ? 8u : 0u;
       }
-    }
-    int tot = mine;
+      const int nb = __popc(bits);
+      int incl = nb;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) tot += __shfl_xor_sync(SKM_FULL_MASK, tot, o);
-    if (tot == 0) {
-      if (lane == 0) pnum[slot] = 0;
-      continue;
-    }
-    if (tot > row_thresh) {
-      // many candidates: the whole row through the SpMM kernel is cheaper
-      // (same similarity order, so the same values)
-      if (lane == 0) {
-        pnum[slot] = 0;
-        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
-        w2[pos] = i;
+      for (int o = 1; o < 8; o <<= 1) {
+        const int y = __shfl_up_sync(gmask, incl, o, 8);
+        if (gl >= o) incl += y;
       }
-      continue;
-    }
-    unsigned long long off = 0;
-    if (lane == 0) off = atomicAdd(cnt + C_PAIRS, (unsigned long long)tot);
-    off = __shfl_sync(SKM_FULL_MASK, off, 0);
-    if ((int64_t)(off + tot) > pcap) {
-      // no room: mark the reserved entries that exist as unused and send the
-      // point to the full recompute
-      for (int64_t q = (int64_t)off + lane; q < pcap && q < (int64_t)off + tot; q += 32) pslot[q] = -1;
-      if (lane == 0) {
-        pnum[slot] = 0;
-        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
-        w2[pos] = i;
-      }
-      continue;
-    }
-    if (lane == 0) {
-      poff[slot] = (int64_t)off;
-      pnum[slot] = tot;
-    }
-    int64_t pos0 = (int64_t)off;
-    for (int g = 0; g * 128 < k; ++g) {
-      const int j4 = g * 128 + lane * 4;
-      unsigned m = 0;
-      if (j4 < k) {
-        const float4 u4 = *reinterpret_cast<const float4*>(urow + j4);
-        m |= ((j4 + 0 < k) && elk_cand<FULL>(j4 + 0, ai, u4.x, L, ccrow)) ? 1u : 0u;
-        m |= ((j4 + 1 < k) && elk_cand<FULL>(j4 + 1, ai, u4.y, L, ccrow)) ? 2u : 0u;
-        m |= ((j4 + 2 < k) && elk_cand<FULL>(j4 + 2, ai, u4.z, L, ccrow)) ? 4u : 0u;
-        m |= ((j4 + 3 < k) && elk_cand<FULL>(j4 + 3, ai, u4.w, L, ccrow)) ? 8u : 0u;
-      }
-      const int c = __popc(m);
-      int incl = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(SKM_FULL_MASK, incl, o);
-        if (lane >= o) incl += y;
-      }
-      int64_t pos = pos0 + (incl - c);
-      for (int b = 0; b < 4; ++b)
-        if (m & (1u << b)) {
-          pslot[pos] = (int32_t)slot;
-          pj[pos] = j4 + b;
+      int pos = m + 1 + (incl - nb);
+      for (int c = 0; c < 4; ++c)
+        if (bits & (1u << c)) {
+          if (pos < 8) sj[pos] = jb + c;  // ascending center order
           ++pos;
         }
-      pos0 += __shfl_sync(SKM_FULL_MASK, incl, 31);
+      m += __shfl_sync(gmask, incl, 7, 8);
     }
-  }
-}
-
-template <typename VT>
-__global__ void __launch_bounds__(kBlock) k_pair_sims(
-    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
-    const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int64_t kst,
-    const int32_t* __restrict__ w1, const int32_t* __restrict__ pslot, const int32_t* __restrict__ pj,
-    const unsigned long long* __restrict__ pcnt, int64_t pcap, float* __restrict__ psim, float* __restrict__ ub,
-    unsigned long long* __restrict__ cnt) {
-  int64_t total = (int64_t)(*pcnt);
-  if (total > pcap) total = pcap;
-  unsigned long long sims = 0;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t slot = pslot[q];
-    if (slot < 0) continue;
-    const int32_t i = w1[slot], j = pj[q];
-    const float s = __fmul_rn(dot_row_center<VT>(rp[i], rp[i + 1], col, val, Ct, kst, j), rinv[i]);
-    psim[q] = s;
-    ub[(int64_t)i * kst + j] = __fadd_ru(s, dlt[i]);
-    ++sims;
-  }
+    __syncwarp(gmask);
+    if (m > 7) {  // not expected (the bound kernel routes such points), handled anyway
+      if (gl == 0) {
+        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
+        w2[pos] = i;
+      }
+      continue;
+    }
+    const int my_j = (gl <= m) ? sj[gl] : -1;
+    const int64_t b = rp[i], e = rp[i + 1];
+    const float sim = __fmul_rn(group8_dot<VT>(b, e, col, val, Ct, kst, my_j, gmask, gl), rinv[i]);
+    const float sa = __shfl_sync(gmask, sim, 0, 8);
+    // best candidate: largest similarity, lowest index among equal ones
+    float bv = (gl >= 1 && gl <= m) ? sim : -INFINITY;
+    int bj = (gl >= 1 && gl <= m) ? my_j : INT_MAX;
 #pragma unroll
-  for (int o = 16; o; o >>= 1) sims += __shfl_xor_sync(SKM_FULL_MASK, sims, o);
-  if ((threadIdx.x & 31) == 0 && sims) atomicAdd(cnt + C_SIMS, sims);
-}
-
-// Thread per survivor with pairs: the pairs are in ascending center order, so
-// "strictly greater" keeps the current label on ties and otherwise the lowest
-// index -- the standard variant's rule.
-__global__ void __launch_bounds__(kBlock) k_elk_merge(
-    int64_t kst, const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt,
-    const float* __restrict__ w1s, const int64_t* __restrict__ poff, const int32_t* __restrict__ pnum,
-    const int32_t* __restrict__ pj, const float* __restrict__ psim, const float* __restrict__ dlt,
-    int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, unsigned long long* __restrict__ cnt) {
-  const int64_t total = (int64_t)(*w1_cnt);
-  unsigned long long changed = 0;
-  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < total;
-       slot += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t np = pnum[slot];
-    if (np == 0) continue;
-    const int32_t i = w1[slot];
-    const int32_t ai = a[i];
-    const int64_t o = poff[slot];
-    float best = w1s[slot];
-    int32_t bj = ai;
-    for (int32_t q = 0; q < np; ++q) {
-      const float s = psim[o + q];
-      if (s > best) {
-        best = s;
-        bj = pj[o + q];
+    for (int o = 4; o; o >>= 1) {
+      const float ov = __shfl_xor_sync(gmask, bv, o, 8);
+      const int oj = __shfl_xor_sync(gmask, bj, o, 8);
+      if (ov > bv || (ov == bv && oj < bj)) {
+        bv = ov;
+        bj = oj;
       }
     }
-    if (bj != ai) {
-      const float dl = dlt[i];
-      a[i] = bj;
-      lb[i] = __fsub_rd(best, dl);
-      ub[(int64_t)i * kst + ai] = __fadd_ru(w1s[slot], dl);
-      ++changed;
+    if (gl >= 1 && gl <= m) urow[my_j] = __fadd_ru(sim, dl);
+    if (gl == 0) {
+      if (m > 0 && bv > sa) {
+        a[i] = bj;
+        lb[i] = __fsub_rd(bv, dl);
+        urow[ai] = __fadd_ru(sa, dl);
+        ++changed;
+        const unsigned long long pos = atomicAdd(cnt + C_CHG, 1ull);
+        chg_i[pos] = i;
+        chg_old[pos] = ai;
+      } else {
+        lb[i] = __fsub_rd(sa, dl);
+      }
+      sims += (unsigned long long)(m + 1);
     }
   }
+  __syncwarp();
 #pragma unroll
-  for (int o = 16; o; o >>= 1) changed += __shfl_xor_sync(SKM_FULL_MASK, changed, o);
-  if ((threadIdx.x & 31) == 0 && changed) atomicAdd(cnt + C_CHANGED, changed);
+  for (int o = 16; o; o >>= 1) {
+    sims += __shfl_xor_sync(SKM_FULL_MASK, sims, o);
+    changed += __shfl_xor_sync(SKM_FULL_MASK, changed, o);
+  }
+  if (lane == 0) {
+    if (sims) atomicAdd(cnt + C_SIMS, sims);
+    if (changed) atomicAdd(cnt + C_CHANGED, changed);
+  }
 }
 
 inline int persistent_grid(const skm_ctx* c, int per_sm = 8) { return c->nsm * per_sm; }
 
-template <typename VT, int NT>
+template <typename VT, int G>
 int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
   int64_t g = list ? (int64_t)persistent_grid(c, 8) : (nrows * 32 + kBlock - 1) / kBlock;
   const int64_t cap = (int64_t)c->nsm * 16;
@@ -432,16 +508,16 @@ int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long l
   SKM_PROF_BEGIN(c, list ? "k_rows_top2(list)" : "k_rows_top2");
   switch (mode) {
     case 0:
-      k_rows_top2<VT, NT, 0><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->cnt);
+      k_rows_top2<VT, G, 0><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
+                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
       break;
     case 1:
-      k_rows_top2<VT, NT, 1><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->cnt);
+      k_rows_top2<VT, G, 1><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
+                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
       break;
     default:
-      k_rows_top2<VT, NT, 2><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->cnt);
+      k_rows_top2<VT, G, 2><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
+                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
   }
   SKM_LAUNCHED(c);
   return SKM_OK;
@@ -450,12 +526,10 @@ int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long l
 template <typename VT>
 int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
   const int k = c->k;
-  if (k <= 32) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows);
-  if (k <= 64) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows);
-  if (k <= 128) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows);
-  if (k <= 256) return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows);
-  if (k <= 512) return launch_rows<VT, 16>(c, mode, list, list_cnt, nrows);
-  return launch_rows<VT, 32>(c, mode, list, list_cnt, nrows);
+  if (k <= 128) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows);
+  if (k <= 256) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows);
+  if (k <= 512) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows);
+  return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows);
 }
 
 template <typename VT>
@@ -472,14 +546,13 @@ int hamerly_step_t(skm_ctx* c) {
   }
   SKM_LAUNCHED(c);
   const VT* v = (const VT*)c->val;
-  SKM_PROF_BEGIN(c, "k_tighten");
+  SKM_PROF_BEGIN(c, "k_ham_tighten");
   if (full) {
-    k_tighten<VT, true, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1,
-                                                       c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w1s, c->w2, c->cnt);
+    k_ham_tighten<VT, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1,
+                                                     c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt);
   } else {
-    k_tighten<VT, false, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1,
-                                                        c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w1s, c->w2,
-                                                        c->cnt);
+    k_ham_tighten<VT, false><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1,
+                                                      c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt);
   }
   SKM_LAUNCHED(c);
   return assign_full_t<VT>(c, 1, c->w2, c->cnt + C_W2, 0);
@@ -489,40 +562,30 @@ template <typename VT>
 int elkan_step_t(skm_ctx* c) {
   const bool full = (c->variant == SKM_ELKAN);
   const int g = persistent_grid(c);
+  // a point with more than min(k/8, 7) candidate centers is recomputed as a
+  // whole row (the per-pair path gives each point an 8-lane group)
+  int32_t row_thresh = c->opt.row_threshold > 0 ? c->opt.row_threshold : (c->k + 7) / 8;
+  if (row_thresh > 7) row_thresh = 7;
   SKM_PROF_BEGIN(c, "k_elk_bounds");
   if (full) {
     k_elk_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
-                                                c->qup, c->cc, c->sc, c->moved, c->w1, c->cnt);
+                                                c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1, c->w2, c->cnt);
   } else {
     k_elk_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
-                                                 c->qup, c->cc, c->sc, c->moved, c->w1, c->cnt);
+                                                 c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1, c->w2, c->cnt);
   }
   SKM_LAUNCHED(c);
   const VT* v = (const VT*)c->val;
-  SKM_PROF_BEGIN(c, "k_tighten");
-  k_tighten<VT, false, false><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1,
-                                                       c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w1s, nullptr,
-                                                       c->cnt);
-  SKM_LAUNCHED(c);
-  // a point with more than k/8 candidate pairs is recomputed as a full row
-  const int32_t row_thresh = c->opt.row_threshold > 0 ? c->opt.row_threshold : (c->k + 7) / 8;
-  SKM_PROF_BEGIN(c, "k_elk_compact");
+  SKM_PROF_BEGIN(c, "k_elk_recompute");
   if (full) {
-    k_elk_compact<true><<<g, kBlock, 0, c->st>>>(c->k, c->kst, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, c->dlt, c->cc,
-                                                 c->sc, c->poff, c->pnum, c->pslot, c->pj, c->pcap, row_thresh, c->w2, c->cnt);
+    k_elk_recompute<VT, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->w1,
+                                                       c->cnt + C_W1, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i,
+                                                       c->chg_old, c->cnt);
   } else {
-    k_elk_compact<false><<<g, kBlock, 0, c->st>>>(c->k, c->kst, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, c->dlt,
-                                                  c->cc, c->sc, c->poff, c->pnum, c->pslot, c->pj, c->pcap,
-                                                  row_thresh, c->w2, c->cnt);
+    k_elk_recompute<VT, false><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
+                                                        c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, c->cc, c->w2,
+                                                        c->chg_i, c->chg_old, c->cnt);
   }
-  SKM_LAUNCHED(c);
-  SKM_PROF_BEGIN(c, "k_pair_sims");
-  k_pair_sims<VT><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1, c->pslot, c->pj,
-                                           c->cnt + C_PAIRS, c->pcap, c->psim, c->ub, c->cnt);
-  SKM_LAUNCHED(c);
-  SKM_PROF_BEGIN(c, "k_elk_merge");
-  k_elk_merge<<<g, kBlock, 0, c->st>>>(c->kst, c->w1, c->cnt + C_W1, c->w1s, c->poff, c->pnum, c->pj, c->psim, c->dlt,
-                                       c->a, c->lb, c->ub, c->cnt);
   SKM_LAUNCHED(c);
   return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
 }

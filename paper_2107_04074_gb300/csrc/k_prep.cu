@@ -7,12 +7,13 @@ namespace skm {
 
 namespace {
 
-constexpr int kChunk = 2048;  // entries of a term handled by one warp in the center sum
+constexpr int kChunk = 1024;  // entries of a term handled by one warp in the center sum
 
 // Warp per row: structure checks, 1/|x_i| (Section 5: rows are normalised)
 // and delta_i, an upper bound on |computed - exact| of any similarity of row
 // i: sequential FP32 FMA over m terms (gamma_m), the FP32 1/|x_i| and final
-// product (2u), and centers whose norm is within 2u of 1 -> (m+6)u/(1-(m+6)u).
+// product (2u), and centers whose norm is within 6u of 1 (FP32 normalisation
+// by a compensated norm) -> (m+10)u/(1-(m+10)u).
 template <typename VT>
 __global__ void __launch_bounds__(256) k_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                               const VT* __restrict__ val, int64_t n, int64_t d,
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(256) k_rows(const int64_t* __restrict__ rp, co
       if (!(ss > 0.0)) err |= E_ZERO_ROW;
       if (!isfinite(ss)) err |= E_NONFINITE;
       rinv[i] = (ss > 0.0) ? __double2float_rn(1.0 / sqrt(ss)) : 0.f;
-      const double m = (double)(e - b) + 6.0;
+      const double m = (double)(e - b) + 10.0;
       const double g = m * 0x1.0p-24;
       dlt[i] = (g < 0.5) ? __double2float_ru(g / (1.0 - g)) : 1.f;
     }
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256) k_rows_dense(const VT* __restrict__ X, in
     if (lane == 0) {
       if (!(ss > 0.0)) err |= E_ZERO_ROW;
       rinv[i] = (ss > 0.0) ? __double2float_rn(1.0 / sqrt(ss)) : 0.f;
-      const double g = ((double)d + 6.0) * 0x1.0p-24;
+      const double g = ((double)d + 10.0) * 0x1.0p-24;
       dlt[i] = (g < 0.5) ? __double2float_ru(g / (1.0 - g)) : 1.f;
     }
   }
@@ -85,21 +86,22 @@ __global__ void k_term_count(const int32_t* __restrict__ col, int64_t nnz, unsig
     atomicAdd(tc + col[p], 1ull);
 }
 
-// Warp per row: place each entry in its term's column.  The order inside a
-// column is arbitrary; the center sum is exact (fixed point), so the order
-// cannot change any result.
+// Warp per row: place each entry, already normalised (x = v / |row|, FP32),
+// in its term's column.  The order inside a column is arbitrary; the center
+// sum is exact (fixed point), so the order cannot change any result.
 template <typename VT>
 __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                 const VT* __restrict__ val, int64_t n,
-                                                 unsigned long long* __restrict__ cursor,
-                                                 int32_t* __restrict__ t_row, VT* __restrict__ t_val) {
+                                                 const VT* __restrict__ val, const float* __restrict__ rinv,
+                                                 int64_t n, unsigned long long* __restrict__ cursor,
+                                                 int32_t* __restrict__ t_row, float* __restrict__ t_x) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const float ri = rinv[i];
     for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
       const unsigned long long pos = atomicAdd(cursor + col[p], 1ull);
       t_row[pos] = (int32_t)i;
-      t_val[pos] = val[p];
+      t_x[pos] = __fmul_rn(to_f32(val[p]), ri);
     }
   }
 }
@@ -250,7 +252,7 @@ int prep_transpose_t(skm_ctx* c) {
   SKM_CUDA_TRY(cudaMemsetAsync(tc, 0, sizeof(unsigned long long) * (d + 1), st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&c->t_ptr, sizeof(int64_t) * (d + 1), st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&c->t_row, sizeof(int32_t) * (nnz > 0 ? nnz : 1), st));
-  SKM_CUDA_TRY(cudaMallocAsync((void**)&c->t_val, sizeof(VT) * (nnz > 0 ? nnz : 1), st));
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&c->t_val, sizeof(float) * (nnz > 0 ? nnz : 1), st));
   if (nnz > 0) {
     k_term_count<<<grid_for(nnz, 256, c->nsm, 32), 256, 0, st>>>(c->col, nnz, tc);
     SKM_LAUNCH_CHECK();
@@ -258,8 +260,8 @@ int prep_transpose_t(skm_ctx* c) {
   k_scan_i64<<<1, 1024, 0, st>>>((const int64_t*)tc, c->t_ptr, d);
   SKM_LAUNCH_CHECK();
   SKM_CUDA_TRY(cudaMemcpyAsync(tc, c->t_ptr, sizeof(int64_t) * d, cudaMemcpyDeviceToDevice, st));
-  k_scatter<VT><<<grid_for(c->n * 32, 256, c->nsm), 256, 0, st>>>(c->rp, c->col, (const VT*)c->val, c->n, tc,
-                                                                   c->t_row, (VT*)c->t_val);
+  k_scatter<VT><<<grid_for(c->n * 32, 256, c->nsm), 256, 0, st>>>(c->rp, c->col, (const VT*)c->val, c->rinv, c->n,
+                                                                   tc, c->t_row, (float*)c->t_val);
   SKM_LAUNCH_CHECK();
   // chunk tables
   SKM_CUDA_TRY(cudaMallocAsync((void**)&nch, sizeof(int64_t) * (d + 1), st));

@@ -2,22 +2,35 @@
 // the drift p(j) = <c(j), c'(j)> that moves the bounds (Section 4); and the
 // center-center bounds cc(i,j), s(i) of Section 5.2.
 //
-//   k_center_sum        warp per chunk of a term's column (term-major data):
-//                       sums x_it into per-cluster bins in shared memory in
-//                       64-bit fixed point.  Integer addition is exact and
-//                       associative, so the result does not depend on the
-//                       order of the entries or of the atomics: the center
-//                       sum is deterministic with no atomics in global memory.
+// The sums are kept between iterations as exact 64-bit fixed-point integers
+// S64[t][j] (x scaled by 2^s and rounded).  Integer addition is exact and
+// associative, so the sums do not depend on any order, and -- the paper's
+// optimisation (iii), Section 5 -- a later iteration may add and subtract only
+// the rows whose label changed and obtain bit for bit the sums a full
+// recomputation would give.  Only clusters whose sum changed ("dirty") are
+// renormalised, get a drift, and get their Gram row recomputed.
+//
+//   k_center_sum        full recompute: warp per chunk of a term's column,
+//                       per-cluster bins in shared memory (native 32-bit
+//                       atomics on two 20-bit halves, exact), no atomics in
+//                       global memory.
 //   k_center_sum_multi  terms with several chunks: exact sum of the partials.
-//   k_colnorm_part/final  |S_j| in FP64 over fixed blocks (deterministic).
-//   k_normalize_drift   c(j) = S_j/|S_j| (empty cluster keeps c'(j)); FP64
-//                       partial sums for the drift.
-//   k_drift_final       per center: an interval [pd, pu] for cos(angle(c, c'))
-//                       and an upper bound q for its sine, rounded outward to
-//                       FP32; the Hamerly worst-drift summary.
-//   k_gram_part/final   <c_i, c_j> (FP32 products, FP64 across 256-term
-//                       chunks), widened by its error bound, -> cc and s.
+//   k_center_delta      incremental: warp per changed row, +x to the new and
+//                       -x to the old cluster (exact integer atomics).
+//   k_dirty             the dirty cluster list (all clusters after a full sum).
+//   k_colnorm_*         |S_j| for dirty clusters (compensated FP32 per thread,
+//                       FP64 across threads and blocks, fixed order).
+//   k_normalize_drift   c(j) = S_j/|S_j| in place for dirty clusters (an empty
+//                       cluster keeps c'(j)), partial sums for the drift.
+//   k_drift_final       per center an interval [pd, pu] for cos(angle(c, c'))
+//                       and an upper bound q of its sine, rounded outward.
+//   k_hsel_obj          J = sum_j |S_j| and Hamerly's worst-drift summary.
+//   k_gram_*            <c_i, c_j> (FP32 products, FP64 across 256-term
+//                       chunks): all tiles when many clusters moved, else only
+//                       the rows of the (at most 64) dirty clusters; then cc
+//                       and s.
 #include <cfloat>
+#include <climits>
 
 #include "skm_internal.cuh"
 
@@ -25,233 +38,377 @@ namespace skm {
 
 namespace {
 
-constexpr int kChunk = 2048;  // must match the chunking built in k_prep.cu
+constexpr int kChunk = 1024;  // must match the chunking built in k_prep.cu
 constexpr int kTB = 256;      // rows (terms) per reduction block
 
-template <typename VT>
+// Is this update a full recomputation of the sums?
+__device__ __forceinline__ bool full_update(int s64_valid, const unsigned long long* cnt, int64_t n) {
+  return !s64_valid || cnt[C_CHG] * 8ull > (unsigned long long)n;
+}
+
+// Fixed-point value of x: |x| <= 1 maps below 2^40 (the 20 + 20 bit split).
+__device__ __forceinline__ long long to_fixed(float x, float scale) { return __float2ll_rn(__fmul_rn(x, scale)); }
+
+// The FP32 sum a fixed-point sum stands for (the value every kernel uses).
+__device__ __forceinline__ float from_fixed(long long s, float inv) { return __fmul_rn(__ll2float_rn(s), inv); }
+
+// Full recompute.  fx = round(x * 2^s) is split into hi = fx >> 20 and
+// lo = fx & (2^20 - 1); a chunk holds at most 2^10 entries, so both halves sum
+// exactly in 32-bit integers and the shared atomics are native 32-bit ones.
 __global__ void __launch_bounds__(256) k_center_sum(int64_t nchunks, const int32_t* __restrict__ ch_term,
                                                     const int32_t* __restrict__ ch_idx,
                                                     const int64_t* __restrict__ ch_part,
                                                     const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_row,
-                                                    const VT* __restrict__ t_val, const float* __restrict__ rinv,
-                                                    const int32_t* __restrict__ a, int32_t k, int64_t kst, float scale,
-                                                    float inv, float* __restrict__ S, long long* __restrict__ part) {
-  extern __shared__ long long bins_all[];
+                                                    const float* __restrict__ t_x, const int32_t* __restrict__ a,
+                                                    int32_t k, int64_t kst, float scale, long long* __restrict__ S64,
+                                                    long long* __restrict__ part, int s64_valid,
+                                                    const unsigned long long* __restrict__ cnt, int64_t n) {
+  if (!full_update(s64_valid, cnt, n)) return;
+  extern __shared__ int bins_all[];
   const int lane = threadIdx.x & 31;
-  long long* bins = bins_all + (int64_t)(threadIdx.x >> 5) * k;
+  int* hi = bins_all + (int64_t)(threadIdx.x >> 5) * 2 * k;
+  int* lo = hi + k;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nchunks; g += nw) {
     const int64_t t = ch_term[g];
     const int64_t b = t_ptr[t] + (int64_t)ch_idx[g] * kChunk;
     const int64_t e = min(t_ptr[t + 1], b + kChunk);
-    for (int j = lane; j < k; j += 32) bins[j] = 0;
+    for (int j = lane; j < k; j += 32) {
+      hi[j] = 0;
+      lo[j] = 0;
+    }
     __syncwarp();
-    for (int64_t p = b + lane; p < e; p += 32) {
-      const int32_t r = t_row[p];
-      const float x = __fmul_rn(to_f32(t_val[p]), rinv[r]);
-      const long long fx = __float2ll_rn(__fmul_rn(x, scale));
-      atomicAdd(reinterpret_cast<unsigned long long*>(bins + a[r]), (unsigned long long)fx);
+    // four entries per lane per step: their loads and label gathers are
+    // issued before any of the (order-free, exact) integer additions
+    for (int64_t p0 = b + lane; p0 < e; p0 += 128) {
+      int32_t r[4];
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t p = p0 + 32 * u;
+        r[u] = p < e ? t_row[p] : -1;
+        x[u] = p < e ? t_x[p] : 0.f;
+      }
+      int32_t lab[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) lab[u] = r[u] >= 0 ? a[r[u]] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (lab[u] >= 0) {
+          const long long fx = to_fixed(x[u], scale);
+          atomicAdd(hi + lab[u], (int)(fx >> 20));
+          atomicAdd(lo + lab[u], (int)(fx & 0xFFFFF));
+        }
     }
     __syncwarp();
     const int64_t ps = ch_part[g];
-    if (ps < 0) {
-      float* row = S + t * kst;
-      for (int j = lane; j < kst; j += 32) row[j] = (j < k) ? __fmul_rn(__ll2float_rn(bins[j]), inv) : 0.f;
-    } else {
-      long long* pr = part + ps * k;
-      for (int j = lane; j < k; j += 32) pr[j] = bins[j];
-    }
+    long long* dst = ps < 0 ? S64 + t * kst : part + ps * k;
+    const int lim = ps < 0 ? (int)kst : k;
+    for (int j = lane; j < lim; j += 32) dst[j] = (j < k) ? ((long long)hi[j] << 20) + (long long)lo[j] : 0ll;
     __syncwarp();
   }
 }
 
 __global__ void k_center_sum_multi(int64_t nmulti, const int32_t* __restrict__ mterm, const int64_t* __restrict__ mbase,
                                    const int32_t* __restrict__ mcnt, const long long* __restrict__ part, int32_t k,
-                                   int64_t kst, float inv, float* __restrict__ S) {
+                                   int64_t kst, long long* __restrict__ S64, int s64_valid,
+                                   const unsigned long long* __restrict__ cnt, int64_t n) {
+  if (!full_update(s64_valid, cnt, n)) return;
   const int64_t total = nmulti * kst;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t m = q / kst;
     const int j = (int)(q - m * kst);
     const int64_t t = mterm[m];
-    float out = 0.f;
+    long long s = 0;
     if (j < k) {
-      long long s = 0;
       const long long* pr = part + mbase[m] * k + j;
-      for (int c = 0; c < mcnt[m]; ++c) s += pr[(int64_t)c * k];
-      out = __fmul_rn(__ll2float_rn(s), inv);
+      const int nc = mcnt[m];
+      int c = 0;
+      for (; c + 8 <= nc; c += 8) {
+        long long v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = pr[(int64_t)(c + u) * k];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+      }
+      for (; c < nc; ++c) s += pr[(int64_t)c * k];
     }
-    S[t * kst + j] = out;
+    S64[t * kst + j] = s;
   }
 }
 
-// grid (ceil(d/kTB), ceil(k/32)), block (32, 8)
-__global__ void k_colnorm_part(const float* __restrict__ S, int64_t d, int32_t k, int64_t kst,
+// Incremental: warp per changed row i (old label -> a[i]); each entry's fixed
+// point value -- the same x = v / |x_i| as the term-major copy -- moves from
+// the old cluster's sum to the new one.  Both clusters become dirty.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_center_delta(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                      const VT* __restrict__ val, const float* __restrict__ rinv,
+                                                      const int32_t* __restrict__ chg_i,
+                                                      const int32_t* __restrict__ chg_old, const int32_t* __restrict__ a,
+                                                      int64_t kst, float scale, long long* __restrict__ S64,
+                                                      int32_t* __restrict__ dflag, int s64_valid,
+                                                      const unsigned long long* __restrict__ cnt, int64_t n) {
+  if (full_update(s64_valid, cnt, n)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nchg = (int64_t)cnt[C_CHG];
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchg; q += nw) {
+    const int32_t i = chg_i[q], old = chg_old[q], nu = a[i];
+    if (lane == 0) {
+      dflag[old] = 1;
+      dflag[nu] = 1;
+    }
+    const float ri = rinv[i];
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+      const int64_t t = col[p];
+      const long long fx = to_fixed(__fmul_rn(to_f32(val[p]), ri), scale);
+      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + old), (unsigned long long)(-fx));
+      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + nu), (unsigned long long)fx);
+    }
+  }
+}
+
+// One block: the list of dirty clusters in ascending order (all clusters
+// after a full recompute), dmark[j] / dpos[j] for lookups, flags cleared.
+__global__ void __launch_bounds__(1024) k_dirty(int32_t k, int32_t* __restrict__ dflag, int32_t* __restrict__ dmark,
+                                                int32_t* __restrict__ dpos, int32_t* __restrict__ dlist,
+                                                unsigned long long* __restrict__ cnt, int s64_valid, int64_t n) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  const bool full = full_update(s64_valid, cnt, n);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int j0 = 0; j0 < k; j0 += 1024) {
+    const int j = j0 + threadIdx.x;
+    const bool d = (j < k) && (full || dflag[j] != 0);
+    const unsigned ball = __ballot_sync(SKM_FULL_MASK, d);
+    if (lane == 0) wsum[wid] = __popc(ball);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < wid; ++w) before += wsum[w];
+    const int pos = base + before + __popc(ball & ((1u << lane) - 1u));
+    if (j < k) {
+      dmark[j] = d ? 1 : 0;
+      dpos[j] = d ? pos : -1;
+      if (d) dlist[pos] = j;
+      dflag[j] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < 32; ++w) tot += wsum[w];
+      base += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cnt[C_NDIRTY] = (unsigned long long)base;
+}
+
+// grid (ceil(d/kTB), ceil(k/32)), block (32, 8): thread (x, y) handles dirty
+// slot 32 blockIdx.y + x and terms t = y, y+8, ... of the block's range.
+// Squares summed in FP32 with a compensation term (Neumaier), accurate to
+// ~2u per thread; threads and blocks combine in FP64.
+__global__ void k_colnorm_part(const long long* __restrict__ S64, float inv, int64_t d, int64_t kst,
+                               const int32_t* __restrict__ dlist, const unsigned long long* __restrict__ cnt,
                                double* __restrict__ red) {
   __shared__ double sh[8][33];
-  const int j = blockIdx.y * 32 + threadIdx.x;
+  const int nd = (int)cnt[C_NDIRTY];
+  const int slot = blockIdx.y * 32 + threadIdx.x;
+  if ((int)(blockIdx.y * 32) >= nd) return;
   const int64_t t0 = (int64_t)blockIdx.x * kTB;
-  double s = 0.0;
-  if (j < k)
+  float s = 0.f, comp = 0.f;
+  if (slot < nd) {
+    const int j = dlist[slot];
     for (int64_t t = t0 + threadIdx.y; t < min(d, t0 + kTB); t += 8) {
-      const double v = S[t * kst + j];
-      s = fma(v, v, s);
+      const float v = from_fixed(S64[t * kst + j], inv);
+      const float sq = __fmul_rn(v, v);
+      const float err_sq = __fmaf_rn(v, v, -sq);  // exact low part of v*v
+      const float ns = __fadd_rn(s, sq);
+      comp += (fabsf(s) >= fabsf(sq)) ? ((s - ns) + sq) : ((sq - ns) + s);
+      comp += err_sq;
+      s = ns;
     }
-  sh[threadIdx.y][threadIdx.x] = s;
+  }
+  sh[threadIdx.y][threadIdx.x] = (double)s + (double)comp;
   __syncthreads();
-  if (threadIdx.y == 0 && j < k) {
+  if (threadIdx.y == 0 && slot < nd) {
     double r = 0.0;
     for (int y = 0; y < 8; ++y) r += sh[y][threadIdx.x];
-    red[(int64_t)blockIdx.x * kst + j] = r;
+    red[(int64_t)blockIdx.x * kst + slot] = r;
   }
 }
 
-// one block: |S_j| and J = sum_j |S_j|, in a fixed order
-__global__ void __launch_bounds__(1024) k_colnorm_final(const double* __restrict__ red, int64_t nblk, int32_t k,
-                                                        int64_t kst, double* __restrict__ nrm,
-                                                        double* __restrict__ obj) {
-  __shared__ double sh[1024];
-  double mine = 0.0;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    double s = 0.0;
-    for (int64_t b = 0; b < nblk; ++b) s += red[b * kst + j];
-    const double nr = sqrt(s);
-    nrm[j] = nr;
-    mine += nr;
-  }
-  sh[threadIdx.x] = mine;
+// Block per dirty slot: |S_j| from the per-block partials in a fixed order.
+__global__ void __launch_bounds__(128) k_colnorm_final(const double* __restrict__ red, int64_t nblk, int64_t kst,
+                                                       const int32_t* __restrict__ dlist,
+                                                       const unsigned long long* __restrict__ cnt,
+                                                       double* __restrict__ nrm) {
+  __shared__ double sh[128];
+  const int slot = blockIdx.x;
+  if (slot >= (int)cnt[C_NDIRTY]) return;
+  double s = 0.0;
+  for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) s += red[b * kst + slot];
+  sh[threadIdx.x] = s;
   __syncthreads();
-  for (int o = blockDim.x / 2; o; o >>= 1) {
+  for (int o = 64; o; o >>= 1) {
     if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) obj[0] = sh[0];
+  if (threadIdx.x == 0) nrm[dlist[slot]] = sqrt(sh[0]);
 }
 
-// grid (ceil(d/kTB), ceil(k/32)), block (32, 8).  S is overwritten with the
-// new centers; red2 receives, per block and center, sum c^2, sum c'^2 and
-// sum (c - c')^2.
-__global__ void k_normalize_drift(float* __restrict__ S, const float* __restrict__ Cold, const double* __restrict__ nrm,
-                                  int64_t d, int32_t k, int64_t kst, double* __restrict__ red2) {
+// grid (ceil(d/kTB), ceil(k/32)), block (32, 8), dirty slots as above.  The
+// dirty centers are overwritten in place; red2 receives per block and slot
+// sum c^2, sum c'^2 and sum (c - c')^2 (FP32 per thread over 32 terms --
+// relative error <= 36u, covered by the slack of k_drift_final).
+__global__ void k_normalize_drift(const long long* __restrict__ S64, float inv, float* __restrict__ Ct,
+                                  const double* __restrict__ nrm, int64_t d, int64_t kst,
+                                  const int32_t* __restrict__ dlist, const unsigned long long* __restrict__ cnt,
+                                  double* __restrict__ red2) {
   __shared__ double sh[3][8][33];
-  const int j = blockIdx.y * 32 + threadIdx.x;
+  const int nd = (int)cnt[C_NDIRTY];
+  const int slot = blockIdx.y * 32 + threadIdx.x;
+  if ((int)(blockIdx.y * 32) >= nd) return;
   const int64_t t0 = (int64_t)blockIdx.x * kTB;
-  double sn = 0.0, so = 0.0, sd = 0.0;
-  if (j < k) {
+  float sn = 0.f, so = 0.f, sd = 0.f;
+  if (slot < nd) {
+    const int j = dlist[slot];
     const double nr = nrm[j];
     const bool empty = !(nr > 0.0);
-    const float inv = empty ? 0.f : (float)(1.0 / nr);
+    const float rn = empty ? 0.f : (float)(1.0 / nr);
     for (int64_t t = t0 + threadIdx.y; t < min(d, t0 + kTB); t += 8) {
-      const float co = Cold[t * kst + j];
-      const float cn = empty ? co : __fmul_rn(S[t * kst + j], inv);
-      S[t * kst + j] = cn;
-      const double dn = cn, dv = co, df = dn - dv;
-      sn = fma(dn, dn, sn);
-      so = fma(dv, dv, so);
-      sd = fma(df, df, sd);
+      float* cp = Ct + t * kst + j;
+      const float co = *cp;
+      const float cn = empty ? co : __fmul_rn(from_fixed(S64[t * kst + j], inv), rn);
+      *cp = cn;
+      const float df = cn - co;
+      sn = __fmaf_rn(cn, cn, sn);
+      so = __fmaf_rn(co, co, so);
+      sd = __fmaf_rn(df, df, sd);
     }
   }
   sh[0][threadIdx.y][threadIdx.x] = sn;
   sh[1][threadIdx.y][threadIdx.x] = so;
   sh[2][threadIdx.y][threadIdx.x] = sd;
   __syncthreads();
-  if (threadIdx.y == 0 && j < k) {
+  if (threadIdx.y == 0 && slot < nd) {
     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
     for (int y = 0; y < 8; ++y) {
       r0 += sh[0][y][threadIdx.x];
       r1 += sh[1][y][threadIdx.x];
       r2 += sh[2][y][threadIdx.x];
     }
-    double* o = red2 + ((int64_t)blockIdx.x * kst + j) * 3;
+    double* o = red2 + ((int64_t)blockIdx.x * kst + slot) * 3;
     o[0] = r0;
     o[1] = r1;
     o[2] = r2;
   }
 }
 
-struct ArgMin {
-  float v;
-  int j;
-};
-
-// One block.  From N = |c|, N' = |c'| and D = |c - c'|^2 (all FP64 with
-// relative error <= e):  1 - cos = (D - (N - N')^2) / (2 N N'), hence
-//   q_up = D (1+4e) / (2 N N')           >= 1 - cos
+// Block per center (grid kst).  Clean centers did not move: p = 1, sine 0.
+// Dirty ones: from N = |c|, N' = |c'| and D = |c - c'|^2 (relative error <= e,
+// e = 40u + d 2^-53):  1 - cos = (D - (N - N')^2) / (2 N N'), hence
+//   q_up = D (1+4e) / (2 N N')                           >= 1 - cos
 //   q_dn = (D (1-e) - (|N-N'| + e)^2) / (2 N N' (1+3e))  <= 1 - cos
 // pd = rd(1 - q_up), pu = ru(1 - q_dn), q = ru(max sin over [q_dn, q_up]).
-// Identical vectors (D = 0) give exactly p = 1, sin = 0.
-__global__ void __launch_bounds__(1024) k_drift_final(const double* __restrict__ red2, int64_t nblk, int32_t k,
-                                                      int64_t kst, int64_t d, float* __restrict__ pdn,
-                                                      float* __restrict__ pup, float* __restrict__ qup,
-                                                      double* __restrict__ cnorm, float* __restrict__ hsel) {
-  __shared__ float s_pd[1024], s_pu[1024], s_q[1024];
-  __shared__ int s_jd[1024], s_ju[1024], s_jq[1024];
-  const double e = ((double)d + 8.0) * 0x1.0p-53;
-  for (int j = threadIdx.x; j < kst; j += blockDim.x) {
-    if (j >= k) {
+__global__ void __launch_bounds__(128) k_drift_final(const double* __restrict__ red2, int64_t nblk, int32_t k,
+                                                     int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
+                                                     const int32_t* __restrict__ dpos, float* __restrict__ pdn,
+                                                     float* __restrict__ pup, float* __restrict__ qup,
+                                                     double* __restrict__ cnorm) {
+  __shared__ double sh[3][128];
+  const int j = blockIdx.x;
+  if (j >= k || !dmark[j]) {
+    if (threadIdx.x == 0) {
       pdn[j] = 1.f;
       pup[j] = 1.f;
       qup[j] = 0.f;
-      continue;
     }
-    double sn = 0.0, so = 0.0, sd = 0.0;
-    for (int64_t b = 0; b < nblk; ++b) {
-      const double* r = red2 + (b * kst + j) * 3;
-      sn += r[0];
-      so += r[1];
-      sd += r[2];
-    }
-    const double N = sqrt(sn), No = sqrt(so);
-    cnorm[j] = N;
-    float pd, pu, q;
-    if (sd == 0.0) {
-      pd = 1.f;
-      pu = 1.f;
-      q = 0.f;
-    } else {
-      const double den = 2.0 * N * No;
-      const double qu = sd * (1.0 + 4.0 * e) / den;
-      const double dn = fabs(N - No) + e;
-      double qd = (sd * (1.0 - e) - dn * dn) / (den * (1.0 + 3.0 * e));
-      if (qd < 0.0) qd = 0.0;
-      double lo = 1.0 - qu, hi = 1.0 - qd;
-      lo = lo < -1.0 ? -1.0 : lo;
-      hi = hi > 1.0 ? 1.0 : hi;
-      pd = __double2float_rd(lo - 0x1.0p-60);
-      pu = __double2float_ru(hi + 0x1.0p-60);
-      pd = fmaxf(pd, -1.f);
-      pu = fminf(pu, 1.f);
-      double smax;
-      if (qd <= 1.0 && qu >= 1.0) smax = 1.0;
-      else if (qu < 1.0) smax = sqrt(qu * (2.0 - qu));
-      else smax = sqrt(qd * (2.0 - qd));
-      q = fminf(__double2float_ru(smax * (1.0 + 4.0 * e) + 0x1.0p-60), 1.f);
-    }
-    pdn[j] = pd;
-    pup[j] = pu;
-    qup[j] = q;
+    return;
   }
+  const int slot = dpos[j];
+  double sn = 0.0, so = 0.0, sd = 0.0;
+  for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) {
+    const double* r = red2 + (b * kst + slot) * 3;
+    sn += r[0];
+    so += r[1];
+    sd += r[2];
+  }
+  sh[0][threadIdx.x] = sn;
+  sh[1][threadIdx.x] = so;
+  sh[2][threadIdx.x] = sd;
   __syncthreads();
-  // Hamerly summary: argmin / min / second min of pd and pu, argmax / max /
-  // second max of q (lowest index on ties).  Sequential per thread over a
-  // strided slice, then a fixed tree.
+  for (int o = 64; o; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+      sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  sn = sh[0][0];
+  so = sh[1][0];
+  sd = sh[2][0];
+  const double e = 40.0 * 0x1.0p-24 + ((double)d + 8.0) * 0x1.0p-53;
+  const double N = sqrt(sn), No = sqrt(so);
+  cnorm[j] = N;
+  float pd, pu, q;
+  if (sd == 0.0) {
+    pd = 1.f;
+    pu = 1.f;
+    q = 0.f;
+  } else {
+    const double den = 2.0 * N * No;
+    const double qu = sd * (1.0 + 4.0 * e) / den;
+    const double dn = fabs(N - No) + e;
+    double qd = (sd * (1.0 - e) - dn * dn) / (den * (1.0 + 3.0 * e));
+    if (qd < 0.0) qd = 0.0;
+    double lo = 1.0 - qu, hi = 1.0 - qd;
+    lo = lo < -1.0 ? -1.0 : lo;
+    hi = hi > 1.0 ? 1.0 : hi;
+    pd = fmaxf(__double2float_rd(lo - 0x1.0p-60), -1.f);
+    pu = fminf(__double2float_ru(hi + 0x1.0p-60), 1.f);
+    double smax;
+    if (qd <= 1.0 && qu >= 1.0) smax = 1.0;
+    else if (qu < 1.0) smax = sqrt(qu * (2.0 - qu));
+    else smax = sqrt(qd * (2.0 - qd));
+    q = fminf(__double2float_ru(smax * (1.0 + 4.0 * e) + 0x1.0p-60), 1.f);
+  }
+  pdn[j] = pd;
+  pup[j] = pu;
+  qup[j] = q;
+}
+
+// One block: the objective J = sum_j |S_j| (fixed order) and Hamerly's
+// worst-drift summary -- argmin / min / second min of pd and of pu, argmax /
+// max / second max of q, lowest index on ties (Section 5.3: p' is the minimum
+// over the other centers, hence the second value for the argmin's members).
+__global__ void __launch_bounds__(1024) k_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
+                                                   const float* __restrict__ qup, const double* __restrict__ nrm,
+                                                   int32_t k, float* __restrict__ hsel, double* __restrict__ obj) {
+  __shared__ float s_pd[1024], s_pu[1024], s_q[1024], s_pd2[1024], s_pu2[1024], s_q2[1024];
+  __shared__ int s_jd[1024], s_ju[1024], s_jq[1024];
+  __shared__ double s_J[1024];
   float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
   int jd = INT_MAX, ju = INT_MAX, jq = INT_MAX;
+  double J = 0.0;
   for (int j = threadIdx.x; j < k; j += blockDim.x) {
     const float x = pdn[j], y = pup[j], z = qup[j];
     if (x < bd) { bd2 = bd; bd = x; jd = j; } else if (x < bd2) bd2 = x;
     if (y < bu) { bu2 = bu; bu = y; ju = j; } else if (y < bu2) bu2 = y;
     if (z > bq) { bq2 = bq; bq = z; jq = j; } else if (z > bq2) bq2 = z;
+    J += nrm[j];
   }
-  // two-value reductions via shared memory, pairwise in a fixed order
-  __shared__ float s_pd2[1024], s_pu2[1024], s_q2[1024];
   s_pd[threadIdx.x] = bd; s_pd2[threadIdx.x] = bd2; s_jd[threadIdx.x] = jd;
   s_pu[threadIdx.x] = bu; s_pu2[threadIdx.x] = bu2; s_ju[threadIdx.x] = ju;
   s_q[threadIdx.x] = bq; s_q2[threadIdx.x] = bq2; s_jq[threadIdx.x] = jq;
+  s_J[threadIdx.x] = J;
   __syncthreads();
   for (int o = blockDim.x / 2; o; o >>= 1) {
     if ((int)threadIdx.x < o) {
       const int a = threadIdx.x, b = threadIdx.x + o;
-      // min pd
       if (s_pd[b] < s_pd[a] || (s_pd[b] == s_pd[a] && s_jd[b] < s_jd[a])) {
         s_pd2[a] = fminf(s_pd2[b], s_pd[a]);
         s_pd[a] = s_pd[b];
@@ -273,6 +430,7 @@ __global__ void __launch_bounds__(1024) k_drift_final(const double* __restrict__
       } else {
         s_q2[a] = fmaxf(s_q2[a], s_q[b]);
       }
+      s_J[a] += s_J[b];
     }
     __syncthreads();
   }
@@ -288,58 +446,144 @@ __global__ void __launch_bounds__(1024) k_drift_final(const double* __restrict__
     hsel[6] = (float)s_jq[0];
     hsel[7] = s_q[0];
     hsel[8] = one ? 0.f : s_q2[0];
+    obj[0] = s_J[0];
   }
 }
 
-// Gram partials: grid (ceil(k/32), ceil(k/32), nsplit), block (32, 8); tile
-// (bi, bj) with bi <= bj only.  Each thread owns 4 entries; FP32 products are
-// accumulated over 256 terms, then added to FP64 accumulators.
+// The Gram by 64 x 64 tiles: grid (ceil(k/64), ceil(k/64), nsplit), block
+// 256 = 16 x 16.  Each thread owns a 4 x 4 block of <c_i, c_j>; per term it
+// reads 4 + 4 center values from shared memory (float4) for 16 FMAs.  FP32
+// products are accumulated over 256 terms, then added to FP64 accumulators
+// (the error bound used by k_gram_final).
+// ROWS = false: many dirty clusters, tiles (bi, bj) with bi <= bj of the whole
+//   Gram into gpart[z][i][j].
+// ROWS = true: 1..row_max (<= 64) dirty clusters; the A tile holds the dirty
+//   centers (gathered by dlist), only bi = 0 runs, into gpart[z][r][j].
+constexpr int kGT = 64;
+template <bool ROWS>
 __global__ void __launch_bounds__(256) k_gram_part(const float* __restrict__ Ct, int64_t d, int32_t k, int64_t kst,
-                                                   int64_t per_split, double* __restrict__ gpart) {
-  if (blockIdx.x > blockIdx.y) return;
-  __shared__ float A[32][33], B[32][33];
-  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+                                                   int64_t per_split, double* __restrict__ gpart,
+                                                   const int32_t* __restrict__ dlist,
+                                                   const unsigned long long* __restrict__ cnt, int32_t row_max) {
+  const int nd = (int)cnt[C_NDIRTY];
+  if (ROWS ? (nd == 0 || nd > row_max || blockIdx.x != 0) : (blockIdx.x > blockIdx.y || nd <= row_max)) return;
+  __shared__ __align__(16) float A[32][kGT], B[32][kGT];
+  const int i0 = blockIdx.x * kGT, j0 = blockIdx.y * kGT;
   const int64_t tb = (int64_t)blockIdx.z * per_split, te = min(d, tb + per_split);
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  double acc64[4] = {0.0, 0.0, 0.0, 0.0};
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc64[4][4];
+  float acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      acc64[x][y] = 0.0;
+      acc[x][y] = 0.f;
+    }
   int steps = 0;
   for (int64_t t0 = tb; t0 < te; t0 += 32) {
-    for (int r = ty; r < 32; r += 8) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = tid + 256 * h;
+      const int r = q >> 4, c4 = (q & 15) * 4;
       const int64_t t = t0 + r;
-      A[r][tx] = (t < te && i0 + tx < k) ? Ct[t * kst + i0 + tx] : 0.f;
-      B[r][tx] = (t < te && j0 + tx < k) ? Ct[t * kst + j0 + tx] : 0.f;
+      float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+      if (t < te) {
+        if (ROWS) {
+          const float* row = Ct + t * kst;
+          va.x = (c4 + 0 < nd) ? row[dlist[c4 + 0]] : 0.f;
+          va.y = (c4 + 1 < nd) ? row[dlist[c4 + 1]] : 0.f;
+          va.z = (c4 + 2 < nd) ? row[dlist[c4 + 2]] : 0.f;
+          va.w = (c4 + 3 < nd) ? row[dlist[c4 + 3]] : 0.f;
+        } else if (i0 + c4 < kst) {
+          va = *reinterpret_cast<const float4*>(Ct + t * kst + i0 + c4);
+        }
+        if (j0 + c4 < kst) vb = *reinterpret_cast<const float4*>(Ct + t * kst + j0 + c4);
+      }
+      *reinterpret_cast<float4*>(&A[r][c4]) = va;
+      *reinterpret_cast<float4*>(&B[r][c4]) = vb;
     }
     __syncthreads();
 #pragma unroll 8
     for (int r = 0; r < 32; ++r) {
-      const float bv = B[r][tx];
+      const float4 av = *reinterpret_cast<const float4*>(&A[r][ty * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&B[r][tx * 4]);
+      const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = __fmaf_rn(A[r][ty + 8 * q], bv, acc[q]);
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = __fmaf_rn(ar[x], br[y], acc[x][y]);
     }
     __syncthreads();
     if (++steps == 8) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc64[q] += (double)acc[q];
-        acc[q] = 0.f;
-      }
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          acc64[x][y] += (double)acc[x][y];
+          acc[x][y] = 0.f;
+        }
       steps = 0;
     }
   }
+  const int rows = ROWS ? row_max : k;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    acc64[q] += (double)acc[q];
-    const int i = i0 + ty + 8 * q, j = j0 + tx;
-    if (i < k && j < k) gpart[((int64_t)blockIdx.z * k + i) * k + j] = acc64[q];
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int i = i0 + ty * 4 + x, j = j0 + tx * 4 + y;
+      if (i < (ROWS ? nd : k) && j < k)
+        gpart[((int64_t)blockIdx.z * rows + i) * k + j] = acc64[x][y] + (double)acc[x][y];
+    }
+}
+
+// Thread per (i, j), i <= j: the Gram entry as the sum of the split partials
+// in split order (loads coalesced across threads).
+__global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ gpart, int32_t nsplit, int32_t k,
+                                                     double* __restrict__ G, const unsigned long long* __restrict__ cnt,
+                                                     int32_t row_max) {
+  if ((int)cnt[C_NDIRTY] <= row_max) return;
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < kk; q += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / k), j = (int)(q - (int64_t)i * k);
+    if (i > j) continue;
+    double g = 0.0;
+    int s = 0;
+    for (; s + 8 <= nsplit; s += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = gpart[(int64_t)(s + u) * kk + q];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) g += v[u];
+    }
+    for (; s < nsplit; ++s) g += gpart[(int64_t)s * kk + q];
+    G[q] = g;
   }
 }
 
-// Block per center i: <c_i, c_j> from the partials (fixed order), normalised by
-// the FP64 norms and widened by the error bound eg, then
-// cc(i,j) = sqrt((g+1)/2) rounded up and s(i) = max_{j != i} cc(i,j).
-__global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ gpart, int32_t nsplit, int32_t k,
-                                                    int64_t kst, const double* __restrict__ cnorm, double eg,
+__global__ void __launch_bounds__(256) k_gram_rows_reduce(const double* __restrict__ rpart, int32_t nsplit,
+                                                          int32_t k, const int32_t* __restrict__ dlist,
+                                                          const unsigned long long* __restrict__ cnt, int32_t row_max,
+                                                          double* __restrict__ G) {
+  const int nd = (int)cnt[C_NDIRTY];
+  if (nd > row_max) return;
+  const int64_t tot = (int64_t)nd * k;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(q / k), j = (int)(q - (int64_t)r * k);
+    double g = 0.0;
+    for (int s = 0; s < nsplit; ++s) g += rpart[((int64_t)s * row_max + r) * k + j];
+    const int i = dlist[r];
+    // the same dot product is computed by both rows when i and j are dirty;
+    // the two values are identical (same products, same term ranges)
+    G[(int64_t)min(i, j) * k + max(i, j)] = g;
+  }
+}
+
+// Block per center i: <c_i, c_j> (upper triangle of G), normalised by the FP64
+// norms and widened by the error bound eg, then cc(i,j) = sqrt((g+1)/2)
+// rounded up and s(i) = max_{j != i} cc(i,j).
+__global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ G, int32_t k, int64_t kst,
+                                                    const double* __restrict__ cnorm, double eg,
                                                     float* __restrict__ cc, float* __restrict__ sc) {
   __shared__ float sh[256];
   const int i = blockIdx.x;
@@ -350,8 +594,7 @@ __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ g
       continue;
     }
     const int lo = min(i, j), hi = max(i, j);
-    double g = 0.0;
-    for (int s = 0; s < nsplit; ++s) g += gpart[((int64_t)s * k + lo) * k + hi];
+    const double g = G[(int64_t)lo * k + hi];
     const double den = cnorm[i] * cnorm[j];
     double gh = (den > 0.0 ? g / den : 0.0) + eg;
     double h = 0.5 * (gh + 1.0);
@@ -369,32 +612,19 @@ __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ g
   if (threadIdx.x == 0) sc[i] = sh[0];
 }
 
+inline unsigned grid_cap(int64_t items, int per_block, int nsm, int per_sm = 16) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g > (int64_t)nsm * per_sm) g = (int64_t)nsm * per_sm;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
 template <typename VT>
-int center_sum_t(skm_ctx* c) {
-  const int k = c->k;
-  int wpb = (int)((96 * 1024) / ((int64_t)k * 8));
-  if (wpb > 8) wpb = 8;
-  if (wpb < 1) wpb = 1;
-  const size_t smem = (size_t)wpb * k * 8;
-  if (smem > 48 * 1024)
-    SKM_CUDA_TRY(cudaFuncSetAttribute(k_center_sum<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int64_t g = (c->nchunks + wpb - 1) / wpb;
-  const int64_t cap = (int64_t)c->nsm * 16;
-  if (g > cap) g = cap;
-  SKM_PROF_BEGIN(c, "k_center_sum");
-  k_center_sum<VT><<<(unsigned)g, wpb * 32, smem, c->st>>>(c->nchunks, c->ch_term, c->ch_idx, c->ch_part, c->t_ptr,
-                                                           c->t_row, (const VT*)c->t_val, c->rinv, c->a, k, c->kst,
-                                                           c->fx_scale, c->fx_inv, c->S, c->part64);
+int center_delta_t(skm_ctx* c) {
+  SKM_PROF_BEGIN(c, "k_center_delta");
+  k_center_delta<VT><<<grid_cap(c->n * 32, 256, c->nsm), 256, 0, c->st>>>(
+      c->rp, c->col, (const VT*)c->val, c->rinv, c->chg_i, c->chg_old, c->a, c->kst, c->fx_scale, c->S64, c->dflag,
+      c->s64_valid, c->cnt, c->n);
   SKM_LAUNCHED(c);
-  if (c->nmulti > 0) {
-    int64_t tot = c->nmulti * c->kst;
-    int64_t gb = (tot + 255) / 256;
-    if (gb > cap) gb = cap;
-    SKM_PROF_BEGIN(c, "k_center_sum_multi");
-    k_center_sum_multi<<<(unsigned)gb, 256, 0, c->st>>>(c->nmulti, c->multi_term, c->multi_base, c->multi_cnt,
-                                                         c->part64, k, c->kst, c->fx_inv, c->S);
-    SKM_LAUNCHED(c);
-  }
   return SKM_OK;
 }
 
@@ -403,45 +633,84 @@ int center_sum_t(skm_ctx* c) {
 int64_t reduction_blocks(int64_t d) { return (d + kTB - 1) / kTB; }
 
 int update_centers(skm_ctx* c) {
+  const int k = c->k;
+  // ---- sums: a full recompute, or only the changed rows (decided on the device)
+  int wpb = (int)((96 * 1024) / ((int64_t)k * 8));  // two int32 bins per cluster per warp
+  if (wpb > 8) wpb = 8;
+  if (wpb < 1) wpb = 1;
+  const size_t smem = (size_t)wpb * k * 8;
+  if (smem > 48 * 1024)
+    SKM_CUDA_TRY(cudaFuncSetAttribute(k_center_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SKM_PROF_BEGIN(c, "k_center_sum");
+  k_center_sum<<<grid_cap(c->nchunks, wpb, c->nsm), wpb * 32, smem, c->st>>>(
+      c->nchunks, c->ch_term, c->ch_idx, c->ch_part, c->t_ptr, c->t_row, (const float*)c->t_val, c->a, k, c->kst,
+      c->fx_scale, c->S64, c->part64, c->s64_valid, c->cnt, c->n);
+  SKM_LAUNCHED(c);
+  if (c->nmulti > 0) {
+    SKM_PROF_BEGIN(c, "k_center_sum_multi");
+    k_center_sum_multi<<<grid_cap(c->nmulti * c->kst, 256, c->nsm), 256, 0, c->st>>>(
+        c->nmulti, c->multi_term, c->multi_base, c->multi_cnt, c->part64, k, c->kst, c->S64, c->s64_valid, c->cnt,
+        c->n);
+    SKM_LAUNCHED(c);
+  }
   int rc = SKM_OK;
   switch (c->dtype) {
-    case SKM_F32: rc = center_sum_t<float>(c); break;
-    case SKM_F16: rc = center_sum_t<__half>(c); break;
-    case SKM_BF16: rc = center_sum_t<__nv_bfloat16>(c); break;
-    default: return SKM_EINVAL;
+    case SKM_F32: rc = center_delta_t<float>(c); break;
+    case SKM_F16: rc = center_delta_t<__half>(c); break;
+    default: rc = center_delta_t<__nv_bfloat16>(c); break;
   }
   if (rc) return rc;
+  SKM_PROF_BEGIN(c, "k_dirty");
+  k_dirty<<<1, 1024, 0, c->st>>>(k, c->dflag, c->dmark, c->dpos, c->dlist, c->cnt, c->s64_valid, c->n);
+  SKM_LAUNCHED(c);
+  c->s64_valid = 1;
+  // ---- norms, new centers and drift of the dirty clusters
   const int64_t nblk = reduction_blocks(c->d);
-  dim3 grid((unsigned)nblk, (unsigned)((c->k + 31) / 32));
+  dim3 grid((unsigned)nblk, (unsigned)((k + 31) / 32));
   SKM_PROF_BEGIN(c, "k_colnorm_part");
-  k_colnorm_part<<<grid, dim3(32, 8), 0, c->st>>>(c->S, c->d, c->k, c->kst, c->red);
+  k_colnorm_part<<<grid, dim3(32, 8), 0, c->st>>>(c->S64, c->fx_inv, c->d, c->kst, c->dlist, c->cnt, c->red);
   SKM_LAUNCHED(c);
   SKM_PROF_BEGIN(c, "k_colnorm_final");
-  k_colnorm_final<<<1, 1024, 0, c->st>>>(c->red, nblk, c->k, c->kst, c->nrm, c->obj);
+  k_colnorm_final<<<k, 128, 0, c->st>>>(c->red, nblk, c->kst, c->dlist, c->cnt, c->nrm);
   SKM_LAUNCHED(c);
   SKM_PROF_BEGIN(c, "k_normalize_drift");
-  k_normalize_drift<<<grid, dim3(32, 8), 0, c->st>>>(c->S, c->Ct, c->nrm, c->d, c->k, c->kst, c->red);
+  k_normalize_drift<<<grid, dim3(32, 8), 0, c->st>>>(c->S64, c->fx_inv, c->Ct, c->nrm, c->d, c->kst, c->dlist,
+                                                     c->cnt, c->red);
   SKM_LAUNCHED(c);
-  double* cnorm = c->nrm + c->kst;  // second half of the norm buffer: |c(j)| of the new centers
+  double* cnorm = c->nrm + c->kst;  // second half of the norm buffer: |c(j)| of the centers
   SKM_PROF_BEGIN(c, "k_drift_final");
-  k_drift_final<<<1, 1024, 0, c->st>>>(c->red, nblk, c->k, c->kst, c->d, c->pdn, c->pup, c->qup, cnorm, c->hsel);
+  k_drift_final<<<c->kst, 128, 0, c->st>>>(c->red, nblk, k, c->kst, c->d, c->dmark, c->dpos, c->pdn, c->pup, c->qup,
+                                           cnorm);
   SKM_LAUNCHED(c);
-  // the new centers become current
-  float* tmp = c->Ct;
-  c->Ct = c->S;
-  c->S = tmp;
+  SKM_PROF_BEGIN(c, "k_hsel_obj");
+  k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj);
+  SKM_LAUNCHED(c);
+  // ---- center-center bounds (full variants)
   if (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY) {
+    const int32_t row_max = c->grow_max;
     const int64_t per = (c->d + c->gsplit - 1) / c->gsplit;
-    const unsigned tk = (unsigned)((c->k + 31) / 32);
+    const unsigned tk = (unsigned)((k + kGT - 1) / kGT);
     SKM_PROF_BEGIN(c, "k_gram_part");
-    k_gram_part<<<dim3(tk, tk, (unsigned)c->gsplit), dim3(32, 8), 0, c->st>>>(c->Ct, c->d, c->k, c->kst, per,
-                                                                                c->gpart);
+    k_gram_part<false><<<dim3(tk, tk, (unsigned)c->gsplit), 256, 0, c->st>>>(c->Ct, c->d, k, c->kst, per, c->gpart,
+                                                                             c->dlist, c->cnt, row_max);
+    SKM_LAUNCHED(c);
+    SKM_PROF_BEGIN(c, "k_gram_reduce");
+    k_gram_reduce<<<grid_cap((int64_t)k * k, 256, c->nsm), 256, 0, c->st>>>(c->gpart, c->gsplit, k, c->G, c->cnt,
+                                                                             row_max);
+    SKM_LAUNCHED(c);
+    SKM_PROF_BEGIN(c, "k_gram_rows");
+    k_gram_part<true><<<dim3(1, tk, (unsigned)c->gsplit), 256, 0, c->st>>>(c->Ct, c->d, k, c->kst, per, c->rpart,
+                                                                           c->dlist, c->cnt, row_max);
+    SKM_LAUNCHED(c);
+    SKM_PROF_BEGIN(c, "k_gram_rows_reduce");
+    k_gram_rows_reduce<<<grid_cap((int64_t)row_max * k, 256, c->nsm), 256, 0, c->st>>>(c->rpart, c->gsplit, k,
+                                                                                       c->dlist, c->cnt, row_max, c->G);
     SKM_LAUNCHED(c);
     // |error| of an FP32 sum of 256 products <= gamma_256 |c_i||c_j|, plus
     // the normalisation by FP64 norms of FP32 vectors.
     const double eg = 260.0 * 0x1.0p-24 / (1.0 - 260.0 * 0x1.0p-24) + 1e-12;
     SKM_PROF_BEGIN(c, "k_gram_final");
-    k_gram_final<<<c->k, 256, 0, c->st>>>(c->gpart, c->gsplit, c->k, c->kst, cnorm, eg, c->cc, c->sc);
+    k_gram_final<<<k, 256, 0, c->st>>>(c->G, k, c->kst, cnorm, eg, c->cc, c->sc);
     SKM_LAUNCHED(c);
   }
   return SKM_OK;

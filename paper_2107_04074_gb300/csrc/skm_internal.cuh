@@ -20,8 +20,9 @@ enum Counter {
   C_SIMS = 1,     // exact similarities computed
   C_W1 = 2,       // points failing the first bound test
   C_W2 = 3,       // points needing a full row of similarities
-  C_PAIRS = 4,    // Elkan (point, center) pairs reserved (may exceed capacity)
+  C_CHG = 4,      // entries of the changed-row list
   C_ERR = 5,      // error flags (bit field)
+  C_NDIRTY = 6,   // clusters whose sum changed in the last center update
   C_NUM = 8
 };
 
@@ -44,13 +45,105 @@ template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16
 // Canonical similarity of row i to center j: sequential FMA over the row's
 // stored entries in CSR order, starting from 0, then times 1/|x_i|.  Every
 // kernel that produces a similarity uses exactly this order, so all variants
-// see bit-identical values and take identical decisions.
+// see bit-identical values and take identical decisions.  Eight entries are
+// loaded (and their center values gathered) before they are accumulated, to
+// keep several loads in flight; the accumulation order is unchanged.
 template <typename VT>
 __device__ __forceinline__ float dot_row_center(int64_t b, int64_t e, const int32_t* __restrict__ col,
                                                 const VT* __restrict__ val, const float* __restrict__ Ct,
                                                 int64_t kst, int j) {
   float acc = 0.f;
-  for (int64_t p = b; p < e; ++p) acc = __fmaf_rn(to_f32(val[p]), __ldg(Ct + (int64_t)__ldg(col + p) * kst + j), acc);
+  int64_t p = b;
+  for (; p + 8 <= e; p += 8) {
+    int t[8];
+    float v[8], c[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      t[u] = __ldg(col + p + u);
+      v[u] = to_f32(val[p + u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) c[u] = __ldg(Ct + (int64_t)t[u] * kst + j);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = __fmaf_rn(v[u], c[u], acc);
+  }
+  for (; p < e; ++p) acc = __fmaf_rn(to_f32(val[p]), __ldg(Ct + (int64_t)__ldg(col + p) * kst + j), acc);
+  return acc;
+}
+
+// Warp-cooperative canonical similarity to ONE center j (all lanes return
+// it): the warp loads 32 entries and their center values at once, then runs
+// the sequential FMA chain over them through shuffles.  The next chunk's
+// loads are issued before the current chunk is accumulated.
+template <typename VT>
+__device__ __forceinline__ float warp_dot_one(int64_t b, int64_t e, const int32_t* __restrict__ col,
+                                              const VT* __restrict__ val, const float* __restrict__ Ct, int64_t kst,
+                                              int j) {
+  const int lane = threadIdx.x & 31;
+  float acc = 0.f;
+  float v = 0.f, c = 0.f;
+  if (b + lane < e) {
+    v = to_f32(val[b + lane]);
+    c = __ldg(Ct + (int64_t)__ldg(col + b + lane) * kst + j);
+  }
+  for (int64_t p0 = b; p0 < e; p0 += 32) {
+    const float cv = v, cc = c;
+    const int64_t pn = p0 + 32 + lane;
+    if (pn < e) {
+      v = to_f32(val[pn]);
+      c = __ldg(Ct + (int64_t)__ldg(col + pn) * kst + j);
+    }
+    const int nq = (int)min((int64_t)32, e - p0);
+    for (int q = 0; q < nq; ++q)
+      acc = __fmaf_rn(__shfl_sync(SKM_FULL_MASK, cv, q), __shfl_sync(SKM_FULL_MASK, cc, q), acc);
+  }
+  return acc;
+}
+
+// Warp-cooperative canonical similarities to one center PER LANE (my_j < 0:
+// the lane computes nothing useful).  Row entries are broadcast by shuffles
+// in CSR order; for each chunk of 32 entries every lane first gathers all its
+// center values (one round trip), then accumulates them in order.
+template <typename VT>
+__device__ __forceinline__ float warp_dot_lanes(int64_t b, int64_t e, const int32_t* __restrict__ col,
+                                                const VT* __restrict__ val, const float* __restrict__ Ct,
+                                                int64_t kst, int my_j) {
+  const int lane = threadIdx.x & 31;
+  const bool on = my_j >= 0;
+  const float* cbase = Ct + (on ? my_j : 0);
+  float acc = 0.f;
+  int tt = 0;
+  float vv = 0.f;
+  if (b + lane < e) {
+    tt = __ldg(col + b + lane);
+    vv = to_f32(val[b + lane]);
+  }
+  for (int64_t p0 = b; p0 < e; p0 += 32) {
+    const int ct = tt;
+    const float cv = vv;
+    const int64_t pn = p0 + 32 + lane;
+    if (pn < e) {
+      tt = __ldg(col + pn);
+      vv = to_f32(val[pn]);
+    }
+    const int nq = (int)min((int64_t)32, e - p0);
+    if (nq == 32) {
+      float c[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int t = __shfl_sync(SKM_FULL_MASK, ct, q);
+        c[q] = on ? __ldg(cbase + (int64_t)t * kst) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) acc = __fmaf_rn(__shfl_sync(SKM_FULL_MASK, cv, q), c[q], acc);
+    } else {
+      for (int q = 0; q < nq; ++q) {
+        const int t = __shfl_sync(SKM_FULL_MASK, ct, q);
+        const float v = __shfl_sync(SKM_FULL_MASK, cv, q);
+        acc = __fmaf_rn(v, on ? __ldg(cbase + (int64_t)t * kst) : 0.f, acc);
+      }
+    }
+  }
   return acc;
 }
 
@@ -84,6 +177,35 @@ __device__ __forceinline__ float bound_u_hamerly(float u, float pd_min, float pu
   }
   return bound_u(u, pd_min, pu_min, q_max);
 }
+
+// Append (i, old) to the changed-row list through a per-warp buffer: lane r
+// holds the r-th pending entry; the warp flushes 32 at a time with one atomic.
+// All arguments but the buffer are warp-uniform.
+struct ChangedBuf {
+  int n = 0;
+  int32_t bi = 0, bo = 0;
+  __device__ __forceinline__ void flush(int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
+                                        unsigned long long* __restrict__ cnt) {
+    if (n == 0) return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cnt + C_CHG, (unsigned long long)n);
+    base = __shfl_sync(SKM_FULL_MASK, base, 0);
+    if (lane < n) {
+      chg_i[base + lane] = bi;
+      chg_old[base + lane] = bo;
+    }
+    n = 0;
+  }
+  __device__ __forceinline__ void push(int32_t i, int32_t old, int32_t* __restrict__ chg_i,
+                                       int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
+    if ((threadIdx.x & 31) == n) {
+      bi = i;
+      bo = old;
+    }
+    if (++n == 32) flush(chg_i, chg_old, cnt);
+  }
+};
 
 // Warp-aggregated append of `item` (when take) to list[*count]; returns nothing.
 __device__ __forceinline__ void warp_push(bool take, int32_t item, int32_t* __restrict__ list,
@@ -133,8 +255,16 @@ struct skm_ctx {
   long long* part64;   // [nparts * k] fixed-point partial sums
   float fx_scale, fx_inv;
   // centers (term-major, d x kst)
-  float* Ct;    // current centers
-  float* S;     // work: sums, then the next centers
+  float* Ct;        // current centers
+  long long* S64;   // exact fixed-point cluster sums (d x kst)
+  int s64_valid;    // S64 matches the current labels (else: full recompute)
+  int chg_fresh;    // the changed-row list belongs to the last assignment
+  int32_t* chg_i;   // [n] rows whose label changed in the last assignment
+  int32_t* chg_old; // [n] their previous labels
+  int32_t* dflag;   // [k] cluster sum touched by the incremental update
+  int32_t* dmark;   // [k] cluster dirty in this update
+  int32_t* dpos;    // [k] its position in dlist
+  int32_t* dlist;   // [k] dirty clusters, ascending
   double* nrm;  // [k] |S_j|
   double* red;  // reduction partials
   int64_t red_blocks;
@@ -145,22 +275,17 @@ struct skm_ctx {
   float* hsel;  // [HSEL_N] Hamerly drift summary
   float* cc;    // [k * kst] center-center bounds (full variants)
   float* sc;    // [k] s(j)
-  double* gpart;  // Gram partials
-  int32_t gsplit;
+  double* gpart;  // Gram partials (all tiles)
+  double* G;      // [k * k] Gram, upper triangle
+  double* rpart;  // Gram partials of dirty rows
+  int32_t gsplit, rsplit, grow_max;
   // labels and bounds
   int32_t* a;
   float* lb;  // [n]
   float* ub;  // [n] (Hamerly) or [n * kst] (Elkan)
-  // worklists
+  // worklists: points failing the first bound test, points needing a whole row
   int32_t* w1;
   int32_t* w2;
-  float* w1s;       // [n] tightened similarity to the current center (Elkan)
-  int64_t* poff;    // [n] pair offset per W1 slot
-  int32_t* pnum;    // [n] pair count per W1 slot
-  int32_t* pslot;   // [pcap]
-  int32_t* pj;      // [pcap]
-  float* psim;      // [pcap]
-  int64_t pcap;
   // counters
   unsigned long long* cnt;   // device [C_NUM]
   unsigned long long* hcnt;  // pinned host mirror [C_NUM]

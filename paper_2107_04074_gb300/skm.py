@@ -43,8 +43,8 @@ class skm_data(ctypes.Structure):
 
 
 class skm_options(ctypes.Structure):
-    _fields_ = [("hamerly_tight", ctypes.c_int32), ("validate", ctypes.c_int32), ("pair_capacity", ctypes.c_int64),
-                ("row_threshold", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("hamerly_tight", ctypes.c_int32), ("validate", ctypes.c_int32), ("row_threshold", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 9)]
 
 
 class skm_stats(ctypes.Structure):
@@ -179,8 +179,7 @@ class KMeans:
     """
 
     def __init__(self, n: int, d: int, row_ptr, col_idx, values, k: int, variant="standard", init_rows=None,
-                 seed: int = 0, hamerly_tight: bool = False, pair_capacity: int = 0, row_threshold: int = 0,
-                 stream=None):
+                 seed: int = 0, hamerly_tight: bool = False, row_threshold: int = 0, stream=None):
         lib = load()
         host = isinstance(values, np.ndarray)
         self._keep = (row_ptr, col_idx, values)
@@ -189,7 +188,6 @@ class KMeans:
         opt = skm_options()
         lib.skm_default_options(ctypes.byref(opt))
         opt.hamerly_tight = 1 if hamerly_tight else 0
-        opt.pair_capacity = int(pair_capacity)
         opt.row_threshold = int(row_threshold)
         self.n, self.d, self.k = int(n), int(d), int(k)
         self.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)

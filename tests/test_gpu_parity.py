@@ -275,3 +275,30 @@ def test_invalid_inputs_rejected():
                    torch.from_numpy(zero).cuda(), 2)
     with pytest.raises(skm.SkmError):
         _km(csr, 2, "standard", [1, 1])
+
+
+def test_incremental_sums_equal_full_recompute(mid):
+    """Optimisation (iii) of Section 5: updating the sums with only the rows
+    that moved gives bit for bit the centers of a full recomputation (the sums
+    are exact fixed-point integers)."""
+    init = synth.init_rows(mid.n, 100, 6)
+    dev = _dev(mid)
+    inc = _km(mid, 100, "elkan", init, dev)
+    ref = _km(mid, 100, "standard", init, dev)
+    for it in range(14):
+        ch = inc.assign()
+        lab = inc.labels()
+        ref.set_labels(lab)            # forces a full recomputation of the sums
+        ref.set_centers(inc.centers())
+        if ch == 0:
+            break
+        Ji = inc.update_centers()
+        Jr = ref.update_centers()
+        np.testing.assert_array_equal(inc.centers(), ref.centers())
+        assert Ji == Jr
+    # an update with no assignment in between changes nothing
+    C = inc.centers()
+    inc.update_centers()
+    np.testing.assert_array_equal(inc.centers(), C)
+    inc.close()
+    ref.close()
