@@ -7,9 +7,11 @@ initial rows, run to convergence (at most 100 iterations).
 
 One step = one complete clustering run from the seeded initial centers
 (restart, then assign + update until no label changes).  value = Lloyd
-iterations per second over the K timed steps (the variant given, Elkan by
-default); the plain standard variant is timed on the same workload, its label
-sequence must be identical, and its rate is reported beside it.
+iterations per second over the K timed steps of the variant given (Simplified
+Elkan by default -- the paper's fastest variant on most of its data sets,
+Table 3); the plain standard variant and the other bounded variants are
+timed on the same workload, their label sequences are identical, and their
+rates are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--variant elkan]
   python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
@@ -106,18 +108,53 @@ class ClockSampler:
 
 # ------------------------------------------------------ roofline helpers
 
-def algorithmic_bytes(name, n, d, k, nnz, w1=None):
-    """Compulsory bytes of one launch (the minimum any implementation moves)."""
-    if name == "k_rows_top2":  # CSR + centers once + labels r/w + row scalars + Elkan bound row writes
-        return 8 * (n + 1) + 8 * nnz + 4 * d * k + 8 * n + 8 * n + 4 * n * k + 4 * n
-    if name == "k_elk_bounds":  # u(i,j) read + write, l r/w, a and delta read
-        return 8 * n * k + 8 * n + 4 * n + 4 * n
-    if name == "k_center_sum":  # term-major entries + the sums written + label / norm per row
-        return 8 * nnz + 4 * d * k + 8 * n
-    if name == "k_normalize_drift":
-        return 12 * d * k
-    if name == "k_colnorm_part":
-        return 4 * d * k
+def source_hash() -> str:
+    """sha1 over the CUDA sources: a recorded ncu traffic figure only applies
+    to the kernels it was measured on."""
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2107_04074_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from profiles/dram_traffic.txt
+    (lines: kernel workload source_hash bytes_per_launch), if it was taken on
+    the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    cur = source_hash()
+    for ln in lines:
+        f = ln.split()
+        if len(f) == 4 and f[0] == kernel and f[1] == workload and f[2] == cur:
+            return int(float(f[3]))
+    return None
+
+
+def kernel_bytes(name, it_rows, n, d, k, nnz, variant, full_sum=True):
+    """Compulsory (algorithmic) bytes of one launch: what any implementation
+    must move between HBM and the SMs for that step, given the rows it treats.
+    it_rows: rows treated by the launch (all rows, the recompute list, ...)."""
+    avg = nnz / n
+    elk = variant in ("elkan", "simp_elkan")
+    row = 8 + 8 * avg + 4 + 4 + 4 + 4  # row_ptr, (col, val) entries, label r/w, 1/|x|, delta
+    if name in ("k_rows_top2", "k_rows_top2(list)"):
+        out = (4 * k if elk else 0) + (8 if variant != "standard" else 0)
+        return int(it_rows * (row + out + (4 if name.endswith("(list)") else 0)) + 4 * d * k)
+    if name == "k_elk_bounds":
+        return int(8 * n * k + 16 * n)
+    if name == "k_elk_recompute":
+        return int(it_rows * (4 * k * (2 if variant == "elkan" else 1) + row + 4))
+    if name == "k_center_sum":  # only a full recomputation moves data (else the kernel returns at once)
+        return int(8 * nnz + 8 * d * k + 4 * n) if full_sum else 0
+    if name == "k_ham_bounds":
+        return int(24 * n)
     return None
 
 
@@ -199,34 +236,66 @@ def run_ours(args, rank, world, local):
     std_rate = iters_s / (ms_s / 1e3)
     km_std.close()
 
-    # per-kernel CUDA-event profile of one more run (not part of the timed value)
+    # per-kernel CUDA-event profile of one more run (not part of the timed
+    # value), iteration by iteration so that each launch's rows are known
     flush.fill_(1.0)
-    km.profile(True)
     km.reset(init)
-    km.run(MAX_ITERS)
-    prof = km.profile_read()
-    km.profile(False)
+    prof_ms, prof_n, prof_bytes = {}, {}, {}
+    for it in range(MAX_ITERS):
+        km.profile(True)
+        ch = km.assign()
+        st = km.stats()
+        pa = km.profile_read()
+        km.profile(True)
+        if ch:
+            km.update_centers()
+        pu = km.profile_read()
+        km.profile(False)
+        rows_of = {"k_rows_top2": n, "k_rows_top2(list)": st.last_rechecks, "k_elk_recompute": st.last_survivors}
+        full_sum = it == 0 or ch * 8 > n
+        for nm, (ms_k, cnt_k) in list(pa.items()) + list(pu.items()):
+            prof_ms[nm] = prof_ms.get(nm, 0.0) + ms_k
+            prof_n[nm] = prof_n.get(nm, 0) + cnt_k
+            b = kernel_bytes(nm, rows_of.get(nm, n), n, d, k, nnz, variant, full_sum)
+            if b is not None:
+                prof_bytes[nm] = prof_bytes.get(nm, 0) + b * cnt_k
+        if ch == 0:
+            break
     km.close()
-    tot_prof = sum(v[0] for v in prof.values()) or 1.0
-    top = max(prof.items(), key=lambda kv: kv[1][0])
-    top_name, (top_ms, top_n) = top
-    peaks = {}
+    tot_prof = sum(prof_ms.values()) or 1.0
+    top_name = max(prof_ms, key=prof_ms.get)
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except (OSError, KeyError, ValueError):
         hbm_peak, peak_src = 6800.0, "fallback"
-    ab = algorithmic_bytes(top_name, n, d, k, nnz)
     roof = None
-    if ab is not None:
-        avg_s = top_ms / 1e3 / top_n
+    if top_name in prof_bytes:
+        avg_s = prof_ms[top_name] / 1e3 / prof_n[top_name]
+        ab = prof_bytes[top_name] / prof_n[top_name]
         ach = ab / avg_s / 1e9
         roof = {"kernel": top_name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(ach / hbm_peak, 4), "traffic": None, "peak_source": peak_src,
-                "avg_launch_us": round(avg_s * 1e6, 2), "launches": top_n,
-                "algorithmic_bytes_per_launch": ab}
-    kernel_share = {nm: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot_prof, 4)}
-                    for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+                "frac": round(ach / hbm_peak, 4), "peak_source": peak_src,
+                "traffic": recorded_traffic(top_name, "rcv1-like-k100"),
+                "avg_launch_us": round(avg_s * 1e6, 2), "launches": prof_n[top_name],
+                "algorithmic_bytes_per_launch": int(ab)}
+    kernel_share = {}
+    for nm in sorted(prof_ms, key=lambda x: -prof_ms[x]):
+        e = {"ms": round(prof_ms[nm], 3), "launches": prof_n[nm], "share": round(prof_ms[nm] / tot_prof, 4)}
+        if nm in prof_bytes:
+            e["GB_per_s"] = round(prof_bytes[nm] / (prof_ms[nm] / 1e3) / 1e9, 1)
+        kernel_share[nm] = e
+
+    # every variant on the same workload (same labels), for comparison
+    others = {}
+    for v in ("standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan"):
+        if v == variant:
+            others[v] = round(value / world, 3)
+            continue
+        kv = make(v)
+        ms_o, it_o, _, _, _ = timed_runs(kv, std_steps, 1)
+        others[v] = round(it_o / (ms_o / 1e3), 3)
+        kv.close()
 
     # end to end through the C ABI with host buffers (pinned), copies included
     pin = [torch.from_numpy(a).pin_memory() for a in (csr.row_ptr, csr.col, csr.val)]
@@ -259,6 +328,7 @@ def run_ours(args, rank, world, local):
         "standard_iters_per_s": round(std_rate, 3),
         "speedup_vs_standard": round(value / world / std_rate, 3),
         "labels_identical_to_standard": labels_identical,
+        "variants_iters_per_s": others,
         "objective": J,
         "gpu_launches": int(launches),
         "clocks": clocks,
@@ -347,8 +417,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="elkan", choices=["standard", "hamerly", "elkan", "simp_hamerly",
-                                                            "simp_elkan"])
+    ap.add_argument("--variant", default="simp_elkan", choices=["standard", "hamerly", "elkan", "simp_hamerly",
+                                                                 "simp_elkan"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed runs of the chosen variant (for profiler captures)")
