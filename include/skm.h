@@ -63,12 +63,21 @@ typedef enum { SKM_F32 = 0, SKM_F16 = 1, SKM_BF16 = 2 } skm_dtype;
 typedef enum { SKM_CSR = 0, SKM_DENSE = 1 } skm_layout;
 typedef enum { SKM_DEVICE = 0, SKM_HOST = 1 } skm_memspace;
 
+/* Arithmetic of the dense similarity bulk.  FP32: the plain FP32 GEMM (the
+ * reference point).  BF16: the precision form -- a BF16 x BF16 -> FP32
+ * tensor-core GEMM whose per-row top-2 decides a label when its margin
+ * exceeds the proven error bound; the other rows are rechecked in FP32, so
+ * the labels are those of the FP32 path. */
+typedef enum { SKM_PREC_FP32 = 0, SKM_PREC_BF16 = 1 } skm_precision;
+
 /* Input vectors x(1..n) in R^d (Section 2: sparse rows stored as sorted
  * (index, value) pairs; dense rows as plain arrays).
  *   CSR:   row_ptr int64[n+1] (row_ptr[0] = 0, non-decreasing), col_idx
  *          int32[nnz] strictly increasing within each row and in [0, d),
  *          values[nnz] of type dtype.
- *   DENSE: values[n*d] row-major of type dtype; row_ptr, col_idx unused.
+ *   DENSE: values[n*d] row-major FP32; row_ptr, col_idx unused.  Dense rows
+ *          support the standard and Hamerly variants (SKM_EUNSUPPORTED for
+ *          Elkan); precision BF16 needs d a multiple of 8 and d <= 448.
  * memspace says where all three pointers live. */
 typedef struct {
   int64_t n;
@@ -90,7 +99,8 @@ typedef struct {
   int32_t row_threshold;   /* Elkan: a point with more candidate centers than
                               this (capped at 7) is recomputed as a whole row;
                               0 = min(k/8, 7) */
-  int32_t reserved[9];
+  int32_t precision;       /* skm_precision, dense rows only (default FP32) */
+  int32_t reserved[8];
 } skm_options;
 
 /* Counters of the last assignment and of the run so far. */
@@ -162,6 +172,13 @@ int skm_set_labels(skm_ctx* ctx, const int32_t* a, int32_t space);
 int skm_get_bounds(skm_ctx* ctx, float* l, float* u, int32_t out_space);
 
 int skm_get_stats(skm_ctx* ctx, skm_stats* out);
+
+/* Diagnostic for the precision form (dense rows, precision BF16): the BF16
+ * tensor-core result of the last assignment for every row as 4 floats
+ * (best similarity, its center index stored as a float, second best, the
+ * similarity to the label the row had) and the error bound eps_b every
+ * BF16 similarity satisfies against the exact one.  SKM_ESTATE otherwise. */
+int skm_get_bf16_top2(skm_ctx* ctx, float* out4n, float* eps_b, int32_t out_space);
 
 /* Bytes of bound state a variant keeps for n points and k centers (labels
  * excluded): standard 0; Hamerly 8n (two FP32 bounds); Elkan 4n + 4nk. */

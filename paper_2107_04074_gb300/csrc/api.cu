@@ -131,7 +131,8 @@ void release(skm_ctx* c) {
                   c->Ct,     c->S64,    c->nrm,    c->red,   c->obj,   c->pdn,   c->pup,   c->qup,
                   c->hsel,   c->cc,     c->sc,     c->gpart, c->a,     c->lb,    c->ub,    c->w1,
                   c->w2,     c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark, c->dpos, c->dlist,
-                  c->G,      c->rpart};
+                  c->G,      c->rpart,  c->Xb,     c->Cr,    c->Cb,    c->top2,  c->lcount, c->loff,
+                  c->lcursor, c->lmembers};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -189,7 +190,17 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
       c->val = x->values;
     }
   } else {
-    return SKM_EUNSUPPORTED;
+    // dense rows: n x d FP32
+    c->nnz = n * d;
+    if (x->memspace == SKM_HOST) {
+      float* X = nullptr;
+      TRY(dalloc(c, &X, (size_t)(n * d)));
+      c->own[2] = X;
+      SKM_CUDA_TRY(cudaMemcpyAsync(X, x->values, sizeof(float) * n * d, cudaMemcpyHostToDevice, c->st));
+      c->val = X;
+    } else {
+      c->val = x->values;
+    }
   }
   // ---- counters and per-row data
   TRY(dalloc(c, &c->cnt, C_NUM));
@@ -201,7 +212,7 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   TRY(prep_rows(c));
   TRY(read_counters(c));
   if (c->hcnt[C_ERR]) return SKM_EINVAL;
-  TRY(prep_transpose(c));
+  if (c->layout == SKM_CSR) TRY(prep_transpose(c));
   // ---- centers
   const int64_t kst = c->kst, k = c->k;
   TRY(dalloc(c, &c->Ct, (size_t)(d * kst)));
@@ -224,7 +235,7 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   TRY(dalloc(c, &c->hsel, HSEL_N));
   const bool full = (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY);
   const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
-  const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
+  const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) || c->layout == SKM_DENSE;
   if (full) {
     // enough d-splits of the Gram (64 x 64 tiles) for ~4 blocks per SM, each
     // split >= 256 terms
@@ -242,6 +253,30 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
     c->grow_max = (int32_t)((k + 3) / 4 < 64 ? (k + 3) / 4 : 64);
     c->rsplit = c->gsplit;
     TRY(dalloc(c, &c->rpart, (size_t)(c->gsplit * c->grow_max * k)));
+  }
+  // ---- dense rows: row-major centers, label sort, BF16 operands
+  if (c->layout == SKM_DENSE) {
+    c->precision = c->opt.precision;
+    c->kpad = (int32_t)((k + 255) / 256 * 256);
+    TRY(dalloc(c, &c->Cr, (size_t)(k * d)));
+    TRY(dalloc(c, &c->lcount, (size_t)k));
+    TRY(dalloc(c, &c->loff, (size_t)(k + 1)));
+    TRY(dalloc(c, &c->lcursor, (size_t)k));
+    TRY(dalloc(c, &c->lmembers, (size_t)n));
+    if (c->precision == SKM_PREC_BF16) {
+      __nv_bfloat16 *xb = nullptr, *cb = nullptr;
+      float4* t2 = nullptr;
+      TRY(dalloc(c, &xb, (size_t)(n * d)));
+      c->Xb = xb;
+      TRY(dalloc(c, &cb, (size_t)(c->kpad * d)));
+      c->Cb = cb;
+      TRY(dalloc(c, &t2, (size_t)n));
+      c->top2 = t2;
+      TRY(dense_prep_bf16(c));
+      // |BF16 similarity - exact| <= (2u_b + u_b^2)(1 + 1e-6) sum|x c| + accumulation over d terms
+      // with truncation (2^-23 per step): 2^-8 + 2^-15 + (d + 16) 2^-23 (sum|x c| <= 1)
+      c->eps_b = (float)(0x1.0p-8 + 0x1.0p-15 + ((double)d + 16.0) * 0x1.0p-23);
+    }
   }
   // ---- labels, bounds, worklists
   TRY(dalloc(c, &c->a, (size_t)n));
@@ -298,6 +333,16 @@ int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const
   c->dtype = x->dtype;
   if (opt) c->opt = *opt;
   else skm_default_options(&c->opt);
+  if (x->layout == SKM_DENSE) {
+    if (x->dtype != SKM_F32 || variant == SKM_ELKAN || variant == SKM_SIMP_ELKAN) {
+      delete c;
+      return SKM_EUNSUPPORTED;
+    }
+    if (c->opt.precision == SKM_PREC_BF16 && !bf16_mma_supported(x->d)) {
+      delete c;
+      return SKM_EUNSUPPORTED;
+    }
+  }
   c->prof = new (std::nothrow) ProfList();
   if (!c->prof) {
     delete c;
@@ -317,11 +362,44 @@ int skm_reset(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
   return set_init(c, init_rows, seed);
 }
 
+namespace {
+
+// One assignment of dense rows (standard or Hamerly; FP32 or BF16 bulk).
+int assign_dense(skm_ctx* c) {
+  TRY(dense_refresh_centers(c));
+  const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
+  const bool first = !c->have_bounds;
+  if (c->precision == SKM_PREC_BF16) {
+    const int32_t* list = nullptr;
+    const unsigned long long* lcnt = nullptr;
+    if (ham && !first) {
+      TRY(hamerly_bounds_only(c));  // survivors of the bound test -> w1
+      list = c->w1;
+      lcnt = c->cnt + C_W1;
+    }
+    TRY(bf16_top2(c, c->Xb, c->Cb, (float4*)c->top2));
+    TRY(dense_classify(c, ham, list, lcnt));  // ambiguous rows -> w2
+    TRY(dense_rows(c, ham ? 1 : 0, c->w2, c->cnt + C_W2));
+  } else if (!ham || first) {
+    TRY(dense_rows(c, ham ? 1 : 0, nullptr, nullptr));
+  } else {
+    TRY(hamerly_bounds_only(c));
+    TRY(dense_tighten(c));
+    TRY(dense_rows(c, 1, c->w2, c->cnt + C_W2));
+  }
+  if (ham) c->have_bounds = 1;
+  return SKM_OK;
+}
+
+}  // namespace
+
 int skm_assign(skm_ctx* c, int64_t* n_changed) {
   if (!c) return SKM_EINVAL;
   SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_ERR, c->st));
   int rc;
-  if (!c->have_bounds || c->variant == SKM_STANDARD) {
+  if (c->layout == SKM_DENSE) {
+    rc = assign_dense(c);
+  } else if (!c->have_bounds || c->variant == SKM_STANDARD) {
     const int mode = (c->variant == SKM_STANDARD) ? 0
                      : (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) ? 1
                                                                                       : 2;
@@ -338,6 +416,7 @@ int skm_assign(skm_ctx* c, int64_t* n_changed) {
   c->stats.iterations++;
   if (n_changed) {
     TRY(read_counters(c));
+    if (c->hcnt[C_ERR] & E_TIMEOUT) return SKM_ETIMEOUT;
     c->stats.total_sims += c->stats.last_sims;
     *n_changed = c->stats.last_changed;
   } else {
@@ -451,6 +530,18 @@ int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
       SKM_CUDA_TRY(cudaMemcpyAsync(u, c->ub, sizeof(float) * c->n, kind, c->st));
   }
   SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  return SKM_OK;
+}
+
+int skm_get_bf16_top2(skm_ctx* c, float* out, float* eps_b, int32_t space) {
+  if (!c) return SKM_EINVAL;
+  if (c->layout != SKM_DENSE || c->precision != SKM_PREC_BF16) return SKM_ESTATE;
+  if (eps_b) *eps_b = c->eps_b;
+  if (out) {
+    SKM_CUDA_TRY(cudaMemcpyAsync(out, c->top2, sizeof(float) * 4 * c->n,
+                                 space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
+    SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  }
   return SKM_OK;
 }
 

@@ -592,6 +592,19 @@ int elkan_step_t(skm_ctx* c) {
 
 }  // namespace
 
+int hamerly_bounds_only(skm_ctx* c) {
+  const int g = persistent_grid(c);
+  SKM_PROF_BEGIN(c, "k_ham_bounds");
+  if (c->variant == SKM_HAMERLY)
+    k_ham_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
+                                                c->sc, c->opt.hamerly_tight, c->moved, c->w1, c->cnt);
+  else
+    k_ham_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
+                                                 c->sc, c->opt.hamerly_tight, c->moved, c->w1, c->cnt);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
 int assign_full(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
   switch (c->dtype) {
     case SKM_F32: return assign_full_t<float>(c, mode, list, list_cnt, nrows);

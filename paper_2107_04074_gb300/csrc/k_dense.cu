@@ -1,0 +1,522 @@
+// Dense rows (embedding-like data): the same Lloyd iteration as the sparse
+// path, with the similarity bulk as a GEMM.
+//
+// Canonical dense similarity: s_ij = fl32(fl32_seq(sum_{t=0..d-1} x_it c_jt)
+// * 1/|x_i|), a sequential FP32 FMA chain over t in order.  k_dense_top2 (a
+// tiled SIMT GEMM) accumulates every output exactly in that order, and so do
+// k_dense_tighten and the FP32 recheck, so all paths agree bit for bit.
+//
+//   k_dense_bf16        unit rows rounded to BF16 (A operand of k_bf16_top2)
+//   k_dense_centers     term-major FP32 centers -> row-major FP32 and BF16
+//   k_dense_top2        FP32 GEMM + fused top-2 (plain FP32 path, whole rows
+//                       for Hamerly, recheck of ambiguous rows)
+//   k_dense_classify    precision form: a BF16 top-2 decides the label when its
+//                       margin exceeds the error bound, else the row is rechecked
+//   k_dense_tighten     Hamerly: exact <x, c_a> (warp per survivor)
+//   k_label_*, k_dense_cluster_sum, k_dense_delta
+//                       exact fixed-point cluster sums: full (rows sorted by
+//                       label) or only the rows whose label changed
+#include <climits>
+
+#include "skm_internal.cuh"
+
+namespace skm {
+
+namespace {
+
+__global__ void k_dense_bf16(const float* __restrict__ X, const float* __restrict__ rinv, int64_t n, int64_t d,
+                             __nv_bfloat16* __restrict__ Xb) {
+  const int64_t tot = n * d;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x)
+    Xb[q] = __float2bfloat16_rn(__fmul_rn(X[q], rinv[q / d]));
+}
+
+// Ct (d x kst, term-major) -> Cr (k x d FP32) and Cb (kpad x d BF16, zero
+// rows past k), through 32 x 32 shared tiles.
+__global__ void k_dense_centers(const float* __restrict__ Ct, int64_t d, int32_t k, int64_t kst, int32_t kpad,
+                                float* __restrict__ Cr, __nv_bfloat16* __restrict__ Cb) {
+  __shared__ float tile[32][33];
+  const int64_t t0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t t = t0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (t < d && j < k) ? Ct[t * kst + j] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = j0 + r, t = t0 + threadIdx.x;
+    if (t < d && j < kpad) {
+      const float v = tile[threadIdx.x][r];
+      if (j < k) Cr[j * d + t] = v;
+      if (Cb) Cb[j * d + t] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// FP32 GEMM with fused top-2.  CTA: 128 rows x all centers (tiles of 128),
+// 256 threads (16 x 16), each thread 8 rows x 8 centers, K in chunks of 32
+// through shared memory.  Rows: all (list == nullptr) or list[0..*list_cnt).
+// MODE 0: labels only; MODE 1: also Hamerly's l = s1 - delta, u = s2 + delta.
+constexpr int kTR = 128, kTC = 128, kKC = 32;
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X, const float* __restrict__ rinv,
+                                                    const float* __restrict__ dlt, const float* __restrict__ Cr,
+                                                    int64_t n, int64_t d, int32_t k, const int32_t* __restrict__ list,
+                                                    const unsigned long long* __restrict__ list_cnt,
+                                                    int32_t* __restrict__ a, float* __restrict__ lb,
+                                                    float* __restrict__ ub, int32_t* __restrict__ chg_i,
+                                                    int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
+  __shared__ __align__(16) float As[kKC][kTR + 4];
+  __shared__ __align__(16) float Bs[kKC][kTC + 4];
+  __shared__ int rows_sh[kTR];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
+  const int64_t total = list ? (int64_t)(*list_cnt) : n;
+  const int64_t ntiles = (total + kTR - 1) / kTR;
+  unsigned long long changed = 0, sims = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();
+    if (tid < kTR) {
+      const int64_t q = tile * kTR + tid;
+      rows_sh[tid] = (q < total) ? (list ? list[q] : (int32_t)q) : -1;
+    }
+    __syncthreads();
+    int32_t myrow[8], cur[8];
+    float v1[8], v2[8], vc[8];
+    int j1[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      myrow[x] = rows_sh[ty * 8 + x];
+      cur[x] = myrow[x] >= 0 ? a[myrow[x]] : -1;
+      v1[x] = v2[x] = vc[x] = -INFINITY;
+      j1[x] = INT_MAX;
+    }
+    for (int j0 = 0; j0 < k; j0 += kTC) {
+      float acc[8][8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+      for (int64_t t0 = 0; t0 < d; t0 += kKC) {
+        // A: 128 rows x 32 terms, B: 128 centers x 32 terms, both transposed
+        for (int q = tid; q < kTR * kKC; q += 256) {
+          const int r = q / kKC, kk = q % kKC;
+          const int32_t row = rows_sh[r];
+          const int64_t t = t0 + kk;
+          As[kk][r] = (row >= 0 && t < d) ? X[(int64_t)row * d + t] : 0.f;
+          const int64_t j = j0 + r;
+          Bs[kk][r] = (j < k && t < d) ? Cr[j * d + t] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kKC; ++kk) {
+          const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
+          const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
+          const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
+          const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
+          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int x = 0; x < 8; ++x)
+#pragma unroll
+            for (int y = 0; y < 8; ++y) acc[x][y] = __fmaf_rn(av[x], bv[y], acc[x][y]);
+        }
+        __syncthreads();
+      }
+      // fold this center tile into the running top-2 of each row
+#pragma unroll
+      for (int x = 0; x < 8; ++x) {
+        const float ri = myrow[x] >= 0 ? rinv[myrow[x]] : 0.f;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) {
+          const int j = j0 + tx * 8 + y;
+          if (j < k) {
+            const float s = __fmul_rn(acc[x][y], ri);
+            if (j == cur[x]) vc[x] = s;
+            if (s > v1[x]) {  // j ascends within a thread: ties keep the lowest index
+              v2[x] = v1[x];
+              v1[x] = s;
+              j1[x] = j;
+            } else if (s > v2[x]) {
+              v2[x] = s;
+            }
+          }
+        }
+      }
+    }
+    // merge across the 16 threads that share these rows (lanes of one half-warp)
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+#pragma unroll
+      for (int o = 8; o; o >>= 1) {
+        const float ov1 = __shfl_xor_sync(SKM_FULL_MASK, v1[x], o);
+        const int oj1 = __shfl_xor_sync(SKM_FULL_MASK, j1[x], o);
+        const float ov2 = __shfl_xor_sync(SKM_FULL_MASK, v2[x], o);
+        if (ov1 > v1[x] || (ov1 == v1[x] && oj1 < j1[x])) {
+          v2[x] = fmaxf(ov2, v1[x]);
+          v1[x] = ov1;
+          j1[x] = oj1;
+        } else {
+          v2[x] = fmaxf(v2[x], ov1);
+        }
+        vc[x] = fmaxf(vc[x], __shfl_xor_sync(SKM_FULL_MASK, vc[x], o));
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int32_t row = myrow[x];
+      int32_t nb = -1;
+      bool moved = false;
+      if (row >= 0) {
+        float ssec;
+        if (cur[x] >= 0 && vc[x] == v1[x]) {
+          nb = cur[x];
+          ssec = (j1[x] == cur[x]) ? v2[x] : v1[x];
+        } else {
+          nb = j1[x];
+          ssec = v2[x];
+        }
+        moved = (nb != cur[x]);
+        if (tx == 0) {
+          a[row] = nb;
+          changed += moved;
+          sims += (unsigned long long)k;
+          const float dl = dlt[row];
+          if (MODE == 1) {
+            lb[row] = __fsub_rd(v1[x], dl);
+            ub[row] = (k > 1) ? __fadd_ru(ssec, dl) : -1.f;
+          }
+        }
+      }
+      // changed-row list: one entry per moved row (lane tx == 0 of its half-warp)
+      const bool take = moved && tx == 0;
+      const unsigned m = __ballot_sync(SKM_FULL_MASK, take);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(cnt + C_CHG, (unsigned long long)__popc(m));
+        base = __shfl_sync(SKM_FULL_MASK, base, leader);
+        if (take) {
+          const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
+          chg_i[pos] = row;
+          chg_old[pos] = cur[x];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    changed += __shfl_xor_sync(SKM_FULL_MASK, changed, o);
+    sims += __shfl_xor_sync(SKM_FULL_MASK, sims, o);
+  }
+  if (lane == 0) {
+    if (changed) atomicAdd(cnt + C_CHANGED, changed);
+    if (sims) atomicAdd(cnt + C_SIMS, sims);
+  }
+}
+
+// Precision form.  For each row (all, or the Hamerly survivors w1) the BF16
+// top-2 (v1, j1, v2) is within eps_b of the exact similarities; if
+// v1 - v2 > 2 (eps_b + delta_i) the FP32 standard variant necessarily picks j1
+// (its similarities are within delta_i of exact), so j1 is the label;
+// Hamerly's bounds become l = v1 - eps_b, u = v2 + eps_b (exact-similarity
+// bounds).  Otherwise the row goes to `recheck` for the FP32 path.
+template <bool HAMERLY>
+__global__ void __launch_bounds__(256) k_dense_classify(const float4* __restrict__ top2, const float* __restrict__ dlt,
+                                                        float eps_b, int64_t n, const int32_t* __restrict__ list,
+                                                        const unsigned long long* __restrict__ list_cnt,
+                                                        int32_t* __restrict__ a, float* __restrict__ lb,
+                                                        float* __restrict__ ub, int32_t* __restrict__ recheck,
+                                                        int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
+                                                        unsigned long long* __restrict__ cnt) {
+  const int64_t total = list ? (int64_t)(*list_cnt) : n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long changed = 0;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+    const int64_t q = base + threadIdx.x;
+    bool amb = false, moved = false;
+    int32_t row = 0, cur = -1;
+    if (q < total) {
+      row = list ? list[q] : (int32_t)q;
+      const float4 t = top2[row];
+      const float v1 = t.x, v2 = t.z;
+      const int j1 = __float_as_int(t.y);
+      const float margin = __fadd_ru(eps_b, dlt[row]);
+      cur = a[row];
+      if (__fsub_rd(v1, v2) > __fmul_ru(2.f, margin)) {
+        moved = (j1 != cur);
+        a[row] = j1;
+        changed += moved;
+        if (HAMERLY) {
+          lb[row] = __fsub_rd(v1, eps_b);
+          ub[row] = __fadd_ru(v2, eps_b);
+        }
+      } else {
+        amb = true;
+      }
+    }
+    warp_push(amb, row, recheck, cnt + C_W2);
+    const unsigned m = __ballot_sync(SKM_FULL_MASK, moved);
+    if (m) {
+      const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+      unsigned long long b0 = 0;
+      if (lane == leader) b0 = atomicAdd(cnt + C_CHG, (unsigned long long)__popc(m));
+      b0 = __shfl_sync(SKM_FULL_MASK, b0, leader);
+      if (moved) {
+        const unsigned long long pos = b0 + __popc(m & ((1u << lane) - 1u));
+        chg_i[pos] = row;
+        chg_old[pos] = cur;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) changed += __shfl_xor_sync(SKM_FULL_MASK, changed, o);
+  if ((threadIdx.x & 31) == 0 && changed) atomicAdd(cnt + C_CHANGED, changed);
+}
+
+// Hamerly on dense rows: warp per survivor, exact <x, c_a> (32 terms loaded at
+// once, sequential FMA chain through shuffles), then the test again; points
+// still failing go to `out`.
+template <bool FULL>
+__global__ void __launch_bounds__(256) k_dense_tighten(const float* __restrict__ X, const float* __restrict__ rinv,
+                                                       const float* __restrict__ dlt, const float* __restrict__ Cr,
+                                                       int64_t d, const int32_t* __restrict__ w1,
+                                                       const unsigned long long* __restrict__ w1_cnt,
+                                                       const int32_t* __restrict__ a, float* __restrict__ lb,
+                                                       const float* __restrict__ ub, const float* __restrict__ sc,
+                                                       int32_t* __restrict__ out, unsigned long long* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)(*w1_cnt);
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long sims = 0;
+  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total; slot += nw) {
+    const int32_t i = w1[slot];
+    const int32_t ai = a[i];
+    const float* xr = X + (int64_t)i * d;
+    const float* cr = Cr + (int64_t)ai * d;
+    float acc = 0.f;
+    for (int64_t t0 = 0; t0 < d; t0 += 32) {
+      const float xv = (t0 + lane < d) ? xr[t0 + lane] : 0.f;
+      const float cv = (t0 + lane < d) ? cr[t0 + lane] : 0.f;
+      const int nq = (int)min((int64_t)32, d - t0);
+      for (int q = 0; q < nq; ++q)
+        acc = __fmaf_rn(__shfl_sync(SKM_FULL_MASK, xv, q), __shfl_sync(SKM_FULL_MASK, cv, q), acc);
+    }
+    const float sim = __fmul_rn(acc, rinv[i]);
+    const float dl = dlt[i];
+    const float l = __fsub_rd(sim, dl);
+    const float L = __fsub_rd(l, 2.f * dl);
+    const bool fail = !((L >= ub[i]) || (FULL && L >= 0.f && L >= sc[ai]));
+    if (lane == 0) {
+      lb[i] = l;
+      ++sims;
+      if (fail) {
+        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
+        out[pos] = i;
+      }
+    }
+  }
+  if (lane == 0 && sims) atomicAdd(cnt + C_SIMS, sims);
+}
+
+// ---- exact fixed-point cluster sums of dense rows
+
+__global__ void k_label_zero(int32_t* __restrict__ cntk, int32_t k, int s64_valid,
+                             const unsigned long long* __restrict__ cnt, int64_t n) {
+  if (!full_update(s64_valid, cnt, n)) return;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) cntk[j] = 0;
+}
+
+__global__ void k_label_count(const int32_t* __restrict__ a, int64_t n, int32_t* __restrict__ cntk, int s64_valid,
+                              const unsigned long long* __restrict__ cnt) {
+  if (!full_update(s64_valid, cnt, n)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(cntk + a[i], 1);
+}
+
+// one block: exclusive scan of k counts into off (k+1) and a cursor copy
+__global__ void __launch_bounds__(1024) k_label_scan(const int32_t* __restrict__ cntk, int32_t k,
+                                                     int32_t* __restrict__ off, int32_t* __restrict__ cursor,
+                                                     int s64_valid, const unsigned long long* __restrict__ cnt,
+                                                     int64_t n) {
+  if (!full_update(s64_valid, cnt, n)) return;
+  __shared__ int sh[1024];
+  const int per = (k + 1023) / 1024;
+  const int b = threadIdx.x * per, e = min(k, b + per);
+  int s = 0;
+  for (int q = b; q < e; ++q) s += cntk[q];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = sh[threadIdx.x] - s;
+  for (int q = b; q < e; ++q) {
+    off[q] = run;
+    cursor[q] = run;
+    run += cntk[q];
+  }
+  if (threadIdx.x == 1023) off[k] = sh[1023];
+}
+
+__global__ void k_label_place(const int32_t* __restrict__ a, int64_t n, int32_t* __restrict__ cursor,
+                              int32_t* __restrict__ members, int s64_valid, const unsigned long long* __restrict__ cnt) {
+  if (!full_update(s64_valid, cnt, n)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    members[atomicAdd(cursor + a[i], 1)] = (int32_t)i;
+}
+
+// Block per (cluster, 128-term slice): sum of the members' fixed-point values
+// (order-free, exact) -> S64[t][j].
+__global__ void __launch_bounds__(128) k_dense_cluster_sum(const float* __restrict__ X, const float* __restrict__ rinv,
+                                                           int64_t d, int64_t kst, const int32_t* __restrict__ off,
+                                                           const int32_t* __restrict__ members, float scale,
+                                                           long long* __restrict__ S64, int s64_valid,
+                                                           const unsigned long long* __restrict__ cnt, int64_t n) {
+  if (!full_update(s64_valid, cnt, n)) return;
+  const int j = blockIdx.x;
+  const int64_t t = (int64_t)blockIdx.y * 128 + threadIdx.x;
+  if (t >= d) return;
+  long long s = 0;
+  const int b = off[j], e = off[j + 1];
+  int m = b;
+  for (; m + 4 <= e; m += 4) {
+    int32_t r[4];
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = members[m + u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = __fmul_rn(X[(int64_t)r[u] * d + t], rinv[r[u]]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += __float2ll_rn(__fmul_rn(x[u], scale));
+  }
+  for (; m < e; ++m) {
+    const int32_t r = members[m];
+    s += __float2ll_rn(__fmul_rn(__fmul_rn(X[(int64_t)r * d + t], rinv[r]), scale));
+  }
+  S64[t * kst + j] = s;
+}
+
+// Incremental: warp per changed row, -x from the old and +x to the new sum.
+__global__ void __launch_bounds__(256) k_dense_delta(const float* __restrict__ X, const float* __restrict__ rinv,
+                                                     int64_t d, int64_t kst, const int32_t* __restrict__ chg_i,
+                                                     const int32_t* __restrict__ chg_old, const int32_t* __restrict__ a,
+                                                     float scale, long long* __restrict__ S64,
+                                                     int32_t* __restrict__ dflag, int s64_valid,
+                                                     const unsigned long long* __restrict__ cnt, int64_t n) {
+  if (full_update(s64_valid, cnt, n)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nchg = (int64_t)cnt[C_CHG];
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchg; q += nw) {
+    const int32_t i = chg_i[q], old = chg_old[q], nu = a[i];
+    if (lane == 0) {
+      dflag[old] = 1;
+      dflag[nu] = 1;
+    }
+    const float ri = rinv[i];
+    for (int64_t t = lane; t < d; t += 32) {
+      const long long fx = __float2ll_rn(__fmul_rn(__fmul_rn(X[(int64_t)i * d + t], ri), scale));
+      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + old), (unsigned long long)(-fx));
+      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + nu), (unsigned long long)fx);
+    }
+  }
+}
+
+inline unsigned grid_cap(int64_t items, int per_block, int nsm, int per_sm = 16) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g > (int64_t)nsm * per_sm) g = (int64_t)nsm * per_sm;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int dense_prep_bf16(skm_ctx* c) {
+  SKM_PROF_BEGIN(c, "k_dense_bf16");
+  k_dense_bf16<<<grid_cap(c->n * c->d, 256, c->nsm), 256, 0, c->st>>>((const float*)c->val, c->rinv, c->n, c->d,
+                                                                      (__nv_bfloat16*)c->Xb);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+int dense_refresh_centers(skm_ctx* c) {
+  dim3 g((unsigned)((c->d + 31) / 32), (unsigned)((c->kpad + 31) / 32));
+  SKM_PROF_BEGIN(c, "k_dense_centers");
+  k_dense_centers<<<g, dim3(32, 8), 0, c->st>>>(c->Ct, c->d, c->k, c->kst, c->kpad, c->Cr, (__nv_bfloat16*)c->Cb);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+int dense_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt) {
+  const int64_t ntiles = (c->n + kTR - 1) / kTR;
+  const unsigned g = (unsigned)(list ? c->nsm * 2 : (ntiles < (int64_t)c->nsm * 4 ? ntiles : (int64_t)c->nsm * 4));
+  SKM_PROF_BEGIN(c, list ? "k_dense_top2(list)" : "k_dense_top2");
+  if (mode == 0)
+    k_dense_top2<0><<<g, 256, 0, c->st>>>((const float*)c->val, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list,
+                                          list_cnt, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+  else
+    k_dense_top2<1><<<g, 256, 0, c->st>>>((const float*)c->val, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list,
+                                          list_cnt, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned long long* list_cnt) {
+  SKM_PROF_BEGIN(c, "k_dense_classify");
+  const unsigned g = c->nsm * 8;
+  if (hamerly)
+    k_dense_classify<true><<<g, 256, 0, c->st>>>((const float4*)c->top2, c->dlt, c->eps_b, c->n, list, list_cnt, c->a,
+                                                 c->lb, c->ub, c->w2, c->chg_i, c->chg_old, c->cnt);
+  else
+    k_dense_classify<false><<<g, 256, 0, c->st>>>((const float4*)c->top2, c->dlt, c->eps_b, c->n, list, list_cnt,
+                                                  c->a, c->lb, c->ub, c->w2, c->chg_i, c->chg_old, c->cnt);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+int dense_tighten(skm_ctx* c) {
+  SKM_PROF_BEGIN(c, "k_dense_tighten");
+  const unsigned g = c->nsm * 8;
+  if (c->variant == SKM_HAMERLY)
+    k_dense_tighten<true><<<g, 256, 0, c->st>>>((const float*)c->val, c->rinv, c->dlt, c->Cr, c->d, c->w1,
+                                                c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt);
+  else
+    k_dense_tighten<false><<<g, 256, 0, c->st>>>((const float*)c->val, c->rinv, c->dlt, c->Cr, c->d, c->w1,
+                                                 c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+// Cluster sums of dense rows: a full recomputation (rows sorted by label,
+// then a block per cluster and 128-term slice) or only the changed rows; the
+// same device-side rule as the sparse path picks one (the other's kernels
+// return at once).
+int dense_center_sums(skm_ctx* c) {
+  const int64_t n = c->n;
+  SKM_PROF_BEGIN(c, "k_label_zero");
+  k_label_zero<<<grid_cap(c->k, 256, c->nsm), 256, 0, c->st>>>(c->lcount, c->k, c->s64_valid, c->cnt, n);
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_label_count");
+  k_label_count<<<grid_cap(n, 256, c->nsm), 256, 0, c->st>>>(c->a, n, c->lcount, c->s64_valid, c->cnt);
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_label_scan");
+  k_label_scan<<<1, 1024, 0, c->st>>>(c->lcount, c->k, c->loff, c->lcursor, c->s64_valid, c->cnt, n);
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_label_place");
+  k_label_place<<<grid_cap(n, 256, c->nsm), 256, 0, c->st>>>(c->a, n, c->lcursor, c->lmembers, c->s64_valid, c->cnt);
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_dense_cluster_sum");
+  k_dense_cluster_sum<<<dim3((unsigned)c->k, (unsigned)((c->d + 127) / 128)), 128, 0, c->st>>>(
+      (const float*)c->val, c->rinv, c->d, c->kst, c->loff, c->lmembers, c->fx_scale, c->S64, c->s64_valid, c->cnt, n);
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_dense_delta");
+  k_dense_delta<<<grid_cap(n * 32, 256, c->nsm), 256, 0, c->st>>>((const float*)c->val, c->rinv, c->d, c->kst,
+                                                                   c->chg_i, c->chg_old, c->a, c->fx_scale, c->S64,
+                                                                   c->dflag, c->s64_valid, c->cnt, n);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+}  // namespace skm

@@ -41,11 +41,6 @@ namespace {
 constexpr int kChunk = 1024;  // must match the chunking built in k_prep.cu
 constexpr int kTB = 256;      // rows (terms) per reduction block
 
-// Is this update a full recomputation of the sums?
-__device__ __forceinline__ bool full_update(int s64_valid, const unsigned long long* cnt, int64_t n) {
-  return !s64_valid || cnt[C_CHG] * 8ull > (unsigned long long)n;
-}
-
 // Fixed-point value of x: |x| <= 1 maps below 2^40 (the 20 + 20 bit split).
 __device__ __forceinline__ long long to_fixed(float x, float scale) { return __float2ll_rn(__fmul_rn(x, scale)); }
 
@@ -634,6 +629,11 @@ int64_t reduction_blocks(int64_t d) { return (d + kTB - 1) / kTB; }
 
 int update_centers(skm_ctx* c) {
   const int k = c->k;
+  if (c->layout == SKM_DENSE) {
+    const int rc = dense_center_sums(c);
+    if (rc) return rc;
+    return finish_update(c);
+  }
   // ---- sums: a full recompute, or only the changed rows (decided on the device)
   int wpb = (int)((96 * 1024) / ((int64_t)k * 8));  // two int32 bins per cluster per warp
   if (wpb > 8) wpb = 8;
@@ -660,6 +660,13 @@ int update_centers(skm_ctx* c) {
     default: rc = center_delta_t<__nv_bfloat16>(c); break;
   }
   if (rc) return rc;
+  return finish_update(c);
+}
+
+// Dirty list, norms, new centers, drift and (full variants) the center-center
+// bounds, shared by the sparse and dense paths.
+int finish_update(skm_ctx* c) {
+  const int k = c->k;
   SKM_PROF_BEGIN(c, "k_dirty");
   k_dirty<<<1, 1024, 0, c->st>>>(k, c->dflag, c->dmark, c->dpos, c->dlist, c->cnt, c->s64_valid, c->n);
   SKM_LAUNCHED(c);

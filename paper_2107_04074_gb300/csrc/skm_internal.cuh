@@ -27,7 +27,7 @@ enum Counter {
 };
 
 // Data-preparation error bits (C_ERR).
-enum ErrBits { E_COLIDX = 1, E_ORDER = 2, E_ZERO_ROW = 4, E_NONFINITE = 8, E_ROWPTR = 16 };
+enum ErrBits { E_COLIDX = 1, E_ORDER = 2, E_ZERO_ROW = 4, E_NONFINITE = 8, E_ROWPTR = 16, E_TIMEOUT = 32 };
 
 // Hamerly drift summary (Section 5.3): for the worst-moving center over all
 // j != a(i) we keep, for "a(i) is the argmin/argmax" and "it is not":
@@ -220,6 +220,12 @@ __device__ __forceinline__ void warp_push(bool take, int32_t item, int32_t* __re
   if (take) list[base + __popc(m & ((1u << lane) - 1u))] = item;
 }
 
+// Is this center update a full recomputation of the sums?  (Else only the
+// rows whose label changed are moved; decided on the device.)
+__device__ __forceinline__ bool full_update(int s64_valid, const unsigned long long* cnt, int64_t n) {
+  return !s64_valid || cnt[C_CHG] * 8ull > (unsigned long long)n;
+}
+
 // ---------------------------------------------------------------- context
 }  // namespace skm
 
@@ -279,6 +285,18 @@ struct skm_ctx {
   double* G;      // [k * k] Gram, upper triangle
   double* rpart;  // Gram partials of dirty rows
   int32_t gsplit, rsplit, grow_max;
+  // dense rows (layout SKM_DENSE)
+  int32_t precision;  // SKM_PREC_*
+  int32_t kpad;       // centers padded to the tensor-core tile (256)
+  float eps_b;        // bound on |BF16 similarity - exact similarity|
+  void* Xb;           // [n x d] BF16 unit rows
+  float* Cr;          // [k x d] FP32 centers, row-major
+  void* Cb;           // [kpad x d] BF16 centers
+  void* top2;         // [n] float4 (v1, j1, v2, v_current) from the BF16 GEMM
+  int32_t* lcount;    // [k] members per cluster
+  int32_t* loff;      // [k+1]
+  int32_t* lcursor;   // [k]
+  int32_t* lmembers;  // [n] rows sorted by label
   // labels and bounds
   int32_t* a;
   float* lb;  // [n]
@@ -321,10 +339,22 @@ int rows_to_centers(skm_ctx* c, const float* in /* k x d */);
 // assignment (k_assign.cu)
 int assign_full(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows);
 int hamerly_step(skm_ctx* c);
+int hamerly_bounds_only(skm_ctx* c);
 int elkan_step(skm_ctx* c);
 
 // update (k_update.cu)
 int update_centers(skm_ctx* c);
+int finish_update(skm_ctx* c);
+
+// dense rows (k_dense.cu, k_mma.cu)
+int dense_prep_bf16(skm_ctx* c);
+int dense_refresh_centers(skm_ctx* c);
+int dense_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt);
+int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned long long* list_cnt);
+int dense_tighten(skm_ctx* c);
+int dense_center_sums(skm_ctx* c);
+int bf16_mma_supported(int64_t d);
+int bf16_top2(skm_ctx* c, const void* Xb, const void* Cb, float4* top2);
 
 }  // namespace skm
 

@@ -20,6 +20,7 @@ STANDARD, HAMERLY, ELKAN, SIMP_HAMERLY, SIMP_ELKAN = 0, 1, 2, 3, 4
 VARIANTS = {"standard": STANDARD, "hamerly": HAMERLY, "elkan": ELKAN, "simp_hamerly": SIMP_HAMERLY,
             "simp_elkan": SIMP_ELKAN}
 F32, F16, BF16 = 0, 1, 2
+PREC_FP32, PREC_BF16 = 0, 1
 CSR, DENSE = 0, 1
 DEVICE, HOST = 0, 1
 
@@ -27,7 +28,7 @@ DEVICE, HOST = 0, 1
 EXPORTS = ["skm_default_options", "skm_init", "skm_reset", "skm_assign", "skm_update_centers", "skm_run",
            "skm_get_labels", "skm_get_centers", "skm_set_centers", "skm_set_labels", "skm_get_bounds",
            "skm_get_stats", "skm_bound_bytes", "skm_kernel_launches", "skm_profile", "skm_profile_read",
-           "skm_destroy", "skm_strerror", "skm_assign_noalloc"]
+           "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_top2"]
 
 
 class SkmError(RuntimeError):
@@ -44,7 +45,7 @@ class skm_data(ctypes.Structure):
 
 class skm_options(ctypes.Structure):
     _fields_ = [("hamerly_tight", ctypes.c_int32), ("validate", ctypes.c_int32), ("row_threshold", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 9)]
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
 
 
 class skm_stats(ctypes.Structure):
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
         "skm_destroy": (None, [P]),
         "skm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "skm_assign_noalloc": (ctypes.c_int, [P, i32, P, P, P, P]),
+        "skm_get_bf16_top2": (ctypes.c_int, [P, P, P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -179,15 +181,19 @@ class KMeans:
     """
 
     def __init__(self, n: int, d: int, row_ptr, col_idx, values, k: int, variant="standard", init_rows=None,
-                 seed: int = 0, hamerly_tight: bool = False, row_threshold: int = 0, stream=None):
+                 seed: int = 0, hamerly_tight: bool = False, row_threshold: int = 0, stream=None,
+                 precision: str = "fp32"):
         lib = load()
         host = isinstance(values, np.ndarray)
         self._keep = (row_ptr, col_idx, values)
-        data = skm_data(n=n, d=d, layout=CSR, dtype=_dtype_code(values.dtype), memspace=HOST if host else DEVICE,
-                        reserved=0, row_ptr=_ptr(row_ptr), col_idx=_ptr(col_idx), values=_ptr(values))
+        dense = row_ptr is None
+        data = skm_data(n=n, d=d, layout=DENSE if dense else CSR, dtype=_dtype_code(values.dtype),
+                        memspace=HOST if host else DEVICE, reserved=0, row_ptr=_ptr(row_ptr),
+                        col_idx=_ptr(col_idx), values=_ptr(values))
         opt = skm_options()
         lib.skm_default_options(ctypes.byref(opt))
         opt.hamerly_tight = 1 if hamerly_tight else 0
+        opt.precision = {"fp32": PREC_FP32, "bf16": PREC_BF16}[precision]
         opt.row_threshold = int(row_threshold)
         self.n, self.d, self.k = int(n), int(d), int(k)
         self.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -204,6 +210,12 @@ class KMeans:
         _check(lib.skm_init(ctypes.byref(h), ctypes.byref(data), int(k), self.variant, _ptr(rows), int(seed),
                             ctypes.byref(opt), ctypes.c_void_p(stream)), "skm_init")
         self._h = h
+
+    @classmethod
+    def dense(cls, X, k: int, **kw) -> "KMeans":
+        """Dense rows X (n x d FP32; torch CUDA tensor, borrowed, or numpy array, copied)."""
+        n, d = X.shape
+        return cls(n, d, None, None, X, k, **kw)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -286,6 +298,14 @@ class KMeans:
             out[buf.value.decode()] = (ms.value, cnt.value)
             idx += 1
         return out
+
+    def bf16_top2(self):
+        """(n x 4 array: best BF16 similarity, its center, second best, similarity to the previous
+        label) of the last assignment, and the error bound eps_b."""
+        out = np.empty((self.n, 4), dtype=np.float32)
+        eps = ctypes.c_float(0)
+        _check(load().skm_get_bf16_top2(self._h, _ptr(out), ctypes.byref(eps), HOST), "skm_get_bf16_top2")
+        return out, eps.value
 
     def stats(self) -> Stats:
         s = skm_stats()
