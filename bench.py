@@ -367,6 +367,78 @@ def trace_run(km, init, n, k):
     return {"trace": rows, "n": n, "k": k}
 
 
+def run_embed(args, rank, world, local):
+    """Precision form on dense embeddings: n = 1e6 unit rows in d = 384 from a
+    mixture of 1000 vMF(kappa = 40) components, k = 1000; FP32 GEMM vs the
+    BF16 tensor-core bulk with FP32 recheck, standard and Hamerly."""
+    import torch
+    from paper_2107_04074_gb300 import skm
+
+    torch.cuda.set_device(local)
+    n, d, k, iters = args.embed_n, 384, 1000, args.embed_iters
+    Xs = synth.vmf(n, d, 1000, 40.0, seed=3)
+    init = synth.init_rows(n, k, 3)
+    X = torch.from_numpy(Xs).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    res, labels = {}, {}
+    for variant, prec in (("standard", "fp32"), ("standard", "bf16"), ("hamerly", "fp32"), ("hamerly", "bf16")):
+        km = skm.KMeans.dense(X, k, variant=variant, init_rows=init, precision=prec, stream=stream.cuda_stream)
+        km.reset(init)
+        km.run(2)  # warm-up
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        km.reset(init)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, J = km.run(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        labels[(variant, prec)] = km.labels()
+        # per-iteration recheck counts and kernel times (separate, profiled run)
+        km.reset(init)
+        rech, cand, prof = [], [], {}
+        for _ in range(it):
+            km.profile(True)
+            ch = km.assign()
+            st = km.stats()
+            for nm, (t, c) in km.profile_read().items():
+                prof.setdefault(nm, [0.0, 0])
+                prof[nm][0] += t
+                prof[nm][1] += c
+            km.profile(False)
+            rech.append(st.last_rechecks)
+            cand.append(st.last_cand_rechecks)
+            if ch == 0:
+                break
+            km.update_centers()
+        km.close()
+        entry = {"iters": it, "ms": round(ms, 3), "iters_per_s": round(it / (ms / 1e3), 3), "objective": J,
+                 "rows_whole_row_recheck_per_iter": rech,
+                 "rows_candidate_recheck_per_iter": cand,
+                 "kernels_ms": {nm: round(v[0], 3) for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+        if "k_bf16_topk" in prof:
+            t_ms, c = prof["k_bf16_topk"]
+            flops = 2.0 * n * ((k + 255) // 256 * 256) * d
+            entry["bf16_gemm_us_per_launch"] = round(t_ms / c * 1e3, 1)
+            entry["bf16_gemm_tflops"] = round(flops / (t_ms / c / 1e3) / 1e12, 1)
+        res[f"{variant}/{prec}"] = entry
+    ref = labels[("standard", "fp32")]
+    same = all(np.array_equal(v, ref) for v in labels.values())
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        peak = 1900.0
+    g = res["standard/bf16"]
+    return {"workload": f"vmf-embeddings n={n} d={d} k={k} kappa=40 ({iters} iterations max)",
+            "labels_identical_across_paths": same, "paths": res,
+            "speedup_bf16_vs_fp32_standard": round(g["iters_per_s"] / res["standard/fp32"]["iters_per_s"], 2),
+            "bf16_gemm_roofline": {"bound": "tensor", "achieved": g.get("bf16_gemm_tflops"), "peak": peak,
+                                   "unit": "TFLOP/s",
+                                   "frac": round(g.get("bf16_gemm_tflops", 0) / peak, 4)}}
+
+
 def cpu_baseline(csr, init, variant, iters=3):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
     first `iters` iterations of the same run on the full data."""
@@ -422,6 +494,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed runs of the chosen variant (for profiler captures)")
+    ap.add_argument("--workload", default="rcv1", choices=["rcv1", "embed"],
+                    help="rcv1: the bench line; embed: the dense precision-form measurement")
+    ap.add_argument("--embed-n", type=int, default=1_000_000)
+    ap.add_argument("--embed-iters", type=int, default=20)
     ap.add_argument("--trace", action="store_true",
                     help="print a per-iteration table (labels changed, similarities, survivors, kernel ms) and exit")
     args = ap.parse_args()
@@ -429,6 +505,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if args.workload == "embed":
+        if rank == 0:
+            print(json.dumps(run_embed(args, rank, world, local)), flush=True)
         return
     if world > 1:
         import torch

@@ -114,6 +114,8 @@ typedef struct {
                              (Hamerly: still failing after l was tightened;
                              Elkan: too many candidate centers) */
   double objective;       /* J = sum_j |S_j| after the last center update */
+  int64_t last_cand_rechecks; /* precision form: ambiguous rows rechecked in
+                                 FP32 against their BF16 candidates only */
 } skm_stats;
 
 typedef struct skm_ctx skm_ctx;
@@ -174,11 +176,13 @@ int skm_get_bounds(skm_ctx* ctx, float* l, float* u, int32_t out_space);
 int skm_get_stats(skm_ctx* ctx, skm_stats* out);
 
 /* Diagnostic for the precision form (dense rows, precision BF16): the BF16
- * tensor-core result of the last assignment for every row as 4 floats
- * (best similarity, its center index stored as a float, second best, the
- * similarity to the label the row had) and the error bound eps_b every
- * BF16 similarity satisfies against the exact one.  SKM_ESTATE otherwise. */
-int skm_get_bf16_top2(skm_ctx* ctx, float* out4n, float* eps_b, int32_t out_space);
+ * tensor-core result of the last assignment, per row the 8 largest BF16
+ * similarities in descending order (vals, float[n*8]) and their centers
+ * (idx, int32[n*8]; equal values: lower center first; -1 / -inf past k),
+ * and the error bound eps_b every BF16 similarity satisfies against the
+ * exact one.  Rows the last Hamerly assignment pruned keep older values.
+ * Any pointer may be NULL.  SKM_ESTATE otherwise. */
+int skm_get_bf16_topk(skm_ctx* ctx, float* vals, int32_t* idx, float* eps_b, int32_t out_space);
 
 /* Bytes of bound state a variant keeps for n points and k centers (labels
  * excluded): standard 0; Hamerly 8n (two FP32 bounds); Elkan 4n + 4nk. */

@@ -131,8 +131,8 @@ void release(skm_ctx* c) {
                   c->Ct,     c->S64,    c->nrm,    c->red,   c->obj,   c->pdn,   c->pup,   c->qup,
                   c->hsel,   c->cc,     c->sc,     c->gpart, c->a,     c->lb,    c->ub,    c->w1,
                   c->w2,     c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark, c->dpos, c->dlist,
-                  c->G,      c->rpart,  c->Xb,     c->Cr,    c->Cb,    c->top2,  c->lcount, c->loff,
-                  c->lcursor, c->lmembers};
+                  c->G,      c->rpart,  c->Xb,     c->Cr,    c->Cb,    c->topv,  c->topi,  c->w3,
+                  c->lcount, c->loff, c->lcursor, c->lmembers};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -149,6 +149,7 @@ int read_counters(skm_ctx* c) {
   c->stats.last_sims = (int64_t)c->hcnt[C_SIMS];
   c->stats.last_survivors = (int64_t)c->hcnt[C_W1];
   c->stats.last_rechecks = (int64_t)c->hcnt[C_W2];
+  c->stats.last_cand_rechecks = (int64_t)c->hcnt[C_W3];
   return SKM_OK;
 }
 
@@ -265,13 +266,13 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
     TRY(dalloc(c, &c->lmembers, (size_t)n));
     if (c->precision == SKM_PREC_BF16) {
       __nv_bfloat16 *xb = nullptr, *cb = nullptr;
-      float4* t2 = nullptr;
       TRY(dalloc(c, &xb, (size_t)(n * d)));
       c->Xb = xb;
       TRY(dalloc(c, &cb, (size_t)(c->kpad * d)));
       c->Cb = cb;
-      TRY(dalloc(c, &t2, (size_t)n));
-      c->top2 = t2;
+      TRY(dalloc(c, &c->topv, (size_t)(n * kTopK)));
+      TRY(dalloc(c, &c->topi, (size_t)(n * kTopK)));
+      TRY(dalloc(c, &c->w3, (size_t)n));
       TRY(dense_prep_bf16(c));
       // |BF16 similarity - exact| <= (2u_b + u_b^2)(1 + 1e-6) sum|x c| + accumulation over d terms
       // with truncation (2^-23 per step): 2^-8 + 2^-15 + (d + 16) 2^-23 (sum|x c| <= 1)
@@ -370,16 +371,24 @@ int assign_dense(skm_ctx* c) {
   const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
   const bool first = !c->have_bounds;
   if (c->precision == SKM_PREC_BF16) {
+    // the precision form keeps Hamerly's l (and u) for every variant: l seeds
+    // the candidate threshold of the tensor-core pass
     const int32_t* list = nullptr;
     const unsigned long long* lcnt = nullptr;
-    if (ham && !first) {
-      TRY(hamerly_bounds_only(c));  // survivors of the bound test -> w1
-      list = c->w1;
-      lcnt = c->cnt + C_W1;
+    if (!first) {
+      if (ham) {
+        TRY(hamerly_bounds_only(c));  // survivors of the bound test -> w1
+        list = c->w1;
+        lcnt = c->cnt + C_W1;
+      } else if (c->moved) {
+        TRY(dense_lower(c));
+      }
     }
-    TRY(bf16_top2(c, c->Xb, c->Cb, (float4*)c->top2));
-    TRY(dense_classify(c, ham, list, lcnt));  // ambiguous rows -> w2
-    TRY(dense_rows(c, ham ? 1 : 0, c->w2, c->cnt + C_W2));
+    TRY(bf16_topk(c, c->Xb, c->Cb, first ? 0 : 1, c->topv, c->topi));
+    TRY(dense_classify(c, true, list, lcnt));  // ambiguous rows -> w3
+    TRY(dense_recheck_cands(c, true));         // unresolved rows -> w2
+    TRY(dense_rows(c, 1, c->w2, c->cnt + C_W2));
+    c->have_bounds = 1;
   } else if (!ham || first) {
     TRY(dense_rows(c, ham ? 1 : 0, nullptr, nullptr));
   } else {
@@ -533,15 +542,14 @@ int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
   return SKM_OK;
 }
 
-int skm_get_bf16_top2(skm_ctx* c, float* out, float* eps_b, int32_t space) {
+int skm_get_bf16_topk(skm_ctx* c, float* vals, int32_t* idx, float* eps_b, int32_t space) {
   if (!c) return SKM_EINVAL;
   if (c->layout != SKM_DENSE || c->precision != SKM_PREC_BF16) return SKM_ESTATE;
   if (eps_b) *eps_b = c->eps_b;
-  if (out) {
-    SKM_CUDA_TRY(cudaMemcpyAsync(out, c->top2, sizeof(float) * 4 * c->n,
-                                 space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
-    SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
-  }
+  const cudaMemcpyKind kind = space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (vals) SKM_CUDA_TRY(cudaMemcpyAsync(vals, c->topv, sizeof(float) * kTopK * c->n, kind, c->st));
+  if (idx) SKM_CUDA_TRY(cudaMemcpyAsync(idx, c->topi, sizeof(int32_t) * kTopK * c->n, kind, c->st));
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
   return SKM_OK;
 }
 

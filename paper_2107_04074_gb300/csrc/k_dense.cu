@@ -6,12 +6,14 @@
 // tiled SIMT GEMM) accumulates every output exactly in that order, and so do
 // k_dense_tighten and the FP32 recheck, so all paths agree bit for bit.
 //
-//   k_dense_bf16        unit rows rounded to BF16 (A operand of k_bf16_top2)
+//   k_dense_bf16        unit rows rounded to BF16 (A operand of k_bf16_topk)
 //   k_dense_centers     term-major FP32 centers -> row-major FP32 and BF16
 //   k_dense_top2        FP32 GEMM + fused top-2 (plain FP32 path, whole rows
 //                       for Hamerly, recheck of ambiguous rows)
-//   k_dense_classify    precision form: a BF16 top-2 decides the label when its
+//   k_dense_classify    precision form: the BF16 top-2 decides the label when its
 //                       margin exceeds the error bound, else the row is rechecked
+//   k_dense_cands       precision form: FP32 recheck of an ambiguous row against
+//                       the BF16 candidates that can still win
 //   k_dense_tighten     Hamerly: exact <x, c_a> (warp per survivor)
 //   k_label_*, k_dense_cluster_sum, k_dense_delta
 //                       exact fixed-point cluster sums: full (rows sorted by
@@ -63,14 +65,16 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
                                                     const float* __restrict__ dlt, const float* __restrict__ Cr,
                                                     int64_t n, int64_t d, int32_t k, const int32_t* __restrict__ list,
                                                     const unsigned long long* __restrict__ list_cnt,
-                                                    int32_t* __restrict__ a, float* __restrict__ lb,
-                                                    float* __restrict__ ub, int32_t* __restrict__ chg_i,
-                                                    int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
+                                                    int64_t few_limit, int32_t* __restrict__ a,
+                                                    float* __restrict__ lb, float* __restrict__ ub,
+                                                    int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
+                                                    unsigned long long* __restrict__ cnt) {
   __shared__ __align__(16) float As[kKC][kTR + 4];
   __shared__ __align__(16) float Bs[kKC][kTC + 4];
   __shared__ int rows_sh[kTR];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
   const int64_t total = list ? (int64_t)(*list_cnt) : n;
+  if (list && total <= few_limit) return;  // k_dense_rows_few takes short lists
   const int64_t ntiles = (total + kTR - 1) / kTR;
   unsigned long long changed = 0, sims = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -214,18 +218,175 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
   }
 }
 
-// Precision form.  For each row (all, or the Hamerly survivors w1) the BF16
-// top-2 (v1, j1, v2) is within eps_b of the exact similarities; if
-// v1 - v2 > 2 (eps_b + delta_i) the FP32 standard variant necessarily picks j1
-// (its similarities are within delta_i of exact), so j1 is the label;
-// Hamerly's bounds become l = v1 - eps_b, u = v2 + eps_b (exact-similarity
-// bounds).  Otherwise the row goes to `recheck` for the FP32 path.
+// Whole-row FP32 recheck of a short list (at most `limit` rows; the tile
+// kernel above takes longer lists): a block of 1024 threads per kFR rows,
+// thread per center (tiles of 1024), reading the term-major centers Ct
+// coalesced while the rows' terms come broadcast from shared memory; each
+// (row, center) dot is the same sequential chain over t.  Top-2 merged across
+// the block with the tie rule.
+constexpr int kFR = 4, kXC = 1024, kFT = 1024;
+
+template <int MODE>
+__global__ void __launch_bounds__(kFT) k_dense_rows_few(const float* __restrict__ X, const float* __restrict__ rinv,
+                                                        const float* __restrict__ dlt, const float* __restrict__ Ct,
+                                                        int64_t d, int64_t kst, int32_t k,
+                                                        const int32_t* __restrict__ list,
+                                                        const unsigned long long* __restrict__ list_cnt, int64_t limit,
+                                                        int32_t* __restrict__ a, float* __restrict__ lb,
+                                                        float* __restrict__ ub, int32_t* __restrict__ chg_i,
+                                                        int32_t* __restrict__ chg_old,
+                                                        unsigned long long* __restrict__ cnt) {
+  const int64_t total = (int64_t)(*list_cnt);
+  if (total > limit) return;
+  constexpr int NW = kFT / 32;
+  __shared__ float xs[kFR][kXC];
+  __shared__ float sv1[NW][kFR], sv2[NW][kFR], svc[NW][kFR];
+  __shared__ int sj1[NW][kFR];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t g0 = (int64_t)blockIdx.x * kFR; g0 < total; g0 += (int64_t)gridDim.x * kFR) {
+    int32_t row[kFR], cur[kFR];
+    float v1[kFR], v2[kFR], vc[kFR];
+    int j1[kFR];
+#pragma unroll
+    for (int r = 0; r < kFR; ++r) {
+      row[r] = (g0 + r < total) ? list[g0 + r] : -1;
+      cur[r] = row[r] >= 0 ? a[row[r]] : -1;
+      v1[r] = v2[r] = vc[r] = -INFINITY;
+      j1[r] = INT_MAX;
+    }
+    for (int j0 = 0; j0 < k; j0 += kFT) {
+      const int j = j0 + tid;
+      float acc[kFR];
+#pragma unroll
+      for (int r = 0; r < kFR; ++r) acc[r] = 0.f;
+      for (int64_t t0 = 0; t0 < d; t0 += kXC) {
+        const int nt = (int)((d - t0) < kXC ? (d - t0) : kXC);
+        __syncthreads();
+        for (int q = tid; q < kFR * kXC; q += kFT) {
+          const int r = q / kXC, tt = q % kXC;
+          xs[r][tt] = (row[r] >= 0 && tt < nt) ? X[(int64_t)row[r] * d + t0 + tt] : 0.f;
+        }
+        __syncthreads();
+        if (j < k) {
+          const float* cp = Ct + t0 * kst + j;
+#pragma unroll 8
+          for (int tt = 0; tt < nt; ++tt) {
+            const float cv = __ldg(cp + (int64_t)tt * kst);
+#pragma unroll
+            for (int r = 0; r < kFR; ++r) acc[r] = __fmaf_rn(xs[r][tt], cv, acc[r]);
+          }
+        }
+      }
+      if (j < k) {
+#pragma unroll
+        for (int r = 0; r < kFR; ++r) {
+          if (row[r] < 0) continue;
+          const float s = __fmul_rn(acc[r], rinv[row[r]]);
+          if (j == cur[r]) vc[r] = s;
+          if (s > v1[r]) {  // j ascends within a thread: ties keep the lowest index
+            v2[r] = v1[r];
+            v1[r] = s;
+            j1[r] = j;
+          } else if (s > v2[r]) {
+            v2[r] = s;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kFR; ++r) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float ov1 = __shfl_xor_sync(SKM_FULL_MASK, v1[r], o);
+        const int oj1 = __shfl_xor_sync(SKM_FULL_MASK, j1[r], o);
+        const float ov2 = __shfl_xor_sync(SKM_FULL_MASK, v2[r], o);
+        if (ov1 > v1[r] || (ov1 == v1[r] && oj1 < j1[r])) {
+          v2[r] = fmaxf(ov2, v1[r]);
+          v1[r] = ov1;
+          j1[r] = oj1;
+        } else {
+          v2[r] = fmaxf(v2[r], ov1);
+        }
+        vc[r] = fmaxf(vc[r], __shfl_xor_sync(SKM_FULL_MASK, vc[r], o));
+      }
+      if (lane == 0) {
+        sv1[warp][r] = v1[r];
+        sv2[warp][r] = v2[r];
+        svc[warp][r] = vc[r];
+        sj1[warp][r] = j1[r];
+      }
+    }
+    __syncthreads();
+    if (tid < kFR && row[tid] >= 0) {
+      const int r = tid;
+      float b1 = sv1[0][r], b2 = sv2[0][r], bc = svc[0][r];
+      int bj = sj1[0][r];
+      for (int w = 1; w < NW; ++w) {
+        const float ov1 = sv1[w][r];
+        const int oj1 = sj1[w][r];
+        if (ov1 > b1 || (ov1 == b1 && oj1 < bj)) {
+          b2 = fmaxf(sv2[w][r], b1);
+          b1 = ov1;
+          bj = oj1;
+        } else {
+          b2 = fmaxf(b2, ov1);
+        }
+        bc = fmaxf(bc, svc[w][r]);
+      }
+      const int32_t i = row[r], ci = cur[r];
+      int32_t nb;
+      float ssec;
+      if (ci >= 0 && bc == b1) {
+        nb = ci;
+        ssec = (bj == ci) ? b2 : b1;
+      } else {
+        nb = bj;
+        ssec = b2;
+      }
+      a[i] = nb;
+      atomicAdd(cnt + C_SIMS, (unsigned long long)k);
+      if (MODE == 1) {
+        const float dl = dlt[i];
+        lb[i] = __fsub_rd(b1, dl);
+        ub[i] = (k > 1) ? __fadd_ru(ssec, dl) : -1.f;
+      }
+      if (nb != ci) {
+        atomicAdd(cnt + C_CHANGED, 1ull);
+        const unsigned long long pos = atomicAdd(cnt + C_CHG, 1ull);
+        chg_i[pos] = i;
+        chg_old[pos] = ci;
+      }
+    }
+  }
+}
+
+// Precision form, standard variant: after the centers moved, l(i) <- the
+// lower bound of Eq. (eqn:l-bound) with the drift of c(a(i)), so that l stays
+// a lower bound on the best similarity (the tensor-core pass starts each
+// row's candidate list above l - eps_b - 2 (eps_b + delta_i)).
+__global__ void k_dense_lower(int64_t n, const int32_t* __restrict__ a, float* __restrict__ lb,
+                              const float* __restrict__ pdn, const float* __restrict__ pup,
+                              const float* __restrict__ qup) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t ai = a[i];
+    lb[i] = bound_l(lb[i], pdn[ai], pup[ai], qup[ai]);
+  }
+}
+
+// Precision form, first pass.  For each row (all, or the Hamerly survivors
+// w1) the BF16 top-8 is within eps_b of the exact similarities (v1 the best
+// at j1, v2 the next); the canonical FP32 similarities are within delta_i of
+// exact.  If v1 - v2 > 2 (eps_b + delta_i) the FP32 standard variant
+// necessarily picks j1, so j1 is the label, and Hamerly's bounds become
+// l = v1 - eps_b, u = v2 + eps_b (exact-similarity bounds).  Otherwise the row
+// goes to `amb` for k_dense_cands.
 template <bool HAMERLY>
-__global__ void __launch_bounds__(256) k_dense_classify(const float4* __restrict__ top2, const float* __restrict__ dlt,
-                                                        float eps_b, int64_t n, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(256) k_dense_classify(const float* __restrict__ topv, const int32_t* __restrict__ topi,
+                                                        const float* __restrict__ dlt, float eps_b, int64_t n,
+                                                        const int32_t* __restrict__ list,
                                                         const unsigned long long* __restrict__ list_cnt,
                                                         int32_t* __restrict__ a, float* __restrict__ lb,
-                                                        float* __restrict__ ub, int32_t* __restrict__ recheck,
+                                                        float* __restrict__ ub, int32_t* __restrict__ amb_out,
                                                         int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
                                                         unsigned long long* __restrict__ cnt) {
   const int64_t total = list ? (int64_t)(*list_cnt) : n;
@@ -237,24 +398,24 @@ __global__ void __launch_bounds__(256) k_dense_classify(const float4* __restrict
     int32_t row = 0, cur = -1;
     if (q < total) {
       row = list ? list[q] : (int32_t)q;
-      const float4 t = top2[row];
-      const float v1 = t.x, v2 = t.z;
-      const int j1 = __float_as_int(t.y);
+      const float2 t = *reinterpret_cast<const float2*>(topv + (int64_t)row * kTopK);
+      const float v1 = t.x, v2 = t.y;
+      const int j1 = topi[(int64_t)row * kTopK];
       const float margin = __fadd_ru(eps_b, dlt[row]);
       cur = a[row];
-      if (__fsub_rd(v1, v2) > __fmul_ru(2.f, margin)) {
+      if (j1 >= 0 && __fsub_rd(v1, v2) > __fmul_ru(2.f, margin)) {
         moved = (j1 != cur);
         a[row] = j1;
         changed += moved;
         if (HAMERLY) {
           lb[row] = __fsub_rd(v1, eps_b);
-          ub[row] = __fadd_ru(v2, eps_b);
+          ub[row] = fmaxf(__fadd_ru(v2, eps_b), -1.f);
         }
       } else {
         amb = true;
       }
     }
-    warp_push(amb, row, recheck, cnt + C_W2);
+    warp_push(amb, row, amb_out, cnt + C_W3);
     const unsigned m = __ballot_sync(SKM_FULL_MASK, moved);
     if (m) {
       const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
@@ -271,6 +432,133 @@ __global__ void __launch_bounds__(256) k_dense_classify(const float4* __restrict
 #pragma unroll
   for (int o = 16; o; o >>= 1) changed += __shfl_xor_sync(SKM_FULL_MASK, changed, o);
   if ((threadIdx.x & 31) == 0 && changed) atomicAdd(cnt + C_CHANGED, changed);
+}
+
+// Canonical FP32 dot of a stored row with a center row: one FMA chain over
+// t = 0..d-1 in order (float4 loads when both rows are 16-byte aligned).
+template <bool V4>
+__device__ __forceinline__ float dense_dot_seq(const float* __restrict__ x, const float* __restrict__ c, int64_t d) {
+  float acc = 0.f;
+  if (V4) {
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* c4 = reinterpret_cast<const float4*>(c);
+#pragma unroll 4
+    for (int64_t t = 0; t < (d >> 2); ++t) {
+      const float4 xv = x4[t], cv = c4[t];
+      acc = __fmaf_rn(xv.x, cv.x, acc);
+      acc = __fmaf_rn(xv.y, cv.y, acc);
+      acc = __fmaf_rn(xv.z, cv.z, acc);
+      acc = __fmaf_rn(xv.w, cv.w, acc);
+    }
+  } else {
+#pragma unroll 4
+    for (int64_t t = 0; t < d; ++t) acc = __fmaf_rn(x[t], c[t], acc);
+  }
+  return acc;
+}
+
+// Precision form, second pass, over the ambiguous rows: an 8-lane group per
+// row, lane q holding the q-th BF16 candidate.  With w = eps_b + delta_i, a
+// center whose BF16 similarity is below v1 - 2w has an FP32 similarity below
+// that of j1, so only the leading candidates with v >= v1 - 2w can win; each
+// gets its canonical FP32 similarity and the winner follows the tie rule (the
+// current label, else the lowest index).  Centers outside the top-8 have BF16
+// similarity <= v8; when all eight are candidates the winner must beat
+// v8 + w, else the row goes to `out` for a whole-row recheck.  Hamerly:
+// l = f_a - delta_i, u = max(other candidates' f + delta_i, next BF16 value
+// + eps_b).
+template <bool HAMERLY, bool V4>
+__global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X, const float* __restrict__ rinv,
+                                                     const float* __restrict__ dlt, const float* __restrict__ Cr,
+                                                     int64_t d, int32_t k, float eps_b,
+                                                     const float* __restrict__ topv, const int32_t* __restrict__ topi,
+                                                     const int32_t* __restrict__ list,
+                                                     const unsigned long long* __restrict__ list_cnt,
+                                                     int32_t* __restrict__ a, float* __restrict__ lb,
+                                                     float* __restrict__ ub, int32_t* __restrict__ out,
+                                                     int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
+                                                     unsigned long long* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31, g = lane >> 3, q = lane & 7;
+  const int64_t total = (int64_t)(*list_cnt);
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  unsigned long long changed = 0, sims = 0;
+  // the loop bound is the same for the whole warp (shuffles inside)
+  for (int64_t gb = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; gb < total; gb += ngroups) {
+    const int64_t slot = gb + g;
+    const bool act = slot < total;
+    const int32_t row = act ? list[slot] : 0;
+    float v = -INFINITY;
+    int32_t j = -1;
+    if (act) {
+      v = topv[(int64_t)row * kTopK + q];
+      j = topi[(int64_t)row * kTopK + q];
+    }
+    const float v1 = __shfl_sync(SKM_FULL_MASK, v, g * 8);
+    const float v8 = __shfl_sync(SKM_FULL_MASK, v, g * 8 + 7);
+    const float dl = act ? dlt[row] : 0.f;
+    const float w = __fadd_ru(eps_b, dl);
+    const float theta = __fsub_rd(v1, __fmul_ru(2.f, w));
+    const bool cand = act && j >= 0 && v >= theta;
+    float f = -INFINITY;
+    if (cand) f = __fmul_rn(dense_dot_seq<V4>(X + (int64_t)row * d, Cr + (int64_t)j * d, d), rinv[row]);
+    const unsigned cm = (__ballot_sync(SKM_FULL_MASK, cand) >> (g * 8)) & 0xFFu;
+    const int ncand = __popc(cm);  // the candidates are a prefix of the descending list
+    const int32_t cur = act ? a[row] : -1;
+    // best candidate under the tie rule
+    float bf = cand ? f : -INFINITY;
+    int32_t bj = cand ? j : INT_MAX;
+#pragma unroll
+    for (int o = 4; o; o >>= 1) {
+      const float of = __shfl_xor_sync(SKM_FULL_MASK, bf, o);
+      const int32_t oj = __shfl_xor_sync(SKM_FULL_MASK, bj, o);
+      const bool take = (of > bf) || (of == bf && oj != bj && (oj == cur || (bj != cur && oj < bj)));
+      if (take) {
+        bf = of;
+        bj = oj;
+      }
+    }
+    // largest BF16 value among the non-candidates (or a bound on it)
+    const float vn_pref = __shfl_sync(SKM_FULL_MASK, v, g * 8 + (ncand < 8 ? ncand : 7));
+    const bool all8 = (ncand == kTopK) && (k > kTopK);
+    const float vnext = (ncand < kTopK) ? vn_pref : (all8 ? v8 : -INFINITY);
+    const bool resolved = ncand > 0 && ((ncand < kTopK) || !all8 || (bf > __fadd_ru(v8, w)));
+    float f2 = -INFINITY;
+    if (HAMERLY) {
+      f2 = (cand && j != bj) ? f : -INFINITY;
+#pragma unroll
+      for (int o = 4; o; o >>= 1) f2 = fmaxf(f2, __shfl_xor_sync(SKM_FULL_MASK, f2, o));
+    }
+    if (act && q == 0) {
+      sims += (unsigned long long)ncand;
+      if (resolved) {
+        a[row] = bj;
+        if (bj != cur) {
+          ++changed;
+          const unsigned long long pos = atomicAdd(cnt + C_CHG, 1ull);
+          chg_i[pos] = row;
+          chg_old[pos] = cur;
+        }
+        if (HAMERLY) {
+          lb[row] = __fsub_rd(bf, dl);
+          const float u1 = (f2 == -INFINITY) ? -1.f : __fadd_ru(f2, dl);
+          const float u2 = (vnext == -INFINITY) ? -1.f : __fadd_ru(vnext, eps_b);
+          ub[row] = fmaxf(fmaxf(u1, u2), -1.f);
+        }
+      } else {
+        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
+        out[pos] = row;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    changed += __shfl_xor_sync(SKM_FULL_MASK, changed, o);
+    sims += __shfl_xor_sync(SKM_FULL_MASK, sims, o);
+  }
+  if (lane == 0) {
+    if (changed) atomicAdd(cnt + C_CHANGED, changed);
+    if (sims) atomicAdd(cnt + C_SIMS, sims);
+  }
 }
 
 // Hamerly on dense rows: warp per survivor, exact <x, c_a> (32 terms loaded at
@@ -452,13 +740,35 @@ int dense_refresh_centers(skm_ctx* c) {
 int dense_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt) {
   const int64_t ntiles = (c->n + kTR - 1) / kTR;
   const unsigned g = (unsigned)(list ? c->nsm * 2 : (ntiles < (int64_t)c->nsm * 4 ? ntiles : (int64_t)c->nsm * 4));
+  // a list of at most few_limit rows goes to k_dense_rows_few, a longer one
+  // to the tile kernel (each returns at once when the other one applies)
+  const int64_t few_limit = (int64_t)c->nsm * 32;
+  const float* X = (const float*)c->val;
   SKM_PROF_BEGIN(c, list ? "k_dense_top2(list)" : "k_dense_top2");
   if (mode == 0)
-    k_dense_top2<0><<<g, 256, 0, c->st>>>((const float*)c->val, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list,
-                                          list_cnt, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+    k_dense_top2<0><<<g, 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list, list_cnt, few_limit,
+                                          c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
   else
-    k_dense_top2<1><<<g, 256, 0, c->st>>>((const float*)c->val, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list,
-                                          list_cnt, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+    k_dense_top2<1><<<g, 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list, list_cnt, few_limit,
+                                          c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+  SKM_LAUNCHED(c);
+  if (list) {
+    SKM_PROF_BEGIN(c, "k_dense_rows_few");
+    const unsigned gf = c->nsm * 2;
+    if (mode == 0)
+      k_dense_rows_few<0><<<gf, kFT, 0, c->st>>>(X, c->rinv, c->dlt, c->Ct, c->d, c->kst, c->k, list, list_cnt,
+                                                 few_limit, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+    else
+      k_dense_rows_few<1><<<gf, kFT, 0, c->st>>>(X, c->rinv, c->dlt, c->Ct, c->d, c->kst, c->k, list, list_cnt,
+                                                 few_limit, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+    SKM_LAUNCHED(c);
+  }
+  return SKM_OK;
+}
+
+int dense_lower(skm_ctx* c) {
+  SKM_PROF_BEGIN(c, "k_dense_lower");
+  k_dense_lower<<<grid_cap(c->n, 256, c->nsm), 256, 0, c->st>>>(c->n, c->a, c->lb, c->pdn, c->pup, c->qup);
   SKM_LAUNCHED(c);
   return SKM_OK;
 }
@@ -467,11 +777,32 @@ int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned
   SKM_PROF_BEGIN(c, "k_dense_classify");
   const unsigned g = c->nsm * 8;
   if (hamerly)
-    k_dense_classify<true><<<g, 256, 0, c->st>>>((const float4*)c->top2, c->dlt, c->eps_b, c->n, list, list_cnt, c->a,
-                                                 c->lb, c->ub, c->w2, c->chg_i, c->chg_old, c->cnt);
+    k_dense_classify<true><<<g, 256, 0, c->st>>>(c->topv, c->topi, c->dlt, c->eps_b, c->n, list, list_cnt, c->a,
+                                                 c->lb, c->ub, c->w3, c->chg_i, c->chg_old, c->cnt);
   else
-    k_dense_classify<false><<<g, 256, 0, c->st>>>((const float4*)c->top2, c->dlt, c->eps_b, c->n, list, list_cnt,
-                                                  c->a, c->lb, c->ub, c->w2, c->chg_i, c->chg_old, c->cnt);
+    k_dense_classify<false><<<g, 256, 0, c->st>>>(c->topv, c->topi, c->dlt, c->eps_b, c->n, list, list_cnt, c->a,
+                                                  c->lb, c->ub, c->w3, c->chg_i, c->chg_old, c->cnt);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+int dense_recheck_cands(skm_ctx* c, bool hamerly) {
+  SKM_PROF_BEGIN(c, "k_dense_cands");
+  const unsigned g = c->nsm * 8;
+  const bool v4 = (c->d % 4 == 0) && ((uintptr_t)c->val % 16 == 0);
+  const float* X = (const float*)c->val;
+#define SKM_CANDS(H, V)                                                                                            \
+  k_dense_cands<H, V><<<g, 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->d, c->k, c->eps_b, c->topv, c->topi,     \
+                                            c->w3, c->cnt + C_W3, c->a, c->lb, c->ub, c->w2, c->chg_i, c->chg_old, \
+                                            c->cnt)
+  if (hamerly) {
+    if (v4) SKM_CANDS(true, true);
+    else SKM_CANDS(true, false);
+  } else {
+    if (v4) SKM_CANDS(false, true);
+    else SKM_CANDS(false, false);
+  }
+#undef SKM_CANDS
   SKM_LAUNCHED(c);
   return SKM_OK;
 }

@@ -1,16 +1,26 @@
 // Dense similarity bulk on the 5th-generation tensor cores (precision form):
 // S^b = X_b * C_b^T with BF16 operands and FP32 accumulation in tensor memory,
-// fused with a per-row top-2 (and the similarity to the current label).
+// fused with the selection of each row's recheck candidates.
 //
 // One CTA per SM, persistent over tiles of 128 rows.  Warp roles:
-//   warp 0  TMA producer: the row tile A (128 x d, all K blocks, resident in
-//           shared memory) and 256 x 64 tiles of the centers B through a
-//           3-stage ring, 128-byte swizzled;
+//   warp 0  TMA producer: per (center tile, K block) one stage of a 4-stage
+//           ring holding the row tile's 128 x 64 slice of A and the 256 x 64
+//           slice of the centers B, 128-byte swizzled (A comes from L2 after
+//           the first center tile);
 //   warp 1  allocates 512 TMEM columns; one lane issues tcgen05.mma
 //           (M = 128, N = 256, K = 16 per instruction) into one of two
 //           256-column accumulators, and tcgen05.commit to the barriers;
-//   warps 2-5  epilogue: tcgen05.ld of their 32-lane TMEM quarter, top-2 per
-//           row while the other accumulator is being filled.
+//   warps 2-9  epilogue, two groups of four: group g drains accumulator g
+//           (tcgen05.ld of the warp's 32-lane TMEM quarter) while the other
+//           group drains the other one.
+// Selection.  A center can be a recheck candidate only if its BF16 similarity
+// is within 2w of the row's best v1 (w = eps_b + delta_i).  Each 64-column
+// chunk first raises the running best, then appends every value above
+// thr = max(tau, v1_run - W2) (W2 slightly above 2w; tau from a lower bound l
+// on the best similarity when one is known) to the row's buffer in shared
+// memory: a predicated store, no divergent code.  At the end of the row tile
+// group 0 merges both groups' buffers into the output list.  A buffer that
+// overflows marks the row for a whole-row recheck.
 // Every barrier wait gives up after one second (globaltimer): the kernel
 // then records an error word and leaves its loops; TMEM is freed on exit.
 #include <cuda.h>
@@ -27,11 +37,12 @@ namespace {
 constexpr int kBM = 128;          // rows per tile (UMMA M)
 constexpr int kBN = 256;          // centers per accumulator (UMMA N)
 constexpr int kBK = 64;           // K elements per 128-byte swizzled row
-constexpr int kStages = 3;        // B ring
-constexpr int kMaxKB = 7;         // K blocks of A kept resident (d <= 448)
-constexpr int kThreads = 192;
-constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KB per K block
+constexpr int kStages = 4;        // A + B ring
+constexpr int kCap = 16;          // appended values a row's buffer holds per group
+constexpr int kThreads = 320;     // 2 + 8 warps
+constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KB per stage
 constexpr uint32_t kBBytes = kBN * kBK * 2;  // 32 KB per stage
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint64_t kTimeoutNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -116,7 +127,8 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// Two 32-column loads in flight, one wait.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, uint32_t (&r)[64]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
       "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -125,43 +137,82 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr + 32));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 struct MmaShared {
-  uint64_t a_full, a_empty;
-  uint64_t b_full[kStages], b_empty[kStages];
+  uint64_t full[kStages], empty[kStages];
   uint64_t acc_full[2], acc_empty[2];
+  uint64_t mg_full[4], mg_empty[4];  // group 1 -> group 0 hand-over, per TMEM quarter
+  int32_t mcount[kBM];               // values group 1 appended per row
   uint32_t tmem_base;
   int abort_flag;
 };
 
-// Per row: v1 (best BF16 similarity), j1 (its center, lowest index on ties),
-// v2 (best over the other centers) and vc (similarity to the current label).
-__global__ void __launch_bounds__(kThreads, 1) k_bf16_top2(const __grid_constant__ CUtensorMap mapA,
+// Insert (s, j) into a list ordered by value (descending), then center
+// (ascending), if it ranks above the last entry; entries with center -1
+// rank below real ones of the same value.
+__device__ __forceinline__ bool ranks_above(float s, int32_t j, float v, int32_t i) {
+  return s > v || (s == v && (i < 0 || j < i));
+}
+__device__ __forceinline__ void topk_insert(float (&tv)[kTopK], int32_t (&ti)[kTopK], float s, int32_t j) {
+  if (!ranks_above(s, j, tv[kTopK - 1], ti[kTopK - 1])) return;
+#pragma unroll
+  for (int p = kTopK - 1; p > 0; --p) {
+    if (ranks_above(s, j, tv[p - 1], ti[p - 1])) {
+      tv[p] = tv[p - 1];
+      ti[p] = ti[p - 1];
+    } else if (ranks_above(s, j, tv[p], ti[p])) {
+      tv[p] = s;
+      ti[p] = j;
+    }
+  }
+  if (ranks_above(s, j, tv[0], ti[0])) {
+    tv[0] = s;
+    ti[0] = j;
+  }
+}
+
+// Per row: the (at most 8) largest BF16 similarities above B in descending
+// order with their centers, then entries with center -1 holding B, where B
+// bounds every center not listed.  A row whose buffer overflowed gets
+// center -1 and value +inf throughout.
+__global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, int64_t n,
-                                                          int32_t k, int nkb, int nnt, const int32_t* __restrict__ a,
-                                                          float4* __restrict__ top2, unsigned long long* __restrict__ cnt) {
+                                                          int32_t k, int nkb, int nnt, const float* __restrict__ lb,
+                                                          const float* __restrict__ dlt, float eps_b, int use_thr,
+                                                          float* __restrict__ topv, int32_t* __restrict__ topi,
+                                                          unsigned long long* __restrict__ cnt) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the swizzled tiles
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* As = base;                                // nkb x 16 KB
-  unsigned char* Bs = base + (size_t)kMaxKB * kABytes;     // kStages x 32 KB
-  MmaShared* sh = reinterpret_cast<MmaShared*>(Bs + (size_t)kStages * kBBytes);
+  unsigned char* St = base;                                         // kStages x (A 16 KB, B 32 KB)
+  uint2* buf = reinterpret_cast<uint2*>(base + (size_t)kStages * kStageBytes);  // [2][kCap][kBM]
+  MmaShared* sh = reinterpret_cast<MmaShared*>(buf + 2 * kCap * kBM);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (n + kBM - 1) / kBM;
   const uint32_t idesc = idesc_bf16(kBM, kBN);
 
   if (threadIdx.x == 0) {
-    mbar_init(&sh->a_full, 1);
-    mbar_init(&sh->a_empty, 1);
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&sh->b_full[s], 1);
-      mbar_init(&sh->b_empty[s], 1);
+      mbar_init(&sh->full[s], 1);
+      mbar_init(&sh->empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh->acc_full[b], 1);
       mbar_init(&sh->acc_empty[b], 128);
+    }
+    for (int q = 0; q < 4; ++q) {
+      mbar_init(&sh->mg_full[q], 32);
+      mbar_init(&sh->mg_empty[q], 32);
     }
     sh->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -183,96 +234,157 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_top2(const __grid_constant
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       uint32_t gidx = 0;
-      int lt = 0;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
-        if (lt > 0) ok = mbar_wait(&sh->a_empty, (lt - 1) & 1, abort_flag);
-        if (!ok) break;
-        mbar_expect_tx(&sh->a_full, kABytes * nkb);
-        for (int kb = 0; kb < nkb; ++kb)
-          tma_load_2d(&mapA, &sh->a_full, As + (size_t)kb * kABytes, kb * kBK, (int)(tile * kBM));
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
         for (int nt = 0; nt < nnt && ok; ++nt)
           for (int kb = 0; kb < nkb; ++kb, ++gidx) {
             const int s = gidx % kStages;
-            if (gidx >= (uint32_t)kStages) ok = mbar_wait(&sh->b_empty[s], ((gidx / kStages) - 1) & 1, abort_flag);
+            if (gidx >= (uint32_t)kStages) ok = mbar_wait(&sh->empty[s], ((gidx / kStages) - 1) & 1, abort_flag);
             if (!ok) break;
-            mbar_expect_tx(&sh->b_full[s], kBBytes);
-            tma_load_2d(&mapB, &sh->b_full[s], Bs + (size_t)s * kBBytes, kb * kBK, nt * kBN);
+            unsigned char* st = St + (size_t)s * kStageBytes;
+            mbar_expect_tx(&sh->full[s], kStageBytes);
+            tma_load_2d(&mapA, &sh->full[s], st, kb * kBK, (int)(tile * kBM));
+            tma_load_2d(&mapB, &sh->full[s], st + kABytes, kb * kBK, nt * kBN);
           }
-      }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t gidx = 0, accidx = 0;
-      int lt = 0;
-      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
-        ok = mbar_wait(&sh->a_full, lt & 1, abort_flag);
-        if (!ok) break;
+      for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         for (int nt = 0; nt < nnt && ok; ++nt, ++accidx) {
-          const uint32_t buf = accidx & 1, use = accidx >> 1;
-          if (use > 0) ok = mbar_wait(&sh->acc_empty[buf], (use - 1) & 1, abort_flag);
+          const uint32_t b = accidx & 1, use = accidx >> 1;
+          if (use > 0) ok = mbar_wait(&sh->acc_empty[b], (use - 1) & 1, abort_flag);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t d_tmem = tmem + buf * kBN;
+          const uint32_t d_tmem = tmem + b * kBN;
           for (int kb = 0; kb < nkb; ++kb, ++gidx) {
             const int s = gidx % kStages;
-            ok = mbar_wait(&sh->b_full[s], (gidx / kStages) & 1, abort_flag);
+            ok = mbar_wait(&sh->full[s], (gidx / kStages) & 1, abort_flag);
             if (!ok) break;
             tc_fence_after();
-            const uint32_t a_addr = smem_u32(As + (size_t)kb * kABytes);
-            const uint32_t b_addr = smem_u32(Bs + (size_t)s * kBBytes);
+            const uint32_t a_addr = smem_u32(St + (size_t)s * kStageBytes);
+            const uint32_t b_addr = a_addr + kABytes;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk)
               umma_bf16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
                         (kb > 0 || kk > 0) ? 1u : 0u);
-            umma_commit(&sh->b_empty[s]);  // the stage is free once these MMAs are done
+            umma_commit(&sh->empty[s]);  // the stage is free once these MMAs are done
           }
           if (!ok) break;
-          umma_commit(&sh->acc_full[buf]);
+          umma_commit(&sh->acc_full[b]);
         }
-        if (!ok) break;
-        umma_commit(&sh->a_empty);
       }
     }
   } else {
-    // ------------------------------------------------ epilogue (warps 2-5)
-    const int quarter = warp & 3;  // the TMEM lanes this warp may read
+    // ------------------------------------------------ epilogue (warps 2-9)
+    const int grp = (warp - 2) >> 2;  // drains accumulator buffer grp
+    const int quarter = warp & 3;     // the TMEM lanes this warp may read
     const int r_in_tile = quarter * 32 + lane;
+    uint2* mybuf = buf + (size_t)grp * kCap * kBM + r_in_tile;  // slot c at mybuf[c * kBM]
     uint32_t accidx = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    int lt = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
       const int64_t row = tile * kBM + r_in_tile;
-      const int32_t cur = (row < n) ? a[row] : -1;
-      float v1 = -INFINITY, v2 = -INFINITY, vc = -INFINITY;
-      int j1 = INT_MAX;
+      const bool valid = row < n;
+      float tau = -INFINITY, W2 = 0.f;
+      if (valid) {
+        W2 = __fadd_ru(__fmul_ru(2.f, __fadd_ru(eps_b, dlt[row])), 0x1.0p-20f);
+        if (use_thr) tau = __fsub_rd(__fsub_rd(__fsub_rd(lb[row], eps_b), W2), 0x1.0p-20f);
+      }
+      float v1 = tau;
+      int nap = 0;  // values appended (may exceed kCap: overflow)
+      bool may_write = (grp == 0) || (lt == 0);
       for (int nt = 0; nt < nnt; ++nt, ++accidx) {
-        const uint32_t buf = accidx & 1, use = accidx >> 1;
-        ok = mbar_wait(&sh->acc_full[buf], use & 1, abort_flag);
+        const uint32_t b = accidx & 1, use = accidx >> 1;
+        if ((int)b != grp) continue;
+        if (!may_write) {
+          // group 0 has read this group's buffer of the previous row tile
+          ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_empty[quarter], (lt - 1) & 1, abort_flag));
+          if (!ok) break;
+          may_write = true;
+        }
+        ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->acc_full[b], use & 1, abort_flag));
         if (!ok) break;
         tc_fence_after();
-        for (int c = 0; c < kBN / 32; ++c) {
-          uint32_t r[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * kBN + c * 32, r);
-          const int jb = nt * kBN + c * 32;
+        for (int c = 0; c < kBN / 64; ++c) {
+          const int jb = nt * kBN + c * 64;
+          if (jb >= k) break;  // the same for the whole warp
+          uint32_t r[64];
+          tmem_ld32x2(tmem + ((uint32_t)(quarter * 32) << 16) + b * kBN + c * 64, r);
+          if (jb + 64 > k) {  // last chunk: columns past k belong to padding centers
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int j = jb + q;
-            const float s = __uint_as_float(r[q]);
-            if (j < k) {
-              if (j == cur) vc = s;
-              if (s > v1) {
-                v2 = v1;
-                v1 = s;
-                j1 = j;
-              } else if (s > v2) {
-                v2 = s;
-              }
+            for (int q = 0; q < 64; ++q)
+              if (jb + q >= k) r[q] = __float_as_uint(-INFINITY);
+          }
+          float cm = __uint_as_float(r[0]);
+#pragma unroll
+          for (int q = 1; q < 64; ++q) cm = fmaxf(cm, __uint_as_float(r[q]));
+          v1 = fmaxf(v1, cm);
+          const float thr = fmaxf(tau, __fsub_rd(v1, W2));
+#pragma unroll
+          for (int q = 0; q < 64; ++q) {
+            if (__uint_as_float(r[q]) > thr) {
+              if (nap < kCap) mybuf[nap * kBM] = make_uint2(r[q], (uint32_t)(jb + q));
+              ++nap;
             }
           }
         }
         tc_fence_before();
-        mbar_arrive(&sh->acc_empty[buf]);
+        mbar_arrive(&sh->acc_empty[b]);
       }
-      if (ok && row < n) top2[row] = make_float4(v1, __int_as_float(j1), v2, vc);
+      if (!ok) break;
+      if (grp == 1) {
+        if (!may_write) {
+          ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_empty[quarter], (lt - 1) & 1, abort_flag));
+          if (!ok) break;
+        }
+        sh->mcount[r_in_tile] = nap;
+        mbar_arrive(&sh->mg_full[quarter]);  // releases the buffer and the count
+      } else {
+        ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_full[quarter], lt & 1, abort_flag));
+        if (!ok) break;
+        const int nap1 = sh->mcount[r_in_tile];
+        const uint2* other = buf + (size_t)kCap * kBM + r_in_tile;
+        const int m0 = nap < kCap ? nap : kCap, m1 = nap1 < kCap ? nap1 : kCap;
+        // the best value is always appended (it exceeds the threshold in force)
+        float best = -INFINITY;
+        for (int q = 0; q < m0; ++q) best = fmaxf(best, __uint_as_float(mybuf[q * kBM].x));
+        for (int q = 0; q < m1; ++q) best = fmaxf(best, __uint_as_float(other[q * kBM].x));
+        const float bnd = fmaxf(tau, __fsub_rd(best, W2));
+        float tv[kTopK];
+        int32_t ti[kTopK];
+#pragma unroll
+        for (int q = 0; q < kTopK; ++q) {
+          tv[q] = bnd;
+          ti[q] = -1;
+        }
+        for (int q = 0; q < m0; ++q) {
+          const uint2 e = mybuf[q * kBM];
+          const float sv = __uint_as_float(e.x);
+          if (sv > bnd) topk_insert(tv, ti, sv, (int32_t)e.y);
+        }
+        for (int q = 0; q < m1; ++q) {
+          const uint2 e = other[q * kBM];
+          const float sv = __uint_as_float(e.x);
+          if (sv > bnd) topk_insert(tv, ti, sv, (int32_t)e.y);
+        }
+        mbar_arrive(&sh->mg_empty[quarter]);  // group 1 may refill its buffer
+        if (nap > kCap || nap1 > kCap || ti[0] < 0) {
+#pragma unroll
+          for (int q = 0; q < kTopK; ++q) {
+            tv[q] = INFINITY;
+            ti[q] = -1;
+          }
+        }
+        if (valid) {
+          float4* vo = reinterpret_cast<float4*>(topv + row * kTopK);
+          int4* io = reinterpret_cast<int4*>(topi + row * kTopK);
+          vo[0] = make_float4(tv[0], tv[1], tv[2], tv[3]);
+          vo[1] = make_float4(tv[4], tv[5], tv[6], tv[7]);
+          io[0] = make_int4(ti[0], ti[1], ti[2], ti[3]);
+          io[1] = make_int4(ti[4], ti[5], ti[6], ti[7]);
+        }
+      }
     }
   }
   if (!ok) atomicOr(cnt + C_ERR, (unsigned long long)E_TIMEOUT);  // a device wait gave up
@@ -315,12 +427,17 @@ int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int
 
 }  // namespace
 
-size_t bf16_mma_smem_bytes() { return 1024 + (size_t)kMaxKB * kABytes + (size_t)kStages * kBBytes + sizeof(MmaShared); }
+size_t bf16_mma_smem_bytes() {
+  return 1024 + (size_t)kStages * kStageBytes + sizeof(uint2) * 2 * kCap * kBM + sizeof(MmaShared);
+}
 
-int bf16_mma_supported(int64_t d) { return (d % 8 == 0) && ((d + kBK - 1) / kBK <= kMaxKB); }
+// rows of 16-byte multiples for the tensor maps
+int bf16_mma_supported(int64_t d) { return d % 8 == 0; }
 
 // Xb: n x d BF16 (unit rows); Cb: (ceil(k/256)*256) x d BF16 (zero rows past k).
-int bf16_top2(skm_ctx* c, const void* Xb, const void* Cb, float4* top2) {
+// Columns past d read as zeros (the tensor map's out-of-bounds fill).
+// use_thr: lb holds a lower bound on every row's best exact similarity.
+int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* topv, int32_t* topi) {
   if (!bf16_mma_supported(c->d)) return SKM_EUNSUPPORTED;
   CUtensorMap mA, mB;
   const int nnt = (c->k + kBN - 1) / kBN;
@@ -329,12 +446,13 @@ int bf16_top2(skm_ctx* c, const void* Xb, const void* Cb, float4* top2) {
   rc = make_map(&mB, Cb, (int64_t)nnt * kBN, c->d, kBN);
   if (rc) return rc;
   const size_t smem = bf16_mma_smem_bytes();
-  SKM_CUDA_TRY(cudaFuncSetAttribute(k_bf16_top2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SKM_CUDA_TRY(cudaFuncSetAttribute(k_bf16_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t ntiles = (c->n + kBM - 1) / kBM;
   const int grid = (int)(ntiles < c->nsm ? ntiles : c->nsm);
   const int nkb = (int)((c->d + kBK - 1) / kBK);
-  SKM_PROF_BEGIN(c, "k_bf16_top2");
-  k_bf16_top2<<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->a, top2, c->cnt);
+  SKM_PROF_BEGIN(c, "k_bf16_topk");
+  k_bf16_topk<<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->eps_b, use_thr, topv,
+                                               topi, c->cnt);
   SKM_LAUNCHED(c);
   return SKM_OK;
 }

@@ -21,8 +21,9 @@ enum Counter {
   C_W1 = 2,       // points failing the first bound test
   C_W2 = 3,       // points needing a full row of similarities
   C_CHG = 4,      // entries of the changed-row list
-  C_ERR = 5,      // error flags (bit field)
-  C_NDIRTY = 6,   // clusters whose sum changed in the last center update
+  C_W3 = 5,       // dense precision form: rows rechecked against a few candidates
+  C_ERR = 6,      // error flags (bit field)
+  C_NDIRTY = 7,   // clusters whose sum changed in the last center update
   C_NUM = 8
 };
 
@@ -292,7 +293,9 @@ struct skm_ctx {
   void* Xb;           // [n x d] BF16 unit rows
   float* Cr;          // [k x d] FP32 centers, row-major
   void* Cb;           // [kpad x d] BF16 centers
-  void* top2;         // [n] float4 (v1, j1, v2, v_current) from the BF16 GEMM
+  float* topv;        // [n x 8] best BF16 similarities per row, descending
+  int32_t* topi;      // [n x 8] their centers
+  int32_t* w3;        // [n] rows rechecked against their candidates
   int32_t* lcount;    // [k] members per cluster
   int32_t* loff;      // [k+1]
   int32_t* lcursor;   // [k]
@@ -354,7 +357,10 @@ int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned
 int dense_tighten(skm_ctx* c);
 int dense_center_sums(skm_ctx* c);
 int bf16_mma_supported(int64_t d);
-int bf16_top2(skm_ctx* c, const void* Xb, const void* Cb, float4* top2);
+constexpr int kTopK = 8;  // BF16 candidates kept per row
+int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* topv, int32_t* topi);
+int dense_lower(skm_ctx* c);
+int dense_recheck_cands(skm_ctx* c, bool hamerly);
 
 }  // namespace skm
 

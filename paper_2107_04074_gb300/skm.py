@@ -28,7 +28,7 @@ DEVICE, HOST = 0, 1
 EXPORTS = ["skm_default_options", "skm_init", "skm_reset", "skm_assign", "skm_update_centers", "skm_run",
            "skm_get_labels", "skm_get_centers", "skm_set_centers", "skm_set_labels", "skm_get_bounds",
            "skm_get_stats", "skm_bound_bytes", "skm_kernel_launches", "skm_profile", "skm_profile_read",
-           "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_top2"]
+           "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_topk"]
 
 
 class SkmError(RuntimeError):
@@ -51,7 +51,8 @@ class skm_options(ctypes.Structure):
 class skm_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("last_changed", ctypes.c_int64), ("last_sims", ctypes.c_int64),
                 ("total_sims", ctypes.c_int64), ("last_survivors", ctypes.c_int64),
-                ("last_rechecks", ctypes.c_int64), ("objective", ctypes.c_double)]
+                ("last_rechecks", ctypes.c_int64), ("objective", ctypes.c_double),
+                ("last_cand_rechecks", ctypes.c_int64)]
 
 
 _LIB = None
@@ -93,7 +94,7 @@ def load(build_if_missing: bool = True):
         "skm_destroy": (None, [P]),
         "skm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "skm_assign_noalloc": (ctypes.c_int, [P, i32, P, P, P, P]),
-        "skm_get_bf16_top2": (ctypes.c_int, [P, P, P, i32]),
+        "skm_get_bf16_topk": (ctypes.c_int, [P, P, P, P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +172,7 @@ class Stats:
     last_survivors: int
     last_rechecks: int
     objective: float
+    last_cand_rechecks: int = 0
 
 
 class KMeans:
@@ -299,16 +301,18 @@ class KMeans:
             idx += 1
         return out
 
-    def bf16_top2(self):
-        """(n x 4 array: best BF16 similarity, its center, second best, similarity to the previous
-        label) of the last assignment, and the error bound eps_b."""
-        out = np.empty((self.n, 4), dtype=np.float32)
+    def bf16_topk(self):
+        """(n x 8 best BF16 similarities in descending order, n x 8 their centers) of the last
+        assignment, and the error bound eps_b."""
+        vals = np.empty((self.n, 8), dtype=np.float32)
+        idx = np.empty((self.n, 8), dtype=np.int32)
         eps = ctypes.c_float(0)
-        _check(load().skm_get_bf16_top2(self._h, _ptr(out), ctypes.byref(eps), HOST), "skm_get_bf16_top2")
-        return out, eps.value
+        _check(load().skm_get_bf16_topk(self._h, _ptr(vals), _ptr(idx), ctypes.byref(eps), HOST),
+               "skm_get_bf16_topk")
+        return vals, idx, eps.value
 
     def stats(self) -> Stats:
         s = skm_stats()
         _check(load().skm_get_stats(self._h, ctypes.byref(s)), "skm_get_stats")
         return Stats(s.iterations, s.last_changed, s.last_sims, s.total_sims, s.last_survivors, s.last_rechecks,
-                     s.objective)
+                     s.objective, s.last_cand_rechecks)
