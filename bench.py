@@ -439,6 +439,105 @@ def run_embed(args, rank, world, local):
                                    "frac": round(g.get("bf16_gemm_tflops", 0) / peak, 4)}}
 
 
+def run_batch(args, rank, world, local):
+    """Batched form: 64 independent runs (n_r lognormal over [5e3, 2e5],
+    d = 2e4, k_r uniform over {10, 50, 100, 250, 500}, at most 50 iterations
+    each) in one context -- simplified Elkan, one launch per phase for all
+    runs, the iteration replayed as a CUDA graph, launch shape autotuned --
+    against the plain FP32 standard variant run by run (one context each, one
+    after the other), at identical labels."""
+    import tempfile
+
+    import torch
+    from paper_2107_04074_gb300 import skm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nruns, iters = args.batch_runs, 50
+    cfgs, ks = synth.batch_runs(nruns)
+    parts = [synth.tfidf(c) for c in cfgs]
+    X, run_rows = synth.concat(parts)
+    inits = [synth.init_rows(p.n, int(k), 1000 + r) for r, (p, k) in enumerate(zip(parts, ks))]
+    init_all = np.concatenate(inits)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    Xd = [torch.from_numpy(a).to(dev) for a in (X.row_ptr, X.col, X.val)]
+    b = skm.Batch(X.n, X.d, *Xd, run_rows, ks, variant="simp_elkan", init_rows=init_all, graph=True,
+                  stream=stream.cuda_stream)
+    cache = os.path.join(tempfile.gettempdir(), "skm_autotune.txt")
+    t0 = time.perf_counter()
+    from_cache = b.autotune(cache, iters=3)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        b.reset(init_all)
+        b.run(iters)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_b, its = 0.0, []
+    l0 = skm.kernel_launches()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.reset(init_all)
+        it, J = b.run(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_b += e0.elapsed_time(e1)
+        its.append(it)
+    launches = skm.kernel_launches() - l0
+    clocks = sampler.stop()
+    lab_b = b.labels()
+    # kernel shares of one eager run with per-kernel events
+    b.reset(init_all)
+    prof = {}
+    for _ in range(iters):
+        b.profile(True)
+        ch = b.assign()
+        if ch:
+            b.update_centers()
+        for nm, (t, c) in b.profile_read().items():
+            prof.setdefault(nm, [0.0, 0])
+            prof[nm][0] += t
+            prof[nm][1] += c
+        b.profile(False)
+        if ch == 0:
+            break
+    b.close()
+    # the plain FP32 standard variant, run by run (contexts built outside the timing)
+    ms_s, it_s, lab_s = 0.0, 0, []
+    for r, p in enumerate(parts):
+        pd = [torch.from_numpy(a).to(dev) for a in (p.row_ptr, p.col, p.val)]
+        km = skm.KMeans(p.n, p.d, *pd, int(ks[r]), variant="standard", init_rows=inits[r],
+                        stream=stream.cuda_stream)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, _ = km.run(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s += e0.elapsed_time(e1)
+        it_s += it
+        lab_s.append(km.labels())
+        km.close()
+    same = bool(np.array_equal(lab_b, np.concatenate(lab_s)))
+    per_step = ms_b / args.steps
+    tot = sum(v[0] for v in prof.values()) or 1.0
+    return {"workload": f"{nruns} sparse TF-IDF runs, n_r in [5e3, 2e5] (sum {X.n}, {X.nnz} nnz), d=20000, "
+                        f"k_r in {{10,50,100,250,500}} (sum {int(ks.sum())}), at most {iters} iterations each",
+            "batch_ms_per_step": round(per_step, 3), "batch_iterations": its[-1],
+            "run_iterations_per_s": round(nruns * its[-1] / (per_step / 1e3), 1),
+            "sequential_standard_ms": round(ms_s, 3), "sequential_standard_run_iterations": it_s,
+            "speedup_vs_sequential_standard": round(ms_s / per_step, 2),
+            "labels_identical_to_standard": same, "gpu_launches_per_step": int(launches / args.steps),
+            "autotune": {"from_cache": from_cache, "seconds": round(tune_s, 2)},
+            "clocks": clocks,
+            "kernel_time_share": {nm: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)}
+                                  for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:12]}}
+
+
 def cpu_baseline(csr, init, variant, iters=3):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
     first `iters` iterations of the same run on the full data."""
@@ -494,8 +593,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed runs of the chosen variant (for profiler captures)")
-    ap.add_argument("--workload", default="rcv1", choices=["rcv1", "embed"],
-                    help="rcv1: the bench line; embed: the dense precision-form measurement")
+    ap.add_argument("--workload", default="rcv1", choices=["rcv1", "embed", "batch"],
+                    help="rcv1: the bench line; embed: the dense precision-form measurement; "
+                         "batch: the batched form")
+    ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--embed-n", type=int, default=1_000_000)
     ap.add_argument("--embed-iters", type=int, default=20)
     ap.add_argument("--trace", action="store_true",
@@ -509,6 +610,10 @@ def main():
     if args.workload == "embed":
         if rank == 0:
             print(json.dumps(run_embed(args, rank, world, local)), flush=True)
+        return
+    if args.workload == "batch":
+        if rank == 0:
+            print(json.dumps(run_batch(args, rank, world, local)), flush=True)
         return
     if world > 1:
         import torch

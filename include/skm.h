@@ -100,7 +100,16 @@ typedef struct {
                               this (capped at 7) is recomputed as a whole row;
                               0 = min(k/8, 7) */
   int32_t precision;       /* skm_precision, dense rows only (default FP32) */
-  int32_t reserved[8];
+  int32_t graph;           /* skm_run on CSR data: 1 = after the first iteration,
+                              replay one whole iteration (assignment and center
+                              update) as a captured CUDA graph and read the
+                              changed-label counts back every graph_check
+                              iterations; iterations after convergence change
+                              nothing.  0 (default): one host sync per iteration */
+  int32_t graph_check;     /* 0 = 8 */
+  int32_t blocks_per_sm;   /* grid of the persistent bound/recompute kernels,
+                              blocks per SM (0 = 8); skm_autotune sets it */
+  int32_t reserved[5];
 } skm_options;
 
 /* Counters of the last assignment and of the run so far. */
@@ -183,6 +192,35 @@ int skm_get_stats(skm_ctx* ctx, skm_stats* out);
  * exact one.  Rows the last Hamerly assignment pruned keep older values.
  * Any pointer may be NULL.  SKM_ESTATE otherwise. */
 int skm_get_bf16_topk(skm_ctx* ctx, float* vals, int32_t* idx, float* eps_b, int32_t out_space);
+
+/* Batched form: nruns independent clusterings of different row blocks of
+ * one CSR matrix (same d) in one context, so that each phase of an iteration
+ * is one launch for all runs.  x holds all rows; run r owns rows
+ * run_rows[r] .. run_rows[r+1]-1 (host int64[nruns+1], run_rows[0] = 0,
+ * run_rows[nruns] = x->n, increasing) and clusters them into ks[r] centers
+ * (host int32[nruns], 1 <= ks[r] <= rows of the run, <= 4096).  init_rows:
+ * host int64[sum ks], for each run in order ks[r] distinct row indices local
+ * to the run, or NULL to draw them from seed (run r uses seed + r).
+ * Variants: SKM_STANDARD and SKM_SIMP_ELKAN (others: SKM_EUNSUPPORTED).
+ * skm_assign / skm_update_centers / skm_run then advance every run;
+ * skm_get_labels returns labels local to each run (in [0, ks[r]));
+ * skm_get_centers returns the runs' centers one after the other
+ * (float[sum ks * d]); the objective and counters are totals over the runs.
+ * skm_set_centers, skm_set_labels and skm_get_bounds return
+ * SKM_EUNSUPPORTED for a batch.  Ownership and errors as skm_init. */
+int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, const int32_t* ks, int32_t nruns,
+                   int32_t variant, const int64_t* init_rows, uint64_t seed, const skm_options* opt,
+                   void* stream);
+
+/* Choose the launch configuration of the persistent bound and recompute
+ * kernels (blocks per SM) and the Elkan whole-row threshold for this
+ * context's shape by timing `iters` iterations per candidate from the
+ * initial centers (results do not depend on the choice), then restore the
+ * initial state.  The choice is kept in the text file cache_path (one line
+ * per device and shape bucket) when cache_path is not NULL, and read from
+ * it instead of timing when the bucket is already there.  *from_cache (may
+ * be NULL) tells which happened. */
+int skm_autotune(skm_ctx* ctx, const char* cache_path, int32_t iters, int32_t* from_cache);
 
 /* Bytes of bound state a variant keeps for n points and k centers (labels
  * excluded): standard 0; Hamerly 8n (two FP32 bounds); Elkan 4n + 4nk. */

@@ -2,6 +2,7 @@
 // memory of a context, and the order of the kernels of one Lloyd iteration.
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <unordered_set>
@@ -54,6 +55,45 @@ using namespace skm;
 
 namespace {
 
+inline unsigned grid_cap(int64_t items, int per_block, int nsm, int per_sm = 16) {
+  int64_t g = (items + per_block - 1) / per_block;
+  if (g > (int64_t)nsm * per_sm) g = (int64_t)nsm * per_sm;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+// Batch: global label -> label local to the row's run.
+__global__ void k_labels_local(const int32_t* __restrict__ a, int64_t n, const int32_t* __restrict__ row_run,
+                               const RunDesc* __restrict__ runs, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = a[i];
+    out[i] = v < 0 ? v : v - runs[row_run[i]].koff;
+  }
+}
+
+// Batch: the runs' centers one after the other as rows (out: sum_r k_r x d);
+// thread per (output row, term), the run found by a walk over the table.
+__global__ void k_centers_batch(const float* __restrict__ Ct, int64_t d, int64_t kst, const RunDesc* __restrict__ runs,
+                                int32_t nruns, int64_t ktot, float* __restrict__ out) {
+  const int64_t total = ktot * d;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = q / d, t = q - o * d;
+    int64_t base = 0;
+    int r = 0;
+    while (r + 1 < nruns && base + runs[r].k <= o) base += runs[r++].k;
+    out[q] = Ct[t * kst + runs[r].koff + (o - base)];
+  }
+}
+
+// Graph replay: record this iteration's changed count and similarities.
+__global__ void k_glog(const unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ glog) {
+  const unsigned long long pos = glog[0];
+  if (pos < (unsigned long long)kLogCap) {
+    glog[2 + 2 * pos] = cnt[C_CHANGED];
+    glog[3 + 2 * pos] = cnt[C_SIMS];
+  }
+  glog[0] = pos + 1;
+}
+
 template <typename T>
 int dalloc(skm_ctx* c, T** p, size_t count) {
   if (count == 0) count = 1;
@@ -91,17 +131,13 @@ void seeded_rows(int64_t n, int32_t k, uint64_t seed, std::vector<int64_t>& out)
   }
 }
 
-int set_init(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
-  std::vector<int64_t> rows;
-  if (init_rows) {
-    std::unordered_set<int64_t> seen;
-    for (int32_t j = 0; j < c->k; ++j) {
-      if (init_rows[j] < 0 || init_rows[j] >= c->n || !seen.insert(init_rows[j]).second) return SKM_EINVAL;
-      rows.push_back(init_rows[j]);
-    }
-  } else {
-    seeded_rows(c->n, c->k, seed, rows);
+int start_from_rows(skm_ctx* c, const std::vector<int64_t>& rows) {
+  // rows: one global row per center column (-1: a batch's padding column)
+  if (!c->hinit) {
+    c->hinit = new (std::nothrow) std::vector<int64_t>();
+    if (!c->hinit) return SKM_ENOMEM;
   }
+  *static_cast<std::vector<int64_t>*>(c->hinit) = rows;
   int64_t* drows = nullptr;
   TRY(dalloc(c, &drows, (size_t)c->k));
   SKM_CUDA_TRY(cudaMemcpyAsync(drows, rows.data(), sizeof(int64_t) * c->k, cudaMemcpyHostToDevice, c->st));
@@ -119,6 +155,40 @@ int set_init(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
   return SKM_OK;
 }
 
+int set_init(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
+  std::vector<int64_t> rows;
+  if (c->nruns > 0) {
+    // per run: ks[r] local rows, placed in the run's slice of the columns
+    const auto& R = *static_cast<std::vector<RunDesc>*>(c->hruns);
+    rows.assign((size_t)c->k, -1);
+    int64_t q = 0;
+    std::vector<int64_t> loc;
+    for (size_t r = 0; r < R.size(); ++r) {
+      if (init_rows) {
+        std::unordered_set<int64_t> seen;
+        loc.clear();
+        for (int32_t j = 0; j < R[r].k; ++j, ++q) {
+          const int64_t v = init_rows[q];
+          if (v < 0 || v >= R[r].n || !seen.insert(v).second) return SKM_EINVAL;
+          loc.push_back(v);
+        }
+      } else {
+        seeded_rows(R[r].n, R[r].k, seed + r, loc);
+      }
+      for (int32_t j = 0; j < R[r].k; ++j) rows[(size_t)(R[r].koff + j)] = R[r].row0 + loc[(size_t)j];
+    }
+  } else if (init_rows) {
+    std::unordered_set<int64_t> seen;
+    for (int32_t j = 0; j < c->k; ++j) {
+      if (init_rows[j] < 0 || init_rows[j] >= c->n || !seen.insert(init_rows[j]).second) return SKM_EINVAL;
+      rows.push_back(init_rows[j]);
+    }
+  } else {
+    seeded_rows(c->n, c->k, seed, rows);
+  }
+  return start_from_rows(c, rows);
+}
+
 void release(skm_ctx* c) {
   if (!c) return;
   if (c->prof) {
@@ -126,13 +196,17 @@ void release(skm_ctx* c) {
     delete static_cast<ProfList*>(c->prof);
     c->prof = nullptr;
   }
-  void* ptrs[] = {c->own[0], c->own[1], c->own[2], c->rinv,  c->dlt,   c->t_ptr, c->t_row, c->t_val,
-                  c->ch_term, c->ch_idx, c->ch_part, c->multi_term, c->multi_base, c->multi_cnt, c->part64,
-                  c->Ct,     c->S64,    c->nrm,    c->red,   c->obj,   c->pdn,   c->pup,   c->qup,
-                  c->hsel,   c->cc,     c->sc,     c->gpart, c->a,     c->lb,    c->ub,    c->w1,
-                  c->w2,     c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark, c->dpos, c->dlist,
-                  c->G,      c->rpart,  c->Xb,     c->Cr,    c->Cb,    c->topv,  c->topi,  c->w3,
-                  c->lcount, c->loff, c->lcursor, c->lmembers};
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
+  delete static_cast<std::vector<RunDesc>*>(c->hruns);
+  delete static_cast<std::vector<int64_t>*>(c->hinit);
+  void* ptrs[] = {c->runs,   c->row_run, c->glog,  c->own[0], c->own[1], c->own[2], c->rinv,  c->dlt,
+                  c->t_ptr,  c->t_row,   c->t_val, c->ch_term, c->ch_idx, c->ch_part, c->multi_term,
+                  c->multi_base, c->multi_cnt, c->part64, c->Ct, c->S64, c->nrm, c->red, c->obj, c->pdn,
+                  c->pup,    c->qup,     c->hsel,  c->cc,     c->sc,     c->gpart,  c->a,     c->lb,
+                  c->ub,     c->w1,      c->w2,    c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark,
+                  c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
+                  c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -283,7 +357,12 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   TRY(dalloc(c, &c->a, (size_t)n));
   if (ham || elk) {
     TRY(dalloc(c, &c->lb, (size_t)n));
-    TRY(dalloc(c, &c->ub, (size_t)(elk ? n * kst : n)));
+    int64_t ucount = elk ? n * kst : n;
+    if (elk && c->nruns > 0) {
+      const auto& R = *static_cast<std::vector<RunDesc>*>(c->hruns);
+      ucount = R.back().uoff + R.back().n * R.back().kst;
+    }
+    TRY(dalloc(c, &c->ub, (size_t)ucount));
     TRY(dalloc(c, &c->w1, (size_t)n));
     TRY(dalloc(c, &c->w2, (size_t)n));
   }
@@ -358,12 +437,141 @@ int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const
   return SKM_OK;
 }
 
+int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, const int32_t* ks, int32_t nruns,
+                   int32_t variant, const int64_t* init_rows, uint64_t seed, const skm_options* opt, void* stream) {
+  if (!out) return SKM_EINVAL;
+  *out = nullptr;
+  if (!x || !run_rows || !ks || nruns < 1 || x->n < 1 || x->d < 1 || x->reserved != 0) return SKM_EINVAL;
+  if (x->layout != SKM_CSR) return SKM_EUNSUPPORTED;
+  if (variant < SKM_STANDARD || variant > SKM_SIMP_ELKAN) return SKM_EINVAL;
+  if (variant != SKM_STANDARD && variant != SKM_SIMP_ELKAN) return SKM_EUNSUPPORTED;
+  if (x->dtype < SKM_F32 || x->dtype > SKM_BF16) return SKM_EINVAL;
+  if (x->memspace != SKM_DEVICE && x->memspace != SKM_HOST) return SKM_EINVAL;
+  if (!x->values || !x->row_ptr || !x->col_idx) return SKM_EINVAL;
+  if (x->d > INT32_MAX || x->n > INT32_MAX || (int64_t)nruns * x->d > INT32_MAX) return SKM_EUNSUPPORTED;
+  if (run_rows[0] != 0 || run_rows[nruns] != x->n) return SKM_EINVAL;
+  std::vector<RunDesc> R((size_t)nruns);
+  int64_t koff = 0, uoff = 0;
+  int32_t kmax = 0;
+  for (int32_t r = 0; r < nruns; ++r) {
+    const int64_t nr = run_rows[r + 1] - run_rows[r];
+    if (nr < 1 || ks[r] < 1 || ks[r] > nr) return SKM_EINVAL;
+    if (ks[r] > 4096) return SKM_EUNSUPPORTED;
+    RunDesc& d = R[(size_t)r];
+    d.row0 = run_rows[r];
+    d.n = nr;
+    d.k = ks[r];
+    d.kst = (ks[r] + 7) / 8 * 8;
+    d.koff = (int32_t)koff;
+    d.uoff = uoff;
+    int32_t cap = opt && opt->row_threshold > 0 ? opt->row_threshold : (ks[r] + 7) / 8;
+    d.cap = cap > 7 ? 7 : cap;
+    koff += d.kst;
+    uoff += nr * d.kst;
+    if (d.kst > kmax) kmax = d.kst;
+  }
+  if (koff > INT32_MAX / 2) return SKM_EUNSUPPORTED;
+  skm_ctx* c = new (std::nothrow) skm_ctx();
+  if (!c) return SKM_ENOMEM;
+  std::memset(c, 0, sizeof(*c));
+  c->st = (cudaStream_t)stream;
+  c->n = x->n;
+  c->d = x->d;
+  c->k = (int32_t)koff;  // every run's slice, padding included
+  c->kst = (int32_t)koff;
+  c->kmax = kmax;
+  c->nruns = nruns;
+  c->variant = variant;
+  c->layout = x->layout;
+  c->dtype = x->dtype;
+  if (opt) c->opt = *opt;
+  else skm_default_options(&c->opt);
+  c->prof = new (std::nothrow) ProfList();
+  c->hruns = new (std::nothrow) std::vector<RunDesc>(R);
+  if (!c->prof || !c->hruns) {
+    release(c);
+    return SKM_ENOMEM;
+  }
+  int rc = SKM_OK;
+  std::vector<int32_t> rr((size_t)x->n);
+  for (int32_t r = 0; r < nruns; ++r)
+    for (int64_t i = run_rows[r]; i < run_rows[r + 1]; ++i) rr[(size_t)i] = r;
+  if ((rc = dalloc(c, &c->runs, (size_t)nruns)) == SKM_OK && (rc = dalloc(c, &c->row_run, (size_t)x->n)) == SKM_OK) {
+    if (cudaMemcpyAsync(c->runs, R.data(), sizeof(RunDesc) * nruns, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(c->row_run, rr.data(), sizeof(int32_t) * x->n, cudaMemcpyHostToDevice, c->st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+      rc = SKM_ECUDA;
+  }
+  if (rc == SKM_OK) rc = build_ctx(c, x, init_rows, seed);
+  if (rc != SKM_OK) {
+    release(c);
+    return rc;
+  }
+  *out = c;
+  return SKM_OK;
+}
+
 int skm_reset(skm_ctx* c, const int64_t* init_rows, uint64_t seed) {
   if (!c) return SKM_EINVAL;
   return set_init(c, init_rows, seed);
 }
 
 namespace {
+
+// One steady-state iteration (assignment, log of its counters, center
+// update) captured from a private stream into a CUDA graph.  Launch counts of
+// the capture are taken back out; each replay adds the graph's kernel nodes.
+int capture_iteration(skm_ctx* c);
+
+int build_graph(skm_ctx* c) {
+  if (!c->cap_st) SKM_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+  if (!c->glog) {
+    TRY(dalloc(c, &c->glog, (size_t)(2 + 2 * kLogCap)));
+    SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  }
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  const long long before = g_launches.load();
+  const skm_stats saved = c->stats;  // the capture runs nothing
+  cudaStream_t orig = c->st;
+  c->st = c->cap_st;
+  SKM_CUDA_TRY(cudaStreamBeginCapture(c->cap_st, cudaStreamCaptureModeRelaxed));
+  const int rc = capture_iteration(c);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(c->cap_st, &g);
+  c->st = orig;
+  c->stats = saved;
+  g_launches.fetch_sub(g_launches.load() - before);
+  if (rc != SKM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ec != cudaSuccess || !g) {
+    (void)cudaGetLastError();
+    return SKM_ECUDA;
+  }
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(g, nodes.data(), &nn);
+  c->gkernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++c->gkernels;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    (void)cudaGetLastError();
+    c->gexec = nullptr;
+    return SKM_ECUDA;
+  }
+  return SKM_OK;
+}
 
 // One assignment of dense rows (standard or Hamerly; FP32 or BF16 bulk).
 int assign_dense(skm_ctx* c) {
@@ -453,14 +661,48 @@ int skm_update_centers(skm_ctx* c, double* objective) {
 int skm_run(skm_ctx* c, int32_t max_iters, int32_t* iters_done, double* objective) {
   if (!c || max_iters < 0) return SKM_EINVAL;
   int32_t it = 0;
-  for (; it < max_iters; ++it) {
+  bool done = false;
+  const bool use_graph = c->opt.graph && c->layout == SKM_CSR && !c->prof_on;
+  // eager iterations (all of them, or the first one before the graph: the
+  // graph holds the steady state, bounds present and centers moved)
+  while (it < max_iters && !done) {
     int64_t ch = 0;
     TRY(skm_assign(c, &ch));
+    ++it;
     if (ch == 0) {
-      ++it;
+      done = true;
       break;
     }
     TRY(skm_update_centers(c, nullptr));
+    if (use_graph) break;
+  }
+  if (use_graph && !done && it < max_iters) {
+    TRY(build_graph(c));
+    int check = c->opt.graph_check > 0 ? c->opt.graph_check : 8;
+    if (check > kLogCap) check = kLogCap;
+    while (it < max_iters && !done) {
+      const int m = (max_iters - it) < check ? (max_iters - it) : check;
+      SKM_CUDA_TRY(cudaMemsetAsync(c->glog, 0, sizeof(unsigned long long), c->st));
+      for (int q = 0; q < m; ++q) SKM_CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+      note_launch((int)(m * c->gkernels));
+      std::vector<unsigned long long> lg((size_t)(2 + 2 * m));
+      SKM_CUDA_TRY(cudaMemcpyAsync(lg.data(), c->glog, sizeof(unsigned long long) * lg.size(),
+                                   cudaMemcpyDeviceToHost, c->st));
+      SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+      for (int q = 0; q < m; ++q) {
+        ++it;
+        c->stats.iterations++;
+        c->stats.last_changed = (int64_t)lg[(size_t)(2 + 2 * q)];
+        c->stats.last_sims = (int64_t)lg[(size_t)(3 + 2 * q)];
+        c->stats.total_sims += c->stats.last_sims;
+        if (c->stats.last_changed == 0) {
+          done = true;  // later replays of this chunk changed nothing
+          break;
+        }
+      }
+    }
+    c->moved = 1;
+    c->chg_fresh = 0;
   }
   SKM_CUDA_TRY(cudaMemcpyAsync(c->hobj, c->obj, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
@@ -472,6 +714,22 @@ int skm_run(skm_ctx* c, int32_t max_iters, int32_t* iters_done, double* objectiv
 
 int skm_get_labels(skm_ctx* c, int32_t* out, int32_t space) {
   if (!c || !out) return SKM_EINVAL;
+  if (c->nruns > 0) {
+    // labels local to each run
+    int32_t* tmp = nullptr;
+    if (space == SKM_HOST) TRY(dalloc(c, &tmp, (size_t)c->n));
+    int32_t* dst = space == SKM_HOST ? tmp : out;
+    k_labels_local<<<grid_cap(c->n, 256, c->nsm), 256, 0, c->st>>>(c->a, c->n, c->row_run, c->runs, dst);
+    note_launch(1);
+    int rc = SKM_OK;
+    if (space == SKM_HOST) {
+      if (cudaMemcpyAsync(out, tmp, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        rc = SKM_ECUDA;
+      cudaFreeAsync(tmp, c->st);
+      if (cudaStreamSynchronize(c->st) != cudaSuccess) rc = SKM_ECUDA;
+    }
+    return rc;
+  }
   SKM_CUDA_TRY(cudaMemcpyAsync(out, c->a, sizeof(int32_t) * c->n,
                                space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->st));
   if (space == SKM_HOST) SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
@@ -480,11 +738,23 @@ int skm_get_labels(skm_ctx* c, int32_t* out, int32_t space) {
 
 int skm_get_centers(skm_ctx* c, float* out, int32_t space) {
   if (!c || !out) return SKM_EINVAL;
-  if (space == SKM_DEVICE) return centers_to_rows(c, out);
+  int64_t krows = c->k;
+  if (c->nruns > 0) {
+    krows = 0;
+    for (const auto& r : *static_cast<std::vector<RunDesc>*>(c->hruns)) krows += r.k;
+  }
+  auto fill = [&](float* dst) -> int {
+    if (c->nruns == 0) return centers_to_rows(c, dst);
+    k_centers_batch<<<grid_cap(krows * c->d, 256, c->nsm), 256, 0, c->st>>>(c->Ct, c->d, c->kst, c->runs, c->nruns,
+                                                                            krows, dst);
+    note_launch(1);
+    return SKM_OK;
+  };
+  if (space == SKM_DEVICE) return fill(out);
   float* tmp = nullptr;
-  TRY(dalloc(c, &tmp, (size_t)(c->k * c->d)));
-  int rc = centers_to_rows(c, tmp);
-  if (rc == SKM_OK && cudaMemcpyAsync(out, tmp, sizeof(float) * c->k * c->d, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+  TRY(dalloc(c, &tmp, (size_t)(krows * c->d)));
+  int rc = fill(tmp);
+  if (rc == SKM_OK && cudaMemcpyAsync(out, tmp, sizeof(float) * krows * c->d, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
     rc = SKM_ECUDA;
   cudaFreeAsync(tmp, c->st);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) rc = SKM_ECUDA;
@@ -493,6 +763,7 @@ int skm_get_centers(skm_ctx* c, float* out, int32_t space) {
 
 int skm_set_centers(skm_ctx* c, const float* C, int32_t space) {
   if (!c || !C) return SKM_EINVAL;
+  if (c->nruns > 0) return SKM_EUNSUPPORTED;
   int rc;
   if (space == SKM_DEVICE) {
     rc = rows_to_centers(c, C);
@@ -513,6 +784,7 @@ int skm_set_centers(skm_ctx* c, const float* C, int32_t space) {
 
 int skm_set_labels(skm_ctx* c, const int32_t* lab, int32_t space) {
   if (!c || !lab) return SKM_EINVAL;
+  if (c->nruns > 0) return SKM_EUNSUPPORTED;
   if (space == SKM_HOST)
     for (int64_t i = 0; i < c->n; ++i)
       if (lab[i] < 0 || lab[i] >= c->k) return SKM_EINVAL;
@@ -527,6 +799,7 @@ int skm_set_labels(skm_ctx* c, const int32_t* lab, int32_t space) {
 
 int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
   if (!c) return SKM_EINVAL;
+  if (c->nruns > 0) return SKM_EUNSUPPORTED;
   if (c->variant == SKM_STANDARD || !c->have_bounds) return SKM_ESTATE;
   const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
   const cudaMemcpyKind kind = space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -614,6 +887,101 @@ int skm_profile_read(skm_ctx* c, int32_t idx, char* name, int32_t name_len, doub
   return SKM_OK;
 }
 
+int skm_autotune(skm_ctx* c, const char* cache_path, int32_t iters, int32_t* from_cache) {
+  if (!c || iters < 1) return SKM_EINVAL;
+  if (from_cache) *from_cache = 0;
+  if (!c->hinit) return SKM_ESTATE;
+  // shape bucket: device, variant, batch or not, log2 of n, k (widest run)
+  // and mean nonzeros per row
+  cudaDeviceProp prop;
+  SKM_CUDA_TRY(cudaGetDeviceProperties(&prop, c->dev));
+  auto lg2 = [](double v) { return v < 1.0 ? 0 : (int)std::floor(std::log2(v)); };
+  const int32_t kb = c->nruns > 0 ? c->kmax : c->k;
+  char key[320];
+  std::snprintf(key, sizeof(key), "%s|sm%d|v%d|b%d|L%d|n%d|k%d|z%d", prop.name, c->nsm, c->variant,
+                c->nruns > 0 ? 1 : 0, c->layout, lg2((double)c->n), lg2((double)kb),
+                lg2((double)c->nnz / (double)c->n));
+  for (char* q = key; *q; ++q)
+    if (*q == ' ') *q = '_';
+  const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
+  auto apply = [&](int32_t bpsm, int32_t thr) -> int {
+    c->opt.blocks_per_sm = bpsm;
+    c->opt.row_threshold = thr;
+    if (c->nruns > 0) {
+      auto& R = *static_cast<std::vector<RunDesc>*>(c->hruns);
+      for (auto& r : R) {
+        const int32_t cap = thr > 0 ? thr : (r.k + 7) / 8;
+        r.cap = cap > 7 ? 7 : cap;
+      }
+      SKM_CUDA_TRY(cudaMemcpyAsync(c->runs, R.data(), sizeof(RunDesc) * R.size(), cudaMemcpyHostToDevice, c->st));
+      SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    }
+    return SKM_OK;
+  };
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[512];
+      int found = 0, bp = 0, th = 0;
+      while (std::fgets(line, sizeof(line), f)) {
+        char k2[320];
+        int b2, t2;
+        if (std::sscanf(line, "%319s %d %d", k2, &b2, &t2) == 3 && std::strcmp(k2, key) == 0) {
+          found = 1;
+          bp = b2;
+          th = t2;
+        }
+      }
+      std::fclose(f);
+      if (found) {
+        TRY(apply(bp, th));
+        if (from_cache) *from_cache = 1;
+        return SKM_OK;
+      }
+    }
+  }
+  const std::vector<int64_t> init = *static_cast<std::vector<int64_t>*>(c->hinit);
+  const int32_t bps[3] = {4, 8, 16};
+  const int32_t thrs[3] = {0, 2, 7};
+  const int nthr = elk ? 3 : 1;
+  cudaEvent_t e0, e1;
+  SKM_CUDA_TRY(cudaEventCreate(&e0));
+  SKM_CUDA_TRY(cudaEventCreate(&e1));
+  float best = INFINITY;
+  int32_t bb = 8, bt = 0;
+  int rc = SKM_OK;
+  for (int a = 0; a < 3 && rc == SKM_OK; ++a)
+    for (int b = 0; b < nthr && rc == SKM_OK; ++b) {
+      if ((rc = apply(bps[a], thrs[b])) != SKM_OK) break;
+      if ((rc = start_from_rows(c, init)) != SKM_OK) break;
+      cudaEventRecord(e0, c->st);
+      for (int32_t it = 0; it < iters && rc == SKM_OK; ++it) {
+        rc = skm_assign(c, nullptr);
+        if (rc == SKM_OK) rc = skm_update_centers(c, nullptr);
+      }
+      cudaEventRecord(e1, c->st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = SKM_ECUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == SKM_OK && ms < best) {
+        best = ms;
+        bb = bps[a];
+        bt = thrs[b];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SKM_OK) return rc;
+  TRY(apply(bb, bt));
+  TRY(start_from_rows(c, init));
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%s %d %d\n", key, bb, bt);
+      std::fclose(f);
+    }
+  }
+  return SKM_OK;
+}
+
 void skm_destroy(skm_ctx* c) { release(c); }
 
 const char* skm_strerror(int s) {
@@ -631,3 +999,14 @@ const char* skm_strerror(int s) {
 }
 
 }  // extern "C"
+
+namespace {
+
+int capture_iteration(skm_ctx* c) {
+  TRY(skm_assign(c, nullptr));
+  k_glog<<<1, 1, 0, c->st>>>(c->cnt, c->glog);
+  SKM_CUDA_TRY(cudaGetLastError());
+  return skm_update_centers(c, nullptr);
+}
+
+}  // namespace

@@ -29,11 +29,14 @@ constexpr int kBlock = 256;
 // Lane L owns the centers j = 128 g + 4 L + c (c = 0..3, g = 0..G-1) and
 // gathers them with one 16-byte load per row entry and group; each center's
 // sum runs over the row entries in CSR order (the canonical order).
+// For a batch (runs != nullptr) each row works on its run's slice of the
+// centers (global ids koff + j) and its run's bound row.
 template <typename VT, int G, int MODE>
 __global__ void __launch_bounds__(kBlock) k_rows_top2(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
-    int64_t kst, const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt, int64_t nrows,
+    int64_t kst, const int32_t* __restrict__ row_run, const RunDesc* __restrict__ runs,
+    const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt, int64_t nrows,
     int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, int32_t* __restrict__ chg_i,
     int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
   constexpr int KT = 128 * G;                     // centers per pass over the row
@@ -45,21 +48,23 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
   ChangedBuf chb;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
     const int64_t i = list ? (int64_t)list[w] : w;
+    const RowGeom rg = row_geom(i, k, kst, 0, row_run, runs);
+    const int32_t kr = rg.k;
     const int64_t b = rp[i], e = rp[i + 1];
     const float ri = rinv[i];
     const float dl = dlt[i];
-    const int32_t cur = a[i];
+    const int32_t cur = a[i] - rg.koff;  // local; negative before the first assignment
     float v1 = -INFINITY, v2 = -INFINITY, vcur = -INFINITY;
     int j1 = INT_MAX;
-    for (int j0 = 0; j0 < k; j0 += KT) {
+    for (int j0 = 0; j0 < kr; j0 += KT) {
       float4 acc[G];
       bool ok[G];  // this lane's 4-center slot of group g lies inside the padded row
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
-        ok[g] = (j0 + g * 128 + lane * 4) < k;
+        ok[g] = (j0 + g * 128 + lane * 4) < kr;
       }
-      const float* cbase = Ct + j0 + lane * 4;
+      const float* cbase = Ct + rg.koff + j0 + lane * 4;
       for (int64_t p0 = b; p0 < e; p0 += 32) {
         int tt = 0;
         float vv = 0.f;
@@ -114,9 +119,9 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int j = j0 + g * 128 + lane * 4 + c;
-          if (j < k) {
+          if (j < kr) {
             const float s = __fmul_rn(av[c], ri);
-            if (MODE == 2) ub[i * kst + j] = __fadd_ru(s, dl);
+            if (MODE == 2) ub[rg.ubase + j] = __fadd_ru(s, dl);
             if (j == cur) vcur = s;
             if (s > v1) {
               v2 = v1;
@@ -153,13 +158,13 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
       ssec = v2;
     }
     if (lane == 0) {
-      a[i] = nb;
+      a[i] = rg.koff + nb;
       my_changed += (nb != cur);
-      my_sims += (unsigned long long)k;
+      my_sims += (unsigned long long)kr;
       if (MODE >= 1) lb[i] = __fsub_rd(v1, dl);
-      if (MODE == 1) ub[i] = (k > 1) ? __fadd_ru(ssec, dl) : -1.f;
+      if (MODE == 1) ub[i] = (kr > 1) ? __fadd_ru(ssec, dl) : -1.f;
     }
-    if (nb != cur) chb.push((int32_t)i, cur, chg_i, chg_old, cnt);
+    if (nb != cur) chb.push((int32_t)i, cur < 0 ? -1 : rg.koff + cur, chg_i, chg_old, cnt);
   }
   chb.flush(chg_i, chg_old, cnt);
   if (lane == 0) {
@@ -269,7 +274,9 @@ __device__ __forceinline__ bool elk_cand(int j, int32_t ai, float u, float L, co
 constexpr int kTile = 8;
 
 template <bool FULL>
-__global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int64_t kst, const int32_t* __restrict__ a,
+__global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int64_t kst,
+                                                       const int32_t* __restrict__ row_run,
+                                                       const RunDesc* __restrict__ runs, const int32_t* __restrict__ a,
                                                        float* __restrict__ lb, float* __restrict__ ub,
                                                        const float* __restrict__ dlt, const float* __restrict__ pdn,
                                                        const float* __restrict__ pup, const float* __restrict__ qup,
@@ -298,18 +305,23 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
     unsigned few = 0, many = 0;
     for (int r = 0; r < rows; ++r) {
       const int64_t i = i0 + r;
-      const int32_t ai = __shfl_sync(SKM_FULL_MASK, my_a, r);
+      const RowGeom rg = row_geom(i, k, kst, cap, row_run, runs);
+      const int32_t kr = rg.k;
+      const int32_t ai = __shfl_sync(SKM_FULL_MASK, my_a, r) - rg.koff;  // local
       const float L = __shfl_sync(SKM_FULL_MASK, my_L, r);
       const bool skip_pt = __shfl_sync(SKM_FULL_MASK, (int)my_skip, r) != 0;
-      float* urow = ub + i * kst;
+      float* urow = ub + rg.ubase;
       const float* ccrow = cc + (int64_t)ai * kst;
+      const float* pdr = pdn + rg.koff;
+      const float* pur = pup + rg.koff;
+      const float* qr = qup + rg.koff;
       int mine = 0;
-      for (int j4 = lane * 4; j4 < k; j4 += 128) {
+      for (int j4 = lane * 4; j4 < kr; j4 += 128) {
         float4 u4 = *reinterpret_cast<const float4*>(urow + j4);
         if (moved) {
-          const float4 pd = *reinterpret_cast<const float4*>(pdn + j4);
-          const float4 pu = *reinterpret_cast<const float4*>(pup + j4);
-          const float4 q = *reinterpret_cast<const float4*>(qup + j4);
+          const float4 pd = *reinterpret_cast<const float4*>(pdr + j4);
+          const float4 pu = *reinterpret_cast<const float4*>(pur + j4);
+          const float4 q = *reinterpret_cast<const float4*>(qr + j4);
           u4.x = bound_u(u4.x, pd.x, pu.x, q.x);
           u4.y = bound_u(u4.y, pd.y, pu.y, q.y);
           u4.z = bound_u(u4.z, pd.z, pu.z, q.z);
@@ -317,15 +329,15 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
           *reinterpret_cast<float4*>(urow + j4) = u4;
         }
         if (!skip_pt) {
-          mine += (j4 + 0 < k) && elk_cand<FULL>(j4 + 0, ai, u4.x, L, ccrow);
-          mine += (j4 + 1 < k) && elk_cand<FULL>(j4 + 1, ai, u4.y, L, ccrow);
-          mine += (j4 + 2 < k) && elk_cand<FULL>(j4 + 2, ai, u4.z, L, ccrow);
-          mine += (j4 + 3 < k) && elk_cand<FULL>(j4 + 3, ai, u4.w, L, ccrow);
+          mine += (j4 + 0 < kr) && elk_cand<FULL>(j4 + 0, ai, u4.x, L, ccrow);
+          mine += (j4 + 1 < kr) && elk_cand<FULL>(j4 + 1, ai, u4.y, L, ccrow);
+          mine += (j4 + 2 < kr) && elk_cand<FULL>(j4 + 2, ai, u4.z, L, ccrow);
+          mine += (j4 + 3 < kr) && elk_cand<FULL>(j4 + 3, ai, u4.w, L, ccrow);
         }
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(SKM_FULL_MASK, mine, o);
-      if (mine > cap) many |= 1u << r;
+      if (mine > rg.cap) many |= 1u << r;
       else if (mine > 0) few |= 1u << r;
     }
     warp_push((few >> lane) & 1u, (int32_t)(i0 + lane), w1, cnt + C_W1);
@@ -397,7 +409,8 @@ template <typename VT, bool FULL>
 __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
-    int64_t kst, const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt,
+    int64_t kst, const int32_t* __restrict__ row_run, const RunDesc* __restrict__ runs,
+    const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt,
     int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, const float* __restrict__ cc,
     int32_t* __restrict__ w2, int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
     unsigned long long* __restrict__ cnt) {
@@ -410,24 +423,26 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
   unsigned long long sims = 0, changed = 0;
   for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total; slot += ngroups) {
     const int32_t i = w1[slot];
-    const int32_t ai = a[i];
+    const RowGeom rg = row_geom(i, k, kst, 0, row_run, runs);
+    const int32_t kr = rg.k;
+    const int32_t ai = a[i] - rg.koff;  // local center ids from here on
     const float dl = dlt[i];
     const float L = __fsub_rd(lb[i], 2.f * dl);
-    float* urow = ub + (int64_t)i * kst;
+    float* urow = ub + rg.ubase;
     const float* ccrow = cc + (int64_t)ai * kst;
     __syncwarp(gmask);
     if (gl == 0) sj[0] = ai;
     // candidates: lane gl scans 4 consecutive centers per step of 32
     int m = 0;
-    for (int j0 = 0; j0 < k; j0 += 32) {
+    for (int j0 = 0; j0 < kr; j0 += 32) {
       const int jb = j0 + gl * 4;
       unsigned bits = 0;
-      if (jb < k) {
+      if (jb < kr) {
         const float4 u4 = *reinterpret_cast<const float4*>(urow + jb);
-        bits |= ((jb + 0 < k) && elk_cand<FULL>(jb + 0, ai, u4.x, L, ccrow)) ? 1u : 0u;
-        bits |= ((jb + 1 < k) && elk_cand<FULL>(jb + 1, ai, u4.y, L, ccrow)) ? 2u : 0u;
-        bits |= ((jb + 2 < k) && elk_cand<FULL>(jb + 2, ai, u4.z, L, ccrow)) ? 4u : 0u;
-        bits |= ((jb + 3 < k) && elk_cand<FULL>(jb + 3, ai, u4.w, L, ccrow)) ? 8u : 0u;
+        bits |= ((jb + 0 < kr) && elk_cand<FULL>(jb + 0, ai, u4.x, L, ccrow)) ? 1u : 0u;
+        bits |= ((jb + 1 < kr) && elk_cand<FULL>(jb + 1, ai, u4.y, L, ccrow)) ? 2u : 0u;
+        bits |= ((jb + 2 < kr) && elk_cand<FULL>(jb + 2, ai, u4.z, L, ccrow)) ? 4u : 0u;
+        bits |= ((jb + 3 < kr) && elk_cand<FULL>(jb + 3, ai, u4.w, L, ccrow)) ? 8u : 0u;
       }
       const int nb = __popc(bits);
       int incl = nb;
@@ -454,7 +469,8 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     }
     const int my_j = (gl <= m) ? sj[gl] : -1;
     const int64_t b = rp[i], e = rp[i + 1];
-    const float sim = __fmul_rn(group8_dot<VT>(b, e, col, val, Ct, kst, my_j, gmask, gl), rinv[i]);
+    const float sim =
+        __fmul_rn(group8_dot<VT>(b, e, col, val, Ct, kst, my_j >= 0 ? rg.koff + my_j : -1, gmask, gl), rinv[i]);
     const float sa = __shfl_sync(gmask, sim, 0, 8);
     // best candidate: largest similarity, lowest index among equal ones
     float bv = (gl >= 1 && gl <= m) ? sim : -INFINITY;
@@ -471,13 +487,13 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     if (gl >= 1 && gl <= m) urow[my_j] = __fadd_ru(sim, dl);
     if (gl == 0) {
       if (m > 0 && bv > sa) {
-        a[i] = bj;
+        a[i] = rg.koff + bj;
         lb[i] = __fsub_rd(bv, dl);
         urow[ai] = __fadd_ru(sa, dl);
         ++changed;
         const unsigned long long pos = atomicAdd(cnt + C_CHG, 1ull);
         chg_i[pos] = i;
-        chg_old[pos] = ai;
+        chg_old[pos] = rg.koff + ai;
       } else {
         lb[i] = __fsub_rd(sa, dl);
       }
@@ -496,11 +512,15 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
   }
 }
 
-inline int persistent_grid(const skm_ctx* c, int per_sm = 8) { return c->nsm * per_sm; }
+// Persistent kernels: blocks per SM from the options (skm_autotune), else 8.
+inline int persistent_grid(const skm_ctx* c) {
+  const int per_sm = c->opt.blocks_per_sm > 0 ? c->opt.blocks_per_sm : 8;
+  return c->nsm * per_sm;
+}
 
 template <typename VT, int G>
 int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
-  int64_t g = list ? (int64_t)persistent_grid(c, 8) : (nrows * 32 + kBlock - 1) / kBlock;
+  int64_t g = list ? (int64_t)persistent_grid(c) : (nrows * 32 + kBlock - 1) / kBlock;
   const int64_t cap = (int64_t)c->nsm * 16;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
@@ -509,15 +529,15 @@ int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long l
   switch (mode) {
     case 0:
       k_rows_top2<VT, G, 0><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+                                                                 c->row_run, c->runs, list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
       break;
     case 1:
       k_rows_top2<VT, G, 1><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+                                                                 c->row_run, c->runs, list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
       break;
     default:
       k_rows_top2<VT, G, 2><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+                                                                 c->row_run, c->runs, list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
   }
   SKM_LAUNCHED(c);
   return SKM_OK;
@@ -526,7 +546,8 @@ int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long l
 template <typename VT>
 int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
   const int k = c->k;
-  if (k <= 128) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows);
+  // a batch walks each row's own slice 128 centers at a time
+  if (k <= 128 || c->nruns > 0) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows);
   if (k <= 256) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows);
   if (k <= 512) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows);
   return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows);
@@ -568,22 +589,23 @@ int elkan_step_t(skm_ctx* c) {
   if (row_thresh > 7) row_thresh = 7;
   SKM_PROF_BEGIN(c, "k_elk_bounds");
   if (full) {
-    k_elk_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
+    k_elk_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->row_run, c->runs, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
                                                 c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1, c->w2, c->cnt);
   } else {
-    k_elk_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
+    k_elk_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->row_run, c->runs, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
                                                  c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1, c->w2, c->cnt);
   }
   SKM_LAUNCHED(c);
   const VT* v = (const VT*)c->val;
   SKM_PROF_BEGIN(c, "k_elk_recompute");
   if (full) {
-    k_elk_recompute<VT, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->w1,
+    k_elk_recompute<VT, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
+                                                       c->row_run, c->runs, c->w1,
                                                        c->cnt + C_W1, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i,
                                                        c->chg_old, c->cnt);
   } else {
     k_elk_recompute<VT, false><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                        c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, c->cc, c->w2,
+                                                        c->row_run, c->runs, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, c->cc, c->w2,
                                                         c->chg_i, c->chg_old, c->cnt);
   }
   SKM_LAUNCHED(c);

@@ -86,20 +86,36 @@ __global__ void k_term_count(const int32_t* __restrict__ col, int64_t nnz, unsig
     atomicAdd(tc + col[p], 1ull);
 }
 
+// Batch: the columns of the term-major copy are (run, term) pairs, key =
+// run * d + term, so that each run's center sums see only its own rows.
+__global__ void __launch_bounds__(256) k_term_count_runs(const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col, int64_t n,
+                                                         const int32_t* __restrict__ row_run, int64_t d,
+                                                         unsigned long long* __restrict__ tc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const int64_t base = (int64_t)row_run[i] * d;
+    for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) atomicAdd(tc + base + col[p], 1ull);
+  }
+}
+
 // Warp per row: place each entry, already normalised (x = v / |row|, FP32),
 // in its term's column.  The order inside a column is arbitrary; the center
 // sum is exact (fixed point), so the order cannot change any result.
 template <typename VT>
 __global__ void __launch_bounds__(256) k_scatter(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                  const VT* __restrict__ val, const float* __restrict__ rinv,
-                                                 int64_t n, unsigned long long* __restrict__ cursor,
+                                                 int64_t n, const int32_t* __restrict__ row_run, int64_t d,
+                                                 unsigned long long* __restrict__ cursor,
                                                  int32_t* __restrict__ t_row, float* __restrict__ t_x) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
     const float ri = rinv[i];
+    const int64_t base = row_run ? (int64_t)row_run[i] * d : 0;
     for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
-      const unsigned long long pos = atomicAdd(cursor + col[p], 1ull);
+      const unsigned long long pos = atomicAdd(cursor + base + col[p], 1ull);
       t_row[pos] = (int32_t)i;
       t_x[pos] = __fmul_rn(to_f32(val[p]), ri);
     }
@@ -176,6 +192,7 @@ __global__ void k_init_centers(const int64_t* __restrict__ rp, const int32_t* __
   const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (j >= k) return;
   const int64_t r = rows[j];
+  if (r < 0) return;  // padding column of a batch: stays zero
   const float ri = rinv[r];
   for (int64_t p = rp[r] + lane; p < rp[r + 1]; p += 32) Ct[(int64_t)col[p] * kst + j] = __fmul_rn(to_f32(val[p]), ri);
 }
@@ -245,7 +262,8 @@ int prep_rows_t(skm_ctx* c) {
 template <typename VT>
 int prep_transpose_t(skm_ctx* c) {
   cudaStream_t st = c->st;
-  const int64_t d = c->d, nnz = c->nnz;
+  // columns: terms, or (run, term) pairs for a batch
+  const int64_t d = c->d * (c->nruns > 0 ? c->nruns : 1), nnz = c->nnz;
   unsigned long long* tc = nullptr;
   int64_t *nch = nullptr, *npart = nullptr, *ism = nullptr, *ch_ptr = nullptr, *pbase = nullptr, *mpos = nullptr;
   SKM_CUDA_TRY(cudaMallocAsync((void**)&tc, sizeof(unsigned long long) * (d + 1), st));
@@ -254,14 +272,18 @@ int prep_transpose_t(skm_ctx* c) {
   SKM_CUDA_TRY(cudaMallocAsync((void**)&c->t_row, sizeof(int32_t) * (nnz > 0 ? nnz : 1), st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&c->t_val, sizeof(float) * (nnz > 0 ? nnz : 1), st));
   if (nnz > 0) {
-    k_term_count<<<grid_for(nnz, 256, c->nsm, 32), 256, 0, st>>>(c->col, nnz, tc);
+    if (c->nruns > 0)
+      k_term_count_runs<<<grid_for(c->n * 32, 256, c->nsm), 256, 0, st>>>(c->rp, c->col, c->n, c->row_run, c->d, tc);
+    else
+      k_term_count<<<grid_for(nnz, 256, c->nsm, 32), 256, 0, st>>>(c->col, nnz, tc);
     SKM_LAUNCH_CHECK();
   }
   k_scan_i64<<<1, 1024, 0, st>>>((const int64_t*)tc, c->t_ptr, d);
   SKM_LAUNCH_CHECK();
   SKM_CUDA_TRY(cudaMemcpyAsync(tc, c->t_ptr, sizeof(int64_t) * d, cudaMemcpyDeviceToDevice, st));
   k_scatter<VT><<<grid_for(c->n * 32, 256, c->nsm), 256, 0, st>>>(c->rp, c->col, (const VT*)c->val, c->rinv, c->n,
-                                                                   tc, c->t_row, (float*)c->t_val);
+                                                                   c->nruns > 0 ? c->row_run : nullptr, c->d, tc,
+                                                                   c->t_row, (float*)c->t_val);
   SKM_LAUNCH_CHECK();
   // chunk tables
   SKM_CUDA_TRY(cudaMallocAsync((void**)&nch, sizeof(int64_t) * (d + 1), st));
@@ -293,7 +315,8 @@ int prep_transpose_t(skm_ctx* c) {
   SKM_CUDA_TRY(cudaMallocAsync((void**)&c->multi_term, sizeof(int32_t) * nm, st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&c->multi_base, sizeof(int64_t) * nm, st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&c->multi_cnt, sizeof(int32_t) * nm, st));
-  SKM_CUDA_TRY(cudaMallocAsync((void**)&c->part64, sizeof(long long) * (c->nparts > 0 ? c->nparts : 1) * c->k, st));
+  const int64_t kbins = c->nruns > 0 ? c->kmax : c->k;
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&c->part64, sizeof(long long) * (c->nparts > 0 ? c->nparts : 1) * kbins, st));
   k_chunk_fill<<<grid_for(d, 256, c->nsm), 256, 0, st>>>(ch_ptr, pbase, mpos, d, c->ch_term, c->ch_idx, c->ch_part,
                                                           c->multi_term, c->multi_base, c->multi_cnt);
   SKM_LAUNCH_CHECK();

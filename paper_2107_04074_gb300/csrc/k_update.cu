@@ -50,25 +50,52 @@ __device__ __forceinline__ float from_fixed(long long s, float inv) { return __f
 // Full recompute.  fx = round(x * 2^s) is split into hi = fx >> 20 and
 // lo = fx & (2^20 - 1); a chunk holds at most 2^10 entries, so both halves sum
 // exactly in 32-bit integers and the shared atomics are native 32-bit ones.
+// A column of the term-major copy: a term, or for a batch a (run, term)
+// pair whose sums fill the run's slice koff .. koff + kw of the term's row.
+struct SumCol {
+  int64_t t;
+  int32_t koff, k, kw;
+};
+__device__ __forceinline__ SumCol sum_col(int64_t key, int32_t k, int64_t kst, const RunDesc* __restrict__ runs,
+                                          int64_t dterm) {
+  SumCol c;
+  if (!runs) {
+    c.t = key;
+    c.koff = 0;
+    c.k = k;
+    c.kw = (int32_t)kst;
+  } else {
+    const int64_t r = key / dterm;
+    c.t = key - r * dterm;
+    c.koff = runs[r].koff;
+    c.k = runs[r].k;
+    c.kw = runs[r].kst;
+  }
+  return c;
+}
+
 __global__ void __launch_bounds__(256) k_center_sum(int64_t nchunks, const int32_t* __restrict__ ch_term,
                                                     const int32_t* __restrict__ ch_idx,
                                                     const int64_t* __restrict__ ch_part,
                                                     const int64_t* __restrict__ t_ptr, const int32_t* __restrict__ t_row,
                                                     const float* __restrict__ t_x, const int32_t* __restrict__ a,
-                                                    int32_t k, int64_t kst, float scale, long long* __restrict__ S64,
-                                                    long long* __restrict__ part, int s64_valid,
-                                                    const unsigned long long* __restrict__ cnt, int64_t n) {
+                                                    int32_t k, int64_t kst, const RunDesc* __restrict__ runs,
+                                                    int64_t dterm, int32_t kbins, float scale,
+                                                    long long* __restrict__ S64, long long* __restrict__ part,
+                                                    int s64_valid, const unsigned long long* __restrict__ cnt,
+                                                    int64_t n) {
   if (!full_update(s64_valid, cnt, n)) return;
   extern __shared__ int bins_all[];
   const int lane = threadIdx.x & 31;
-  int* hi = bins_all + (int64_t)(threadIdx.x >> 5) * 2 * k;
-  int* lo = hi + k;
+  int* hi = bins_all + (int64_t)(threadIdx.x >> 5) * 2 * kbins;
+  int* lo = hi + kbins;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nchunks; g += nw) {
-    const int64_t t = ch_term[g];
-    const int64_t b = t_ptr[t] + (int64_t)ch_idx[g] * kChunk;
-    const int64_t e = min(t_ptr[t + 1], b + kChunk);
-    for (int j = lane; j < k; j += 32) {
+    const int64_t key = ch_term[g];
+    const SumCol sc = sum_col(key, k, kst, runs, dterm);
+    const int64_t b = t_ptr[key] + (int64_t)ch_idx[g] * kChunk;
+    const int64_t e = min(t_ptr[key + 1], b + kChunk);
+    for (int j = lane; j < sc.k; j += 32) {
       hi[j] = 0;
       lo[j] = 0;
     }
@@ -86,7 +113,7 @@ __global__ void __launch_bounds__(256) k_center_sum(int64_t nchunks, const int32
       }
       int32_t lab[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) lab[u] = r[u] >= 0 ? a[r[u]] : -1;
+      for (int u = 0; u < 4; ++u) lab[u] = r[u] >= 0 ? a[r[u]] - sc.koff : -1;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (lab[u] >= 0) {
@@ -97,38 +124,41 @@ __global__ void __launch_bounds__(256) k_center_sum(int64_t nchunks, const int32
     }
     __syncwarp();
     const int64_t ps = ch_part[g];
-    long long* dst = ps < 0 ? S64 + t * kst : part + ps * k;
-    const int lim = ps < 0 ? (int)kst : k;
-    for (int j = lane; j < lim; j += 32) dst[j] = (j < k) ? ((long long)hi[j] << 20) + (long long)lo[j] : 0ll;
+    long long* dst = ps < 0 ? S64 + sc.t * kst + sc.koff : part + ps * kbins;
+    const int lim = ps < 0 ? sc.kw : sc.k;
+    for (int j = lane; j < lim; j += 32) dst[j] = (j < sc.k) ? ((long long)hi[j] << 20) + (long long)lo[j] : 0ll;
     __syncwarp();
   }
 }
 
 __global__ void k_center_sum_multi(int64_t nmulti, const int32_t* __restrict__ mterm, const int64_t* __restrict__ mbase,
                                    const int32_t* __restrict__ mcnt, const long long* __restrict__ part, int32_t k,
-                                   int64_t kst, long long* __restrict__ S64, int s64_valid,
+                                   int64_t kst, const RunDesc* __restrict__ runs, int64_t dterm, int32_t kbins,
+                                   long long* __restrict__ S64, int s64_valid,
                                    const unsigned long long* __restrict__ cnt, int64_t n) {
   if (!full_update(s64_valid, cnt, n)) return;
-  const int64_t total = nmulti * kst;
+  const int64_t kbw = runs ? kbins : kst;  // slice width iterated per column
+  const int64_t total = nmulti * kbw;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t m = q / kst;
-    const int j = (int)(q - m * kst);
-    const int64_t t = mterm[m];
+    const int64_t m = q / kbw;
+    const int j = (int)(q - m * kbw);
+    const SumCol sc = sum_col(mterm[m], k, kst, runs, dterm);
+    if (j >= sc.kw) continue;
     long long s = 0;
-    if (j < k) {
-      const long long* pr = part + mbase[m] * k + j;
+    if (j < sc.k) {
+      const long long* pr = part + mbase[m] * kbins + j;
       const int nc = mcnt[m];
       int c = 0;
       for (; c + 8 <= nc; c += 8) {
         long long v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = pr[(int64_t)(c + u) * k];
+        for (int u = 0; u < 8; ++u) v[u] = pr[(int64_t)(c + u) * kbins];
 #pragma unroll
         for (int u = 0; u < 8; ++u) s += v[u];
       }
-      for (; c < nc; ++c) s += pr[(int64_t)c * k];
+      for (; c < nc; ++c) s += pr[(int64_t)c * kbins];
     }
-    S64[t * kst + j] = s;
+    S64[sc.t * kst + sc.koff + j] = s;
   }
 }
 
@@ -635,22 +665,24 @@ int update_centers(skm_ctx* c) {
     return finish_update(c);
   }
   // ---- sums: a full recompute, or only the changed rows (decided on the device)
-  int wpb = (int)((96 * 1024) / ((int64_t)k * 8));  // two int32 bins per cluster per warp
+  const int32_t kbins = c->nruns > 0 ? c->kmax : k;
+  int wpb = (int)((96 * 1024) / ((int64_t)kbins * 8));  // two int32 bins per cluster per warp
   if (wpb > 8) wpb = 8;
   if (wpb < 1) wpb = 1;
-  const size_t smem = (size_t)wpb * k * 8;
+  const size_t smem = (size_t)wpb * kbins * 8;
   if (smem > 48 * 1024)
     SKM_CUDA_TRY(cudaFuncSetAttribute(k_center_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   SKM_PROF_BEGIN(c, "k_center_sum");
   k_center_sum<<<grid_cap(c->nchunks, wpb, c->nsm), wpb * 32, smem, c->st>>>(
       c->nchunks, c->ch_term, c->ch_idx, c->ch_part, c->t_ptr, c->t_row, (const float*)c->t_val, c->a, k, c->kst,
-      c->fx_scale, c->S64, c->part64, c->s64_valid, c->cnt, c->n);
+      c->runs, c->d, kbins, c->fx_scale, c->S64, c->part64, c->s64_valid, c->cnt, c->n);
   SKM_LAUNCHED(c);
   if (c->nmulti > 0) {
+    const int64_t kbw = c->nruns > 0 ? kbins : c->kst;
     SKM_PROF_BEGIN(c, "k_center_sum_multi");
-    k_center_sum_multi<<<grid_cap(c->nmulti * c->kst, 256, c->nsm), 256, 0, c->st>>>(
-        c->nmulti, c->multi_term, c->multi_base, c->multi_cnt, c->part64, k, c->kst, c->S64, c->s64_valid, c->cnt,
-        c->n);
+    k_center_sum_multi<<<grid_cap(c->nmulti * kbw, 256, c->nsm), 256, 0, c->st>>>(
+        c->nmulti, c->multi_term, c->multi_base, c->multi_cnt, c->part64, k, c->kst, c->runs, c->d, kbins, c->S64,
+        c->s64_valid, c->cnt, c->n);
     SKM_LAUNCHED(c);
   }
   int rc = SKM_OK;

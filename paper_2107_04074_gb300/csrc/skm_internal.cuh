@@ -230,6 +230,43 @@ __device__ __forceinline__ bool full_update(int s64_valid, const unsigned long l
 // ---------------------------------------------------------------- context
 }  // namespace skm
 
+constexpr int kLogCap = 256;  // iterations a graph replay logs between host reads
+
+// One run of a batch (many independent clusterings in one context): rows
+// [row0, row0 + n) of the concatenated data, centers koff .. koff + k - 1 in
+// global numbering (the run's slice of the term-major arrays is kst wide, a
+// multiple of 8, so koff is too), Elkan bound rows of kst floats from uoff.
+// Labels are global center ids.
+struct RunDesc {
+  int64_t row0, n, uoff;
+  int32_t koff, k, kst, cap;
+};
+
+// Where a row's centers and bounds live: its run's slice, or for a single
+// run the whole center range.
+struct RowGeom {
+  int64_t ubase;
+  int32_t koff, k, cap;
+};
+__device__ __forceinline__ RowGeom row_geom(int64_t i, int32_t k, int64_t kst, int32_t cap,
+                                            const int32_t* __restrict__ row_run,
+                                            const RunDesc* __restrict__ runs) {
+  RowGeom g;
+  if (!runs) {
+    g.ubase = i * kst;
+    g.koff = 0;
+    g.k = k;
+    g.cap = cap;
+  } else {
+    const RunDesc& R = runs[row_run[i]];
+    g.ubase = R.uoff + (i - R.row0) * (int64_t)R.kst;
+    g.koff = R.koff;
+    g.k = R.k;
+    g.cap = R.cap;
+  }
+  return g;
+}
+
 struct skm_ctx {
   cudaStream_t st;
   int dev;
@@ -238,6 +275,18 @@ struct skm_ctx {
   int64_t n, d, nnz;
   int32_t k, kst;  // kst = row stride of the term-major center arrays (k rounded up to 8)
   int32_t variant, layout, dtype;
+  // batch of independent runs (nruns == 0: a single run)
+  int32_t nruns;
+  int32_t kmax;         // widest run slice (bins of the center sums)
+  RunDesc* runs;        // [nruns] device
+  int32_t* row_run;     // [n] run of each row
+  void* hruns;          // std::vector<RunDesc> host copy
+  void* hinit;          // std::vector<int64_t>: the initial rows (global), for resets
+  // whole iteration as a CUDA graph (skm_run with opt.graph)
+  cudaGraphExec_t gexec;
+  cudaStream_t cap_st;
+  int64_t gkernels;       // kernel nodes in the graph
+  unsigned long long* glog;  // [2 + 2 * kLogCap]: position, then (changed, sims) per iteration
   skm_options opt;
   // data (borrowed, or owned copies when given in host memory)
   const int64_t* rp;

@@ -28,7 +28,8 @@ DEVICE, HOST = 0, 1
 EXPORTS = ["skm_default_options", "skm_init", "skm_reset", "skm_assign", "skm_update_centers", "skm_run",
            "skm_get_labels", "skm_get_centers", "skm_set_centers", "skm_set_labels", "skm_get_bounds",
            "skm_get_stats", "skm_bound_bytes", "skm_kernel_launches", "skm_profile", "skm_profile_read",
-           "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_topk"]
+           "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_topk", "skm_batch_init",
+           "skm_autotune"]
 
 
 class SkmError(RuntimeError):
@@ -45,7 +46,8 @@ class skm_data(ctypes.Structure):
 
 class skm_options(ctypes.Structure):
     _fields_ = [("hamerly_tight", ctypes.c_int32), ("validate", ctypes.c_int32), ("row_threshold", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 8)]
+                ("precision", ctypes.c_int32), ("graph", ctypes.c_int32), ("graph_check", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class skm_stats(ctypes.Structure):
@@ -95,6 +97,8 @@ def load(build_if_missing: bool = True):
         "skm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "skm_assign_noalloc": (ctypes.c_int, [P, i32, P, P, P, P]),
         "skm_get_bf16_topk": (ctypes.c_int, [P, P, P, P, i32]),
+        "skm_batch_init": (ctypes.c_int, [P, P, P, P, i32, i32, P, u64, P, P]),
+        "skm_autotune": (ctypes.c_int, [P, ctypes.c_char_p, i32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -184,7 +188,7 @@ class KMeans:
 
     def __init__(self, n: int, d: int, row_ptr, col_idx, values, k: int, variant="standard", init_rows=None,
                  seed: int = 0, hamerly_tight: bool = False, row_threshold: int = 0, stream=None,
-                 precision: str = "fp32"):
+                 precision: str = "fp32", graph: bool = False, graph_check: int = 0, blocks_per_sm: int = 0):
         lib = load()
         host = isinstance(values, np.ndarray)
         self._keep = (row_ptr, col_idx, values)
@@ -197,6 +201,9 @@ class KMeans:
         opt.hamerly_tight = 1 if hamerly_tight else 0
         opt.precision = {"fp32": PREC_FP32, "bf16": PREC_BF16}[precision]
         opt.row_threshold = int(row_threshold)
+        opt.graph = 1 if graph else 0
+        opt.graph_check = int(graph_check)
+        opt.blocks_per_sm = int(blocks_per_sm)
         self.n, self.d, self.k = int(n), int(d), int(k)
         self.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         rows = None
@@ -311,8 +318,71 @@ class KMeans:
                "skm_get_bf16_topk")
         return vals, idx, eps.value
 
+    def autotune(self, cache_path=None, iters: int = 3) -> bool:
+        """Pick the persistent kernels' launch shape (and the Elkan whole-row
+        threshold) by timing; True when the choice came from cache_path."""
+        fc = ctypes.c_int32(0)
+        path = None if cache_path is None else str(cache_path).encode()
+        _check(load().skm_autotune(self._h, path, int(iters), ctypes.byref(fc)), "skm_autotune")
+        return bool(fc.value)
+
     def stats(self) -> Stats:
         s = skm_stats()
         _check(load().skm_get_stats(self._h, ctypes.byref(s)), "skm_get_stats")
         return Stats(s.iterations, s.last_changed, s.last_sims, s.total_sims, s.last_survivors, s.last_rechecks,
                      s.objective, s.last_cand_rechecks)
+
+
+class Batch(KMeans):
+    """Batched form: independent runs over row blocks of one CSR matrix.
+
+    run_rows: nruns + 1 row offsets; ks: centers per run; init_rows: for each
+    run in order ks[r] row indices local to the run (or None: seeded).
+    labels() are local to each run; centers() stacks the runs' centers.
+    """
+
+    def __init__(self, n: int, d: int, row_ptr, col_idx, values, run_rows, ks, variant="simp_elkan",
+                 init_rows=None, seed: int = 0, row_threshold: int = 0, stream=None, graph: bool = False,
+                 graph_check: int = 0, blocks_per_sm: int = 0):
+        lib = load()
+        host = isinstance(values, np.ndarray)
+        self._keep = (row_ptr, col_idx, values)
+        data = skm_data(n=n, d=d, layout=CSR, dtype=_dtype_code(values.dtype), memspace=HOST if host else DEVICE,
+                        reserved=0, row_ptr=_ptr(row_ptr), col_idx=_ptr(col_idx), values=_ptr(values))
+        opt = skm_options()
+        lib.skm_default_options(ctypes.byref(opt))
+        opt.row_threshold = int(row_threshold)
+        opt.graph = 1 if graph else 0
+        opt.graph_check = int(graph_check)
+        opt.blocks_per_sm = int(blocks_per_sm)
+        self.run_rows = np.ascontiguousarray(np.asarray(run_rows, dtype=np.int64))
+        self.ks = np.ascontiguousarray(np.asarray(ks, dtype=np.int32))
+        self.nruns = len(self.ks)
+        if self.run_rows.shape != (self.nruns + 1,):
+            raise ValueError("run_rows must have nruns + 1 entries")
+        self.n, self.d, self.k = int(n), int(d), int(self.ks.sum())
+        self.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        rows = None
+        if init_rows is not None:
+            rows = np.ascontiguousarray(np.asarray(init_rows, dtype=np.int64))
+            if rows.shape != (self.k,):
+                raise ValueError("init_rows must have sum(ks) entries")
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream if not host else 0
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(lib.skm_batch_init(ctypes.byref(h), ctypes.byref(data), _ptr(self.run_rows), _ptr(self.ks),
+                                  self.nruns, self.variant, _ptr(rows), int(seed), ctypes.byref(opt),
+                                  ctypes.c_void_p(stream)), "skm_batch_init")
+        self._h = h
+
+    def run_centers(self, C=None):
+        """List of per-run center arrays (k_r x d) from centers()."""
+        C = self.centers() if C is None else C
+        off = np.concatenate([[0], np.cumsum(self.ks)])
+        return [C[off[r]:off[r + 1]] for r in range(self.nruns)]
+
+    def run_labels(self, lab=None):
+        lab = self.labels() if lab is None else lab
+        return [lab[self.run_rows[r]:self.run_rows[r + 1]] for r in range(self.nruns)]

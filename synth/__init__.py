@@ -181,3 +181,37 @@ def init_rows(n: int, k: int, seed: int) -> np.ndarray:
     out = np.empty(k, dtype=np.int64)
     _lib().synth_init_rows(n, k, seed, _ptr(out))
     return out
+
+
+# The batched workload: many independent runs of uneven size and k.
+BATCH_K_CHOICES = (10, 50, 100, 250, 500)
+
+
+def batch_runs(nruns: int = 64, d: int = 20_000, seed: int = 4, n_lo: int = 5_000, n_hi: int = 200_000,
+               k_choices=BATCH_K_CHOICES, row_cfg: SparseCfg = CSR_RCV1_LIKE):
+    """Recipes of `nruns` independent runs: run r has n_r rows with
+    ln n_r ~ Normal(ln sqrt(n_lo n_hi), (ln(n_hi / n_lo) / 4)^2) clipped to
+    [n_lo, n_hi], rows drawn like ``row_cfg`` over a vocabulary of d terms
+    with seed 1000 + r, and k_r uniform over k_choices.  Returns (list of
+    SparseCfg, numpy int32 array of k_r)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mu = 0.5 * (np.log(n_lo) + np.log(n_hi))
+    sigma = np.log(n_hi / n_lo) / 4.0
+    ns = np.clip(np.exp(rng.normal(mu, sigma, nruns)), n_lo, n_hi).astype(np.int64)
+    ks = np.asarray(k_choices, dtype=np.int32)[rng.integers(0, len(k_choices), nruns)]
+    cfgs = [SparseCfg(n=int(ns[r]), d=d, seed=1000 + r, nnz_kind=row_cfg.nnz_kind, a=row_cfg.a, b=row_cfg.b,
+                      lo=row_cfg.lo, hi=row_cfg.hi, zipf=row_cfg.zipf, dtype=row_cfg.dtype) for r in range(nruns)]
+    return cfgs, ks
+
+
+def concat(parts) -> tuple:
+    """Stack CSR blocks (same d) into one CSR; returns (CSR, run_rows)."""
+    d = parts[0].d
+    run_rows = np.zeros(len(parts) + 1, dtype=np.int64)
+    np.cumsum([p.n for p in parts], out=run_rows[1:])
+    nnz = np.zeros(len(parts) + 1, dtype=np.int64)
+    np.cumsum([p.nnz for p in parts], out=nnz[1:])
+    rp = np.concatenate([parts[0].row_ptr[:1]] + [p.row_ptr[1:] + nnz[r] for r, p in enumerate(parts)])
+    col = np.concatenate([p.col for p in parts])
+    val = np.concatenate([p.val for p in parts])
+    return CSR(int(run_rows[-1]), d, rp.astype(np.int64), col, val), run_rows
