@@ -340,7 +340,41 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(csr, init, variant)
+    if rank == 0 and not args.no_extras:
+        # the other two forms of the path, summarised (their own modes:
+        # --workload embed / batch); a failure there is reported, not fatal
+        del km, km_std, rp, col, val, flush
+        torch.cuda.empty_cache()
+        for key, fn in (("precision_form", summarize_embed), ("batched_form", summarize_batch)):
+            try:
+                out[key] = fn(args, rank, world, local)
+            except Exception as ex:  # noqa: BLE001
+                out[key] = {"error": f"{type(ex).__name__}: {ex}"}
+            torch.cuda.empty_cache()
     return out
+
+
+def summarize_embed(args, rank, world, local):
+    r = run_embed(args, rank, world, local)
+    p = r["paths"]
+    keep = ("iters", "iters_per_s")
+    return {"workload": r["workload"], "labels_identical_across_paths": r["labels_identical_across_paths"],
+            "iters_per_s": {k: v["iters_per_s"] for k, v in p.items()},
+            "speedup_bf16_vs_fp32_standard": r["speedup_bf16_vs_fp32_standard"],
+            "roofline": r["bf16_gemm_roofline"],
+            "rows_candidate_recheck_first_last": [p["standard/bf16"]["rows_candidate_recheck_per_iter"][0],
+                                                  p["standard/bf16"]["rows_candidate_recheck_per_iter"][-1]],
+            "note": "BF16 tcgen05 bulk with candidate selection, FP32 recheck; see --workload embed"} \
+        if all(k in p["standard/bf16"] for k in keep) else r
+
+
+def summarize_batch(args, rank, world, local):
+    a = argparse.Namespace(**vars(args))
+    a.steps, a.warmup = 2, 1
+    r = run_batch(a, rank, world, local)
+    r.pop("kernel_time_share", None)
+    r["note"] = "see --workload batch"
+    return r
 
 
 def trace_run(km, init, n, k):
@@ -538,6 +572,80 @@ def run_batch(args, rank, world, local):
                                   for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:12]}}
 
 
+def sampled_parity(km, csr, sample, prev, C):
+    """Teacher-forced check of the assignment just made from centers C on the
+    sampled rows against the FP64 oracle (labels differ only below the 1e-6
+    similarity gap).  Returns (rows checked, mismatches, near-ties)."""
+    import oracle
+    sub = csr.rows(sample)
+    X = oracle.Data.from_csr(sub)
+    want, _, _, _, gap = oracle.assign(X, oracle.rinv(X), C.astype(np.float64), prev[sample])
+    lab = km.labels()[sample]
+    diff = want != lab
+    return int(len(sample)), int(np.sum(diff & (gap >= 1e-6))), int(np.sum(diff & (gap < 1e-6)))
+
+
+def run_large(args, rank, world, local):
+    """Large sparse workload: n = 4e6 rows, d = 2e5, nnz/row lognormal(200,
+    0.9) clipped to [10, 5000] (~8e8 nnz), Zipf(1.05), FP16 values, k = 1000,
+    30 iterations; Elkan, Hamerly and standard at identical labels, with the
+    first and last assignments of the Elkan run checked against the FP64
+    oracle on 2000 sampled rows."""
+    import torch
+    from paper_2107_04074_gb300 import skm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.CSR_LARGE
+    if args.large_frac < 1.0:
+        cfg = synth.scaled(cfg, n=int(cfg.n * args.large_frac))
+    t0 = time.perf_counter()
+    csr = synth.tfidf(cfg)
+    gen_s = time.perf_counter() - t0
+    k, iters = 1000, 30
+    init = synth.init_rows(csr.n, k, cfg.seed)
+    stream = torch.cuda.current_stream(dev)
+    Xd = [torch.from_numpy(a).to(dev) for a in (csr.row_ptr, csr.col, csr.val)]
+    rng = np.random.Generator(np.random.PCG64(55))
+    sample = np.sort(rng.choice(csr.n, size=min(2000, csr.n), replace=False))
+    res, labels = {}, {}
+    for variant in ("elkan", "hamerly", "standard"):
+        km = skm.KMeans(csr.n, csr.d, *Xd, k, variant=variant, init_rows=init, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, J = km.run(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        labels[variant] = km.labels()
+        res[variant] = {"iterations": it, "ms": round(ms, 1), "iters_per_s": round(it / (ms / 1e3), 3),
+                        "sims_evaluated": km.stats().total_sims, "objective": J}
+        if variant == "elkan":
+            # teacher-forced oracle checks of the first and the last assignment
+            km.reset(init)
+            prev = np.full(csr.n, -1, np.int32)
+            checks = []
+            for t in range(it):
+                C = km.centers() if t in (0, it - 1) else None
+                km.assign()
+                if C is not None:
+                    checks.append({"iteration": t + 1, **dict(zip(("rows", "mismatches", "near_ties"),
+                                                                  sampled_parity(km, csr, sample, prev, C)))})
+                if t == it - 2:
+                    prev = km.labels()
+                if t < it - 1:
+                    km.update_centers()
+            res[variant]["oracle_sample"] = checks
+        km.close()
+    same = all(np.array_equal(v, labels["standard"]) for v in labels.values())
+    return {"workload": f"large sparse n={csr.n} d={csr.d} nnz={csr.nnz} (FP16 values) k={k} "
+                        f"{iters} iterations", "generate_s": round(gen_s, 1), "labels_identical": same,
+            "variants": res,
+            "speedup_elkan_vs_standard": round(res["elkan"]["iters_per_s"] / res["standard"]["iters_per_s"], 2),
+            "speedup_hamerly_vs_standard": round(res["hamerly"]["iters_per_s"] / res["standard"]["iters_per_s"], 2)}
+
+
 def cpu_baseline(csr, init, variant, iters=3):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
     first `iters` iterations of the same run on the full data."""
@@ -591,12 +699,15 @@ def main():
     ap.add_argument("--variant", default="simp_elkan", choices=["standard", "hamerly", "elkan", "simp_hamerly",
                                                                  "simp_elkan"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision-form and batched-form summaries of the default line")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed runs of the chosen variant (for profiler captures)")
-    ap.add_argument("--workload", default="rcv1", choices=["rcv1", "embed", "batch"],
+    ap.add_argument("--workload", default="rcv1", choices=["rcv1", "embed", "batch", "large"],
                     help="rcv1: the bench line; embed: the dense precision-form measurement; "
-                         "batch: the batched form")
+                         "batch: the batched form; large: the 8e8-nonzero sparse workload")
     ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--large-frac", type=float, default=1.0, help="fraction of the large workload's rows")
     ap.add_argument("--embed-n", type=int, default=1_000_000)
     ap.add_argument("--embed-iters", type=int, default=20)
     ap.add_argument("--trace", action="store_true",
@@ -614,6 +725,10 @@ def main():
     if args.workload == "batch":
         if rank == 0:
             print(json.dumps(run_batch(args, rank, world, local)), flush=True)
+        return
+    if args.workload == "large":
+        if rank == 0:
+            print(json.dumps(run_large(args, rank, world, local)), flush=True)
         return
     if world > 1:
         import torch

@@ -31,7 +31,7 @@ constexpr int kBlock = 256;
 // sum runs over the row entries in CSR order (the canonical order).
 // For a batch (runs != nullptr) each row works on its run's slice of the
 // centers (global ids koff + j) and its run's bound row.
-template <typename VT, int G, int MODE>
+template <typename VT, int G, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_rows_top2(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
   ChangedBuf chb;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
     const int64_t i = list ? (int64_t)list[w] : w;
-    const RowGeom rg = row_geom(i, k, kst, 0, row_run, runs);
+    const RowGeom rg = row_geom<BATCH>(i, k, kst, 0, row_run, runs);
     const int32_t kr = rg.k;
     const int64_t b = rp[i], e = rp[i + 1];
     const float ri = rinv[i];
@@ -273,7 +273,7 @@ __device__ __forceinline__ bool elk_cand(int j, int32_t ai, float u, float L, co
 // row); each list gets one atomic per tile.
 constexpr int kTile = 8;
 
-template <bool FULL>
+template <bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int64_t kst,
                                                        const int32_t* __restrict__ row_run,
                                                        const RunDesc* __restrict__ runs, const int32_t* __restrict__ a,
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
     unsigned few = 0, many = 0;
     for (int r = 0; r < rows; ++r) {
       const int64_t i = i0 + r;
-      const RowGeom rg = row_geom(i, k, kst, cap, row_run, runs);
+      const RowGeom rg = row_geom<BATCH>(i, k, kst, cap, row_run, runs);
       const int32_t kr = rg.k;
       const int32_t ai = __shfl_sync(SKM_FULL_MASK, my_a, r) - rg.koff;  // local
       const float L = __shfl_sync(SKM_FULL_MASK, my_L, r);
@@ -405,7 +405,7 @@ __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t*
 // variant's rule, because every center left out satisfies sim <= sim(a)
 // (bounds with the 2 delta margin).  The bound kernel only sends points with
 // 1..7 candidates here; anything else is recomputed as a whole row.
-template <typename VT, bool FULL>
+template <typename VT, bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
   unsigned long long sims = 0, changed = 0;
   for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total; slot += ngroups) {
     const int32_t i = w1[slot];
-    const RowGeom rg = row_geom(i, k, kst, 0, row_run, runs);
+    const RowGeom rg = row_geom<BATCH>(i, k, kst, 0, row_run, runs);
     const int32_t kr = rg.k;
     const int32_t ai = a[i] - rg.koff;  // local center ids from here on
     const float dl = dlt[i];
@@ -518,36 +518,40 @@ inline int persistent_grid(const skm_ctx* c) {
   return c->nsm * per_sm;
 }
 
-template <typename VT, int G>
-int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
+template <typename VT, int G, bool BATCH>
+int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
   int64_t g = list ? (int64_t)persistent_grid(c) : (nrows * 32 + kBlock - 1) / kBlock;
   const int64_t cap = (int64_t)c->nsm * 16;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   const VT* v = (const VT*)c->val;
   SKM_PROF_BEGIN(c, list ? "k_rows_top2(list)" : "k_rows_top2");
+#define SKM_ROWS(M)                                                                                              \
+  k_rows_top2<VT, G, M, BATCH><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, \
+                                                                  c->kst, c->row_run, c->runs, list, list_cnt,     \
+                                                                  nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, \
+                                                                  c->cnt)
   switch (mode) {
-    case 0:
-      k_rows_top2<VT, G, 0><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 c->row_run, c->runs, list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
-      break;
-    case 1:
-      k_rows_top2<VT, G, 1><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 c->row_run, c->runs, list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
-      break;
-    default:
-      k_rows_top2<VT, G, 2><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                                 c->row_run, c->runs, list, list_cnt, nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+    case 0: SKM_ROWS(0); break;
+    case 1: SKM_ROWS(1); break;
+    default: SKM_ROWS(2);
   }
+#undef SKM_ROWS
   SKM_LAUNCHED(c);
   return SKM_OK;
+}
+
+template <typename VT, int G>
+int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
+  return launch_rows_b<VT, G, false>(c, mode, list, list_cnt, nrows);
 }
 
 template <typename VT>
 int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
   const int k = c->k;
   // a batch walks each row's own slice 128 centers at a time
-  if (k <= 128 || c->nruns > 0) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows);
+  if (c->nruns > 0) return launch_rows_b<VT, 1, true>(c, mode, list, list_cnt, nrows);
+  if (k <= 128) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows);
   if (k <= 256) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows);
   if (k <= 512) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows);
   return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows);
@@ -588,26 +592,25 @@ int elkan_step_t(skm_ctx* c) {
   int32_t row_thresh = c->opt.row_threshold > 0 ? c->opt.row_threshold : (c->k + 7) / 8;
   if (row_thresh > 7) row_thresh = 7;
   SKM_PROF_BEGIN(c, "k_elk_bounds");
-  if (full) {
-    k_elk_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->row_run, c->runs, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
-                                                c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1, c->w2, c->cnt);
-  } else {
-    k_elk_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->row_run, c->runs, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup,
-                                                 c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1, c->w2, c->cnt);
-  }
+#define SKM_ELKB(F, B)                                                                                            \
+  k_elk_bounds<F, B><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->row_run, c->runs, c->a, c->lb, c->ub, c->dlt, \
+                                              c->pdn, c->pup, c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1,   \
+                                              c->w2, c->cnt)
+  if (c->nruns > 0) SKM_ELKB(false, true);
+  else if (full) SKM_ELKB(true, false);
+  else SKM_ELKB(false, false);
+#undef SKM_ELKB
   SKM_LAUNCHED(c);
   const VT* v = (const VT*)c->val;
   SKM_PROF_BEGIN(c, "k_elk_recompute");
-  if (full) {
-    k_elk_recompute<VT, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                       c->row_run, c->runs, c->w1,
-                                                       c->cnt + C_W1, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i,
-                                                       c->chg_old, c->cnt);
-  } else {
-    k_elk_recompute<VT, false><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,
-                                                        c->row_run, c->runs, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, c->cc, c->w2,
-                                                        c->chg_i, c->chg_old, c->cnt);
-  }
+#define SKM_ELKR(F, B)                                                                                           \
+  k_elk_recompute<VT, F, B><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,     \
+                                                     c->row_run, c->runs, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, \
+                                                     c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
+  if (c->nruns > 0) SKM_ELKR(false, true);
+  else if (full) SKM_ELKR(true, false);
+  else SKM_ELKR(false, false);
+#undef SKM_ELKR
   SKM_LAUNCHED(c);
   return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
 }

@@ -18,9 +18,10 @@
 // chunk first raises the running best, then appends every value above
 // thr = max(tau, v1_run - W2) (W2 slightly above 2w; tau from a lower bound l
 // on the best similarity when one is known) to the row's buffer in shared
-// memory: a predicated store, no divergent code.  At the end of the row tile
-// group 0 merges both groups' buffers into the output list.  A buffer that
-// overflows marks the row for a whole-row recheck.
+// memory: a predicated store, no divergent code; a buffer more than half full
+// first drops the entries the rising threshold has passed.  At the end of the
+// row tile group 0 merges both groups' buffers into the output list.  A buffer
+// that still overflows marks the row for a whole-row recheck.
 // Every barrier wait gives up after one second (globaltimer): the kernel
 // then records an error word and leaves its loops; TMEM is freed on exit.
 #include <cuda.h>
@@ -126,6 +127,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// max(a, b, c) in one instruction.
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
 
 // Two 32-column loads in flight, one wait.
 __device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, uint32_t (&r)[64]) {
@@ -316,17 +324,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
             for (int q = 0; q < 64; ++q)
               if (jb + q >= k) r[q] = __float_as_uint(-INFINITY);
           }
-          float cm = __uint_as_float(r[0]);
+          // chunk maximum by a tree of three-input maxima (64 -> 22 -> 8 -> 3 -> 1)
+          float m1[22];
 #pragma unroll
-          for (int q = 1; q < 64; ++q) cm = fmaxf(cm, __uint_as_float(r[q]));
+          for (int q = 0; q < 21; ++q)
+            m1[q] = fmax3(__uint_as_float(r[3 * q]), __uint_as_float(r[3 * q + 1]), __uint_as_float(r[3 * q + 2]));
+          m1[21] = __uint_as_float(r[63]);
+          float m2[8];
+#pragma unroll
+          for (int q = 0; q < 7; ++q) m2[q] = fmax3(m1[3 * q], m1[3 * q + 1], m1[3 * q + 2]);
+          m2[7] = m1[21];
+          const float cm = fmax3(fmax3(m2[0], m2[1], m2[2]), fmax3(m2[3], m2[4], m2[5]), fmaxf(m2[6], m2[7]));
           v1 = fmaxf(v1, cm);
           const float thr = fmaxf(tau, __fsub_rd(v1, W2));
+          // a buffer more than half full drops the entries the threshold has
+          // passed by since (one warp-uniform test per chunk; rarely taken)
+          if (__any_sync(SKM_FULL_MASK, nap > kCap / 2)) {
+            if (nap > kCap / 2 && nap <= kCap) {
+              int w = 0;
+              for (int q = 0; q < nap; ++q) {
+                const uint2 e = mybuf[q * kBM];
+                if (__uint_as_float(e.x) > thr) {
+                  mybuf[w * kBM] = e;
+                  ++w;
+                }
+              }
+              nap = w;
+            }
+          }
+          // predicated appends, no branches: the store happens only while the
+          // row's buffer has room, the count goes on (overflow is detected)
 #pragma unroll
           for (int q = 0; q < 64; ++q) {
-            if (__uint_as_float(r[q]) > thr) {
-              if (nap < kCap) mybuf[nap * kBM] = make_uint2(r[q], (uint32_t)(jb + q));
-              ++nap;
-            }
+            const bool keep = __uint_as_float(r[q]) > thr;
+            const bool room = nap < kCap;
+            if (keep && room) mybuf[nap * kBM] = make_uint2(r[q], (uint32_t)(jb + q));
+            nap += keep ? 1 : 0;
           }
         }
         tc_fence_before();

@@ -248,11 +248,12 @@ struct RowGeom {
   int64_t ubase;
   int32_t koff, k, cap;
 };
+template <bool BATCH>
 __device__ __forceinline__ RowGeom row_geom(int64_t i, int32_t k, int64_t kst, int32_t cap,
                                             const int32_t* __restrict__ row_run,
                                             const RunDesc* __restrict__ runs) {
   RowGeom g;
-  if (!runs) {
+  if (!BATCH) {
     g.ubase = i * kst;
     g.koff = 0;
     g.k = k;
