@@ -108,14 +108,26 @@ class ClockSampler:
 
 # ------------------------------------------------------ roofline helpers
 
-def source_hash() -> str:
-    """sha1 over the CUDA sources: a recorded ncu traffic figure only applies
-    to the kernels it was measured on."""
+# the source file of each profiled kernel (with the shared header)
+KERNEL_FILES = {"k_rows_top2": "k_assign.cu", "k_rows_top2(list)": "k_assign.cu", "k_elk_bounds": "k_assign.cu",
+                "k_elk_recompute": "k_assign.cu", "k_ham_bounds": "k_assign.cu", "k_center_sum": "k_update.cu",
+                "k_center_sum_multi": "k_update.cu", "k_colnorm_part": "k_update.cu",
+                "k_normalize_drift": "k_update.cu", "k_bf16_topk": "k_mma.cu"}
+
+
+def source_hash(kernel: str | None = None) -> str:
+    """sha1 over the CUDA source of `kernel` (its file and the shared header;
+    all sources when unknown): a recorded ncu traffic figure only applies to
+    the kernel code it was measured on."""
     import glob
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2107_04074_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+    if kernel in KERNEL_FILES:
+        files = [os.path.join(csrc, KERNEL_FILES[kernel]), os.path.join(csrc, "skm_internal.cuh")]
+    else:
+        files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
+    for f in files:
         h.update(open(f, "rb").read())
     return h.hexdigest()[:12]
 
@@ -123,13 +135,13 @@ def source_hash() -> str:
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from profiles/dram_traffic.txt
     (lines: kernel workload source_hash bytes_per_launch), if it was taken on
-    the current sources; else None."""
+    the kernel's current source; else None."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    cur = source_hash()
+    cur = source_hash(kernel)
     for ln in lines:
         f = ln.split()
         if len(f) == 4 and f[0] == kernel and f[1] == workload and f[2] == cur:
@@ -465,12 +477,14 @@ def run_embed(args, rank, world, local):
     except (OSError, KeyError, ValueError):
         peak = 1900.0
     g = res["standard/bf16"]
+    traffic = recorded_traffic("k_bf16_topk", "vmf-n1e6-d384-k1000") if n == 1_000_000 else None
     return {"workload": f"vmf-embeddings n={n} d={d} k={k} kappa=40 ({iters} iterations max)",
             "labels_identical_across_paths": same, "paths": res,
             "speedup_bf16_vs_fp32_standard": round(g["iters_per_s"] / res["standard/fp32"]["iters_per_s"], 2),
-            "bf16_gemm_roofline": {"bound": "tensor", "achieved": g.get("bf16_gemm_tflops"), "peak": peak,
-                                   "unit": "TFLOP/s",
-                                   "frac": round(g.get("bf16_gemm_tflops", 0) / peak, 4)}}
+            "bf16_gemm_roofline": {"kernel": "k_bf16_topk", "bound": "tensor", "achieved": g.get("bf16_gemm_tflops"),
+                                   "peak": peak, "unit": "TFLOP/s", "peak_source": "measured (burst)",
+                                   "frac": round(g.get("bf16_gemm_tflops", 0) / peak, 4), "traffic": traffic,
+                                   "traffic_note": "ncu DRAM bytes of an n=2e5 launch scaled by rows"}}
 
 
 def run_batch(args, rank, world, local):

@@ -348,9 +348,14 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
       TRY(dalloc(c, &c->topi, (size_t)(n * kTopK)));
       TRY(dalloc(c, &c->w3, (size_t)n));
       TRY(dense_prep_bf16(c));
-      // |BF16 similarity - exact| <= (2u_b + u_b^2)(1 + 1e-6) sum|x c| + accumulation over d terms
-      // with truncation (2^-23 per step): 2^-8 + 2^-15 + (d + 16) 2^-23 (sum|x c| <= 1)
-      c->eps_b = (float)(0x1.0p-8 + 0x1.0p-15 + ((double)d + 16.0) * 0x1.0p-23);
+      // |BF16 similarity - exact| for a unit row and a center of norm <= 1 + 6u:
+      // each operand is rounded to BF16 (8 significant bits, unit roundoff
+      // u_b = 2^-8) from FP32 values within 2^-24 relative, so a product
+      // carries at most (2 u_b + u_b^2)(1 + 2^-22) |x c|, and sum |x c| <= 1 + 6u
+      // (Cauchy-Schwarz): 2^-7 + 2^-15 covers it.  The FP32 accumulation of d
+      // products (directed or truncating steps, 2^-23 each, partial sums <= 1)
+      // adds (d + 16) 2^-23.
+      c->eps_b = (float)(0x1.0p-7 + 0x1.0p-15 + ((double)d + 16.0) * 0x1.0p-23);
     }
   }
   // ---- labels, bounds, worklists
