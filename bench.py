@@ -187,7 +187,10 @@ def run_ours(args, rank, world, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
     def make(variant):
-        return skm.KMeans(n, d, rp, col, val, k, variant=variant, init_rows=init, stream=stream.cuda_stream)
+        # every variant (the plain standard one included) replays its steady-state
+        # iteration as a CUDA graph
+        return skm.KMeans(n, d, rp, col, val, k, variant=variant, init_rows=init, stream=stream.cuda_stream,
+                          graph=not args.no_graph)
 
     def timed_runs(km, steps, warmup):
         for _ in range(warmup):
@@ -318,7 +321,7 @@ def run_ours(args, rank, world, local):
     e2e_iters = 0
     for _ in range(e2e_steps):
         kh = skm.KMeans(n, d, host[0], host[1], host[2], k, variant=variant, init_rows=init,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, graph=not args.no_graph)
         it, _ = kh.run(MAX_ITERS)
         lab_h = kh.labels()
         kh.close()
@@ -713,6 +716,8 @@ def main():
     ap.add_argument("--variant", default="simp_elkan", choices=["standard", "hamerly", "elkan", "simp_hamerly",
                                                                  "simp_elkan"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="eager iterations (one host sync each) instead of the "
+                                                             "CUDA-graph replay")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision-form and batched-form summaries of the default line")
     ap.add_argument("--quick", action="store_true",

@@ -222,6 +222,25 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
  * be NULL) tells which happened. */
 int skm_autotune(skm_ctx* ctx, const char* cache_path, int32_t iters, int32_t* from_cache);
 
+/* Spherical k-means++ seeding (Section 5.6) of a context's centers: the
+ * first center is row floor(u[0] n); center j > 0 is drawn with probability
+ * proportional to 1 - max_c <x(i), c> over the centers chosen so far, as
+ * follows: q_i = round((1 - m_i) 2^40) (0 if negative), W = sum q_i,
+ * T = floor(u[j] W), and the row whose inclusive prefix sum of q first
+ * exceeds T is chosen (if W = 0, the first row not chosen yet).  u: host
+ * double[k] of uniform draws in [0, 1) supplied by the caller.  The chosen
+ * rows become the centers and the context restarts from them as after
+ * skm_reset (labels unassigned, bounds dropped); rows_out (host int64[k], may
+ * be NULL) receives them.  SKM_EUNSUPPORTED for a batch. */
+int skm_seed_kmeanspp(skm_ctx* ctx, const double* u, int64_t* rows_out);
+
+/* Self-test of the failure path of every device-side wait (the tensor-core
+ * kernel's barrier waits): launches one warp that waits on a barrier nothing
+ * completes, with the given limit (1 ns .. 2 s).  Returns SKM_ETIMEOUT when
+ * the wait gave up as it must (the GPU context stays usable), SKM_OK if the
+ * wait completed (a defect), SKM_ECUDA on a CUDA error. */
+int skm_selftest_wait(int64_t timeout_ns, void* stream);
+
 /* Bytes of bound state a variant keeps for n points and k centers (labels
  * excluded): standard 0; Hamerly 8n (two FP32 bounds); Elkan 4n + 4nk. */
 int skm_bound_bytes(int32_t variant, int64_t n, int32_t k, int64_t* bytes);

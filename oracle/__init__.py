@@ -89,6 +89,8 @@ def _lib():
             lib.sko_u_hamerly.restype = dbl
             lib.sko_run.argtypes = data + [ip, i64, ci, ip, i32, ci, ci, ip, ip, ip, ip, ip, ip]
             lib.sko_run.restype = ci
+            lib.sko_kmeanspp.argtypes = data + [ip, i64, ip, ip]
+            lib.sko_kmeanspp.restype = ci
             _LIB = lib
     return _LIB
 
@@ -149,6 +151,15 @@ def unit_rows(X: Data, rows) -> np.ndarray:
 def sim(X: Data, ri: np.ndarray, i: int, c: np.ndarray) -> float:
     c = np.ascontiguousarray(c, dtype=np.float64)
     return _lib().sko_sim(*X.args(), _p(ri), int(i), _p(c))
+
+
+def kmeanspp(X: Data, ri: np.ndarray, u) -> np.ndarray:
+    """Spherical k-means++ seeding (Section 5.6) from the uniform draws u (k of
+    them, in [0, 1)); returns the chosen rows."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    rows = np.empty(len(u), dtype=np.int64)
+    _lib().sko_kmeanspp(*X.args(), _p(ri), len(u), _p(u), _p(rows))
+    return rows
 
 
 def assign(X: Data, ri: np.ndarray, C: np.ndarray, a: np.ndarray | None = None):

@@ -19,7 +19,9 @@
  *     s(i) = max_{j!=i} cc(i,j) (Section 5.2);
  *   - Simplified Elkan (5.1), Elkan (5.2), Hamerly with Eq. (eqn:u-hamerly-2)
  *     (5.3), Hamerly's center test and Simplified Hamerly (5.4), each walked
- *     point by point in the paper's order.
+ *     point by point in the paper's order;
+ *   - spherical k-means++ seeding (Section 5.6): the first center uniform,
+ *     the others drawn proportional to 1 - max_c <x(i), c>.
  *
  * Readings where the paper is silent (stated once here, listed in the design doc):
  *   T  ties: the current label wins; among other centers the lowest index
@@ -419,5 +421,60 @@ int sko_run(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32
   if (iters_done) *iters_done = it;
   if (violations) *violations = viol;
   free(a); free(l); free(uh); free(ue); free(s); free(Cn); free(p); free(sp); free(cc); free(sc);
+  return 0;
+}
+
+/* Spherical k-means++ (Section 5.6).  The caller supplies the uniform draws
+ * u[0..k-1] in [0, 1).  Row floor(u[0] n) is the first center.  Then, with
+ * m_i = max over the chosen centers of <x_i, c> (kept up to date as centers
+ * are added), each row weighs 1 - m_i, quantised to q_i = round((1 - m_i) 2^40)
+ * (0 if negative); with W = sum q_i and T = floor(u[j] W) the next center is
+ * the first row whose running sum of q exceeds T, or, if W = 0, the first row
+ * not chosen yet.  Writes the k chosen rows; returns 0. */
+int sko_kmeanspp(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32_t* col,
+                 const double* val, const double* rinv, int64_t k, const double* u, int64_t* rows) {
+  sko_data X = {n, d, dense, row_ptr, col, val};
+  double* c = (double*)malloc(sizeof(double) * (size_t)d);
+  double* m = (double*)malloc(sizeof(double) * (size_t)n);
+  int64_t r = (int64_t)(u[0] * (double)n);
+  if (r >= n) r = n - 1;
+  for (int64_t j = 0; j < k; ++j) {
+    rows[j] = r;
+    /* the new center: the chosen row, normalised */
+    memset(c, 0, sizeof(double) * (size_t)d);
+    if (dense) {
+      for (int64_t t = 0; t < d; ++t) c[t] = val[r * d + t] * rinv[r];
+    } else {
+      for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) c[col[p]] = val[p] * rinv[r];
+    }
+    if (j + 1 == k) break;
+    long long W = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double s = sim(&X, rinv, i, c);
+      m[i] = (j == 0 || s > m[i]) ? s : m[i];
+      long long q = llround((1.0 - m[i]) * 0x1.0p40);
+      W += q > 0 ? q : 0;
+    }
+    int64_t next = -1;
+    if (W > 0) {
+      long long T = (long long)(u[j + 1] * (double)W);
+      if (T >= W) T = W - 1;
+      long long acc = 0;
+      for (int64_t i = 0; i < n && next < 0; ++i) {
+        long long q = llround((1.0 - m[i]) * 0x1.0p40);
+        acc += q > 0 ? q : 0;
+        if (acc > T) next = i;
+      }
+    } else {
+      for (int64_t i = 0; i < n && next < 0; ++i) {
+        int taken = 0;
+        for (int64_t cc = 0; cc <= j && !taken; ++cc) taken = rows[cc] == i;
+        if (!taken) next = i;
+      }
+    }
+    r = next;
+  }
+  free(c);
+  free(m);
   return 0;
 }

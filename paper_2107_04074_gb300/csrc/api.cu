@@ -987,6 +987,28 @@ int skm_autotune(skm_ctx* c, const char* cache_path, int32_t iters, int32_t* fro
   return SKM_OK;
 }
 
+int skm_seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_out) {
+  if (!c || !u) return SKM_EINVAL;
+  if (c->nruns > 0) return SKM_EUNSUPPORTED;
+  for (int32_t j = 0; j < c->k; ++j)
+    if (!(u[j] >= 0.0 && u[j] < 1.0)) return SKM_EINVAL;
+  std::vector<int64_t> rows((size_t)c->k);
+  TRY(seed_kmeanspp(c, u, rows.data()));
+  {
+    std::unordered_set<int64_t> seen;
+    for (int64_t r : rows)
+      if (r < 0 || r >= c->n || !seen.insert(r).second) return SKM_ECUDA;  // not reachable
+  }
+  TRY(start_from_rows(c, rows));
+  if (rows_out) std::memcpy(rows_out, rows.data(), sizeof(int64_t) * rows.size());
+  return SKM_OK;
+}
+
+int skm_selftest_wait(int64_t timeout_ns, void* stream) {
+  if (timeout_ns < 1 || timeout_ns > 2000000000ll) return SKM_EINVAL;
+  return wait_selftest(timeout_ns, (cudaStream_t)stream);
+}
+
 void skm_destroy(skm_ctx* c) { release(c); }
 
 const char* skm_strerror(int s) {

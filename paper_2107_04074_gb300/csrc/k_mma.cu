@@ -74,17 +74,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait for the phase with the given parity; false on timeout (which
 // also raises the CTA's abort flag so that the other roles stop too) or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t timeout_ns = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = now_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (now_ns() - t0 > kTimeoutNs) {
+    if (now_ns() - t0 > timeout_ns) {
       *abort_flag = 1;
       return false;
     }
   }
+}
+
+// Self-test of the bounded wait: one warp waits on a barrier that nothing
+// completes; the wait must give up after timeout_ns and report E_TIMEOUT.
+__global__ void k_wait_selftest(uint64_t timeout_ns, unsigned long long* __restrict__ flag) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, &abort_flag, timeout_ns);
+  if (!ok && threadIdx.x == 0) atomicOr(flag, (unsigned long long)E_TIMEOUT);
 }
 
 __device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
@@ -488,6 +504,20 @@ int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* to
                                                topi, c->cnt);
   SKM_LAUNCHED(c);
   return SKM_OK;
+}
+
+int wait_selftest(int64_t timeout_ns, cudaStream_t st) {
+  unsigned long long* flag = nullptr;
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&flag, sizeof(unsigned long long), st));
+  SKM_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(unsigned long long), st));
+  k_wait_selftest<<<1, 32, 0, st>>>((uint64_t)timeout_ns, flag);
+  SKM_CUDA_TRY(cudaGetLastError());
+  note_launch(1);
+  unsigned long long h = 0;
+  SKM_CUDA_TRY(cudaMemcpyAsync(&h, flag, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SKM_CUDA_TRY(cudaFreeAsync(flag, st));
+  SKM_CUDA_TRY(cudaStreamSynchronize(st));
+  return (h & E_TIMEOUT) ? SKM_ETIMEOUT : SKM_OK;
 }
 
 }  // namespace skm

@@ -1,0 +1,211 @@
+// Spherical k-means++ seeding (Section 5.6): the first center is a row drawn
+// uniformly, each further center a row drawn with probability proportional to
+// 1 - max_c <x(i), c> over the centers chosen so far (the analogue of the
+// squared Euclidean distance of k-means++), the maximum cached per row so the
+// whole seeding costs O(nk) similarities.
+//
+// The uniform draws u_0 .. u_{k-1} in [0, 1) are inputs.  Discrete rule: the
+// first row is floor(u_0 n); the weights are quantised to integers
+// q_i = round((1 - m_i) 2^40) (0 when negative), W = sum q_i, T = floor(u_j W),
+// and the chosen row is the first whose inclusive prefix sum of q exceeds T;
+// integer sums make the choice independent of summation order.  If W = 0
+// (every row already equals a center) the first row not chosen yet is taken.
+//
+// Each chosen row becomes its center column of the term-major array Ct, the
+// same values k_init_centers writes, and the similarities use the canonical
+// FP32 chain of the assignment kernels.
+//   k_seed_column  center column j <- row rows[j] (normalised)
+//   k_seed_sims    warp per row: m_i = max(m_i, <x_i, c_j>), q_i, block sums
+//   k_seed_pick    one block: W, T, the chosen row for column j + 1
+#include <climits>
+
+#include "skm_internal.cuh"
+
+namespace skm {
+
+namespace {
+
+constexpr int kSeedRows = 64;  // rows per block of k_seed_sims (8 per warp)
+
+template <typename VT>
+__global__ void k_seed_column(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const VT* __restrict__ val, const float* __restrict__ rinv, int64_t n, int64_t d,
+                              int dense, int64_t kst, int j, const int64_t* __restrict__ rows, float* __restrict__ Ct) {
+  const int64_t r = rows[j];
+  if (r < 0 || r >= n) return;  // not reachable: the pick always finds a row
+  const float ri = rinv[r];
+  if (dense) {
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) Ct[t * kst + j] = __fmul_rn(to_f32(val[r * d + t]), ri);
+  } else {
+    for (int64_t p = rp[r] + threadIdx.x; p < rp[r + 1]; p += blockDim.x)
+      Ct[(int64_t)col[p] * kst + j] = __fmul_rn(to_f32(val[p]), ri);
+  }
+}
+
+// Canonical dense similarity chain (t in order) against center column j.
+template <typename VT>
+__device__ __forceinline__ float warp_dot_dense_col(const VT* __restrict__ x, int64_t d,
+                                                    const float* __restrict__ Ct, int64_t kst, int j) {
+  const int lane = threadIdx.x & 31;
+  float acc = 0.f;
+  for (int64_t t0 = 0; t0 < d; t0 += 32) {
+    const float xv = (t0 + lane < d) ? to_f32(x[t0 + lane]) : 0.f;
+    const float cv = (t0 + lane < d) ? __ldg(Ct + (t0 + lane) * kst + j) : 0.f;
+    const int nq = (int)min((int64_t)32, d - t0);
+    for (int q = 0; q < nq; ++q)
+      acc = __fmaf_rn(__shfl_sync(SKM_FULL_MASK, xv, q), __shfl_sync(SKM_FULL_MASK, cv, q), acc);
+  }
+  return acc;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(256) k_seed_sims(int64_t n, int64_t d, int dense, const int64_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                   const float* __restrict__ rinv, const float* __restrict__ Ct,
+                                                   int64_t kst, int j, float* __restrict__ m,
+                                                   long long* __restrict__ q, long long* __restrict__ bsum) {
+  __shared__ long long wsum[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long s = 0;
+  for (int u = 0; u < kSeedRows / 8; ++u) {
+    const int64_t i = (int64_t)blockIdx.x * kSeedRows + warp * (kSeedRows / 8) + u;
+    if (i >= n) break;
+    float dot;
+    if (dense) dot = warp_dot_dense_col<VT>(val + i * d, d, Ct, kst, j);
+    else dot = warp_dot_one<VT>(rp[i], rp[i + 1], col, val, Ct, kst, j);
+    const float sim = __fmul_rn(dot, rinv[i]);
+    if (lane == 0) {
+      const float mi = j == 0 ? sim : fmaxf(m[i], sim);
+      m[i] = mi;
+      long long qi = __double2ll_rn((1.0 - (double)mi) * 0x1.0p40);
+      if (qi < 0) qi = 0;
+      q[i] = qi;
+      s += qi;
+    }
+  }
+  if (lane == 0) wsum[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_seed_pick(const long long* __restrict__ bsum, int64_t nblk,
+                                                    const long long* __restrict__ q, int64_t n, double u,
+                                                    int64_t* __restrict__ rows, int j) {
+  __shared__ long long part[1024];
+  __shared__ long long total, target, before;
+  __shared__ int owner;
+  __shared__ int64_t found;
+  const int tid = threadIdx.x;
+  const int64_t per = (nblk + 1023) / 1024;
+  const int64_t b0 = tid * per, b1 = min(nblk, b0 + per);
+  long long s = 0;
+  for (int64_t b = b0; b < b1; ++b) s += bsum[b];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    long long t = 0;
+    for (int w = 0; w < 1024; ++w) t += part[w];
+    total = t;
+    long long T = (long long)(u * (double)t);
+    if (T >= t) T = t - 1;
+    target = T;
+    found = -1;
+    owner = -1;
+    long long acc = 0;
+    for (int w = 0; w < 1024 && t > 0; ++w) {
+      if (T < acc + part[w]) {
+        owner = w;
+        before = acc;
+        break;
+      }
+      acc += part[w];
+    }
+  }
+  __syncthreads();
+  if (total <= 0) {
+    // every row equals a chosen center: the first row not chosen yet
+    if (tid == 0) {
+      for (int64_t i = 0; i < n && found < 0; ++i) {
+        bool taken = false;
+        for (int c = 0; c < j && !taken; ++c) taken = rows[c] == i;
+        if (!taken) found = i;
+      }
+      rows[j] = found < 0 ? 0 : found;
+    }
+    return;
+  }
+  // the owner thread walks its blocks, then the rows of the block that holds the target
+  if (tid == owner) {
+    long long acc = before;
+    for (int64_t b = b0; b < b1; ++b) {
+      if (target < acc + bsum[b]) {
+        const int64_t r0 = b * kSeedRows, r1 = min(n, r0 + kSeedRows);
+        for (int64_t i = r0; i < r1; ++i) {
+          acc += q[i];
+          if (acc > target) {
+            found = i;
+            break;
+          }
+        }
+        break;
+      }
+      acc += bsum[b];
+    }
+    rows[j] = found;
+  }
+}
+
+template <typename VT>
+int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
+  const int64_t n = c->n, d = c->d, kst = c->kst;
+  const int k = c->k;
+  const int dense = c->layout == SKM_DENSE;
+  const int64_t nblk = (n + kSeedRows - 1) / kSeedRows;
+  float* m = nullptr;
+  long long *q = nullptr, *bsum = nullptr;
+  int64_t* rows = nullptr;
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&m, sizeof(float) * n, c->st));
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&q, sizeof(long long) * n, c->st));
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&bsum, sizeof(long long) * nblk, c->st));
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&rows, sizeof(int64_t) * k, c->st));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->Ct, 0, sizeof(float) * d * kst, c->st));
+  int64_t r0 = (int64_t)(u[0] * (double)n);
+  if (r0 >= n) r0 = n - 1;
+  rows_host[0] = r0;
+  SKM_CUDA_TRY(cudaMemcpyAsync(rows, rows_host, sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
+  const VT* v = (const VT*)c->val;
+  for (int j = 0; j < k; ++j) {
+    k_seed_column<VT><<<1, 256, 0, c->st>>>(c->rp, c->col, v, c->rinv, n, d, dense, kst, j, rows, c->Ct);
+    SKM_LAUNCH_CHECK();
+    if (j + 1 == k) break;
+    k_seed_sims<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, d, dense, c->rp, c->col, v, c->rinv, c->Ct, kst, j, m, q,
+                                                       bsum);
+    SKM_LAUNCH_CHECK();
+    k_seed_pick<<<1, 1024, 0, c->st>>>(bsum, nblk, q, n, u[j + 1], rows, j + 1);
+    SKM_LAUNCH_CHECK();
+  }
+  SKM_CUDA_TRY(cudaMemcpyAsync(rows_host, rows, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, c->st));
+  cudaFreeAsync(m, c->st);
+  cudaFreeAsync(q, c->st);
+  cudaFreeAsync(bsum, c->st);
+  cudaFreeAsync(rows, c->st);
+  SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
+  return SKM_OK;
+}
+
+}  // namespace
+
+int seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_host) {
+  switch (c->dtype) {
+    case SKM_F32: return seed_t<float>(c, u, rows_host);
+    case SKM_F16: return seed_t<__half>(c, u, rows_host);
+    case SKM_BF16: return seed_t<__nv_bfloat16>(c, u, rows_host);
+  }
+  return SKM_EINVAL;
+}
+
+}  // namespace skm

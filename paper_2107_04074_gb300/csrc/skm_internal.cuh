@@ -411,6 +411,8 @@ constexpr int kTopK = 8;  // BF16 candidates kept per row
 int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* topv, int32_t* topi);
 int dense_lower(skm_ctx* c);
 int dense_recheck_cands(skm_ctx* c, bool hamerly);
+int wait_selftest(int64_t timeout_ns, cudaStream_t st);
+int seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_host);
 
 }  // namespace skm
 

@@ -29,7 +29,7 @@ EXPORTS = ["skm_default_options", "skm_init", "skm_reset", "skm_assign", "skm_up
            "skm_get_labels", "skm_get_centers", "skm_set_centers", "skm_set_labels", "skm_get_bounds",
            "skm_get_stats", "skm_bound_bytes", "skm_kernel_launches", "skm_profile", "skm_profile_read",
            "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_topk", "skm_batch_init",
-           "skm_autotune"]
+           "skm_autotune", "skm_selftest_wait", "skm_seed_kmeanspp"]
 
 
 class SkmError(RuntimeError):
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
         "skm_get_bf16_topk": (ctypes.c_int, [P, P, P, P, i32]),
         "skm_batch_init": (ctypes.c_int, [P, P, P, P, i32, i32, P, u64, P, P]),
         "skm_autotune": (ctypes.c_int, [P, ctypes.c_char_p, i32, P]),
+        "skm_selftest_wait": (ctypes.c_int, [i64, P]),
+        "skm_seed_kmeanspp": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -118,6 +120,11 @@ def _strerror(code: int) -> str:
 def _check(code: int, what: str):
     if code != OK:
         raise SkmError(code, what)
+
+
+def selftest_wait(timeout_ns: int, stream=None) -> int:
+    """Status of a device wait on a barrier nothing completes (SKM_ETIMEOUT expected)."""
+    return int(load().skm_selftest_wait(int(timeout_ns), ctypes.c_void_p(stream or 0)))
 
 
 def kernel_launches() -> int:
@@ -317,6 +324,16 @@ class KMeans:
         _check(load().skm_get_bf16_topk(self._h, _ptr(vals), _ptr(idx), ctypes.byref(eps), HOST),
                "skm_get_bf16_topk")
         return vals, idx, eps.value
+
+    def seed_kmeanspp(self, u) -> np.ndarray:
+        """Spherical k-means++ seeding from the k uniform draws u (Section 5.6);
+        returns the chosen rows, which become the centers."""
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+        if u.shape != (self.k,):
+            raise ValueError("u must have k entries")
+        rows = np.empty(self.k, dtype=np.int64)
+        _check(load().skm_seed_kmeanspp(self._h, _ptr(u), _ptr(rows)), "skm_seed_kmeanspp")
+        return rows
 
     def autotune(self, cache_path=None, iters: int = 3) -> bool:
         """Pick the persistent kernels' launch shape (and the Elkan whole-row

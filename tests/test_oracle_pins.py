@@ -376,3 +376,61 @@ def test_memory_figures_from_the_paper():
     elkan = n * g["k"] * 8 / 1e9
     assert 1.0 < elkan < g["elkan_bound_gb_stated"]
     assert abs(elkan - 1.47) < 0.01
+
+
+# ---------------------------------------------------------------- k-means++ seeding (Section 5.6)
+
+def _unit_dense(X):
+    X = np.asarray(X, dtype=np.float64)
+    return X / np.linalg.norm(X, axis=1, keepdims=True)
+
+
+def test_kmeanspp_first_center_is_uniform_draw():
+    X = np.abs(np.random.default_rng(3).normal(size=(10, 4))) + 0.1
+    d = oracle.Data.from_dense(X.astype(np.float32))
+    ri = oracle.rinv(d)
+    for u0, want in ((0.0, 0), (0.05, 0), (0.1, 1), (0.55, 5), (0.999, 9)):
+        assert oracle.kmeanspp(d, ri, [u0])[0] == want
+
+
+def test_kmeanspp_second_center_proportional_to_one_minus_cos():
+    """Sweeping the second draw over a fine grid, each row is chosen for a
+    share of the grid equal to (1 - cos(x_i, c_1)) / sum, the paper's weight,
+    computed here directly from the normalised rows."""
+    X = np.abs(np.random.default_rng(5).normal(size=(7, 5))) + 0.05
+    d = oracle.Data.from_dense(X.astype(np.float32))
+    ri = oracle.rinv(d)
+    Xn = _unit_dense(X.astype(np.float32))
+    u0 = 0.3  # first center: row 2
+    w = 1.0 - Xn @ Xn[2]
+    w = np.clip(w, 0.0, None)
+    M = 20000
+    counts = np.zeros(len(X))
+    for m in range(M):
+        r = oracle.kmeanspp(d, ri, [u0, (m + 0.5) / M])
+        assert r[0] == 2
+        counts[r[1]] += 1
+    np.testing.assert_allclose(counts / M, w / w.sum(), atol=2.0 / M)
+    assert counts[2] == 0  # the chosen row has weight 0
+
+
+def test_kmeanspp_k_equals_n_chooses_every_row_once():
+    X = np.abs(np.random.default_rng(8).normal(size=(12, 6))) + 0.01
+    X[5] = X[3]  # an exact duplicate: weight 0 once its twin is chosen
+    d = oracle.Data.from_dense(X.astype(np.float32))
+    ri = oracle.rinv(d)
+    rows = oracle.kmeanspp(d, ri, np.random.default_rng(1).random(12))
+    assert sorted(rows.tolist()) == list(range(12))
+
+
+def test_kmeanspp_spreads_over_separated_clusters():
+    """Three tight, mutually orthogonal clusters: after one center, the other
+    clusters carry all the weight, so three draws land in three clusters."""
+    rng = np.random.default_rng(2)
+    base = np.eye(3)
+    X = np.concatenate([base[c] + 1e-3 * np.abs(rng.normal(size=(20, 3))) for c in range(3)])
+    d = oracle.Data.from_dense(X.astype(np.float32))
+    ri = oracle.rinv(d)
+    for s in range(25):
+        rows = oracle.kmeanspp(d, ri, np.random.default_rng(100 + s).random(3))
+        assert len({int(r) // 20 for r in rows}) == 3
