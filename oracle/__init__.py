@@ -19,7 +19,8 @@ Functions and the passages they follow:
 * ``l_update``        Eq. (eqn:l-bound), clamped (rule CL)
 * ``u_update``        Eq. (eqn:u-elkan), clamped (rule CL)
 * ``u_hamerly``       Eq. (eqn:u-hamerly-2) under rule HG (Section 5.3)
-* ``run``             full runs of the five variants (Sections 5, 5.1-5.4)
+* ``run``             full runs of the five variants (Sections 5, 5.1-5.4) and of
+                      Yin-Yang group bounds (Section 5.5)
 
 The rule letters (T, E, CL, HG, V, D, M) are defined in the header of
 ``skm_oracle.c``.
@@ -38,9 +39,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
 _LOCK = threading.Lock()
 
-STANDARD, HAMERLY, ELKAN, SIMP_HAMERLY, SIMP_ELKAN = 0, 1, 2, 3, 4
+STANDARD, HAMERLY, ELKAN, SIMP_HAMERLY, SIMP_ELKAN, YINYANG = 0, 1, 2, 3, 4, 5
 VARIANTS = {"standard": STANDARD, "hamerly": HAMERLY, "elkan": ELKAN, "simp_hamerly": SIMP_HAMERLY,
-            "simp_elkan": SIMP_ELKAN}
+            "simp_elkan": SIMP_ELKAN, "yinyang": YINYANG}
 
 
 def _lib_path() -> str:

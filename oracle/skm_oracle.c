@@ -21,7 +21,9 @@
  *     (5.3), Hamerly's center test and Simplified Hamerly (5.4), each walked
  *     point by point in the paper's order;
  *   - spherical k-means++ seeding (Section 5.6): the first center uniform,
- *     the others drawn proportional to 1 - max_c <x(i), c>.
+ *     the others drawn proportional to 1 - max_c <x(i), c>;
+ *   - Yin-Yang group bounds (Section 5.5 names them without a cosine form;
+ *     reading YY below).
  *
  * Readings where the paper is silent (stated once here, listed in the design doc):
  *   T  ties: the current label wins; among other centers the lowest index
@@ -37,6 +39,16 @@
  *      assignment that changes no label (its update would be a no-op).
  *   D  1 - p^2 is evaluated as q(2 - q), q = |c/|c| - c'/|c'||^2 / 2, which
  *      avoids the cancellation the paper warns about (Section 2).
+ *   YY Yin-Yang on cosines: the centers are split into groups of YY_GROUP
+ *      consecutive indices; l(i) bounds <x_i, c_a(i)> from below and u(i,G)
+ *      bounds max_{j in G, j != a(i)} <x_i, c_j> from above.  After the
+ *      centers move, l follows Eq. (eqn:l-bound) with p(a) and u(i,G) the
+ *      clamped Eq. (eqn:u-elkan) with the group's smallest p (valid for every
+ *      center of the group: that update grows as p shrinks).  A point is
+ *      skipped if l >= max_G u(i,G); otherwise l is made tight and every group
+ *      with l < u(i,G) is recomputed exactly; the best of a(i) and those
+ *      centers is the new label (rule T); recomputed groups get their exact
+ *      bound, and the old label's group takes its similarity if it left it.
  *   M  pruning keeps the exact labels of the standard variant: a bound test
  *      is passed with a margin of 2*delta_i, delta_i covering the FP64
  *      rounding of a similarity of row i, and every bound update carries a
@@ -52,6 +64,8 @@
 #define SKO_ELKAN 2
 #define SKO_SIMP_HAMERLY 3
 #define SKO_SIMP_ELKAN 4
+#define SKO_YINYANG 5
+#define YY_GROUP 8 /* centers per Yin-Yang group: j / YY_GROUP */
 
 #define UPD_SLACK 4e-15
 
@@ -275,6 +289,12 @@ int sko_run(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32
   int elkan = (variant == SKO_ELKAN || variant == SKO_SIMP_ELKAN);
   int hamerly = (variant == SKO_HAMERLY || variant == SKO_SIMP_HAMERLY);
   int full = (variant == SKO_ELKAN || variant == SKO_HAMERLY);
+  int yy = (variant == SKO_YINYANG);
+  int64_t ng = (k + YY_GROUP - 1) / YY_GROUP;
+  double* ug = yy ? (double*)malloc(sizeof(double) * (size_t)(n * ng)) : NULL;
+  double* pg = yy ? (double*)malloc(sizeof(double) * (size_t)ng) : NULL;
+  double* spg = yy ? (double*)malloc(sizeof(double) * (size_t)ng) : NULL;
+  char* live = yy ? (char*)malloc((size_t)ng) : NULL;
   int32_t* a = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
   double* l = (double*)malloc(sizeof(double) * (size_t)n);
   double* uh = (double*)malloc(sizeof(double) * (size_t)n);
@@ -308,6 +328,71 @@ int sko_run(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32
         uh[i] = (k > 1) ? o + dl : -1.0;
         if (elkan)
           for (int64_t j = 0; j < k; ++j) ue[i * k + j] = s[j] + dl;
+        if (yy)
+          for (int64_t g = 0; g < ng; ++g) {
+            double o2 = -INFINITY;
+            for (int64_t j = g * YY_GROUP; j < k && j < (g + 1) * YY_GROUP; ++j)
+              if (j != nb && s[j] > o2) o2 = s[j];
+            ug[i * ng + g] = (o2 == -INFINITY) ? -1.0 : o2 + dl;
+          }
+      }
+    } else if (yy) {
+      /* the worst drift of each group */
+      for (int64_t g = 0; g < ng; ++g) {
+        int64_t jm = g * YY_GROUP;
+        for (int64_t j = jm; j < k && j < (g + 1) * YY_GROUP; ++j)
+          if (p[j] < p[jm]) jm = j;
+        pg[g] = p[jm];
+        spg[g] = sp[jm];
+      }
+      for (int64_t i = 0; i < n; ++i) {
+        int32_t ai = a[i];
+        double dl = delta_row(&X, i);
+        l[i] = sko_l_update(l[i], p[ai], sp[ai]);
+        double umax = -INFINITY;
+        for (int64_t g = 0; g < ng; ++g) {
+          ug[i * ng + g] = sko_u_update(ug[i * ng + g], pg[g], spg[g]);
+          if (ug[i * ng + g] > umax) umax = ug[i * ng + g];
+        }
+        if (check_bounds) {
+          for (int64_t j = 0; j < k; ++j) s[j] = sim(&X, rinv, i, C + j * d);
+          if (l[i] > s[ai] + dl) viol++;
+          for (int64_t j = 0; j < k; ++j)
+            if (j != ai && ug[i * ng + j / YY_GROUP] < s[j] - dl) viol++;
+        }
+        double L = l[i] - 2.0 * dl;
+        if (L >= umax) continue; /* global test */
+        double sa = sim(&X, rinv, i, C + ai * d);
+        sims++;
+        l[i] = sa - dl;
+        L = l[i] - 2.0 * dl;
+        if (L >= umax) continue;
+        /* group test; the recomputed groups' similarities (a(i) known) */
+        for (int64_t j = 0; j < k; ++j) s[j] = -INFINITY;
+        s[ai] = sa;
+        for (int64_t g = 0; g < ng; ++g) {
+          live[g] = L < ug[i * ng + g];
+          if (!live[g]) continue;
+          for (int64_t j = g * YY_GROUP; j < k && j < (g + 1) * YY_GROUP; ++j) {
+            if (j == ai) continue;
+            s[j] = sim(&X, rinv, i, C + j * d);
+            sims++;
+          }
+        }
+        int32_t nb = pick_rule_t(s, k, ai);
+        if (nb != ai) changed++;
+        a[i] = nb;
+        l[i] = s[nb] - dl;
+        for (int64_t g = 0; g < ng; ++g) {
+          if (!live[g]) continue;
+          double o2 = -INFINITY;
+          for (int64_t j = g * YY_GROUP; j < k && j < (g + 1) * YY_GROUP; ++j)
+            if (j != nb && s[j] > o2) o2 = s[j];
+          ug[i * ng + g] = (o2 == -INFINITY) ? -1.0 : o2 + dl;
+        }
+        /* the old label left a group that was not recomputed */
+        int64_t go = ai / YY_GROUP;
+        if (nb != ai && !live[go] && sa + dl > ug[i * ng + go]) ug[i * ng + go] = sa + dl;
       }
     } else {
       /* p'(j) = min_{j' != j} p(j') for Hamerly (Section 5.3) */
@@ -421,6 +506,7 @@ int sko_run(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32
   if (iters_done) *iters_done = it;
   if (violations) *violations = viol;
   free(a); free(l); free(uh); free(ue); free(s); free(Cn); free(p); free(sp); free(cc); free(sc);
+  free(ug); free(pg); free(spg); free(live);
   return 0;
 }
 

@@ -17,7 +17,7 @@ import oracle
 import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-VARIANTS = ["standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan"]
+VARIANTS = ["standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan", "yinyang"]
 
 
 def _unit(v):
@@ -265,6 +265,22 @@ def test_hamerly_bound_dominates_every_center():
             h = oracle.u_hamerly(u, float(ps.min()), tight=tight)
             for p in ps:
                 assert h >= oracle.u_update(u, float(p)) - 1e-15
+
+
+def test_u_update_grows_as_drift_grows():
+    """Yin-Yang's group bound moves with the group's smallest p: Eq.
+    (eqn:u-elkan) with the clamp never decreases when p decreases, so that
+    update bounds every center of the group."""
+    rng = np.random.default_rng(12)
+    for _ in range(4000):
+        u = rng.uniform(-1, 1)
+        p1, p2 = np.sort(rng.uniform(-1, 1, 2))
+        assert oracle.u_update(u, p1) >= oracle.u_update(u, p2) - 1e-15
+    # and against the arc form: cos(max(0, arccos u - arccos p)) is the bound for one center
+    for u in np.linspace(-0.99, 0.99, 41):
+        for pp in np.linspace(-0.99, 0.99, 41):
+            want = np.cos(max(0.0, np.arccos(u) - np.arccos(pp)))
+            assert abs(oracle.u_update(u, pp) - want) < 1e-9
 
 
 # ------------------------------------------------------------- full runs
