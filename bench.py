@@ -303,7 +303,7 @@ def run_ours(args, rank, world, local):
 
     # every variant on the same workload (same labels), for comparison
     others = {}
-    for v in ("standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan"):
+    for v in ("standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan", "yinyang"):
         if v == variant:
             others[v] = round(value / world, 3)
             continue
@@ -714,7 +714,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="simp_elkan", choices=["standard", "hamerly", "elkan", "simp_hamerly",
-                                                                 "simp_elkan"])
+                                                                 "simp_elkan", "yinyang"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager iterations (one host sync each) instead of the "
                                                              "CUDA-graph replay")

@@ -50,13 +50,16 @@ extern "C" {
 /* ---- enumerations ---- */
 /* Variants (Section 5): standard Lloyd; Hamerly (5.3 + center test 5.4);
  * Elkan (5.2); Simplified Hamerly (5.4, no center test); Simplified Elkan
- * (5.1, no center-center tests). */
+ * (5.1, no center-center tests); Yin-Yang group bounds (5.5, CSR data only:
+ * one upper bound per group of 8 consecutive centers, moved by the group's
+ * worst drift). */
 typedef enum {
   SKM_STANDARD = 0,
   SKM_HAMERLY = 1,
   SKM_ELKAN = 2,
   SKM_SIMP_HAMERLY = 3,
-  SKM_SIMP_ELKAN = 4
+  SKM_SIMP_ELKAN = 4,
+  SKM_YINYANG = 5
 } skm_variant;
 
 typedef enum { SKM_F32 = 0, SKM_F16 = 1, SKM_BF16 = 2 } skm_dtype;
@@ -177,8 +180,9 @@ int skm_set_centers(skm_ctx* ctx, const float* C, int32_t space);
 int skm_set_labels(skm_ctx* ctx, const int32_t* a, int32_t space);
 
 /* Copy out the bounds for inspection: l (float[n]); u is float[n] for the
- * Hamerly variants and float[n*k] (row-major u(i,j)) for the Elkan variants;
- * either pointer may be NULL.  SKM_ESTATE before the first assignment or for
+ * Hamerly variants, float[n*k] (row-major u(i,j)) for the Elkan variants and
+ * float[ceil(k/8)*n] (group-major u(i,G) at [G*n + i]) for Yin-Yang; either
+ * pointer may be NULL.  SKM_ESTATE before the first assignment or for
  * the standard variant. */
 int skm_get_bounds(skm_ctx* ctx, float* l, float* u, int32_t out_space);
 
@@ -242,7 +246,8 @@ int skm_seed_kmeanspp(skm_ctx* ctx, const double* u, int64_t* rows_out);
 int skm_selftest_wait(int64_t timeout_ns, void* stream);
 
 /* Bytes of bound state a variant keeps for n points and k centers (labels
- * excluded): standard 0; Hamerly 8n (two FP32 bounds); Elkan 4n + 4nk. */
+ * excluded): standard 0; Hamerly 8n (two FP32 bounds); Elkan 4n + 4nk;
+ * Yin-Yang 4n + 4n ceil(k/8). */
 int skm_bound_bytes(int32_t variant, int64_t n, int32_t k, int64_t* bytes);
 
 /* Number of CUDA kernels this library has launched in this process. */

@@ -200,7 +200,7 @@ void release(skm_ctx* c) {
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   delete static_cast<std::vector<RunDesc>*>(c->hruns);
   delete static_cast<std::vector<int64_t>*>(c->hinit);
-  void* ptrs[] = {c->runs,   c->row_run, c->glog,  c->own[0], c->own[1], c->own[2], c->rinv,  c->dlt,
+  void* ptrs[] = {c->gdrift, c->runs,   c->row_run, c->glog,  c->own[0], c->own[1], c->own[2], c->rinv,  c->dlt,
                   c->t_ptr,  c->t_row,   c->t_val, c->ch_term, c->ch_idx, c->ch_part, c->multi_term,
                   c->multi_base, c->multi_cnt, c->part64, c->Ct, c->S64, c->nrm, c->red, c->obj, c->pdn,
                   c->pup,    c->qup,     c->hsel,  c->cc,     c->sc,     c->gpart,  c->a,     c->lb,
@@ -310,7 +310,8 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   TRY(dalloc(c, &c->hsel, HSEL_N));
   const bool full = (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY);
   const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
-  const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) || c->layout == SKM_DENSE;
+  const bool yy = (c->variant == SKM_YINYANG);
+  const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) || c->layout == SKM_DENSE || yy;
   if (full) {
     // enough d-splits of the Gram (64 x 64 tiles) for ~4 blocks per SM, each
     // split >= 256 terms
@@ -362,7 +363,8 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   TRY(dalloc(c, &c->a, (size_t)n));
   if (ham || elk) {
     TRY(dalloc(c, &c->lb, (size_t)n));
-    int64_t ucount = elk ? n * kst : n;
+    int64_t ucount = elk ? n * kst : yy ? n * ((k + 7) / 8) : n;
+    if (yy) TRY(dalloc(c, &c->gdrift, (size_t)(3 * ((k + 7) / 8))));
     if (elk && c->nruns > 0) {
       const auto& R = *static_cast<std::vector<RunDesc>*>(c->hruns);
       ucount = R.back().uoff + R.back().n * R.back().kst;
@@ -398,9 +400,10 @@ int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const
   if (!out) return SKM_EINVAL;
   *out = nullptr;
   if (!x || x->n < 1 || x->d < 1 || k < 1 || k > x->n || x->reserved != 0) return SKM_EINVAL;
-  if (variant < SKM_STANDARD || variant > SKM_SIMP_ELKAN) return SKM_EINVAL;
+  if (variant < SKM_STANDARD || variant > SKM_YINYANG) return SKM_EINVAL;
   if (x->dtype < SKM_F32 || x->dtype > SKM_BF16) return SKM_EINVAL;
   if (x->layout != SKM_CSR && x->layout != SKM_DENSE) return SKM_EINVAL;
+  if (variant == SKM_YINYANG && x->layout != SKM_CSR) return SKM_EUNSUPPORTED;
   if (x->memspace != SKM_DEVICE && x->memspace != SKM_HOST) return SKM_EINVAL;
   if (!x->values || (x->layout == SKM_CSR && (!x->row_ptr || !x->col_idx))) return SKM_EINVAL;
   if (x->d > INT32_MAX || x->n > INT32_MAX) return SKM_EUNSUPPORTED;
@@ -448,7 +451,7 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
   *out = nullptr;
   if (!x || !run_rows || !ks || nruns < 1 || x->n < 1 || x->d < 1 || x->reserved != 0) return SKM_EINVAL;
   if (x->layout != SKM_CSR) return SKM_EUNSUPPORTED;
-  if (variant < SKM_STANDARD || variant > SKM_SIMP_ELKAN) return SKM_EINVAL;
+  if (variant < SKM_STANDARD || variant > SKM_YINYANG) return SKM_EINVAL;
   if (variant != SKM_STANDARD && variant != SKM_SIMP_ELKAN) return SKM_EUNSUPPORTED;
   if (x->dtype < SKM_F32 || x->dtype > SKM_BF16) return SKM_EINVAL;
   if (x->memspace != SKM_DEVICE && x->memspace != SKM_HOST) return SKM_EINVAL;
@@ -624,11 +627,14 @@ int skm_assign(skm_ctx* c, int64_t* n_changed) {
   } else if (!c->have_bounds || c->variant == SKM_STANDARD) {
     const int mode = (c->variant == SKM_STANDARD) ? 0
                      : (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) ? 1
+                     : (c->variant == SKM_YINYANG)                                   ? 3
                                                                                       : 2;
     rc = assign_full(c, mode, nullptr, nullptr, c->n);
     if (rc == SKM_OK) c->have_bounds = (c->variant != SKM_STANDARD);
   } else if (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) {
     rc = hamerly_step(c);
+  } else if (c->variant == SKM_YINYANG) {
+    rc = yinyang_step(c);
   } else {
     rc = elkan_step(c);
   }
@@ -813,6 +819,8 @@ int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
     if (elk)
       SKM_CUDA_TRY(cudaMemcpy2DAsync(u, sizeof(float) * c->k, c->ub, sizeof(float) * c->kst, sizeof(float) * c->k,
                                      (size_t)c->n, kind, c->st));
+    else if (c->variant == SKM_YINYANG)
+      SKM_CUDA_TRY(cudaMemcpyAsync(u, c->ub, sizeof(float) * c->n * ((c->k + 7) / 8), kind, c->st));
     else
       SKM_CUDA_TRY(cudaMemcpyAsync(u, c->ub, sizeof(float) * c->n, kind, c->st));
   }
@@ -845,6 +853,7 @@ int skm_bound_bytes(int32_t variant, int64_t n, int32_t k, int64_t* bytes) {
     case SKM_SIMP_HAMERLY: *bytes = 8 * n; return SKM_OK;
     case SKM_ELKAN:
     case SKM_SIMP_ELKAN: *bytes = 4 * n + 4 * n * (int64_t)k; return SKM_OK;
+    case SKM_YINYANG: *bytes = 4 * n + 4 * n * (int64_t)((k + 7) / 8); return SKM_OK;
   }
   return SKM_EINVAL;
 }

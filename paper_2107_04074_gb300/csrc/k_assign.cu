@@ -25,7 +25,12 @@ namespace {
 constexpr int kBlock = 256;
 
 // MODE 0: labels only (standard).  MODE 1: also l(i) and Hamerly's u(i).
-// MODE 2: also l(i) and every Elkan bound u(i,j).
+// MODE 2: also l(i) and every Elkan bound u(i,j).  MODE 3 (Yin-Yang): only
+// the centers of the live groups (a group of 8 consecutive centers is live
+// when its bound u(i,G) = ub[G * ustride + i] exceeds l(i) - 2 delta, and
+// always for the group of a(i); before the first assignment all are live)
+// are gathered and compared; l(i) and the live groups' bounds are rewritten.
+// A lane's four centers always lie in one group.
 // Lane L owns the centers j = 128 g + 4 L + c (c = 0..3, g = 0..G-1) and
 // gathers them with one 16-byte load per row entry and group; each center's
 // sum runs over the row entries in CSR order (the canonical order).
@@ -37,8 +42,8 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
     int64_t kst, const int32_t* __restrict__ row_run, const RunDesc* __restrict__ runs,
     const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt, int64_t nrows,
-    int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, int32_t* __restrict__ chg_i,
-    int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
+    int64_t ustride, int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub,
+    int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
   constexpr int KT = 128 * G;                     // centers per pass over the row
   constexpr int NB = G >= 8 ? 1 : 8 / G;          // row entries batched per step
   const int lane = threadIdx.x & 31;
@@ -56,6 +61,10 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
     const int32_t cur = a[i] - rg.koff;  // local; negative before the first assignment
     float v1 = -INFINITY, v2 = -INFINITY, vcur = -INFINITY;
     int j1 = INT_MAX;
+    float sv[MODE == 3 ? G : 1][4];  // Yin-Yang: this lane's similarities (-inf: not live)
+    bool live[MODE == 3 ? G : 1];
+    unsigned live_cnt = 0;
+    const float L3 = (MODE == 3 && cur >= 0) ? __fsub_rd(lb[i], 2.f * dl) : -INFINITY;
     for (int j0 = 0; j0 < kr; j0 += KT) {
       float4 acc[G];
       bool ok[G];  // this lane's 4-center slot of group g lies inside the padded row
@@ -63,6 +72,11 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
       for (int g = 0; g < G; ++g) {
         acc[g] = make_float4(0.f, 0.f, 0.f, 0.f);
         ok[g] = (j0 + g * 128 + lane * 4) < kr;
+        if (MODE == 3) {
+          const int grp = (j0 + g * 128 + lane * 4) >> 3;
+          live[g] = ok[g] && (cur < 0 || grp == (cur >> 3) || __ldg(ub + (int64_t)grp * ustride + i) > L3);
+          ok[g] = live[g];
+        }
       }
       const float* cbase = Ct + rg.koff + j0 + lane * 4;
       for (int64_t p0 = b; p0 < e; p0 += 32) {
@@ -119,8 +133,13 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int j = j0 + g * 128 + lane * 4 + c;
-          if (j < kr) {
+          if (MODE == 3) sv[g][c] = -INFINITY;
+          if (j < kr && (MODE != 3 || live[g])) {
             const float s = __fmul_rn(av[c], ri);
+            if (MODE == 3) {
+              sv[g][c] = s;
+              ++live_cnt;
+            }
             if (MODE == 2) ub[rg.ubase + j] = __fadd_ru(s, dl);
             if (j == cur) vcur = s;
             if (s > v1) {
@@ -157,10 +176,27 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
       nb = j1;
       ssec = v2;
     }
+    if (MODE == 3) {
+      // the live groups' new bounds: the best of their other centers (two
+      // lanes per group)
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int jb = g * 128 + lane * 4;  // one pass: kr <= KT for this variant
+        float m = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (jb + c != nb) m = fmaxf(m, sv[g][c]);
+        m = fmaxf(m, __shfl_xor_sync(SKM_FULL_MASK, m, 1));
+        if (live[g] && (lane & 1) == 0)
+          ub[(int64_t)(jb >> 3) * ustride + i] = (m == -INFINITY) ? -1.f : __fadd_ru(m, dl);
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) live_cnt += __shfl_xor_sync(SKM_FULL_MASK, live_cnt, o);
+    }
     if (lane == 0) {
       a[i] = rg.koff + nb;
       my_changed += (nb != cur);
-      my_sims += (unsigned long long)kr;
+      my_sims += MODE == 3 ? (unsigned long long)live_cnt : (unsigned long long)kr;
       if (MODE >= 1) lb[i] = __fsub_rd(v1, dl);
       if (MODE == 1) ub[i] = (kr > 1) ? __fadd_ru(ssec, dl) : -1.f;
     }
@@ -263,6 +299,63 @@ __device__ __forceinline__ bool elk_cand(int j, int32_t ai, float u, float L, co
   if (j == ai || !(u > L)) return false;
   if (FULL && L >= 0.f && __ldg(ccrow + j) <= L) return false;
   return true;
+}
+
+// ------------------------------------------------------------- Yin-Yang
+
+// Per group of 8 consecutive centers, the worst drift: the smallest cosine
+// lower bound, the largest upper bound and the largest sine bound of its
+// centers (together they bound the drift of every center of the group).
+__global__ void k_yy_drift(int32_t k, int32_t ng, const float* __restrict__ pdn, const float* __restrict__ pup,
+                           const float* __restrict__ qup, float* __restrict__ gd) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    float pd = 1.f, pu = -1.f, q = 0.f;
+    for (int j = 8 * g; j < k && j < 8 * g + 8; ++j) {
+      pd = fminf(pd, pdn[j]);
+      pu = fmaxf(pu, pup[j]);
+      q = fmaxf(q, qup[j]);
+    }
+    gd[g] = pd;
+    gd[ng + g] = pu;
+    gd[2 * ng + g] = q;
+  }
+}
+
+// Thread per point: Eq. (eqn:l-bound) for l(i) with the drift of c(a(i)),
+// the clamped Eq. (eqn:u-elkan) for every group bound with the group's worst
+// drift (the update grows as the drift grows, so it bounds every center of
+// the group), then the global test l - 2 delta >= max_G u(i,G).  Group bounds
+// are group-major (ug[G * n + i]).  Survivors go to w1.
+__global__ void __launch_bounds__(kBlock) k_yy_bounds(int64_t n, int32_t ng, const int32_t* __restrict__ a,
+                                                      float* __restrict__ lb, float* __restrict__ ug,
+                                                      const float* __restrict__ dlt, const float* __restrict__ pdn,
+                                                      const float* __restrict__ pup, const float* __restrict__ qup,
+                                                      const float* __restrict__ gd, int moved,
+                                                      int32_t* __restrict__ w1, unsigned long long* __restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    bool take = false;
+    if (i < n) {
+      const int32_t ai = a[i];
+      float l = lb[i];
+      if (moved) {
+        l = bound_l(l, pdn[ai], pup[ai], qup[ai]);
+        lb[i] = l;
+      }
+      float umax = -INFINITY;
+      for (int g = 0; g < ng; ++g) {
+        float u = ug[(int64_t)g * n + i];
+        if (moved) {
+          u = bound_u(u, gd[g], gd[ng + g], gd[2 * ng + g]);
+          ug[(int64_t)g * n + i] = u;
+        }
+        umax = fmaxf(umax, u);
+      }
+      take = !(__fsub_rd(l, 2.f * dlt[i]) >= umax);
+    }
+    warp_push(take, (int32_t)i, w1, cnt + C_W1);
+  }
 }
 
 // Warp per point; each warp walks a tile of kTile consecutive points: lanes
@@ -529,12 +622,13 @@ int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long
 #define SKM_ROWS(M)                                                                                              \
   k_rows_top2<VT, G, M, BATCH><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, \
                                                                   c->kst, c->row_run, c->runs, list, list_cnt,     \
-                                                                  nrows, c->a, c->lb, c->ub, c->chg_i, c->chg_old, \
-                                                                  c->cnt)
+                                                                  nrows, c->n, c->a, c->lb, c->ub, c->chg_i,       \
+                                                                  c->chg_old, c->cnt)
   switch (mode) {
     case 0: SKM_ROWS(0); break;
     case 1: SKM_ROWS(1); break;
-    default: SKM_ROWS(2);
+    case 2: SKM_ROWS(2); break;
+    default: SKM_ROWS(3);
   }
 #undef SKM_ROWS
   SKM_LAUNCHED(c);
@@ -615,6 +709,24 @@ int elkan_step_t(skm_ctx* c) {
   return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
 }
 
+template <typename VT>
+int yinyang_step_t(skm_ctx* c) {
+  const int g = persistent_grid(c);
+  const int32_t ng = (c->k + 7) / 8;
+  if (c->moved) {
+    SKM_PROF_BEGIN(c, "k_yy_drift");
+    k_yy_drift<<<(ng + 127) / 128, 128, 0, c->st>>>(c->k, ng, c->pdn, c->pup, c->qup, c->gdrift);
+    SKM_LAUNCHED(c);
+  }
+  SKM_PROF_BEGIN(c, "k_yy_bounds");
+  k_yy_bounds<<<g, kBlock, 0, c->st>>>(c->n, ng, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->gdrift,
+                                       c->moved, c->w1, c->cnt);
+  SKM_LAUNCHED(c);
+  // the survivors go straight to the group pass: its group test uses the
+  // moved (not tightened) l, and a(i)'s own group is always recomputed
+  return assign_full_t<VT>(c, 3, c->w1, c->cnt + C_W1, 0);
+}
+
 }  // namespace
 
 int hamerly_bounds_only(skm_ctx* c) {
@@ -653,6 +765,19 @@ int elkan_step(skm_ctx* c) {
     case SKM_F32: return elkan_step_t<float>(c);
     case SKM_F16: return elkan_step_t<__half>(c);
     case SKM_BF16: return elkan_step_t<__nv_bfloat16>(c);
+  }
+  return SKM_EINVAL;
+}
+
+}  // namespace skm
+
+namespace skm {
+
+int yinyang_step(skm_ctx* c) {
+  switch (c->dtype) {
+    case SKM_F32: return yinyang_step_t<float>(c);
+    case SKM_F16: return yinyang_step_t<__half>(c);
+    case SKM_BF16: return yinyang_step_t<__nv_bfloat16>(c);
   }
   return SKM_EINVAL;
 }

@@ -329,6 +329,7 @@ struct skm_ctx {
   float* pdn;   // [kst] drift cosine lower bound
   float* pup;   // [kst] drift cosine upper bound
   float* qup;   // [kst] drift sine upper bound
+  float* gdrift;  // [3 ng] Yin-Yang: per group of 8 centers min pd, max pu, max q
   float* hsel;  // [HSEL_N] Hamerly drift summary
   float* cc;    // [k * kst] center-center bounds (full variants)
   float* sc;    // [k] s(j)
@@ -413,6 +414,7 @@ int dense_lower(skm_ctx* c);
 int dense_recheck_cands(skm_ctx* c, bool hamerly);
 int wait_selftest(int64_t timeout_ns, cudaStream_t st);
 int seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_host);
+int yinyang_step(skm_ctx* c);
 
 }  // namespace skm
 

@@ -16,9 +16,9 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
-STANDARD, HAMERLY, ELKAN, SIMP_HAMERLY, SIMP_ELKAN = 0, 1, 2, 3, 4
+STANDARD, HAMERLY, ELKAN, SIMP_HAMERLY, SIMP_ELKAN, YINYANG = 0, 1, 2, 3, 4, 5
 VARIANTS = {"standard": STANDARD, "hamerly": HAMERLY, "elkan": ELKAN, "simp_hamerly": SIMP_HAMERLY,
-            "simp_elkan": SIMP_ELKAN}
+            "simp_elkan": SIMP_ELKAN, "yinyang": YINYANG}
 F32, F16, BF16 = 0, 1, 2
 PREC_FP32, PREC_BF16 = 0, 1
 CSR, DENSE = 0, 1
@@ -293,7 +293,10 @@ class KMeans:
     def bounds(self):
         l = np.empty(self.n, dtype=np.float32)
         elk = self.variant in (ELKAN, SIMP_ELKAN)
-        u = np.empty((self.n, self.k) if elk else self.n, dtype=np.float32)
+        if self.variant == YINYANG:
+            u = np.empty(((self.k + 7) // 8, self.n), dtype=np.float32)
+        else:
+            u = np.empty((self.n, self.k) if elk else self.n, dtype=np.float32)
         _check(load().skm_get_bounds(self._h, _ptr(l), _ptr(u), HOST), "skm_get_bounds")
         return l, u
 

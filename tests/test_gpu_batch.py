@@ -117,7 +117,7 @@ def test_graph_replay_single_run():
     init = synth.init_rows(X.n, 40, 21)
     dev = [torch.from_numpy(a).cuda() for a in (X.row_ptr, X.col, X.val)]
     out = {}
-    for variant in ("standard", "elkan", "simp_elkan", "hamerly"):
+    for variant in ("standard", "elkan", "simp_elkan", "hamerly", "yinyang"):
         for graph in (False, True):
             km = skm.KMeans(X.n, X.d, *dev, 40, variant=variant, init_rows=init, graph=graph)
             out[(variant, graph)] = (km.run(60), km.labels())
@@ -151,7 +151,7 @@ def test_autotune_and_cache(small_batch, tmp_path):
 def test_batch_rejections(small_batch):
     parts, X, run_rows, ks, inits = small_batch
     dev = [torch.from_numpy(a).cuda() for a in (X.row_ptr, X.col, X.val)]
-    for variant in ("hamerly", "elkan", "simp_hamerly"):
+    for variant in ("hamerly", "elkan", "simp_hamerly", "yinyang"):
         with pytest.raises(skm.SkmError):
             skm.Batch(X.n, X.d, *dev, run_rows, ks, variant=variant)
     bad = ks.copy()

@@ -24,7 +24,7 @@ from paper_2107_04074_gb300 import skm  # noqa: E402
 
 GAP = 1e-6
 CTOL = 1e-5
-VARIANTS = ["standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan"]
+VARIANTS = ["standard", "hamerly", "elkan", "simp_hamerly", "simp_elkan", "yinyang"]
 
 
 def _dev(csr):
@@ -141,10 +141,11 @@ def test_variants_bit_identical_and_match_oracle_trajectory(tiny):
     np.testing.assert_allclose(seqs["standard"][1], tr.J[:len(seqs["standard"][1])], rtol=CTOL)
 
 
-@pytest.mark.parametrize("variant", ["hamerly", "elkan", "simp_hamerly", "simp_elkan"])
+@pytest.mark.parametrize("variant", ["hamerly", "elkan", "simp_hamerly", "simp_elkan", "yinyang"])
 def test_bounds_hold_against_exact_similarities(mid, variant):
     """Section 4 invariants after every assignment: l(i) <= <x,c_a>,
-    u(i,j) >= <x,c_j> (Elkan), u(i) >= max_{j != a} <x,c_j> (Hamerly)."""
+    u(i,j) >= <x,c_j> (Elkan), u(i) >= max_{j != a} <x,c_j> (Hamerly),
+    u(i,G) >= max_{j in G, j != a} <x,c_j> (Yin-Yang, groups of 8)."""
     k = 100
     init = synth.init_rows(mid.n, k, 3)
     X = oracle.Data.from_csr(mid)
@@ -162,7 +163,13 @@ def test_bounds_hold_against_exact_similarities(mid, variant):
         S = Xs @ C.T
         s_a = S[np.arange(len(rows)), lab[rows]]
         assert np.all(l[rows] <= s_a + 1e-12)
-        if u.ndim == 2:
+        if variant == "yinyang":
+            S2 = S.copy()
+            S2[np.arange(len(rows)), lab[rows]] = -np.inf
+            for g in range(u.shape[0]):
+                m = S2[:, 8 * g:8 * g + 8].max(axis=1)
+                assert np.all(u[g, rows] >= m - 1e-12)
+        elif u.ndim == 2:
             uu = u[rows]
             mask = np.ones_like(S, dtype=bool)
             mask[np.arange(len(rows)), lab[rows]] = False
@@ -180,7 +187,7 @@ def test_pruning_saves_similarities(mid):
     init = synth.init_rows(mid.n, 100, 2)
     dev = _dev(mid)
     tot = {}
-    for v in ["standard", "hamerly", "elkan"]:
+    for v in ["standard", "hamerly", "elkan", "yinyang"]:
         km = _km(mid, 100, v, init, dev)
         s = 0
         for _ in range(15):
@@ -192,6 +199,7 @@ def test_pruning_saves_similarities(mid):
         tot[v] = s
         km.close()
     assert tot["elkan"] < tot["standard"] and tot["hamerly"] < tot["standard"]
+    assert tot["yinyang"] < tot["standard"]
 
 
 @pytest.mark.parametrize("dtype", ["f16", "bf16"])
