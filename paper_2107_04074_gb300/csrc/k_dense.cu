@@ -436,10 +436,28 @@ __global__ void __launch_bounds__(256) k_dense_classify(const float* __restrict_
 
 // Canonical FP32 dot of a stored row with a center row: one FMA chain over
 // t = 0..d-1 in order (float4 loads when both rows are 16-byte aligned).
-template <bool V4>
+// Canonical FP32 dot of a stored row with a center row: one FMA chain over
+// t = 0..d-1 in order.  V = 8: 32-byte loads (rows 32-byte aligned, d % 8 == 0),
+// V = 4: 16-byte loads, V = 1: scalar loads; the chain is the same.
+__device__ __forceinline__ void ldg_v8(const float* p, float (&r)[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+               : "l"(p));
+}
+
+template <int V>
 __device__ __forceinline__ float dense_dot_seq(const float* __restrict__ x, const float* __restrict__ c, int64_t d) {
   float acc = 0.f;
-  if (V4) {
+  if (V == 8) {
+#pragma unroll 2
+    for (int64_t t = 0; t < d; t += 8) {
+      float xv[8], cv[8];
+      ldg_v8(x + t, xv);
+      ldg_v8(c + t, cv);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc = __fmaf_rn(xv[q], cv[q], acc);
+    }
+  } else if (V == 4) {
     const float4* x4 = reinterpret_cast<const float4*>(x);
     const float4* c4 = reinterpret_cast<const float4*>(c);
 #pragma unroll 4
@@ -467,7 +485,7 @@ __device__ __forceinline__ float dense_dot_seq(const float* __restrict__ x, cons
 // v8 + w, else the row goes to `out` for a whole-row recheck.  Hamerly:
 // l = f_a - delta_i, u = max(other candidates' f + delta_i, next BF16 value
 // + eps_b).
-template <bool HAMERLY, bool V4>
+template <bool HAMERLY, int V>
 __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X, const float* __restrict__ rinv,
                                                      const float* __restrict__ dlt, const float* __restrict__ Cr,
                                                      int64_t d, int32_t k, float eps_b,
@@ -500,7 +518,7 @@ __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X
     const float theta = __fsub_rd(v1, __fmul_ru(2.f, w));
     const bool cand = act && j >= 0 && v >= theta;
     float f = -INFINITY;
-    if (cand) f = __fmul_rn(dense_dot_seq<V4>(X + (int64_t)row * d, Cr + (int64_t)j * d, d), rinv[row]);
+    if (cand) f = __fmul_rn(dense_dot_seq<V>(X + (int64_t)row * d, Cr + (int64_t)j * d, d), rinv[row]);
     const unsigned cm = (__ballot_sync(SKM_FULL_MASK, cand) >> (g * 8)) & 0xFFu;
     const int ncand = __popc(cm);  // the candidates are a prefix of the descending list
     const int32_t cur = act ? a[row] : -1;
@@ -789,18 +807,21 @@ int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned
 int dense_recheck_cands(skm_ctx* c, bool hamerly) {
   SKM_PROF_BEGIN(c, "k_dense_cands");
   const unsigned g = c->nsm * 8;
-  const bool v4 = (c->d % 4 == 0) && ((uintptr_t)c->val % 16 == 0);
+  const uintptr_t xa = (uintptr_t)c->val, ca = (uintptr_t)c->Cr;
+  const int v = (c->d % 8 == 0 && xa % 32 == 0 && ca % 32 == 0) ? 8 : (c->d % 4 == 0 && xa % 16 == 0) ? 4 : 1;
   const float* X = (const float*)c->val;
 #define SKM_CANDS(H, V)                                                                                            \
   k_dense_cands<H, V><<<g, 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->d, c->k, c->eps_b, c->topv, c->topi,     \
                                             c->w3, c->cnt + C_W3, c->a, c->lb, c->ub, c->w2, c->chg_i, c->chg_old, \
                                             c->cnt)
   if (hamerly) {
-    if (v4) SKM_CANDS(true, true);
-    else SKM_CANDS(true, false);
+    if (v == 8) SKM_CANDS(true, 8);
+    else if (v == 4) SKM_CANDS(true, 4);
+    else SKM_CANDS(true, 1);
   } else {
-    if (v4) SKM_CANDS(false, true);
-    else SKM_CANDS(false, false);
+    if (v == 8) SKM_CANDS(false, 8);
+    else if (v == 4) SKM_CANDS(false, 4);
+    else SKM_CANDS(false, 1);
   }
 #undef SKM_CANDS
   SKM_LAUNCHED(c);

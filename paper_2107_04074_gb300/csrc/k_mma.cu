@@ -177,6 +177,7 @@ struct MmaShared {
   uint64_t acc_full[2], acc_empty[2];
   uint64_t mg_full[4], mg_empty[4];  // group 1 -> group 0 hand-over, per TMEM quarter
   int32_t mcount[kBM];               // values group 1 appended per row
+  float mbest[kBM];                  // group 1's best value per row
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -203,6 +204,19 @@ __device__ __forceinline__ void topk_insert(float (&tv)[kTopK], int32_t (&ti)[kT
     tv[0] = s;
     ti[0] = j;
   }
+}
+
+// Keep the buffer entries above thr (in order); returns the count.
+__device__ __forceinline__ int compact_buf(uint2* b, int nap, float thr) {
+  int w = 0;
+  for (int q = 0; q < nap; ++q) {
+    const uint2 e = b[q * kBM];
+    if (__uint_as_float(e.x) > thr) {
+      b[w * kBM] = e;
+      ++w;
+    }
+  }
+  return w;
 }
 
 // Per row: the (at most 8) largest BF16 similarities above B in descending
@@ -382,12 +396,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
         mbar_arrive(&sh->acc_empty[b]);
       }
       if (!ok) break;
+      // keep only the entries above the group's final threshold
+      if (nap <= kCap) nap = compact_buf(mybuf, nap, fmaxf(tau, __fsub_rd(v1, W2)));
       if (grp == 1) {
         if (!may_write) {
           ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_empty[quarter], (lt - 1) & 1, abort_flag));
           if (!ok) break;
         }
         sh->mcount[r_in_tile] = nap;
+        sh->mbest[r_in_tile] = v1;
         mbar_arrive(&sh->mg_full[quarter]);  // releases the buffer and the count
       } else {
         ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_full[quarter], lt & 1, abort_flag));
@@ -395,10 +412,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
         const int nap1 = sh->mcount[r_in_tile];
         const uint2* other = buf + (size_t)kCap * kBM + r_in_tile;
         const int m0 = nap < kCap ? nap : kCap, m1 = nap1 < kCap ? nap1 : kCap;
-        // the best value is always appended (it exceeds the threshold in force)
-        float best = -INFINITY;
-        for (int q = 0; q < m0; ++q) best = fmaxf(best, __uint_as_float(mybuf[q * kBM].x));
-        for (int q = 0; q < m1; ++q) best = fmaxf(best, __uint_as_float(other[q * kBM].x));
+        // the best value of the row: both groups' running maxima (each one
+        // was appended when it became the maximum)
+        const float best = fmaxf(v1, sh->mbest[r_in_tile]);
         const float bnd = fmaxf(tau, __fsub_rd(best, W2));
         float tv[kTopK];
         int32_t ti[kTopK];
