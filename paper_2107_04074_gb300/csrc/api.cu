@@ -221,7 +221,7 @@ int read_counters(skm_ctx* c) {
   SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
   c->stats.last_changed = (int64_t)c->hcnt[C_CHANGED];
   c->stats.last_sims = (int64_t)c->hcnt[C_SIMS];
-  c->stats.last_survivors = (int64_t)c->hcnt[C_W1];
+  c->stats.last_survivors = (int64_t)(c->hcnt[C_W1] + c->hcnt[C_W1L]);
   c->stats.last_rechecks = (int64_t)c->hcnt[C_W2];
   c->stats.last_cand_rechecks = (int64_t)c->hcnt[C_W3];
   return SKM_OK;

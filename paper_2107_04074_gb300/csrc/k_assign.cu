@@ -14,6 +14,8 @@
 //   k_elk_recompute  8-lane group per survivor: its surviving (point, center)
 //                    pairs compacted into lanes, their exact similarities in
 //                    one pass over the row, reassignment under the tie rule.
+//   k_elk_recompute_long  the same for survivors with long rows, a warp per
+//                    point (32 row entries gathered per round trip).
 #include <climits>
 
 #include "skm_internal.cuh"
@@ -36,8 +38,13 @@ constexpr int kBlock = 256;
 // sum runs over the row entries in CSR order (the canonical order).
 // For a batch (runs != nullptr) each row works on its run's slice of the
 // centers (global ids koff + j) and its run's bound row.
+// Resident blocks asked of the compiler: three (at most 80 registers, no
+// spills) up to 512 centers, two for the widest form.  Latency-bound as it is,
+// the kernel runs faster with more warps than with more registers.
+constexpr int rows_min_blocks(int G) { return G >= 8 ? 2 : 3; }
+
 template <typename VT, int G, int MODE, bool BATCH>
-__global__ void __launch_bounds__(kBlock) k_rows_top2(
+__global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
     int64_t kst, const int32_t* __restrict__ row_run, const RunDesc* __restrict__ runs,
@@ -79,12 +86,19 @@ __global__ void __launch_bounds__(kBlock) k_rows_top2(
         }
       }
       const float* cbase = Ct + rg.koff + j0 + lane * 4;
+      // the row's entries 32 at a time, the next 32 loaded ahead
+      int tt_n = 0;
+      float vv_n = 0.f;
+      if (b + lane < e) {
+        tt_n = __ldg(col + b + lane);
+        vv_n = to_f32(val[b + lane]);
+      }
       for (int64_t p0 = b; p0 < e; p0 += 32) {
-        int tt = 0;
-        float vv = 0.f;
-        if (p0 + lane < e) {
-          tt = __ldg(col + p0 + lane);
-          vv = to_f32(val[p0 + lane]);
+        const int tt = tt_n;
+        const float vv = vv_n;
+        if (p0 + 32 + lane < e) {
+          tt_n = __ldg(col + p0 + 32 + lane);
+          vv_n = to_f32(val[p0 + 32 + lane]);
         }
         const int nq = (int)min((int64_t)32, e - p0);
         int q = 0;
@@ -362,12 +376,16 @@ __global__ void __launch_bounds__(kBlock) k_yy_bounds(int64_t n, int32_t ng, con
 // 0..kTile-1 first update l and test the point-level rule for one point each
 // (so the scalar loads overlap), then the warp streams each point's bound
 // row and counts its candidate centers.  A point with 1..cap candidates goes
-// to w1 (recomputed pair by pair), one with more to w2 (recomputed as a whole
-// row); each list gets one atomic per tile.
+// to w1 (recomputed pair by pair) -- from the bottom of w1 up when its row
+// has at most kLongRow entries, else from the top down (w1[n - 1 - pos], for
+// the warp-per-point recompute) -- and one with more to w2 (recomputed as a
+// whole row); each list gets one atomic per tile.
 constexpr int kTile = 8;
+constexpr int kLongRow = 256;
 
 template <bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int64_t kst,
+                                                       const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ row_run,
                                                        const RunDesc* __restrict__ runs, const int32_t* __restrict__ a,
                                                        float* __restrict__ lb, float* __restrict__ ub,
@@ -383,9 +401,10 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
     const int rows = (int)min((int64_t)kTile, n - i0);
     int32_t my_a = 0;
     float my_L = 0.f;
-    bool my_skip = true;
+    bool my_skip = true, my_long = false;
     if (lane < rows) {
       const int64_t i = i0 + lane;
+      my_long = rp[i + 1] - rp[i] > kLongRow;
       my_a = a[i];
       float l = lb[i];
       if (moved) {
@@ -433,7 +452,9 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
       if (mine > rg.cap) many |= 1u << r;
       else if (mine > 0) few |= 1u << r;
     }
-    warp_push((few >> lane) & 1u, (int32_t)(i0 + lane), w1, cnt + C_W1);
+    const bool is_few = (few >> lane) & 1u;
+    warp_push(is_few && !my_long, (int32_t)(i0 + lane), w1, cnt + C_W1);
+    warp_push_down(is_few && my_long, (int32_t)(i0 + lane), w1 + (n - 1), cnt + C_W1L);
     warp_push((many >> lane) & 1u, (int32_t)(i0 + lane), w2, cnt + C_W2);
   }
 }
@@ -487,17 +508,92 @@ __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t*
   return acc;
 }
 
+// The candidates of an Elkan survivor, for an 8-lane group (lane gl): a(i)
+// itself in slot 0, then every j != a with u(i,j) > L and, for full Elkan,
+// cc(a,j) > L (Section 5.2), in ascending center order (lane gl scans 4
+// consecutive centers per step of 32).  Returns their number minus one.
+template <bool FULL>
+__device__ __forceinline__ int elk_candidates(const float* __restrict__ urow, const float* __restrict__ ccrow,
+                                              int32_t ai, float L, int32_t kr, unsigned gmask, int gl, int* sj) {
+  __syncwarp(gmask);
+  if (gl == 0) sj[0] = ai;
+  int m = 0;
+  for (int j0 = 0; j0 < kr; j0 += 32) {
+    const int jb = j0 + gl * 4;
+    unsigned bits = 0;
+    if (jb < kr) {
+      const float4 u4 = *reinterpret_cast<const float4*>(urow + jb);
+      bits |= ((jb + 0 < kr) && elk_cand<FULL>(jb + 0, ai, u4.x, L, ccrow)) ? 1u : 0u;
+      bits |= ((jb + 1 < kr) && elk_cand<FULL>(jb + 1, ai, u4.y, L, ccrow)) ? 2u : 0u;
+      bits |= ((jb + 2 < kr) && elk_cand<FULL>(jb + 2, ai, u4.z, L, ccrow)) ? 4u : 0u;
+      bits |= ((jb + 3 < kr) && elk_cand<FULL>(jb + 3, ai, u4.w, L, ccrow)) ? 8u : 0u;
+    }
+    const int nb = __popc(bits);
+    int incl = nb;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int y = __shfl_up_sync(gmask, incl, o, 8);
+      if (gl >= o) incl += y;
+    }
+    int pos = m + 1 + (incl - nb);
+    for (int c = 0; c < 4; ++c)
+      if (bits & (1u << c)) {
+        if (pos < 8) sj[pos] = jb + c;  // ascending center order
+        ++pos;
+      }
+    m += __shfl_sync(gmask, incl, 7, 8);
+  }
+  __syncwarp(gmask);
+  return m;
+}
+
+// The decision for an Elkan survivor from its candidates' canonical
+// similarities (lane gl holds candidate sj[gl]; lane 0 is a(i)): the best
+// candidate replaces a(i) only on a strict improvement, and among equal maxima
+// the lowest index wins -- the standard variant's rule, because every center
+// left out satisfies sim <= sim(a) (bounds with the 2 delta margin).  Writes
+// the exact u(i,j) of the candidates, l(i), and the label.
+__device__ __forceinline__ void elk_decide(int32_t i, int32_t koff, int32_t ai, int m, int my_j, float sim, float dl,
+                                           float* __restrict__ urow, int32_t* __restrict__ a,
+                                           float* __restrict__ lb, int32_t* __restrict__ chg_i,
+                                           int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt,
+                                           unsigned gmask, int gl, unsigned long long& sims,
+                                           unsigned long long& changed) {
+  const float sa = __shfl_sync(gmask, sim, 0, 8);
+  float bv = (gl >= 1 && gl <= m) ? sim : -INFINITY;
+  int bj = (gl >= 1 && gl <= m) ? my_j : INT_MAX;
+#pragma unroll
+  for (int o = 4; o; o >>= 1) {
+    const float ov = __shfl_xor_sync(gmask, bv, o, 8);
+    const int oj = __shfl_xor_sync(gmask, bj, o, 8);
+    if (ov > bv || (ov == bv && oj < bj)) {
+      bv = ov;
+      bj = oj;
+    }
+  }
+  if (gl >= 1 && gl <= m) urow[my_j] = __fadd_ru(sim, dl);
+  if (gl == 0) {
+    if (m > 0 && bv > sa) {
+      a[i] = koff + bj;
+      lb[i] = __fsub_rd(bv, dl);
+      urow[ai] = __fadd_ru(sa, dl);
+      ++changed;
+      const unsigned long long pos = atomicAdd(cnt + C_CHG, 1ull);
+      chg_i[pos] = i;
+      chg_old[pos] = koff + ai;
+    } else {
+      lb[i] = __fsub_rd(sa, dl);
+    }
+    sims += (unsigned long long)(m + 1);
+  }
+}
+
 // Elkan survivors, an 8-lane group per point (four points per warp).  The
-// surviving (point, center) pairs of the point -- a(i) itself and every
-// j != a with u(i,j) > L and, for full Elkan, cc(a,j) > L (Section 5.2) --
-// are compacted into the group's lanes in ascending center order (lane 0:
-// a(i)); one pass over the row computes all their canonical similarities.
-// This makes l(i) tight (<x, c_a>, Section 5.1) and gives the exact u(i,j) of
-// every candidate; the best candidate replaces a(i) only on a strict
-// improvement, and among equal maxima the lowest index wins -- the standard
-// variant's rule, because every center left out satisfies sim <= sim(a)
-// (bounds with the 2 delta margin).  The bound kernel only sends points with
-// 1..7 candidates here; anything else is recomputed as a whole row.
+// surviving (point, center) pairs of the point are compacted into the group's
+// lanes (elk_candidates); one pass over the row computes all their canonical
+// similarities.  This makes l(i) tight (<x, c_a>, Section 5.1) and gives the
+// exact u(i,j) of every candidate (elk_decide).  The bound kernel only sends
+// points with 1..7 candidates and rows of at most kLongRow entries here.
 template <typename VT, bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
@@ -517,42 +613,11 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
   for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total; slot += ngroups) {
     const int32_t i = w1[slot];
     const RowGeom rg = row_geom<BATCH>(i, k, kst, 0, row_run, runs);
-    const int32_t kr = rg.k;
     const int32_t ai = a[i] - rg.koff;  // local center ids from here on
     const float dl = dlt[i];
     const float L = __fsub_rd(lb[i], 2.f * dl);
     float* urow = ub + rg.ubase;
-    const float* ccrow = cc + (int64_t)ai * kst;
-    __syncwarp(gmask);
-    if (gl == 0) sj[0] = ai;
-    // candidates: lane gl scans 4 consecutive centers per step of 32
-    int m = 0;
-    for (int j0 = 0; j0 < kr; j0 += 32) {
-      const int jb = j0 + gl * 4;
-      unsigned bits = 0;
-      if (jb < kr) {
-        const float4 u4 = *reinterpret_cast<const float4*>(urow + jb);
-        bits |= ((jb + 0 < kr) && elk_cand<FULL>(jb + 0, ai, u4.x, L, ccrow)) ? 1u : 0u;
-        bits |= ((jb + 1 < kr) && elk_cand<FULL>(jb + 1, ai, u4.y, L, ccrow)) ? 2u : 0u;
-        bits |= ((jb + 2 < kr) && elk_cand<FULL>(jb + 2, ai, u4.z, L, ccrow)) ? 4u : 0u;
-        bits |= ((jb + 3 < kr) && elk_cand<FULL>(jb + 3, ai, u4.w, L, ccrow)) ? 8u : 0u;
-      }
-      const int nb = __popc(bits);
-      int incl = nb;
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        const int y = __shfl_up_sync(gmask, incl, o, 8);
-        if (gl >= o) incl += y;
-      }
-      int pos = m + 1 + (incl - nb);
-      for (int c = 0; c < 4; ++c)
-        if (bits & (1u << c)) {
-          if (pos < 8) sj[pos] = jb + c;  // ascending center order
-          ++pos;
-        }
-      m += __shfl_sync(gmask, incl, 7, 8);
-    }
-    __syncwarp(gmask);
+    const int m = elk_candidates<FULL>(urow, cc + (int64_t)ai * kst, ai, L, rg.k, gmask, gl, sj);
     if (m > 7) {  // not expected (the bound kernel routes such points), handled anyway
       if (gl == 0) {
         const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
@@ -561,37 +626,127 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
       continue;
     }
     const int my_j = (gl <= m) ? sj[gl] : -1;
-    const int64_t b = rp[i], e = rp[i + 1];
-    const float sim =
-        __fmul_rn(group8_dot<VT>(b, e, col, val, Ct, kst, my_j >= 0 ? rg.koff + my_j : -1, gmask, gl), rinv[i]);
-    const float sa = __shfl_sync(gmask, sim, 0, 8);
-    // best candidate: largest similarity, lowest index among equal ones
-    float bv = (gl >= 1 && gl <= m) ? sim : -INFINITY;
-    int bj = (gl >= 1 && gl <= m) ? my_j : INT_MAX;
+    const float sim = __fmul_rn(
+        group8_dot<VT>(rp[i], rp[i + 1], col, val, Ct, kst, my_j >= 0 ? rg.koff + my_j : -1, gmask, gl), rinv[i]);
+    elk_decide(i, rg.koff, ai, m, my_j, sim, dl, urow, a, lb, chg_i, chg_old, cnt, gmask, gl, sims, changed);
+  }
+  __syncwarp();
 #pragma unroll
-    for (int o = 4; o; o >>= 1) {
-      const float ov = __shfl_xor_sync(gmask, bv, o, 8);
-      const int oj = __shfl_xor_sync(gmask, bj, o, 8);
-      if (ov > bv || (ov == bv && oj < bj)) {
-        bv = ov;
-        bj = oj;
+  for (int o = 16; o; o >>= 1) {
+    sims += __shfl_xor_sync(SKM_FULL_MASK, sims, o);
+    changed += __shfl_xor_sync(SKM_FULL_MASK, changed, o);
+  }
+  if (lane == 0) {
+    if (sims) atomicAdd(cnt + C_SIMS, sims);
+    if (changed) atomicAdd(cnt + C_CHANGED, changed);
+  }
+}
+
+// The same for survivors with long rows (more than kLongRow entries), a warp
+// per point: lanes 0-7 find the candidates and decide as above.  The dot
+// walks the row 64 entries at a time: every lane takes two entries of a chunk
+// and gathers the center values of all candidates for them into the warp's
+// half of a double buffer in shared memory; the gathers of the next chunk are
+// in flight while the candidate lanes run their FMA chains over this one in
+// CSR order (the chain of group8_dot, so the similarities are bit-identical).
+constexpr int kLongChunk = 64;
+
+template <typename VT, bool FULL, bool BATCH>
+__global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
+    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
+    const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
+    int64_t kst, const int32_t* __restrict__ row_run, const RunDesc* __restrict__ runs,
+    const int32_t* __restrict__ w1_top, const unsigned long long* __restrict__ w1_cnt,
+    int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, const float* __restrict__ cc,
+    int32_t* __restrict__ w2, int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
+    unsigned long long* __restrict__ cnt) {
+  constexpr int NW = kBlock / 32, CH = kLongChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t total = (int64_t)(*w1_cnt);
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  __shared__ int slot_j[NW][8];
+  __shared__ float tile[NW][2][CH][9];  // [buffer][entry of the chunk][candidate], padded
+  __shared__ float tvl[NW][2][CH];      // the chunk's values
+  int* sj = slot_j[warp];
+  unsigned long long sims = 0, changed = 0;
+  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total; slot += nwarps) {
+    const int32_t i = w1_top[-slot];
+    const RowGeom rg = row_geom<BATCH>(i, k, kst, 0, row_run, runs);
+    const int32_t ai = a[i] - rg.koff;
+    const float dl = dlt[i];
+    const float L = __fsub_rd(lb[i], 2.f * dl);
+    float* urow = ub + rg.ubase;
+    int m = 0;
+    if (lane < 8) m = elk_candidates<FULL>(urow, cc + (int64_t)ai * kst, ai, L, rg.k, 0xFFu, lane, sj);
+    m = __shfl_sync(SKM_FULL_MASK, m, 0);
+    __syncwarp();
+    if (m > 7) {
+      if (lane == 0) {
+        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
+        w2[pos] = i;
       }
+      continue;
     }
-    if (gl >= 1 && gl <= m) urow[my_j] = __fadd_ru(sim, dl);
-    if (gl == 0) {
-      if (m > 0 && bv > sa) {
-        a[i] = rg.koff + bj;
-        lb[i] = __fsub_rd(bv, dl);
-        urow[ai] = __fadd_ru(sa, dl);
-        ++changed;
-        const unsigned long long pos = atomicAdd(cnt + C_CHG, 1ull);
-        chg_i[pos] = i;
-        chg_old[pos] = rg.koff + ai;
-      } else {
-        lb[i] = __fsub_rd(sa, dl);
+    const int64_t b = rp[i], e = rp[i + 1];
+    const float* cb = Ct + rg.koff;
+    int jq[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) jq[q] = q <= m ? sj[q] : 0;
+    // entries p0 + lane and p0 + 32 + lane of chunk p0: columns, values, gathers
+    int t0 = b + lane < e ? __ldg(col + b + lane) : 0;
+    int t1 = b + 32 + lane < e ? __ldg(col + b + 32 + lane) : 0;
+    float x0 = b + lane < e ? to_f32(val[b + lane]) : 0.f;
+    float x1 = b + 32 + lane < e ? to_f32(val[b + 32 + lane]) : 0.f;
+    float g0[8], g1[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      g0[q] = (b + lane < e && q <= m) ? __ldg(cb + (int64_t)t0 * kst + jq[q]) : 0.f;
+      g1[q] = (b + 32 + lane < e && q <= m) ? __ldg(cb + (int64_t)t1 * kst + jq[q]) : 0.f;
+    }
+    float acc = 0.f;
+    int buf = 0;
+    for (int64_t p0 = b; p0 < e; p0 += CH, buf ^= 1) {
+      // this chunk into the buffer (the previous reader of this half finished
+      // before the __syncwarp of the last chunk)
+      tvl[warp][buf][lane] = x0;
+      tvl[warp][buf][32 + lane] = x1;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        tile[warp][buf][lane][q] = g0[q];
+        tile[warp][buf][32 + lane][q] = g1[q];
       }
-      sims += (unsigned long long)(m + 1);
+      __syncwarp();
+      // the next chunk's gathers go out before this chunk's FMA chains
+      const int64_t pn = p0 + CH;
+      const bool in0 = pn + lane < e, in1 = pn + 32 + lane < e;
+      t0 = in0 ? __ldg(col + pn + lane) : 0;
+      t1 = in1 ? __ldg(col + pn + 32 + lane) : 0;
+      x0 = in0 ? to_f32(val[pn + lane]) : 0.f;
+      x1 = in1 ? to_f32(val[pn + 32 + lane]) : 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        g0[q] = (in0 && q <= m) ? __ldg(cb + (int64_t)t0 * kst + jq[q]) : 0.f;
+        g1[q] = (in1 && q <= m) ? __ldg(cb + (int64_t)t1 * kst + jq[q]) : 0.f;
+      }
+      if (lane <= m) {
+        const float* tv = tvl[warp][buf];
+        const float(*tl)[9] = tile[warp][buf];
+        if (e - p0 >= CH) {
+#pragma unroll 16
+          for (int q = 0; q < CH; ++q) acc = __fmaf_rn(tv[q], tl[q][lane], acc);
+        } else {
+          const int nq = (int)(e - p0);
+          for (int q = 0; q < nq; ++q) acc = __fmaf_rn(tv[q], tl[q][lane], acc);
+        }
+      }
+      __syncwarp();
     }
+    if (lane < 8) {
+      const int my_j = (lane <= m) ? sj[lane] : -1;
+      const float sim = __fmul_rn(acc, rinv[i]);
+      elk_decide(i, rg.koff, ai, m, my_j, sim, dl, urow, a, lb, chg_i, chg_old, cnt, 0xFFu, lane, sims, changed);
+    }
+    __syncwarp();
   }
   __syncwarp();
 #pragma unroll
@@ -687,7 +842,8 @@ int elkan_step_t(skm_ctx* c) {
   if (row_thresh > 7) row_thresh = 7;
   SKM_PROF_BEGIN(c, "k_elk_bounds");
 #define SKM_ELKB(F, B)                                                                                            \
-  k_elk_bounds<F, B><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->row_run, c->runs, c->a, c->lb, c->ub, c->dlt, \
+  k_elk_bounds<F, B><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->rp, c->row_run, c->runs, c->a, c->lb, c->ub, \
+                                              c->dlt,                                                              \
                                               c->pdn, c->pup, c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1,   \
                                               c->w2, c->cnt)
   if (c->nruns > 0) SKM_ELKB(false, true);
@@ -705,6 +861,16 @@ int elkan_step_t(skm_ctx* c) {
   else if (full) SKM_ELKR(true, false);
   else SKM_ELKR(false, false);
 #undef SKM_ELKR
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_elk_recompute_long");
+#define SKM_ELKL(F, B)                                                                                         \
+  k_elk_recompute_long<VT, F, B><<<g, kBlock, 0, c->st>>>(                                                     \
+      c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->row_run, c->runs, c->w1 + (c->n - 1),         \
+      c->cnt + C_W1L, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
+  if (c->nruns > 0) SKM_ELKL(false, true);
+  else if (full) SKM_ELKL(true, false);
+  else SKM_ELKL(false, false);
+#undef SKM_ELKL
   SKM_LAUNCHED(c);
   return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
 }

@@ -22,9 +22,10 @@ enum Counter {
   C_W2 = 3,       // points needing a full row of similarities
   C_CHG = 4,      // entries of the changed-row list
   C_W3 = 5,       // dense precision form: rows rechecked against a few candidates
-  C_ERR = 6,      // error flags (bit field)
-  C_NDIRTY = 7,   // clusters whose sum changed in the last center update
-  C_NUM = 8
+  C_W1L = 6,      // Elkan: survivors with long rows (kept at the top of w1)
+  C_ERR = 7,      // error flags (bit field)
+  C_NDIRTY = 8,   // clusters whose sum changed in the last center update
+  C_NUM = 9
 };
 
 // Data-preparation error bits (C_ERR).
@@ -219,6 +220,19 @@ __device__ __forceinline__ void warp_push(bool take, int32_t item, int32_t* __re
   if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
   base = __shfl_sync(SKM_FULL_MASK, base, leader);
   if (take) list[base + __popc(m & ((1u << lane) - 1u))] = item;
+}
+
+// The same, filling the list downwards from list_top (list_top[-pos]).
+__device__ __forceinline__ void warp_push_down(bool take, int32_t item, int32_t* __restrict__ list_top,
+                                               unsigned long long* __restrict__ count) {
+  const unsigned m = __ballot_sync(SKM_FULL_MASK, take);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+  base = __shfl_sync(SKM_FULL_MASK, base, leader);
+  if (take) list_top[-(int64_t)(base + __popc(m & ((1u << lane) - 1u)))] = item;
 }
 
 // Is this center update a full recomputation of the sums?  (Else only the
