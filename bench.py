@@ -410,7 +410,8 @@ def trace_run(km, init, n, k):
                      "rows": st.last_rechecks,
                      "assign_ms": round(sum(v[0] for v in pa.values()), 4),
                      "update_ms": round(sum(v[0] for v in pu.values()), 4),
-                     "assign_kernels": {kk: round(v[0], 4) for kk, v in pa.items()}})
+                     "assign_kernels": {kk: round(v[0], 4) for kk, v in pa.items()},
+                     "update_kernels": {kk: round(v[0], 4) for kk, v in pu.items()}})
         if ch == 0:
             break
     return {"trace": rows, "n": n, "k": k}

@@ -17,6 +17,8 @@
 //   k_elk_recompute_long  the same for survivors with long rows, a warp per
 //                    point (32 row entries gathered per round trip).
 #include <climits>
+#include <mutex>
+#include <unordered_map>
 
 #include "skm_internal.cuh"
 
@@ -25,6 +27,21 @@ namespace skm {
 namespace {
 
 constexpr int kBlock = 256;
+
+// Dynamic scheduling over `total` items by `nworkers` warps (or 8-lane
+// groups): worker w takes item w first, then items nworkers + c for
+// c = 0, 1, ... from the counter cnt[C_CURSOR] (one atomic per item, issued
+// while the worker is busy with its current item and read when it is done),
+// so that long rows do not leave the rest of a persistent grid idle.  When
+// every item fits the first round no atomic is issued.  The launcher zeroes
+// the cursor.
+__device__ __forceinline__ unsigned long long grab_issue(unsigned long long* cursor, bool leader, int64_t nworkers,
+                                                         int64_t total) {
+  return (leader && total > nworkers) ? (unsigned long long)nworkers + atomicAdd(cursor, 1ull) : ~0ull >> 1;
+}
+__device__ __forceinline__ int64_t grab_take(unsigned long long v, unsigned mask, int width) {
+  return (int64_t)__shfl_sync(mask, v, 0, width);
+}
 
 // MODE 0: labels only (standard).  MODE 1: also l(i) and Hamerly's u(i).
 // MODE 2: also l(i) and every Elkan bound u(i,j).  MODE 3 (Yin-Yang): only
@@ -54,11 +71,15 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
   constexpr int KT = 128 * G;                     // centers per pass over the row
   constexpr int NB = G >= 8 ? 1 : 8 / G;          // row entries batched per step
   const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t total = list ? (int64_t)(*list_cnt) : nrows;
   unsigned long long my_changed = 0, my_sims = 0;
   ChangedBuf chb;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+  unsigned long long* cursor = cnt + C_CURSOR;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nxt;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
+       w = grab_take(nxt, SKM_FULL_MASK, 32)) {
+    nxt = grab_issue(cursor, lane == 0, nw, total);
     const int64_t i = list ? (int64_t)list[w] : w;
     const RowGeom rg = row_geom<BATCH>(i, k, kst, 0, row_run, runs);
     const int32_t kr = rg.k;
@@ -606,11 +627,15 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
   const int lane = threadIdx.x & 31, gid = lane >> 3, gl = lane & 7;
   const unsigned gmask = 0xFFu << (8 * gid);
   const int64_t total = (int64_t)(*w1_cnt);
-  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
   __shared__ int slot_j[kBlock / 8][8];  // per group: center of each compacted lane
   int* sj = slot_j[threadIdx.x >> 3];
   unsigned long long sims = 0, changed = 0;
-  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total; slot += ngroups) {
+  unsigned long long* cursor = cnt + C_CURSOR;
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  unsigned long long nxt;
+  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total;
+       slot = grab_take(nxt, gmask, 8)) {
+    nxt = grab_issue(cursor, gl == 0, ngroups, total);
     const int32_t i = w1[slot];
     const RowGeom rg = row_geom<BATCH>(i, k, kst, 0, row_run, runs);
     const int32_t ai = a[i] - rg.koff;  // local center ids from here on
@@ -663,13 +688,17 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
   constexpr int NW = kBlock / 32, CH = kLongChunk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t total = (int64_t)(*w1_cnt);
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   __shared__ int slot_j[NW][8];
   __shared__ float tile[NW][2][CH][9];  // [buffer][entry of the chunk][candidate], padded
   __shared__ float tvl[NW][2][CH];      // the chunk's values
   int* sj = slot_j[warp];
   unsigned long long sims = 0, changed = 0;
-  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total; slot += nwarps) {
+  unsigned long long* cursor = cnt + C_CURSOR;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long nxt;
+  for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total;
+       slot = grab_take(nxt, SKM_FULL_MASK, 32)) {
+    nxt = grab_issue(cursor, lane == 0, nwarps, total);
     const int32_t i = w1_top[-slot];
     const RowGeom rg = row_geom<BATCH>(i, k, kst, 0, row_run, runs);
     const int32_t ai = a[i] - rg.koff;
@@ -760,19 +789,49 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
   }
 }
 
-// Persistent kernels: blocks per SM from the options (skm_autotune), else 8.
-inline int persistent_grid(const skm_ctx* c) {
-  const int per_sm = c->opt.blocks_per_sm > 0 ? c->opt.blocks_per_sm : 8;
+// Blocks of a kernel (kBlock threads, static shared memory) resident on one
+// SM, from the occupancy calculator; cached per kernel.
+int fit_blocks(const void* kernel) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(kernel);
+  if (it != cache.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kBlock, 0) != cudaSuccess || nb < 1) {
+    (void)cudaGetLastError();
+    nb = 1;
+  }
+  cache.emplace(kernel, nb);
+  return nb;
+}
+
+// Persistent kernels: as many blocks as are resident at once (at most the
+// blocks per SM of the options, which skm_autotune sets), so that no block
+// waits for a second wave.
+inline int persistent_grid(const skm_ctx* c, const void* kernel) {
+  int per_sm = fit_blocks(kernel);
+  if (c->opt.blocks_per_sm > 0 && c->opt.blocks_per_sm < per_sm) per_sm = c->opt.blocks_per_sm;
   return c->nsm * per_sm;
+}
+
+// Zero the work cursor of the next dynamically scheduled launch.
+inline int reset_cursor(skm_ctx* c) {
+  SKM_CUDA_TRY(cudaMemsetAsync(c->cnt + C_CURSOR, 0, sizeof(unsigned long long), c->st));
+  return SKM_OK;
 }
 
 template <typename VT, int G, bool BATCH>
 int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
-  int64_t g = list ? (int64_t)persistent_grid(c) : (nrows * 32 + kBlock - 1) / kBlock;
-  const int64_t cap = (int64_t)c->nsm * 16;
-  if (g > cap) g = cap;
+  const void* kern = mode == 0   ? (const void*)k_rows_top2<VT, G, 0, BATCH>
+                     : mode == 1 ? (const void*)k_rows_top2<VT, G, 1, BATCH>
+                     : mode == 2 ? (const void*)k_rows_top2<VT, G, 2, BATCH>
+                                 : (const void*)k_rows_top2<VT, G, 3, BATCH>;
+  int64_t g = persistent_grid(c, kern);
+  if (!list && g > (nrows * 32 + kBlock - 1) / kBlock) g = (nrows * 32 + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
   const VT* v = (const VT*)c->val;
+  if (int rc = reset_cursor(c)) return rc;
   SKM_PROF_BEGIN(c, list ? "k_rows_top2(list)" : "k_rows_top2");
 #define SKM_ROWS(M)                                                                                              \
   k_rows_top2<VT, G, M, BATCH><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, \
@@ -809,7 +868,7 @@ int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long
 template <typename VT>
 int hamerly_step_t(skm_ctx* c) {
   const bool full = (c->variant == SKM_HAMERLY);
-  const int g = persistent_grid(c);
+  const int g = persistent_grid(c, full ? (const void*)k_ham_bounds<true> : (const void*)k_ham_bounds<false>);
   SKM_PROF_BEGIN(c, "k_ham_bounds");
   if (full) {
     k_ham_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
@@ -835,39 +894,42 @@ int hamerly_step_t(skm_ctx* c) {
 template <typename VT>
 int elkan_step_t(skm_ctx* c) {
   const bool full = (c->variant == SKM_ELKAN);
-  const int g = persistent_grid(c);
+  const bool batch = c->nruns > 0;
   // a point with more than min(k/8, 7) candidate centers is recomputed as a
   // whole row (the per-pair path gives each point an 8-lane group)
   int32_t row_thresh = c->opt.row_threshold > 0 ? c->opt.row_threshold : (c->k + 7) / 8;
   if (row_thresh > 7) row_thresh = 7;
   SKM_PROF_BEGIN(c, "k_elk_bounds");
 #define SKM_ELKB(F, B)                                                                                            \
-  k_elk_bounds<F, B><<<g, kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->rp, c->row_run, c->runs, c->a, c->lb, c->ub, \
+  k_elk_bounds<F, B><<<persistent_grid(c, (const void*)k_elk_bounds<F, B>), kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->rp, c->row_run, c->runs, c->a, c->lb, c->ub, \
                                               c->dlt,                                                              \
                                               c->pdn, c->pup, c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1,   \
                                               c->w2, c->cnt)
-  if (c->nruns > 0) SKM_ELKB(false, true);
+  if (batch) SKM_ELKB(false, true);
   else if (full) SKM_ELKB(true, false);
   else SKM_ELKB(false, false);
 #undef SKM_ELKB
   SKM_LAUNCHED(c);
   const VT* v = (const VT*)c->val;
+  if (int rc = reset_cursor(c)) return rc;
   SKM_PROF_BEGIN(c, "k_elk_recompute");
 #define SKM_ELKR(F, B)                                                                                           \
-  k_elk_recompute<VT, F, B><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,     \
+  k_elk_recompute<VT, F, B><<<persistent_grid(c, (const void*)k_elk_recompute<VT, F, B>), kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,     \
                                                      c->row_run, c->runs, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, \
                                                      c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
-  if (c->nruns > 0) SKM_ELKR(false, true);
+  if (batch) SKM_ELKR(false, true);
   else if (full) SKM_ELKR(true, false);
   else SKM_ELKR(false, false);
 #undef SKM_ELKR
   SKM_LAUNCHED(c);
+  if (int rc = reset_cursor(c)) return rc;
   SKM_PROF_BEGIN(c, "k_elk_recompute_long");
 #define SKM_ELKL(F, B)                                                                                         \
-  k_elk_recompute_long<VT, F, B><<<g, kBlock, 0, c->st>>>(                                                     \
+  k_elk_recompute_long<VT, F, B><<<persistent_grid(c, (const void*)k_elk_recompute_long<VT, F, B>), kBlock, 0, \
+                                   c->st>>>(                                                                   \
       c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->row_run, c->runs, c->w1 + (c->n - 1),         \
       c->cnt + C_W1L, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
-  if (c->nruns > 0) SKM_ELKL(false, true);
+  if (batch) SKM_ELKL(false, true);
   else if (full) SKM_ELKL(true, false);
   else SKM_ELKL(false, false);
 #undef SKM_ELKL
@@ -877,7 +939,7 @@ int elkan_step_t(skm_ctx* c) {
 
 template <typename VT>
 int yinyang_step_t(skm_ctx* c) {
-  const int g = persistent_grid(c);
+  const int g = persistent_grid(c, (const void*)k_yy_bounds);
   const int32_t ng = (c->k + 7) / 8;
   if (c->moved) {
     SKM_PROF_BEGIN(c, "k_yy_drift");
@@ -896,7 +958,8 @@ int yinyang_step_t(skm_ctx* c) {
 }  // namespace
 
 int hamerly_bounds_only(skm_ctx* c) {
-  const int g = persistent_grid(c);
+  const int g = persistent_grid(
+      c, c->variant == SKM_HAMERLY ? (const void*)k_ham_bounds<true> : (const void*)k_ham_bounds<false>);
   SKM_PROF_BEGIN(c, "k_ham_bounds");
   if (c->variant == SKM_HAMERLY)
     k_ham_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
