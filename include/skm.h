@@ -110,8 +110,9 @@ typedef struct {
                               iterations; iterations after convergence change
                               nothing.  0 (default): one host sync per iteration */
   int32_t graph_check;     /* 0 = 8 */
-  int32_t blocks_per_sm;   /* grid of the persistent bound/recompute kernels,
-                              blocks per SM (0 = 8); skm_autotune sets it */
+  int32_t blocks_per_sm;   /* grid of the persistent bound/recompute kernels:
+                              at most this many blocks per SM (0 = as many
+                              as are resident at once); skm_autotune sets it */
   int32_t reserved[5];
 } skm_options;
 

@@ -310,3 +310,31 @@ def test_incremental_sums_equal_full_recompute(mid):
     np.testing.assert_array_equal(inc.centers(), C)
     inc.close()
     ref.close()
+
+
+@pytest.mark.parametrize("variant", ["elkan", "simp_elkan"])
+def test_long_rows_elkan(variant):
+    """Rows of 200-2000 entries: the Elkan survivors go to the warp-per-point
+    recompute (rows above 256 entries) as well as the 8-lane one.  Teacher-
+    forced against the oracle, and bit for bit the standard variant's labels
+    at every iteration."""
+    cfg = synth.SparseCfg(n=3000, d=8000, seed=31, nnz_kind=1, a=600.0, b=0.5, lo=200, hi=2000, zipf=1.1)
+    csr = synth.tfidf(cfg)
+    assert np.mean(np.diff(csr.row_ptr) > 256) > 0.5
+    init = synth.init_rows(csr.n, 40, 31)
+    seq = _teacher_forced(csr, 40, variant, init, 25)
+    std = _km(csr, 40, "standard", init)
+    km = _km(csr, 40, variant, init)
+    survivors = 0
+    for t in range(len(seq)):
+        ch = km.assign()
+        std.assign()
+        survivors += km.stats().last_survivors
+        np.testing.assert_array_equal(km.labels(), std.labels())
+        np.testing.assert_array_equal(km.labels(), seq[t])
+        if ch == 0:
+            break
+        assert km.update_centers() == std.update_centers()
+    assert survivors > 0  # the per-pair recompute ran
+    km.close()
+    std.close()
