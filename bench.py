@@ -170,6 +170,15 @@ def kernel_bytes(name, it_rows, n, d, k, nnz, variant, full_sum=True):
     return None
 
 
+def gather_bytes(name, it_rows, n, k, nnz):
+    """Center values a whole-row launch gathers (4 B per center of the padded
+    slice per non-zero of the rows it treats): the traffic that binds it, served
+    from L1/L2 since the term-major centers are L2-resident."""
+    if name in ("k_rows_top2", "k_rows_top2(list)"):
+        return int(it_rows * (nnz / n) * 4 * ((k + 7) // 8 * 8))
+    return None
+
+
 def run_ours(args, rank, world, local):
     import torch
     from paper_2107_04074_gb300 import skm
@@ -255,7 +264,7 @@ def run_ours(args, rank, world, local):
     # value), iteration by iteration so that each launch's rows are known
     flush.fill_(1.0)
     km.reset(init)
-    prof_ms, prof_n, prof_bytes = {}, {}, {}
+    prof_ms, prof_n, prof_bytes, prof_gather = {}, {}, {}, {}
     for it in range(MAX_ITERS):
         km.profile(True)
         ch = km.assign()
@@ -274,6 +283,9 @@ def run_ours(args, rank, world, local):
             b = kernel_bytes(nm, rows_of.get(nm, n), n, d, k, nnz, variant, full_sum)
             if b is not None:
                 prof_bytes[nm] = prof_bytes.get(nm, 0) + b * cnt_k
+            gb = gather_bytes(nm, rows_of.get(nm, n), n, k, nnz)
+            if gb is not None:
+                prof_gather[nm] = prof_gather.get(nm, 0) + gb * cnt_k
         if ch == 0:
             break
     km.close()
@@ -294,6 +306,12 @@ def run_ours(args, rank, world, local):
                 "traffic": recorded_traffic(top_name, "rcv1-like-k100"),
                 "avg_launch_us": round(avg_s * 1e6, 2), "launches": prof_n[top_name],
                 "algorithmic_bytes_per_launch": int(ab)}
+        if top_name in prof_gather:
+            gpl = prof_gather[top_name] / prof_n[top_name]
+            roof["gathered_bytes_per_launch"] = int(gpl)
+            roof["gather_GBps"] = round(gpl / avg_s / 1e9, 1)
+            roof["note"] = ("bound by the L1/L2 gathers of center slices (ncu: L1 throughput ~71% of peak, "
+                            "profiles/k_rows_top2_rcv1.md), not by HBM")
     kernel_share = {}
     for nm in sorted(prof_ms, key=lambda x: -prof_ms[x]):
         e = {"ms": round(prof_ms[nm], 3), "launches": prof_n[nm], "share": round(prof_ms[nm] / tot_prof, 4)}

@@ -475,16 +475,19 @@ __device__ __forceinline__ float dense_dot_seq(const float* __restrict__ x, cons
   return acc;
 }
 
-// Precision form, second pass, over the ambiguous rows: an 8-lane group per
-// row, lane q holding the q-th BF16 candidate.  With w = eps_b + delta_i, a
-// center whose BF16 similarity is below v1 - 2w has an FP32 similarity below
-// that of j1, so only the leading candidates with v >= v1 - 2w can win; each
-// gets its canonical FP32 similarity and the winner follows the tie rule (the
-// current label, else the lowest index).  Centers outside the top-8 have BF16
-// similarity <= v8; when all eight are candidates the winner must beat
-// v8 + w, else the row goes to `out` for a whole-row recheck.  Hamerly:
-// l = f_a - delta_i, u = max(other candidates' f + delta_i, next BF16 value
-// + eps_b).
+// Precision form, second pass, over the ambiguous rows.  With w = eps_b +
+// delta_i, a center whose BF16 similarity is below v1 - 2w has an FP32
+// similarity below that of j1, so only the leading candidates of a row's list
+// with v >= v1 - 2w can win; each gets its canonical FP32 similarity and the
+// winner follows the tie rule (the current label, else the lowest index).
+// Centers outside the top-8 have BF16 similarity <= v8; when all eight are
+// candidates the winner must beat v8 + w, else the row goes to `out` for a
+// whole-row recheck.  Hamerly: l = f_a - delta_i, u = max(other candidates'
+// f + delta_i, next BF16 value + eps_b).
+// A warp takes 32 rows at a time (lane r: row r) and spreads their
+// (row, candidate) pairs over its lanes, 32 pairs per round, so that no lane
+// idles while a row has few candidates; each pair's similarity is one lane's
+// FMA chain.  Lane r then decides row r from the similarities in shared memory.
 template <bool HAMERLY, int V>
 __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X, const float* __restrict__ rinv,
                                                      const float* __restrict__ dlt, const float* __restrict__ Cr,
@@ -496,57 +499,92 @@ __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X
                                                      float* __restrict__ ub, int32_t* __restrict__ out,
                                                      int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
                                                      unsigned long long* __restrict__ cnt) {
-  const int lane = threadIdx.x & 31, g = lane >> 3, q = lane & 7;
+  __shared__ int32_t s_j[8][32][kTopK];  // per warp: the listed centers of its 32 rows
+  __shared__ float s_f[8][32][kTopK];    // their FP32 similarities (candidates only)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t total = (int64_t)(*list_cnt);
-  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long changed = 0, sims = 0;
-  // the loop bound is the same for the whole warp (shuffles inside)
-  for (int64_t gb = ((int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 3; gb < total; gb += ngroups) {
-    const int64_t slot = gb + g;
+  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < total;
+       base += nwarps * 32) {
+    const int64_t slot = base + lane;
     const bool act = slot < total;
     const int32_t row = act ? list[slot] : 0;
-    float v = -INFINITY;
-    int32_t j = -1;
+    float v[kTopK];
+    int32_t jj[kTopK];
+    float dl = 0.f, w = 0.f;
+    int ncand = 0;
     if (act) {
-      v = topv[(int64_t)row * kTopK + q];
-      j = topi[(int64_t)row * kTopK + q];
-    }
-    const float v1 = __shfl_sync(SKM_FULL_MASK, v, g * 8);
-    const float v8 = __shfl_sync(SKM_FULL_MASK, v, g * 8 + 7);
-    const float dl = act ? dlt[row] : 0.f;
-    const float w = __fadd_ru(eps_b, dl);
-    const float theta = __fsub_rd(v1, __fmul_ru(2.f, w));
-    const bool cand = act && j >= 0 && v >= theta;
-    float f = -INFINITY;
-    if (cand) f = __fmul_rn(dense_dot_seq<V>(X + (int64_t)row * d, Cr + (int64_t)j * d, d), rinv[row]);
-    const unsigned cm = (__ballot_sync(SKM_FULL_MASK, cand) >> (g * 8)) & 0xFFu;
-    const int ncand = __popc(cm);  // the candidates are a prefix of the descending list
-    const int32_t cur = act ? a[row] : -1;
-    // best candidate under the tie rule
-    float bf = cand ? f : -INFINITY;
-    int32_t bj = cand ? j : INT_MAX;
+      const float4* vp = reinterpret_cast<const float4*>(topv + (int64_t)row * kTopK);
+      const int4* ip = reinterpret_cast<const int4*>(topi + (int64_t)row * kTopK);
+      const float4 v0 = vp[0], v1 = vp[1];
+      const int4 i0 = ip[0], i1 = ip[1];
+      v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w; v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
+      jj[0] = i0.x; jj[1] = i0.y; jj[2] = i0.z; jj[3] = i0.w; jj[4] = i1.x; jj[5] = i1.y; jj[6] = i1.z; jj[7] = i1.w;
+      dl = dlt[row];
+      w = __fadd_ru(eps_b, dl);
+      const float theta = __fsub_rd(v[0], __fmul_ru(2.f, w));
+      // the candidates are a prefix of the descending list
 #pragma unroll
-    for (int o = 4; o; o >>= 1) {
-      const float of = __shfl_xor_sync(SKM_FULL_MASK, bf, o);
-      const int32_t oj = __shfl_xor_sync(SKM_FULL_MASK, bj, o);
-      const bool take = (of > bf) || (of == bf && oj != bj && (oj == cur || (bj != cur && oj < bj)));
-      if (take) {
-        bf = of;
-        bj = oj;
+      for (int q = 0; q < kTopK; ++q) ncand += (jj[q] >= 0 && v[q] >= theta) ? 1 : 0;
+#pragma unroll
+      for (int q = 0; q < kTopK; ++q) s_j[warp][lane][q] = jj[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kTopK; ++q) {
+        v[q] = -INFINITY;
+        jj[q] = -1;
       }
     }
-    // largest BF16 value among the non-candidates (or a bound on it)
-    const float vn_pref = __shfl_sync(SKM_FULL_MASK, v, g * 8 + (ncand < 8 ? ncand : 7));
-    const bool all8 = (ncand == kTopK) && (k > kTopK);
-    const float vnext = (ncand < kTopK) ? vn_pref : (all8 ? v8 : -INFINITY);
-    const bool resolved = ncand > 0 && ((ncand < kTopK) || !all8 || (bf > __fadd_ru(v8, w)));
-    float f2 = -INFINITY;
-    if (HAMERLY) {
-      f2 = (cand && j != bj) ? f : -INFINITY;
+    // pairs: exclusive prefix of the candidate counts over the lanes
+    int incl = ncand;
 #pragma unroll
-      for (int o = 4; o; o >>= 1) f2 = fmaxf(f2, __shfl_xor_sync(SKM_FULL_MASK, f2, o));
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(SKM_FULL_MASK, incl, o);
+      if (lane >= o) incl += y;
     }
-    if (act && q == 0) {
+    const int npairs = __shfl_sync(SKM_FULL_MASK, incl, 31);
+    __syncwarp();
+    for (int p0 = 0; p0 < npairs; p0 += 32) {
+      const int p = p0 + lane;
+      // the row r of pair p: the first lane whose inclusive count exceeds p
+      int r = 0;
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const int c = __shfl_sync(SKM_FULL_MASK, incl, r + step - 1);
+        if (c <= p) r += step;
+      }
+      const int excl_r = __shfl_sync(SKM_FULL_MASK, incl - ncand, r);
+      const int32_t row_r = __shfl_sync(SKM_FULL_MASK, row, r);
+      if (p < npairs) {
+        const int q = p - excl_r;
+        const int32_t j = s_j[warp][r][q];
+        s_f[warp][r][q] = __fmul_rn(dense_dot_seq<V>(X + (int64_t)row_r * d, Cr + (int64_t)j * d, d), rinv[row_r]);
+      }
+    }
+    __syncwarp();
+    if (act) {
+      const int32_t cur = a[row];
+      // best candidate under the tie rule (a total order: any scan order)
+      float bf = -INFINITY;
+      int32_t bj = INT_MAX;
+      for (int q = 0; q < ncand; ++q) {
+        const float of = s_f[warp][lane][q];
+        const int32_t oj = jj[q];
+        const bool take = (of > bf) || (of == bf && oj != bj && (oj == cur || (bj != cur && oj < bj)));
+        if (take) {
+          bf = of;
+          bj = oj;
+        }
+      }
+      // largest BF16 value among the non-candidates (or a bound on it)
+      const bool all8 = (ncand == kTopK) && (k > kTopK);
+      float vnext = -INFINITY;
+#pragma unroll
+      for (int q = 0; q < kTopK; ++q)
+        if (q == ncand) vnext = v[q];
+      if (ncand == kTopK) vnext = all8 ? v[kTopK - 1] : -INFINITY;
+      const bool resolved = ncand > 0 && ((ncand < kTopK) || !all8 || (bf > __fadd_ru(v[kTopK - 1], w)));
       sims += (unsigned long long)ncand;
       if (resolved) {
         a[row] = bj;
@@ -557,6 +595,9 @@ __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X
           chg_old[pos] = cur;
         }
         if (HAMERLY) {
+          float f2 = -INFINITY;
+          for (int q = 0; q < ncand; ++q)
+            if (jj[q] != bj) f2 = fmaxf(f2, s_f[warp][lane][q]);
           lb[row] = __fsub_rd(bf, dl);
           const float u1 = (f2 == -INFINITY) ? -1.f : __fadd_ru(f2, dl);
           const float u2 = (vnext == -INFINITY) ? -1.f : __fadd_ru(vnext, eps_b);
@@ -567,6 +608,7 @@ __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X
         out[pos] = row;
       }
     }
+    __syncwarp();
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
@@ -804,14 +846,27 @@ int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned
   return SKM_OK;
 }
 
+// Blocks of k_dense_cands<H, V> resident on one SM (the occupancy calculator).
+template <bool H, int V>
+int cands_fit() {
+  static int nb = 0;
+  if (nb == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dense_cands<H, V>, 256, 0) != cudaSuccess || nb < 1) {
+      (void)cudaGetLastError();
+      nb = 1;
+    }
+  }
+  return nb;
+}
+
 int dense_recheck_cands(skm_ctx* c, bool hamerly) {
   SKM_PROF_BEGIN(c, "k_dense_cands");
-  const unsigned g = c->nsm * 8;
   const uintptr_t xa = (uintptr_t)c->val, ca = (uintptr_t)c->Cr;
   const int v = (c->d % 8 == 0 && xa % 32 == 0 && ca % 32 == 0) ? 8 : (c->d % 4 == 0 && xa % 16 == 0) ? 4 : 1;
   const float* X = (const float*)c->val;
+  // one resident wave: every warp takes 32 rows at a time
 #define SKM_CANDS(H, V)                                                                                            \
-  k_dense_cands<H, V><<<g, 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->d, c->k, c->eps_b, c->topv, c->topi,     \
+  k_dense_cands<H, V><<<c->nsm * cands_fit<H, V>(), 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->d, c->k, c->eps_b, c->topv, c->topi,     \
                                             c->w3, c->cnt + C_W3, c->a, c->lb, c->ub, c->w2, c->chg_i, c->chg_old, \
                                             c->cnt)
   if (hamerly) {
