@@ -30,11 +30,13 @@ constexpr int kBlock = 256;
 
 // Dynamic scheduling over `total` items by `nworkers` warps (or 8-lane
 // groups): worker w takes item w first, then items nworkers + c for
-// c = 0, 1, ... from the counter cnt[C_CURSOR] (one atomic per item, issued
-// while the worker is busy with its current item and read when it is done),
-// so that long rows do not leave the rest of a persistent grid idle.  When
-// every item fits the first round no atomic is issued.  The launcher zeroes
-// the cursor.
+// c = 0, 1, ... from the kernel's own cursor counter (one atomic per item,
+// issued while the worker is busy with its current item and read when it is
+// done), so that long rows do not leave the rest of a persistent grid idle.
+// When every item fits the first round no atomic is issued.  The cursors are
+// zeroed with the other counters at the start of each assignment (each of
+// these kernels runs at most once per assignment), so no memset separates
+// the kernels of an iteration.
 __device__ __forceinline__ unsigned long long grab_issue(unsigned long long* cursor, bool leader, int64_t nworkers,
                                                          int64_t total) {
   return (leader && total > nworkers) ? (unsigned long long)nworkers + atomicAdd(cursor, 1ull) : ~0ull >> 1;
@@ -630,7 +632,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
   __shared__ int slot_j[kBlock / 8][8];  // per group: center of each compacted lane
   int* sj = slot_j[threadIdx.x >> 3];
   unsigned long long sims = 0, changed = 0;
-  unsigned long long* cursor = cnt + C_CURSOR;
+  unsigned long long* cursor = cnt + C_CURSOR_R;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
   unsigned long long nxt;
   for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total;
@@ -693,7 +695,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
   __shared__ float tvl[NW][2][CH];      // the chunk's values
   int* sj = slot_j[warp];
   unsigned long long sims = 0, changed = 0;
-  unsigned long long* cursor = cnt + C_CURSOR;
+  unsigned long long* cursor = cnt + C_CURSOR_L;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nxt;
   for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total;
@@ -815,11 +817,6 @@ inline int persistent_grid(const skm_ctx* c, const void* kernel) {
   return c->nsm * per_sm;
 }
 
-// Zero the work cursor of the next dynamically scheduled launch.
-inline int reset_cursor(skm_ctx* c) {
-  SKM_CUDA_TRY(cudaMemsetAsync(c->cnt + C_CURSOR, 0, sizeof(unsigned long long), c->st));
-  return SKM_OK;
-}
 
 template <typename VT, int G, bool BATCH>
 int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
@@ -831,7 +828,6 @@ int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long
   if (!list && g > (nrows * 32 + kBlock - 1) / kBlock) g = (nrows * 32 + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
   const VT* v = (const VT*)c->val;
-  if (int rc = reset_cursor(c)) return rc;
   SKM_PROF_BEGIN(c, list ? "k_rows_top2(list)" : "k_rows_top2");
 #define SKM_ROWS(M)                                                                                              \
   k_rows_top2<VT, G, M, BATCH><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, \
@@ -911,7 +907,6 @@ int elkan_step_t(skm_ctx* c) {
 #undef SKM_ELKB
   SKM_LAUNCHED(c);
   const VT* v = (const VT*)c->val;
-  if (int rc = reset_cursor(c)) return rc;
   SKM_PROF_BEGIN(c, "k_elk_recompute");
 #define SKM_ELKR(F, B)                                                                                           \
   k_elk_recompute<VT, F, B><<<persistent_grid(c, (const void*)k_elk_recompute<VT, F, B>), kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,     \
@@ -922,7 +917,6 @@ int elkan_step_t(skm_ctx* c) {
   else SKM_ELKR(false, false);
 #undef SKM_ELKR
   SKM_LAUNCHED(c);
-  if (int rc = reset_cursor(c)) return rc;
   SKM_PROF_BEGIN(c, "k_elk_recompute_long");
 #define SKM_ELKL(F, B)                                                                                         \
   k_elk_recompute_long<VT, F, B><<<persistent_grid(c, (const void*)k_elk_recompute_long<VT, F, B>), kBlock, 0, \

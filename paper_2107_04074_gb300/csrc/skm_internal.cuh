@@ -23,10 +23,12 @@ enum Counter {
   C_CHG = 4,      // entries of the changed-row list
   C_W3 = 5,       // dense precision form: rows rechecked against a few candidates
   C_W1L = 6,      // Elkan: survivors with long rows (kept at the top of w1)
-  C_CURSOR = 7,   // next work item of a dynamically scheduled kernel (reset before each launch)
-  C_ERR = 8,      // error flags (bit field)
-  C_NDIRTY = 9,   // clusters whose sum changed in the last center update
-  C_NUM = 10
+  C_CURSOR = 7,   // next work item of k_rows_top2 (dynamic scheduling)
+  C_CURSOR_R = 8,  // ... of k_elk_recompute
+  C_CURSOR_L = 9,  // ... of k_elk_recompute_long
+  C_ERR = 10,     // error flags (bit field)
+  C_NDIRTY = 11,  // clusters whose sum changed in the last center update
+  C_NUM = 12
 };
 
 // Data-preparation error bits (C_ERR).
