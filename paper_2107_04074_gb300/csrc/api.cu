@@ -151,6 +151,7 @@ int start_from_rows(skm_ctx* c, const std::vector<int64_t>& rows) {
   c->moved = 0;
   c->s64_valid = 0;
   c->chg_fresh = 0;
+  c->cnt_clear = 0;
   std::memset(&c->stats, 0, sizeof(c->stats));
   return SKM_OK;
 }
@@ -620,7 +621,8 @@ int assign_dense(skm_ctx* c) {
 
 int skm_assign(skm_ctx* c, int64_t* n_changed) {
   if (!c) return SKM_EINVAL;
-  SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_ERR, c->st));
+  if (!c->cnt_clear) SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_ERR, c->st));
+  c->cnt_clear = 0;
   int rc;
   if (c->layout == SKM_DENSE) {
     rc = assign_dense(c);
@@ -659,6 +661,7 @@ int skm_update_centers(skm_ctx* c, double* objective) {
   if (!c->chg_fresh) SKM_CUDA_TRY(cudaMemsetAsync(c->cnt + C_CHG, 0, sizeof(unsigned long long), c->st));
   TRY(update_centers(c));
   c->chg_fresh = 0;
+  c->cnt_clear = 1;  // its last kernel zeroed the assignment counters
   c->moved = 1;
   if (objective) {
     SKM_CUDA_TRY(cudaMemcpyAsync(c->hobj, c->obj, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -714,6 +717,7 @@ int skm_run(skm_ctx* c, int32_t max_iters, int32_t* iters_done, double* objectiv
     }
     c->moved = 1;
     c->chg_fresh = 0;
+    c->cnt_clear = 0;
   }
   SKM_CUDA_TRY(cudaMemcpyAsync(c->hobj, c->obj, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
@@ -790,6 +794,7 @@ int skm_set_centers(skm_ctx* c, const float* C, int32_t space) {
   c->moved = 0;
   c->s64_valid = 0;
   c->chg_fresh = 0;
+  c->cnt_clear = 0;
   return rc;
 }
 
@@ -805,6 +810,7 @@ int skm_set_labels(skm_ctx* c, const int32_t* lab, int32_t space) {
   c->have_bounds = 0;
   c->s64_valid = 0;
   c->chg_fresh = 0;
+  c->cnt_clear = 0;
   return SKM_OK;
 }
 

@@ -24,7 +24,8 @@
 //                       cluster keeps c'(j)), partial sums for the drift.
 //   k_drift_final       per center an interval [pd, pu] for cos(angle(c, c'))
 //                       and an upper bound q of its sine, rounded outward.
-//   k_hsel_obj          J = sum_j |S_j| and Hamerly's worst-drift summary.
+//   k_hsel_obj          J = sum_j |S_j| and Hamerly's worst-drift summary; zeroes
+//                       the assignment counters for the next assignment.
 //   k_gram_*            <c_i, c_j> (FP32 products, FP64 across 256-term
 //                       chunks): all tiles when many clusters moved, else only
 //                       the rows of the (at most 64) dirty clusters; then cc
@@ -412,7 +413,11 @@ __global__ void __launch_bounds__(128) k_drift_final(const double* __restrict__ 
 // over the other centers, hence the second value for the argmin's members).
 __global__ void __launch_bounds__(1024) k_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
                                                    const float* __restrict__ qup, const double* __restrict__ nrm,
-                                                   int32_t k, float* __restrict__ hsel, double* __restrict__ obj) {
+                                                   int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
+                                                   unsigned long long* __restrict__ cnt) {
+  // the last kernel of the update to read the assignment's counters has run:
+  // zero them for the next assignment (which then needs no memset)
+  if (threadIdx.x < C_ERR) cnt[threadIdx.x] = 0ull;
   __shared__ float s_pd[1024], s_pu[1024], s_q[1024], s_pd2[1024], s_pu2[1024], s_q2[1024];
   __shared__ int s_jd[1024], s_ju[1024], s_jq[1024];
   __shared__ double s_J[1024];
@@ -722,7 +727,7 @@ int finish_update(skm_ctx* c) {
                                            cnorm);
   SKM_LAUNCHED(c);
   SKM_PROF_BEGIN(c, "k_hsel_obj");
-  k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj);
+  k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj, c->cnt);
   SKM_LAUNCHED(c);
   // ---- center-center bounds (full variants)
   if (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY) {
