@@ -84,15 +84,6 @@ __global__ void k_centers_batch(const float* __restrict__ Ct, int64_t d, int64_t
   }
 }
 
-// Graph replay: record this iteration's changed count and similarities.
-__global__ void k_glog(const unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ glog) {
-  const unsigned long long pos = glog[0];
-  if (pos < (unsigned long long)kLogCap) {
-    glog[2 + 2 * pos] = cnt[C_CHANGED];
-    glog[3 + 2 * pos] = cnt[C_SIMS];
-  }
-  glog[0] = pos + 1;
-}
 
 template <typename T>
 int dalloc(skm_ctx* c, T** p, size_t count) {
@@ -1046,9 +1037,10 @@ namespace {
 
 int capture_iteration(skm_ctx* c) {
   TRY(skm_assign(c, nullptr));
-  k_glog<<<1, 1, 0, c->st>>>(c->cnt, c->glog);
-  SKM_CUDA_TRY(cudaGetLastError());
-  return skm_update_centers(c, nullptr);
+  c->glog_active = c->glog;  // the update's first kernel logs the changed count
+  const int rc = skm_update_centers(c, nullptr);
+  c->glog_active = nullptr;
+  return rc;
 }
 
 }  // namespace

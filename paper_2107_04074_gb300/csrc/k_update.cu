@@ -84,7 +84,17 @@ __global__ void __launch_bounds__(256) k_center_sum(int64_t nchunks, const int32
                                                     int64_t dterm, int32_t kbins, float scale,
                                                     long long* __restrict__ S64, long long* __restrict__ part,
                                                     int s64_valid, const unsigned long long* __restrict__ cnt,
-                                                    int64_t n) {
+                                                    int64_t n, unsigned long long* __restrict__ glog) {
+  // graph replay: the first kernel of the update records the assignment's
+  // changed count and similarities (glog[0] = entries written so far)
+  if (glog && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long pos = glog[0];
+    if (pos < (unsigned long long)kLogCap) {
+      glog[2 + 2 * pos] = cnt[C_CHANGED];
+      glog[3 + 2 * pos] = cnt[C_SIMS];
+    }
+    glog[0] = pos + 1;
+  }
   if (!full_update(s64_valid, cnt, n)) return;
   extern __shared__ int bins_all[];
   const int lane = threadIdx.x & 31;
@@ -680,7 +690,7 @@ int update_centers(skm_ctx* c) {
   SKM_PROF_BEGIN(c, "k_center_sum");
   k_center_sum<<<grid_cap(c->nchunks, wpb, c->nsm), wpb * 32, smem, c->st>>>(
       c->nchunks, c->ch_term, c->ch_idx, c->ch_part, c->t_ptr, c->t_row, (const float*)c->t_val, c->a, k, c->kst,
-      c->runs, c->d, kbins, c->fx_scale, c->S64, c->part64, c->s64_valid, c->cnt, c->n);
+      c->runs, c->d, kbins, c->fx_scale, c->S64, c->part64, c->s64_valid, c->cnt, c->n, c->glog_active);
   SKM_LAUNCHED(c);
   if (c->nmulti > 0) {
     const int64_t kbw = c->nruns > 0 ? kbins : c->kst;

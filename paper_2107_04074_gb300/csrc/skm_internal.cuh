@@ -334,6 +334,7 @@ struct skm_ctx {
   int s64_valid;    // S64 matches the current labels (else: full recompute)
   int chg_fresh;    // the changed-row list belongs to the last assignment
   int cnt_clear;    // the counters [0, C_ERR) were zeroed by the last center update
+  unsigned long long* glog_active;  // while capturing the replayed iteration: glog (k_center_sum logs into it)
   int32_t* chg_i;   // [n] rows whose label changed in the last assignment
   int32_t* chg_old; // [n] their previous labels
   int32_t* dflag;   // [k] cluster sum touched by the incremental update
