@@ -56,9 +56,19 @@ __global__ void k_dense_centers(const float* __restrict__ Ct, int64_t d, int32_t
 
 // FP32 GEMM with fused top-2.  CTA: 128 rows x all centers (tiles of 128),
 // 256 threads (16 x 16), each thread 8 rows x 8 centers, K in chunks of 32
-// through shared memory.  Rows: all (list == nullptr) or list[0..*list_cnt).
-// MODE 0: labels only; MODE 1: also Hamerly's l = s1 - delta, u = s2 + delta.
+// through shared memory, double-buffered: the asynchronous copies of the next
+// chunk (4-byte cp.async into the transposed tiles, zero-filled outside the
+// data) are in flight while this one is multiplied.  Rows: all (list ==
+// nullptr) or list[0..*list_cnt).  MODE 0: labels only; MODE 1: also
+// Hamerly's l = s1 - delta, u = s2 + delta.
 constexpr int kTR = 128, kTC = 128, kKC = 32;
+constexpr size_t kDenseSmem = sizeof(float) * 2 * kKC * (kTR + 4) * 2;
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool in) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(in ? 4 : 0)
+               : "memory");
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X, const float* __restrict__ rinv,
@@ -69,8 +79,9 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
                                                     float* __restrict__ lb, float* __restrict__ ub,
                                                     int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
                                                     unsigned long long* __restrict__ cnt) {
-  __shared__ __align__(16) float As[kKC][kTR + 4];
-  __shared__ __align__(16) float Bs[kKC][kTC + 4];
+  extern __shared__ __align__(16) float dense_smem[];
+  float(*As)[kKC][kTR + 4] = reinterpret_cast<float(*)[kKC][kTR + 4]>(dense_smem);                      // [2]
+  float(*Bs)[kKC][kTC + 4] = reinterpret_cast<float(*)[kKC][kTC + 4]>(dense_smem + 2 * kKC * (kTR + 4));  // [2]
   __shared__ int rows_sh[kTR];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
   const int64_t total = list ? (int64_t)(*list_cnt) : n;
@@ -94,38 +105,53 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
       v1[x] = v2[x] = vc[x] = -INFINITY;
       j1[x] = INT_MAX;
     }
-    for (int j0 = 0; j0 < k; j0 += kTC) {
-      float acc[8][8];
-#pragma unroll
-      for (int x = 0; x < 8; ++x)
-#pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
-      for (int64_t t0 = 0; t0 < d; t0 += kKC) {
-        // A: 128 rows x 32 terms, B: 128 centers x 32 terms, both transposed
-        for (int q = tid; q < kTR * kKC; q += 256) {
-          const int r = q / kKC, kk = q % kKC;
-          const int32_t row = rows_sh[r];
-          const int64_t t = t0 + kk;
-          As[kk][r] = (row >= 0 && t < d) ? X[(int64_t)row * d + t] : 0.f;
-          const int64_t j = j0 + r;
-          Bs[kk][r] = (j < k && t < d) ? Cr[j * d + t] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kKC; ++kk) {
-          const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 8]);
-          const float4 a1 = *reinterpret_cast<const float4*>(&As[kk][ty * 8 + 4]);
-          const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
-          const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
-          const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-          for (int x = 0; x < 8; ++x)
-#pragma unroll
-            for (int y = 0; y < 8; ++y) acc[x][y] = __fmaf_rn(av[x], bv[y], acc[x][y]);
-        }
-        __syncthreads();
+    // chunks ci = (center tile, term chunk) in order; chunk ci + 1 is copied
+    // while chunk ci is multiplied
+    const int nkc = (int)((d + kKC - 1) / kKC), nct = (k + kTC - 1) / kTC, nch = nkc * nct;
+    auto issue = [&](int ci) {
+      const int64_t j0c = (int64_t)(ci / nkc) * kTC, t0c = (int64_t)(ci % nkc) * kKC;
+      const int sb = ci & 1;
+      // A: 128 rows x 32 terms, B: 128 centers x 32 terms, both transposed
+      for (int q = tid; q < kTR * kKC; q += 256) {
+        const int r = q / kKC, kk = q % kKC;
+        const int32_t row = rows_sh[r];
+        const int64_t t = t0c + kk, j = j0c + r;
+        const bool ina = row >= 0 && t < d, inb = j < k && t < d;
+        cp_async4(&As[sb][kk][r], ina ? X + (int64_t)row * d + t : X, ina);
+        cp_async4(&Bs[sb][kk][r], inb ? Cr + j * d + t : Cr, inb);
       }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    issue(0);
+    float acc[8][8];
+    for (int ci = 0; ci < nch; ++ci) {
+      if (ci + 1 < nch) issue(ci + 1);
+      else asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      __syncthreads();
+      const int kc = ci % nkc, sb = ci & 1;
+      if (kc == 0) {
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+      }
+#pragma unroll 4
+      for (int kk = 0; kk < kKC; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[sb][kk][ty * 8]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[sb][kk][ty * 8 + 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[sb][kk][tx * 8]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[sb][kk][tx * 8 + 4]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int x = 0; x < 8; ++x)
+#pragma unroll
+          for (int y = 0; y < 8; ++y) acc[x][y] = __fmaf_rn(av[x], bv[y], acc[x][y]);
+      }
+      __syncthreads();  // this stage is refilled by the copies of chunk ci + 2
+      if (kc != nkc - 1) continue;
+      const int j0 = (ci / nkc) * kTC;
       // fold this center tile into the running top-2 of each row
 #pragma unroll
       for (int x = 0; x < 8; ++x) {
@@ -804,13 +830,19 @@ int dense_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long lo
   // to the tile kernel (each returns at once when the other one applies)
   const int64_t few_limit = (int64_t)c->nsm * 32;
   const float* X = (const float*)c->val;
+  static bool attr = false;
+  if (!attr) {
+    SKM_CUDA_TRY(cudaFuncSetAttribute(k_dense_top2<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem));
+    SKM_CUDA_TRY(cudaFuncSetAttribute(k_dense_top2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem));
+    attr = true;
+  }
   SKM_PROF_BEGIN(c, list ? "k_dense_top2(list)" : "k_dense_top2");
   if (mode == 0)
-    k_dense_top2<0><<<g, 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list, list_cnt, few_limit,
-                                          c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+    k_dense_top2<0><<<g, 256, kDenseSmem, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list, list_cnt,
+                                                   few_limit, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
   else
-    k_dense_top2<1><<<g, 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list, list_cnt, few_limit,
-                                          c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
+    k_dense_top2<1><<<g, 256, kDenseSmem, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->n, c->d, c->k, list, list_cnt,
+                                                   few_limit, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt);
   SKM_LAUNCHED(c);
   if (list) {
     SKM_PROF_BEGIN(c, "k_dense_rows_few");
