@@ -951,14 +951,14 @@ int skm_autotune(skm_ctx* c, const char* cache_path, int32_t iters, int32_t* fro
     }
   }
   const std::vector<int64_t> init = *static_cast<std::vector<int64_t>*>(c->hinit);
-  const int32_t bps[3] = {2, 4, 0};  // blocks per SM of the persistent kernels (0: all that are resident)
+  const int32_t bps[3] = {4, 8, 16};  // blocks per SM of the persistent kernels, capped at what is resident
   const int32_t thrs[3] = {0, 2, 7};
   const int nthr = elk ? 3 : 1;
   cudaEvent_t e0, e1;
   SKM_CUDA_TRY(cudaEventCreate(&e0));
   SKM_CUDA_TRY(cudaEventCreate(&e1));
   float best = INFINITY;
-  int32_t bb = 0, bt = 0;
+  int32_t bb = 8, bt = 0;
   int rc = SKM_OK;
   for (int a = 0; a < 3 && rc == SKM_OK; ++a)
     for (int b = 0; b < nthr && rc == SKM_OK; ++b) {
