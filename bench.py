@@ -265,6 +265,7 @@ def run_ours(args, rank, world, local):
     flush.fill_(1.0)
     km.reset(init)
     prof_ms, prof_n, prof_bytes, prof_gather = {}, {}, {}, {}
+    upd = {"full": [0.0, 0], "incremental": [0.0, 0]}  # center update: ms, count
     for it in range(MAX_ITERS):
         km.profile(True)
         ch = km.assign()
@@ -277,6 +278,10 @@ def run_ours(args, rank, world, local):
         km.profile(False)
         rows_of = {"k_rows_top2": n, "k_rows_top2(list)": st.last_rechecks, "k_elk_recompute": st.last_survivors}
         full_sum = it == 0 or ch * 8 > n
+        if ch:
+            u = upd["full" if full_sum else "incremental"]
+            u[0] += sum(v[0] for v in pu.values())
+            u[1] += 1
         for nm, (ms_k, cnt_k) in list(pa.items()) + list(pu.items()):
             prof_ms[nm] = prof_ms.get(nm, 0.0) + ms_k
             prof_n[nm] = prof_n.get(nm, 0) + cnt_k
@@ -289,6 +294,21 @@ def run_ours(args, rank, world, local):
         if ch == 0:
             break
     km.close()
+    center_update = {kind: {"iterations": c, "ms_per_update": round(t / c, 4) if c else None}
+                     for kind, (t, c) in upd.items()}
+    center_update["note"] = ("CUDA events over all kernels of one center update; incremental = only the changed "
+                             "rows' contributions moved in the exact fixed-point sums (full recompute when more "
+                             "than n/8 labels changed)")
+    # spherical k-means++ seeding of the same data (k passes over the rows)
+    seed_u = np.random.Generator(np.random.PCG64(INIT_SEED + 1)).random(k)
+    kp = make(variant)
+    kp.seed_kmeanspp(seed_u)
+    torch.cuda.synchronize()
+    t_seed = time.perf_counter()
+    kp.seed_kmeanspp(seed_u)
+    torch.cuda.synchronize()
+    seed_ms = (time.perf_counter() - t_seed) * 1e3
+    kp.close()
     tot_prof = sum(prof_ms.values()) or 1.0
     top_name = max(prof_ms, key=prof_ms.get)
     try:
@@ -367,6 +387,9 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "roofline": roof,
         "kernel_time_share": kernel_share,
+        "center_update": center_update,
+        "kmeanspp_seeding": {"ms": round(seed_ms, 3), "k": k, "rows": n,
+                             "note": "one skm_seed_kmeanspp call on the bench data (host-timed, synchronised)"},
         "e2e": {"value": round(e2e_iters / e2e_s, 3), "unit": "Lloyd iterations/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "note": "skm_init with host CSR (H2D copy, row norms, term-major copy) + run + labels to host"},

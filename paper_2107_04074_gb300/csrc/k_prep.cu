@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(1024) k_scan_i64(const int64_t* __restrict__ i
   const int64_t per = (len + 1023) / 1024;
   const int64_t b = tid * per, e = min(len, b + per);
   int64_t s = 0;
+#pragma unroll 8
   for (int64_t q = b; q < e; ++q) s += in[q];
   sh[tid] = s;
   __syncthreads();
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(1024) k_scan_i64(const int64_t* __restrict__ i
     __syncthreads();
   }
   int64_t run = sh[tid] - s;
+#pragma unroll 8
   for (int64_t q = b; q < e; ++q) {
     const int64_t v = in[q];
     out[q] = run;
