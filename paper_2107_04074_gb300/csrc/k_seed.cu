@@ -14,7 +14,8 @@
 // Each chosen row becomes its center column of the term-major array Ct, the
 // same values k_init_centers writes, and the similarities use the canonical
 // FP32 chain of the assignment kernels.
-//   k_seed_column  center column j <- row rows[j] (normalised)
+//   k_seed_column  center column j <- row rows[j] (normalised), also as a
+//                  contiguous vector
 //   k_seed_sims    warp per row: m_i = max(m_i, <x_i, c_j>), q_i, block sums
 //   k_seed_pick    one block: W, T, the chosen row for column j + 1
 #include <climits>
@@ -27,18 +28,36 @@ namespace {
 
 constexpr int kSeedRows = 64;  // rows per block of k_seed_sims (8 per warp)
 
+// Also writes the center as a contiguous vector cvec (d values, all zero but
+// the current center's terms for CSR data), which the similarity pass gathers
+// from: nearby terms share its cache lines, unlike the strided column of Ct.
 template <typename VT>
 __global__ void k_seed_column(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                               const VT* __restrict__ val, const float* __restrict__ rinv, int64_t n, int64_t d,
-                              int dense, int64_t kst, int j, const int64_t* __restrict__ rows, float* __restrict__ Ct) {
+                              int dense, int64_t kst, int j, const int64_t* __restrict__ rows, float* __restrict__ Ct,
+                              float* __restrict__ cvec) {
   const int64_t r = rows[j];
   if (r < 0 || r >= n) return;  // not reachable: the pick always finds a row
   const float ri = rinv[r];
   if (dense) {
-    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) Ct[t * kst + j] = __fmul_rn(to_f32(val[r * d + t]), ri);
+    for (int64_t t = threadIdx.x; t < d; t += blockDim.x) {
+      const float v = __fmul_rn(to_f32(val[r * d + t]), ri);
+      Ct[t * kst + j] = v;
+      cvec[t] = v;
+    }
   } else {
-    for (int64_t p = rp[r] + threadIdx.x; p < rp[r + 1]; p += blockDim.x)
-      Ct[(int64_t)col[p] * kst + j] = __fmul_rn(to_f32(val[p]), ri);
+    // clear the previous center's entries of the vector, then write this one
+    if (j > 0) {
+      const int64_t r0 = rows[j - 1];
+      if (r0 >= 0 && r0 < n)
+        for (int64_t p = rp[r0] + threadIdx.x; p < rp[r0 + 1]; p += blockDim.x) cvec[col[p]] = 0.f;
+      __syncthreads();
+    }
+    for (int64_t p = rp[r] + threadIdx.x; p < rp[r + 1]; p += blockDim.x) {
+      const float v = __fmul_rn(to_f32(val[p]), ri);
+      Ct[(int64_t)col[p] * kst + j] = v;
+      cvec[col[p]] = v;
+    }
   }
 }
 
@@ -62,7 +81,7 @@ template <typename VT>
 __global__ void __launch_bounds__(256) k_seed_sims(int64_t n, int64_t d, int dense, const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ col, const VT* __restrict__ val,
                                                    const float* __restrict__ rinv, const float* __restrict__ Ct,
-                                                   int64_t kst, int j, float* __restrict__ m,
+                                                   int64_t kst, int jc, int j, float* __restrict__ m,
                                                    long long* __restrict__ q, long long* __restrict__ bsum) {
   __shared__ long long wsum[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -71,8 +90,8 @@ __global__ void __launch_bounds__(256) k_seed_sims(int64_t n, int64_t d, int den
     const int64_t i = (int64_t)blockIdx.x * kSeedRows + warp * (kSeedRows / 8) + u;
     if (i >= n) break;
     float dot;
-    if (dense) dot = warp_dot_dense_col<VT>(val + i * d, d, Ct, kst, j);
-    else dot = warp_dot_one<VT>(rp[i], rp[i + 1], col, val, Ct, kst, j);
+    if (dense) dot = warp_dot_dense_col<VT>(val + i * d, d, Ct, kst, jc);
+    else dot = warp_dot_one<VT>(rp[i], rp[i + 1], col, val, Ct, kst, jc);
     const float sim = __fmul_rn(dot, rinv[i]);
     if (lane == 0) {
       const float mi = j == 0 ? sim : fmaxf(m[i], sim);
@@ -165,10 +184,11 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
   const int k = c->k;
   const int dense = c->layout == SKM_DENSE;
   const int64_t nblk = (n + kSeedRows - 1) / kSeedRows;
-  float* m = nullptr;
+  float *m = nullptr, *cvec = nullptr;
   long long *q = nullptr, *bsum = nullptr;
   int64_t* rows = nullptr;
   SKM_CUDA_TRY(cudaMallocAsync((void**)&m, sizeof(float) * n, c->st));
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&cvec, sizeof(float) * d, c->st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&q, sizeof(long long) * n, c->st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&bsum, sizeof(long long) * nblk, c->st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&rows, sizeof(int64_t) * k, c->st));
@@ -178,18 +198,22 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
   rows_host[0] = r0;
   SKM_CUDA_TRY(cudaMemcpyAsync(rows, rows_host, sizeof(int64_t), cudaMemcpyHostToDevice, c->st));
   const VT* v = (const VT*)c->val;
+  if (!dense) SKM_CUDA_TRY(cudaMemsetAsync(cvec, 0, sizeof(float) * d, c->st));
   for (int j = 0; j < k; ++j) {
-    k_seed_column<VT><<<1, 256, 0, c->st>>>(c->rp, c->col, v, c->rinv, n, d, dense, kst, j, rows, c->Ct);
+    k_seed_column<VT><<<1, 256, 0, c->st>>>(c->rp, c->col, v, c->rinv, n, d, dense, kst, j, rows, c->Ct, cvec);
     SKM_LAUNCH_CHECK();
     if (j + 1 == k) break;
-    k_seed_sims<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, d, dense, c->rp, c->col, v, c->rinv, c->Ct, kst, j, m, q,
-                                                       bsum);
+    // the similarities to center j, read from its contiguous copy (the same
+    // FP32 values as column j of Ct)
+    k_seed_sims<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, d, dense, c->rp, c->col, v, c->rinv, cvec, 1, 0, j, m,
+                                                       q, bsum);
     SKM_LAUNCH_CHECK();
     k_seed_pick<<<1, 1024, 0, c->st>>>(bsum, nblk, q, n, u[j + 1], rows, j + 1);
     SKM_LAUNCH_CHECK();
   }
   SKM_CUDA_TRY(cudaMemcpyAsync(rows_host, rows, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, c->st));
   cudaFreeAsync(m, c->st);
+  cudaFreeAsync(cvec, c->st);
   cudaFreeAsync(q, c->st);
   cudaFreeAsync(bsum, c->st);
   cudaFreeAsync(rows, c->st);
