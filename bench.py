@@ -50,6 +50,23 @@ def config_block(cfg, variant, l2_note):
             "parallelism": "replicas"}
 
 
+def whole_job_ms(ms, world, device):
+    """The whole job's time: the slowest rank's (identity for one rank).  Every
+    rank calls it with its own time."""
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms
+
+
+def job_value(world, iters_per_rank, job_ms):
+    """Whole-job throughput of independent replicas (weak scaling): every rank
+    ran iters_per_rank iterations within job_ms."""
+    return world * iters_per_rank / (job_ms / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -244,12 +261,9 @@ def run_ours(args, rank, world, local):
         return {"metric": METRIC, "value": round(world * iters / (ms / 1e3), 3), "unit": "Lloyd iterations/s",
                 "quick": True, "ms_per_step": round(ms / args.steps, 4), "iterations_per_run": iters / args.steps}
     # whole-job time = max over ranks
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = whole_job_ms(ms, world, dev)
     it_per_step = iters / args.steps
-    value = world * iters / (ms / 1e3)
+    value = job_value(world, iters, ms)
 
     # the plain FP32 standard variant at identical labels
     std_steps = max(1, min(args.steps, 3))
