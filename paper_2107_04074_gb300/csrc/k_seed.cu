@@ -16,7 +16,8 @@
 // FP32 chain of the assignment kernels.
 //   k_seed_column  center column j <- row rows[j] (normalised), also as a
 //                  contiguous vector
-//   k_seed_sims    warp per row: m_i = max(m_i, <x_i, c_j>), q_i, block sums
+//   k_seed_sims    m_i = max(m_i, <x_i, c_j>), q_i, block sums (dense rows: a
+//                  warp per row; CSR rows: k_seed_sims_lane, a lane per row)
 //   k_seed_pick    one block: W, T, the chosen row for column j + 1
 #include <climits>
 
@@ -111,9 +112,64 @@ __global__ void __launch_bounds__(256) k_seed_sims(int64_t n, int64_t d, int den
   }
 }
 
+// CSR rows, a lane per row (32 rows per warp, kSeedRowsLane per block): the
+// lane walks its row entry by entry -- four entries' columns, values and
+// center values loaded together -- so that many short FMA chains run side by
+// side instead of one warp-wide chain per row; the chain is the canonical one
+// (CSR order from 0), so the similarities equal warp_dot_one's.
+constexpr int kSeedRowsLane = 256;
+
+template <typename VT>
+__global__ void __launch_bounds__(256) k_seed_sims_lane(int64_t n, const int64_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                        const float* __restrict__ rinv,
+                                                        const float* __restrict__ cvec, int j,
+                                                        float* __restrict__ m, long long* __restrict__ q,
+                                                        long long* __restrict__ bsum) {
+  __shared__ long long wsum[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kSeedRowsLane + threadIdx.x;
+  long long qi = 0;
+  if (i < n) {
+    const int64_t b = rp[i], e = rp[i + 1];
+    float acc = 0.f;
+    int64_t p = b;
+    for (; p + 4 <= e; p += 4) {
+      int t[4];
+      float x[4], c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        t[u] = __ldg(col + p + u);
+        x[u] = to_f32(val[p + u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) c[u] = __ldg(cvec + t[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = __fmaf_rn(x[u], c[u], acc);
+    }
+    for (; p < e; ++p) acc = __fmaf_rn(to_f32(val[p]), __ldg(cvec + __ldg(col + p)), acc);
+    const float sim = __fmul_rn(acc, rinv[i]);
+    const float mi = j == 0 ? sim : fmaxf(m[i], sim);
+    m[i] = mi;
+    qi = __double2ll_rn((1.0 - (double)mi) * 0x1.0p40);
+    if (qi < 0) qi = 0;
+    q[i] = qi;
+  }
+  long long s = qi;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(SKM_FULL_MASK, s, o);
+  if (lane == 0) wsum[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
 __global__ void __launch_bounds__(1024) k_seed_pick(const long long* __restrict__ bsum, int64_t nblk,
-                                                    const long long* __restrict__ q, int64_t n, double u,
-                                                    int64_t* __restrict__ rows, int j) {
+                                                    int64_t rows_per_block, const long long* __restrict__ q,
+                                                    int64_t n, double u, int64_t* __restrict__ rows, int j) {
   __shared__ long long part[1024];
   __shared__ long long total, target, before;
   __shared__ int owner;
@@ -162,7 +218,7 @@ __global__ void __launch_bounds__(1024) k_seed_pick(const long long* __restrict_
     long long acc = before;
     for (int64_t b = b0; b < b1; ++b) {
       if (target < acc + bsum[b]) {
-        const int64_t r0 = b * kSeedRows, r1 = min(n, r0 + kSeedRows);
+        const int64_t r0 = b * rows_per_block, r1 = min(n, r0 + rows_per_block);
         for (int64_t i = r0; i < r1; ++i) {
           acc += q[i];
           if (acc > target) {
@@ -183,7 +239,8 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
   const int64_t n = c->n, d = c->d, kst = c->kst;
   const int k = c->k;
   const int dense = c->layout == SKM_DENSE;
-  const int64_t nblk = (n + kSeedRows - 1) / kSeedRows;
+  const int64_t rpb = dense ? kSeedRows : kSeedRowsLane;  // rows per block of the similarity pass
+  const int64_t nblk = (n + rpb - 1) / rpb;
   float *m = nullptr, *cvec = nullptr;
   long long *q = nullptr, *bsum = nullptr;
   int64_t* rows = nullptr;
@@ -205,10 +262,13 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
     if (j + 1 == k) break;
     // the similarities to center j, read from its contiguous copy (the same
     // FP32 values as column j of Ct)
-    k_seed_sims<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, d, dense, c->rp, c->col, v, c->rinv, cvec, 1, 0, j, m,
-                                                       q, bsum);
+    if (dense)
+      k_seed_sims<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, d, dense, c->rp, c->col, v, c->rinv, cvec, 1, 0, j, m,
+                                                         q, bsum);
+    else
+      k_seed_sims_lane<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, c->rp, c->col, v, c->rinv, cvec, j, m, q, bsum);
     SKM_LAUNCH_CHECK();
-    k_seed_pick<<<1, 1024, 0, c->st>>>(bsum, nblk, q, n, u[j + 1], rows, j + 1);
+    k_seed_pick<<<1, 1024, 0, c->st>>>(bsum, nblk, rpb, q, n, u[j + 1], rows, j + 1);
     SKM_LAUNCH_CHECK();
   }
   SKM_CUDA_TRY(cudaMemcpyAsync(rows_host, rows, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, c->st));
