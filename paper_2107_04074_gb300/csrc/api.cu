@@ -198,7 +198,7 @@ void release(skm_ctx* c) {
                   c->pup,    c->qup,     c->hsel,  c->cc,     c->sc,     c->gpart,  c->a,     c->lb,
                   c->ub,     c->w1,      c->w2,    c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark,
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
-                  c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers};
+                  c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -339,6 +339,8 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
       c->Cb = cb;
       TRY(dalloc(c, &c->topv, (size_t)(n * kTopK)));
       TRY(dalloc(c, &c->topi, (size_t)(n * kTopK)));
+      TRY(dalloc(c, &c->cand, (size_t)(n * 2 * 16)));
+      TRY(dalloc(c, &c->cand_n, (size_t)(n * 2)));
       TRY(dalloc(c, &c->w3, (size_t)n));
       TRY(dense_prep_bf16(c));
       // |BF16 similarity - exact| for a unit row and a center of norm <= 1 + 6u:

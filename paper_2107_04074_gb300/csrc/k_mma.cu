@@ -20,8 +20,10 @@
 // on the best similarity when one is known) to the row's buffer in shared
 // memory: a predicated store, no divergent code; a buffer more than half full
 // first drops the entries the rising threshold has passed.  At the end of the
-// row tile group 0 merges both groups' buffers into the output list.  A buffer
-// that still overflows marks the row for a whole-row recheck.
+// row tile each group compacts its buffer to its final threshold and writes it
+// out; k_topk_merge then merges the two lists of a row into the output list,
+// off the tensor kernel's critical path.  A buffer that still overflows marks
+// the row for a whole-row recheck.
 // Every barrier wait gives up after one second (globaltimer): the kernel
 // then records an error word and leaves its loops; TMEM is freed on exit.
 #include <cuda.h>
@@ -175,12 +177,13 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, uint32_t (&r)[64]) {
 struct MmaShared {
   uint64_t full[kStages], empty[kStages];
   uint64_t acc_full[2], acc_empty[2];
-  uint64_t mg_full[4], mg_empty[4];  // group 1 -> group 0 hand-over, per TMEM quarter
-  int32_t mcount[kBM];               // values group 1 appended per row
-  float mbest[kBM];                  // group 1's best value per row
   uint32_t tmem_base;
   int abort_flag;
 };
+
+// A group's list of a row as written out: cand_n[g n + row] = its length
+// (0..kCap) or kCandOverflow; entry q at cand[(g kCap + q) n + row].
+constexpr uint8_t kCandOverflow = 0xFF;
 
 // Insert (s, j) into a list ordered by value (descending), then center
 // (ascending), if it ranks above the last entry; entries with center -1
@@ -219,15 +222,13 @@ __device__ __forceinline__ int compact_buf(uint2* b, int nap, float thr) {
   return w;
 }
 
-// Per row: the (at most 8) largest BF16 similarities above B in descending
-// order with their centers, then entries with center -1 holding B, where B
-// bounds every center not listed.  A row whose buffer overflowed gets
-// center -1 and value +inf throughout.
+// Per row and group: the BF16 similarities above the group's final
+// threshold (with their centers), or an overflow mark.
 __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, int64_t n,
                                                           int32_t k, int nkb, int nnt, const float* __restrict__ lb,
                                                           const float* __restrict__ dlt, float eps_b, int use_thr,
-                                                          float* __restrict__ topv, int32_t* __restrict__ topi,
+                                                          uint2* __restrict__ cand, uint8_t* __restrict__ cand_n,
                                                           unsigned long long* __restrict__ cnt) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the swizzled tiles
@@ -247,10 +248,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
     for (int b = 0; b < 2; ++b) {
       mbar_init(&sh->acc_full[b], 1);
       mbar_init(&sh->acc_empty[b], 128);
-    }
-    for (int q = 0; q < 4; ++q) {
-      mbar_init(&sh->mg_full[q], 32);
-      mbar_init(&sh->mg_empty[q], 32);
     }
     sh->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -331,16 +328,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
       }
       float v1 = tau;
       int nap = 0;  // values appended (may exceed kCap: overflow)
-      bool may_write = (grp == 0) || (lt == 0);
       for (int nt = 0; nt < nnt; ++nt, ++accidx) {
         const uint32_t b = accidx & 1, use = accidx >> 1;
         if ((int)b != grp) continue;
-        if (!may_write) {
-          // group 0 has read this group's buffer of the previous row tile
-          ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_empty[quarter], (lt - 1) & 1, abort_flag));
-          if (!ok) break;
-          may_write = true;
-        }
         ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->acc_full[b], use & 1, abort_flag));
         if (!ok) break;
         tc_fence_after();
@@ -396,59 +386,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
         mbar_arrive(&sh->acc_empty[b]);
       }
       if (!ok) break;
-      // keep only the entries above the group's final threshold
+      // keep only the entries above the group's final threshold, and write
+      // them out (coalesced: consecutive rows of a slot are adjacent)
       if (nap <= kCap) nap = compact_buf(mybuf, nap, fmaxf(tau, __fsub_rd(v1, W2)));
-      if (grp == 1) {
-        if (!may_write) {
-          ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_empty[quarter], (lt - 1) & 1, abort_flag));
-          if (!ok) break;
-        }
-        sh->mcount[r_in_tile] = nap;
-        sh->mbest[r_in_tile] = v1;
-        mbar_arrive(&sh->mg_full[quarter]);  // releases the buffer and the count
-      } else {
-        ok = __all_sync(SKM_FULL_MASK, mbar_wait(&sh->mg_full[quarter], lt & 1, abort_flag));
-        if (!ok) break;
-        const int nap1 = sh->mcount[r_in_tile];
-        const uint2* other = buf + (size_t)kCap * kBM + r_in_tile;
-        const int m0 = nap < kCap ? nap : kCap, m1 = nap1 < kCap ? nap1 : kCap;
-        // the best value of the row: both groups' running maxima (each one
-        // was appended when it became the maximum)
-        const float best = fmaxf(v1, sh->mbest[r_in_tile]);
-        const float bnd = fmaxf(tau, __fsub_rd(best, W2));
-        float tv[kTopK];
-        int32_t ti[kTopK];
-#pragma unroll
-        for (int q = 0; q < kTopK; ++q) {
-          tv[q] = bnd;
-          ti[q] = -1;
-        }
-        for (int q = 0; q < m0; ++q) {
-          const uint2 e = mybuf[q * kBM];
-          const float sv = __uint_as_float(e.x);
-          if (sv > bnd) topk_insert(tv, ti, sv, (int32_t)e.y);
-        }
-        for (int q = 0; q < m1; ++q) {
-          const uint2 e = other[q * kBM];
-          const float sv = __uint_as_float(e.x);
-          if (sv > bnd) topk_insert(tv, ti, sv, (int32_t)e.y);
-        }
-        mbar_arrive(&sh->mg_empty[quarter]);  // group 1 may refill its buffer
-        if (nap > kCap || nap1 > kCap || ti[0] < 0) {
-#pragma unroll
-          for (int q = 0; q < kTopK; ++q) {
-            tv[q] = INFINITY;
-            ti[q] = -1;
-          }
-        }
-        if (valid) {
-          float4* vo = reinterpret_cast<float4*>(topv + row * kTopK);
-          int4* io = reinterpret_cast<int4*>(topi + row * kTopK);
-          vo[0] = make_float4(tv[0], tv[1], tv[2], tv[3]);
-          vo[1] = make_float4(tv[4], tv[5], tv[6], tv[7]);
-          io[0] = make_int4(ti[0], ti[1], ti[2], ti[3]);
-          io[1] = make_int4(ti[4], ti[5], ti[6], ti[7]);
-        }
+      if (valid) {
+        cand_n[(int64_t)grp * n + row] = nap > kCap ? kCandOverflow : (uint8_t)nap;
+        if (nap <= kCap)
+          for (int q = 0; q < nap; ++q) cand[(int64_t)(grp * kCap + q) * n + row] = mybuf[q * kBM];
       }
     }
   }
@@ -458,6 +402,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
+// Thread per row: the two groups' lists of k_bf16_topk merged into the
+// output.  Per row: the (at most 8) largest BF16 similarities above B in
+// descending order with their centers, then entries with center -1 holding
+// B = max(tau, best - W2), where best is the row's largest value (each group
+// appended its running best whenever it rose) -- B bounds every center not
+// listed.  A row with an overflowed list, or with nothing above B, gets
+// center -1 and value +inf throughout (a whole-row recheck).
+__global__ void __launch_bounds__(256) k_topk_merge(const uint2* __restrict__ cand, const uint8_t* __restrict__ cand_n,
+                                                    int64_t n, const float* __restrict__ lb,
+                                                    const float* __restrict__ dlt, float eps_b, int use_thr,
+                                                    float* __restrict__ topv, int32_t* __restrict__ topi) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const float W2 = __fadd_ru(__fmul_ru(2.f, __fadd_ru(eps_b, dlt[row])), 0x1.0p-20f);
+    const float tau = use_thr ? __fsub_rd(__fsub_rd(__fsub_rd(lb[row], eps_b), W2), 0x1.0p-20f) : -INFINITY;
+    const int c0 = cand_n[row], c1 = cand_n[n + row];
+    const bool over = c0 == kCandOverflow || c1 == kCandOverflow;
+    float tv[kTopK];
+    int32_t ti[kTopK];
+#pragma unroll
+    for (int q = 0; q < kTopK; ++q) {
+      tv[q] = INFINITY;
+      ti[q] = -1;
+    }
+    if (!over) {
+      float best = tau;
+      for (int q = 0; q < c0; ++q) best = fmaxf(best, __uint_as_float(cand[(int64_t)q * n + row].x));
+      for (int q = 0; q < c1; ++q) best = fmaxf(best, __uint_as_float(cand[(int64_t)(kCap + q) * n + row].x));
+      const float bnd = fmaxf(tau, __fsub_rd(best, W2));
+#pragma unroll
+      for (int q = 0; q < kTopK; ++q) tv[q] = bnd;
+      for (int q = 0; q < c0; ++q) {
+        const uint2 e = cand[(int64_t)q * n + row];
+        const float sv = __uint_as_float(e.x);
+        if (sv > bnd) topk_insert(tv, ti, sv, (int32_t)e.y);
+      }
+      for (int q = 0; q < c1; ++q) {
+        const uint2 e = cand[(int64_t)(kCap + q) * n + row];
+        const float sv = __uint_as_float(e.x);
+        if (sv > bnd) topk_insert(tv, ti, sv, (int32_t)e.y);
+      }
+      if (ti[0] < 0) {
+#pragma unroll
+        for (int q = 0; q < kTopK; ++q) tv[q] = INFINITY;
+      }
+    }
+    float4* vo = reinterpret_cast<float4*>(topv + row * kTopK);
+    int4* io = reinterpret_cast<int4*>(topi + row * kTopK);
+    vo[0] = make_float4(tv[0], tv[1], tv[2], tv[3]);
+    vo[1] = make_float4(tv[4], tv[5], tv[6], tv[7]);
+    io[0] = make_int4(ti[0], ti[1], ti[2], ti[3]);
+    io[1] = make_int4(ti[4], ti[5], ti[6], ti[7]);
   }
 }
 
@@ -516,8 +515,13 @@ int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* to
   const int grid = (int)(ntiles < c->nsm ? ntiles : c->nsm);
   const int nkb = (int)((c->d + kBK - 1) / kBK);
   SKM_PROF_BEGIN(c, "k_bf16_topk");
-  k_bf16_topk<<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->eps_b, use_thr, topv,
-                                               topi, c->cnt);
+  k_bf16_topk<<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->eps_b, use_thr,
+                                               c->cand, c->cand_n, c->cnt);
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_topk_merge");
+  const int64_t gm = (c->n + 255) / 256, gcap = (int64_t)c->nsm * 16;
+  k_topk_merge<<<(unsigned)(gm < gcap ? gm : gcap), 256, 0, c->st>>>(c->cand, c->cand_n, c->n, c->lb, c->dlt,
+                                                                     c->eps_b, use_thr, topv, topi);
   SKM_LAUNCHED(c);
   return SKM_OK;
 }

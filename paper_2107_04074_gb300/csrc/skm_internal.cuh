@@ -365,6 +365,8 @@ struct skm_ctx {
   void* Cb;           // [kpad x d] BF16 centers
   float* topv;        // [n x 8] best BF16 similarities per row, descending
   int32_t* topi;      // [n x 8] their centers
+  uint2* cand;        // [2 x 16 x n] the tensor kernel's per-group lists (value bits, center)
+  uint8_t* cand_n;    // [2 x n] their lengths
   int32_t* w3;        // [n] rows rechecked against their candidates
   int32_t* lcount;    // [k] members per cluster
   int32_t* loff;      // [k+1]
