@@ -25,7 +25,7 @@
  *   - Yin-Yang group bounds (Section 5.5 names them without a cosine form;
  *     reading YY below).
  *
- * Readings where the paper is silent (stated once here, listed in the design doc):
+ * Readings where the paper is silent (stated once here):
  *   T  ties: the current label wins; among other centers the lowest index
  *      wins, i.e. a point only moves on a strict improvement.  Before the
  *      first assignment there is no current label.

@@ -84,7 +84,8 @@ class SparseCfg:
     dtype: str = "f32"  # stored value type: f32 | f16
 
 
-# The sparse workloads (see the design doc for the derivation of each recipe).
+# The sparse workloads: TF-IDF-shaped rows whose lengths follow nnz_kind (a, b, lo, hi) and whose
+# terms follow a Zipf law over the vocabulary.
 CSR_TINY = SparseCfg(n=2000, d=5000, seed=1, nnz_kind=0, a=50.0, b=0.0, lo=1, hi=5000, zipf=1.1)
 CSR_RCV1_LIKE = SparseCfg(n=100_000, d=50_000, seed=2, nnz_kind=1, a=120.0, b=0.8, lo=5, hi=2000, zipf=1.1)
 CSR_LARGE = SparseCfg(n=4_000_000, d=200_000, seed=5, nnz_kind=1, a=200.0, b=0.9, lo=10, hi=5000, zipf=1.05,
