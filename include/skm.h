@@ -193,10 +193,15 @@ int skm_get_stats(skm_ctx* ctx, skm_stats* out);
  * tensor-core result of the last assignment, per row the 8 largest BF16
  * similarities in descending order (vals, float[n*8]) and their centers
  * (idx, int32[n*8]; equal values: lower center first; -1 / -inf past k),
- * and the error bound eps_b every BF16 similarity satisfies against the
- * exact one.  Rows the last Hamerly assignment pruned keep older values.
- * Any pointer may be NULL.  SKM_ESTATE otherwise. */
-int skm_get_bf16_topk(skm_ctx* ctx, float* vals, int32_t* idx, float* eps_b, int32_t out_space);
+ * and per row the error bound eps (float[n]) that every BF16 similarity of
+ * the row to the current centers satisfies against the exact one:
+ * eps_i = |xb_i - x_i| (1 + 6u + E_c) + E_c + 1.02 (d + 16) 2^-23, rounded up,
+ * with x_i the unit row, xb_i its BF16 copy, E_c = max_j |bf16(c_j) - c_j| and
+ * u = 2^-24 (Cauchy-Schwarz on <xb, cb> - <x, c>; at most
+ * 2^-7 + 2^-15 + (d + 16) 2^-23, the bound for the worst-case rounding).
+ * Rows the last Hamerly assignment pruned keep older values.  Any pointer may
+ * be NULL; vals/idx/eps live in out_space.  SKM_ESTATE otherwise. */
+int skm_get_bf16_topk(skm_ctx* ctx, float* vals, int32_t* idx, float* eps, int32_t out_space);
 
 /* Batched form: nruns independent clusterings of different row blocks of
  * one CSR matrix (same d) in one context, so that each phase of an iteration

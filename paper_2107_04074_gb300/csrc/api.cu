@@ -198,7 +198,8 @@ void release(skm_ctx* c) {
                   c->pup,    c->qup,     c->hsel,  c->cc,     c->sc,     c->gpart,  c->a,     c->lb,
                   c->ub,     c->w1,      c->w2,    c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark,
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
-                  c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n};
+                  c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n,
+                  c->exr,    c->ebc,     c->ebw};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -342,15 +343,16 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
       TRY(dalloc(c, &c->cand, (size_t)(n * 2 * 16)));
       TRY(dalloc(c, &c->cand_n, (size_t)(n * 2)));
       TRY(dalloc(c, &c->w3, (size_t)n));
+      // |BF16 similarity - exact| for the unit row x and a center c (|c| <= 1 + 6u)
+      // rounded to xb and cb: <xb, cb> - <x, c> = <xb - x, cb> + <x, cb - c>, so by
+      // Cauchy-Schwarz it is at most |xb - x| (1 + 6u + |cb - c|) + |cb - c|, plus
+      // the FP32 accumulation of d products.  exr holds |xb - x| per row (set here,
+      // once), ebc the center terms (set after every center refresh).
+      TRY(dalloc(c, &c->exr, (size_t)n));
+      TRY(dalloc(c, &c->ebc, (size_t)2));
+      TRY(dalloc(c, &c->ebw, (size_t)2));
+      SKM_CUDA_TRY(cudaMemsetAsync(c->ebw, 0, sizeof(unsigned) * 2, c->st));
       TRY(dense_prep_bf16(c));
-      // |BF16 similarity - exact| for a unit row and a center of norm <= 1 + 6u:
-      // each operand is rounded to BF16 (8 significant bits, unit roundoff
-      // u_b = 2^-8) from FP32 values within 2^-24 relative, so a product
-      // carries at most (2 u_b + u_b^2)(1 + 2^-22) |x c|, and sum |x c| <= 1 + 6u
-      // (Cauchy-Schwarz): 2^-7 + 2^-15 covers it.  The FP32 accumulation of d
-      // products (directed or truncating steps, 2^-23 each, partial sums <= 1)
-      // adds (d + 16) 2^-23.
-      c->eps_b = (float)(0x1.0p-7 + 0x1.0p-15 + ((double)d + 16.0) * 0x1.0p-23);
     }
   }
   // ---- labels, bounds, worklists
@@ -827,11 +829,19 @@ int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
   return SKM_OK;
 }
 
-int skm_get_bf16_topk(skm_ctx* c, float* vals, int32_t* idx, float* eps_b, int32_t space) {
+int skm_get_bf16_topk(skm_ctx* c, float* vals, int32_t* idx, float* eps, int32_t space) {
   if (!c) return SKM_EINVAL;
   if (c->layout != SKM_DENSE || c->precision != SKM_PREC_BF16) return SKM_ESTATE;
-  if (eps_b) *eps_b = c->eps_b;
   const cudaMemcpyKind kind = space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (eps) {
+    float* out = eps;
+    if (space == SKM_HOST) TRY(dalloc(c, &out, (size_t)c->n));
+    TRY(dense_bf16_eps(c, out));
+    if (space == SKM_HOST) {
+      SKM_CUDA_TRY(cudaMemcpyAsync(eps, out, sizeof(float) * c->n, cudaMemcpyDeviceToHost, c->st));
+      SKM_CUDA_TRY(cudaFreeAsync(out, c->st));
+    }
+  }
   if (vals) SKM_CUDA_TRY(cudaMemcpyAsync(vals, c->topv, sizeof(float) * kTopK * c->n, kind, c->st));
   if (idx) SKM_CUDA_TRY(cudaMemcpyAsync(idx, c->topi, sizeof(int32_t) * kTopK * c->n, kind, c->st));
   SKM_CUDA_TRY(cudaStreamSynchronize(c->st));

@@ -26,11 +26,86 @@ namespace skm {
 
 namespace {
 
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(SKM_FULL_MASK, v, o);
+  return v;
+}
+
+// Upper bound on a norm from the FP64 sum of its d squared terms: the sum
+// and the terms (a quotient by an FP64 norm) carry at most ~(d + 8) 2^-53
+// relative error, covered by a relative and an absolute (d + 8) 2^-52.
+__device__ __forceinline__ float norm_up(double ss, int64_t d) {
+  const double m = ((double)d + 8.0) * 0x1.0p-52;
+  return __double2float_ru(__dadd_ru(__dmul_ru(__dsqrt_ru(ss), 1.0 + m), m));
+}
+
+// Xb = bf16(x_i * rinv_i), a warp per row, and exr_i >= |Xb_i - x_i/|x_i||
+// (the exact unit row; FP64 norm).  A zero row gives Xb = 0, exr = 0 + margin.
 __global__ void k_dense_bf16(const float* __restrict__ X, const float* __restrict__ rinv, int64_t n, int64_t d,
-                             __nv_bfloat16* __restrict__ Xb) {
-  const int64_t tot = n * d;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x)
-    Xb[q] = __float2bfloat16_rn(__fmul_rn(X[q], rinv[q / d]));
+                             __nv_bfloat16* __restrict__ Xb, float* __restrict__ exr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const float* x = X + i * d;
+    double ss = 0.0;
+    for (int64_t t = lane; t < d; t += 32) ss = fma((double)x[t], (double)x[t], ss);
+    ss = warp_sum_f64(ss);
+    const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+    const float ri = rinv[i];
+    double e2 = 0.0;
+    for (int64_t t = lane; t < d; t += 32) {
+      const __nv_bfloat16 b = __float2bfloat16_rn(__fmul_rn(x[t], ri));
+      Xb[i * d + t] = b;
+      const double df = (double)__bfloat162float(b) - (double)x[t] * inv;
+      e2 = fma(df, df, e2);
+    }
+    e2 = warp_sum_f64(e2);
+    if (lane == 0) exr[i] = norm_up(e2, d);
+  }
+}
+
+// ec_j = |bf16(c_j) - c_j| for every center (a warp each), reduced to
+// E_c = max_j ec_j (float bits compare as unsigned for values >= 0); the
+// last block to finish writes ebc = {1 + 6u + E_c, E_c + 1.02 (d + 16) 2^-23}
+// rounded up -- the per-row bound's center terms: |c_j| <= 1 + 6u, and the
+// FP32 accumulation of d products adds at most 2^-23 of the running sum of
+// |products| <= (1 + ex_i)(1 + 6u + E_c) < 1.02 per step (reading TC) --
+// and zeroes the max and the counter for the next launch.
+__global__ void __launch_bounds__(256) k_center_err(const float* __restrict__ Cr, const __nv_bfloat16* __restrict__ Cb,
+                                                    int64_t d, int32_t k, unsigned* __restrict__ ebw,
+                                                    float* __restrict__ ebc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j < k) {
+    double e2 = 0.0;
+    for (int64_t t = lane; t < d; t += 32) {
+      const double df = (double)__bfloat162float(Cb[j * d + t]) - (double)Cr[j * d + t];
+      e2 = fma(df, df, e2);
+    }
+    e2 = warp_sum_f64(e2);
+    if (lane == 0) {
+      atomicMax(ebw, __float_as_uint(norm_up(e2, d)));
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ebw + 1, 1u) == gridDim.x - 1) {
+      __threadfence();
+      const double ec = (double)__uint_as_float(atomicExch(ebw, 0u));
+      ebc[0] = __double2float_ru(__dadd_ru(1.0 + 6.0 * 0x1.0p-24, ec));
+      ebc[1] = __double2float_ru(__dadd_ru(ec, ((double)d + 16.0) * 0x1.0p-23 * 1.02));
+      atomicExch(ebw + 1, 0u);
+    }
+  }
+}
+
+__global__ void k_bf16_eps_rows(const float* __restrict__ exr, const float* __restrict__ ebc, int64_t n,
+                                float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = bf16_eps(exr, ebc, i);
 }
 
 // Ct (d x kst, term-major) -> Cr (k x d FP32) and Cb (kpad x d BF16, zero
@@ -408,7 +483,8 @@ __global__ void k_dense_lower(int64_t n, const int32_t* __restrict__ a, float* _
 // goes to `amb` for k_dense_cands.
 template <bool HAMERLY>
 __global__ void __launch_bounds__(256) k_dense_classify(const float* __restrict__ topv, const int32_t* __restrict__ topi,
-                                                        const float* __restrict__ dlt, float eps_b, int64_t n,
+                                                        const float* __restrict__ dlt, const float* __restrict__ exr,
+                                                        const float* __restrict__ ebc, int64_t n,
                                                         const int32_t* __restrict__ list,
                                                         const unsigned long long* __restrict__ list_cnt,
                                                         int32_t* __restrict__ a, float* __restrict__ lb,
@@ -427,6 +503,7 @@ __global__ void __launch_bounds__(256) k_dense_classify(const float* __restrict_
       const float2 t = *reinterpret_cast<const float2*>(topv + (int64_t)row * kTopK);
       const float v1 = t.x, v2 = t.y;
       const int j1 = topi[(int64_t)row * kTopK];
+      const float eps_b = bf16_eps(exr, ebc, row);
       const float margin = __fadd_ru(eps_b, dlt[row]);
       cur = a[row];
       if (j1 >= 0 && __fsub_rd(v1, v2) > __fmul_ru(2.f, margin)) {
@@ -517,7 +594,8 @@ __device__ __forceinline__ float dense_dot_seq(const float* __restrict__ x, cons
 template <bool HAMERLY, int V>
 __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X, const float* __restrict__ rinv,
                                                      const float* __restrict__ dlt, const float* __restrict__ Cr,
-                                                     int64_t d, int32_t k, float eps_b,
+                                                     int64_t d, int32_t k, const float* __restrict__ exr,
+                                                     const float* __restrict__ ebc,
                                                      const float* __restrict__ topv, const int32_t* __restrict__ topi,
                                                      const int32_t* __restrict__ list,
                                                      const unsigned long long* __restrict__ list_cnt,
@@ -538,7 +616,7 @@ __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X
     const int32_t row = act ? list[slot] : 0;
     float v[kTopK];
     int32_t jj[kTopK];
-    float dl = 0.f, w = 0.f;
+    float dl = 0.f, w = 0.f, eps_b = 0.f;
     int ncand = 0;
     if (act) {
       const float4* vp = reinterpret_cast<const float4*>(topv + (int64_t)row * kTopK);
@@ -548,6 +626,7 @@ __global__ void __launch_bounds__(256) k_dense_cands(const float* __restrict__ X
       v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w; v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
       jj[0] = i0.x; jj[1] = i0.y; jj[2] = i0.z; jj[3] = i0.w; jj[4] = i1.x; jj[5] = i1.y; jj[6] = i1.z; jj[7] = i1.w;
       dl = dlt[row];
+      eps_b = bf16_eps(exr, ebc, row);
       w = __fadd_ru(eps_b, dl);
       const float theta = __fsub_rd(v[0], __fmul_ru(2.f, w));
       // the candidates are a prefix of the descending list
@@ -809,8 +888,16 @@ inline unsigned grid_cap(int64_t items, int per_block, int nsm, int per_sm = 16)
 
 int dense_prep_bf16(skm_ctx* c) {
   SKM_PROF_BEGIN(c, "k_dense_bf16");
-  k_dense_bf16<<<grid_cap(c->n * c->d, 256, c->nsm), 256, 0, c->st>>>((const float*)c->val, c->rinv, c->n, c->d,
-                                                                      (__nv_bfloat16*)c->Xb);
+  k_dense_bf16<<<grid_cap(c->n, 8, c->nsm), 256, 0, c->st>>>((const float*)c->val, c->rinv, c->n, c->d,
+                                                             (__nv_bfloat16*)c->Xb, c->exr);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
+// out[i] = the row's current BF16 error bound (device memory, n floats).
+int dense_bf16_eps(skm_ctx* c, float* out) {
+  SKM_PROF_BEGIN(c, "k_bf16_eps_rows");
+  k_bf16_eps_rows<<<grid_cap(c->n, 256, c->nsm), 256, 0, c->st>>>(c->exr, c->ebc, c->n, out);
   SKM_LAUNCHED(c);
   return SKM_OK;
 }
@@ -820,6 +907,12 @@ int dense_refresh_centers(skm_ctx* c) {
   SKM_PROF_BEGIN(c, "k_dense_centers");
   k_dense_centers<<<g, dim3(32, 8), 0, c->st>>>(c->Ct, c->d, c->k, c->kst, c->kpad, c->Cr, (__nv_bfloat16*)c->Cb);
   SKM_LAUNCHED(c);
+  if (c->Cb) {
+    SKM_PROF_BEGIN(c, "k_center_err");
+    k_center_err<<<(unsigned)((c->k + 7) / 8), 256, 0, c->st>>>(c->Cr, (const __nv_bfloat16*)c->Cb, c->d, c->k,
+                                                              c->ebw, c->ebc);
+    SKM_LAUNCHED(c);
+  }
   return SKM_OK;
 }
 
@@ -869,10 +962,10 @@ int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned
   SKM_PROF_BEGIN(c, "k_dense_classify");
   const unsigned g = c->nsm * 8;
   if (hamerly)
-    k_dense_classify<true><<<g, 256, 0, c->st>>>(c->topv, c->topi, c->dlt, c->eps_b, c->n, list, list_cnt, c->a,
+    k_dense_classify<true><<<g, 256, 0, c->st>>>(c->topv, c->topi, c->dlt, c->exr, c->ebc, c->n, list, list_cnt, c->a,
                                                  c->lb, c->ub, c->w3, c->chg_i, c->chg_old, c->cnt);
   else
-    k_dense_classify<false><<<g, 256, 0, c->st>>>(c->topv, c->topi, c->dlt, c->eps_b, c->n, list, list_cnt, c->a,
+    k_dense_classify<false><<<g, 256, 0, c->st>>>(c->topv, c->topi, c->dlt, c->exr, c->ebc, c->n, list, list_cnt, c->a,
                                                   c->lb, c->ub, c->w3, c->chg_i, c->chg_old, c->cnt);
   SKM_LAUNCHED(c);
   return SKM_OK;
@@ -898,7 +991,7 @@ int dense_recheck_cands(skm_ctx* c, bool hamerly) {
   const float* X = (const float*)c->val;
   // one resident wave: every warp takes 32 rows at a time
 #define SKM_CANDS(H, V)                                                                                            \
-  k_dense_cands<H, V><<<c->nsm * cands_fit<H, V>(), 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->d, c->k, c->eps_b, c->topv, c->topi,     \
+  k_dense_cands<H, V><<<c->nsm * cands_fit<H, V>(), 256, 0, c->st>>>(X, c->rinv, c->dlt, c->Cr, c->d, c->k, c->exr, c->ebc, c->topv, c->topi,     \
                                             c->w3, c->cnt + C_W3, c->a, c->lb, c->ub, c->w2, c->chg_i, c->chg_old, \
                                             c->cnt)
   if (hamerly) {

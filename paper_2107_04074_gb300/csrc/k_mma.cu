@@ -227,7 +227,8 @@ __device__ __forceinline__ int compact_buf(uint2* b, int nap, float thr) {
 __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, int64_t n,
                                                           int32_t k, int nkb, int nnt, const float* __restrict__ lb,
-                                                          const float* __restrict__ dlt, float eps_b, int use_thr,
+                                                          const float* __restrict__ dlt, const float* __restrict__ exr,
+                                                          const float* __restrict__ ebc, int use_thr,
                                                           uint2* __restrict__ cand, uint8_t* __restrict__ cand_n,
                                                           unsigned long long* __restrict__ cnt) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -323,6 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
       const bool valid = row < n;
       float tau = -INFINITY, W2 = 0.f;
       if (valid) {
+        const float eps_b = bf16_eps(exr, ebc, row);
         W2 = __fadd_ru(__fmul_ru(2.f, __fadd_ru(eps_b, dlt[row])), 0x1.0p-20f);
         if (use_thr) tau = __fsub_rd(__fsub_rd(__fsub_rd(lb[row], eps_b), W2), 0x1.0p-20f);
       }
@@ -414,10 +416,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
 // center -1 and value +inf throughout (a whole-row recheck).
 __global__ void __launch_bounds__(256) k_topk_merge(const uint2* __restrict__ cand, const uint8_t* __restrict__ cand_n,
                                                     int64_t n, const float* __restrict__ lb,
-                                                    const float* __restrict__ dlt, float eps_b, int use_thr,
+                                                    const float* __restrict__ dlt, const float* __restrict__ exr,
+                                                    const float* __restrict__ ebc, int use_thr,
                                                     float* __restrict__ topv, int32_t* __restrict__ topi) {
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
        row += (int64_t)gridDim.x * blockDim.x) {
+    const float eps_b = bf16_eps(exr, ebc, row);
     const float W2 = __fadd_ru(__fmul_ru(2.f, __fadd_ru(eps_b, dlt[row])), 0x1.0p-20f);
     const float tau = use_thr ? __fsub_rd(__fsub_rd(__fsub_rd(lb[row], eps_b), W2), 0x1.0p-20f) : -INFINITY;
     const int c0 = cand_n[row], c1 = cand_n[n + row];
@@ -515,13 +519,13 @@ int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* to
   const int grid = (int)(ntiles < c->nsm ? ntiles : c->nsm);
   const int nkb = (int)((c->d + kBK - 1) / kBK);
   SKM_PROF_BEGIN(c, "k_bf16_topk");
-  k_bf16_topk<<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->eps_b, use_thr,
-                                               c->cand, c->cand_n, c->cnt);
+  k_bf16_topk<<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->exr, c->ebc,
+                                               use_thr, c->cand, c->cand_n, c->cnt);
   SKM_LAUNCHED(c);
   SKM_PROF_BEGIN(c, "k_topk_merge");
   const int64_t gm = (c->n + 255) / 256, gcap = (int64_t)c->nsm * 16;
   k_topk_merge<<<(unsigned)(gm < gcap ? gm : gcap), 256, 0, c->st>>>(c->cand, c->cand_n, c->n, c->lb, c->dlt,
-                                                                     c->eps_b, use_thr, topv, topi);
+                                                                     c->exr, c->ebc, use_thr, topv, topi);
   SKM_LAUNCHED(c);
   return SKM_OK;
 }

@@ -152,6 +152,14 @@ __device__ __forceinline__ float warp_dot_lanes(int64_t b, int64_t e, const int3
   return acc;
 }
 
+// Precision form: bound on |BF16 tensor-core similarity - exact similarity|
+// for row i against every center, eps_i = ex_i (1 + 6u + E_c) + E_c + acc
+// (rounded up), from the row's and the centers' rounding errors as vectors
+// (Cauchy-Schwarz); ebc holds the two per-iteration terms.
+__device__ __forceinline__ float bf16_eps(const float* __restrict__ exr, const float* __restrict__ ebc, int64_t i) {
+  return __fmaf_ru(exr[i], ebc[0], ebc[1]);
+}
+
 // Eq. (eqn:l-bound) with the clamp of the angle triangle inequality, in FP32
 // rounded towards -inf.  The drift of the center is an interval: its cosine p
 // lies in [pd, pu] and its sine is at most q.
@@ -359,7 +367,9 @@ struct skm_ctx {
   // dense rows (layout SKM_DENSE)
   int32_t precision;  // SKM_PREC_*
   int32_t kpad;       // centers padded to the tensor-core tile (256)
-  float eps_b;        // bound on |BF16 similarity - exact similarity|
+  float* exr;         // [n] |bf16(x_i/|x_i|) - x_i/|x_i||, rounded up (precision form)
+  float* ebc;         // [2] {1 + 6u + E_c, E_c + accumulation term}, E_c = max_j |bf16(c_j) - c_j|
+  unsigned* ebw;      // [2] k_center_err's running max (float bits) and block counter; zero between launches
   void* Xb;           // [n x d] BF16 unit rows
   float* Cr;          // [k x d] FP32 centers, row-major
   void* Cb;           // [kpad x d] BF16 centers
@@ -424,6 +434,7 @@ int finish_update(skm_ctx* c);
 // dense rows (k_dense.cu, k_mma.cu)
 int dense_prep_bf16(skm_ctx* c);
 int dense_refresh_centers(skm_ctx* c);
+int dense_bf16_eps(skm_ctx* c, float* out);
 int dense_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt);
 int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned long long* list_cnt);
 int dense_tighten(skm_ctx* c);

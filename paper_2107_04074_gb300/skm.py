@@ -320,13 +320,13 @@ class KMeans:
 
     def bf16_topk(self):
         """(n x 8 best BF16 similarities in descending order, n x 8 their centers) of the last
-        assignment, and the error bound eps_b."""
+        assignment, and each row's error bound eps (n floats) against the exact similarities."""
         vals = np.empty((self.n, 8), dtype=np.float32)
         idx = np.empty((self.n, 8), dtype=np.int32)
-        eps = ctypes.c_float(0)
-        _check(load().skm_get_bf16_topk(self._h, _ptr(vals), _ptr(idx), ctypes.byref(eps), HOST),
+        eps = np.empty(self.n, dtype=np.float32)
+        _check(load().skm_get_bf16_topk(self._h, _ptr(vals), _ptr(idx), _ptr(eps), HOST),
                "skm_get_bf16_topk")
-        return vals, idx, eps.value
+        return vals, idx, eps
 
     def seed_kmeanspp(self, u) -> np.ndarray:
         """Spherical k-means++ seeding from the k uniform draws u (Section 5.6);
