@@ -26,46 +26,41 @@ namespace skm {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum_f64(double v) {
+// Sum over a warp, each step rounded up (an upper bound for terms >= 0).
+__device__ __forceinline__ float warp_sum_up(float v) {
 #pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(SKM_FULL_MASK, v, o);
+  for (int o = 16; o; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(SKM_FULL_MASK, v, o));
   return v;
 }
 
-// Upper bound on a norm from the FP64 sum of its d squared terms: the sum
-// and the terms (a quotient by an FP64 norm) carry at most ~(d + 8) 2^-53
-// relative error, covered by a relative and an absolute (d + 8) 2^-52.
-__device__ __forceinline__ float norm_up(double ss, int64_t d) {
-  const double m = ((double)d + 8.0) * 0x1.0p-52;
-  return __double2float_ru(__dadd_ru(__dmul_ru(__dsqrt_ru(ss), 1.0 + m), m));
-}
-
-// Xb = bf16(x_i * rinv_i), a warp per row, and exr_i >= |Xb_i - x_i/|x_i||
-// (the exact unit row; FP64 norm).  A zero row gives Xb = 0, exr = 0 + margin.
+// Xb = bf16(y_i), y_i = fl(x_i * rinv_i) (a warp per row), and
+// exr_i >= |Xb_i - x_i/|x_i||.  The BF16 rounding error y - bf16(y) of an
+// FP32 value is exact in FP32, and its squares are summed with every step
+// rounded up; y_i itself is within 2^-23 (1 + (d + 8) 2^-30) of the exact
+// unit row (one rounding of each product, one of rinv from an FP64 norm of d
+// squares), added at the end.
 __global__ void k_dense_bf16(const float* __restrict__ X, const float* __restrict__ rinv, int64_t n, int64_t d,
                              __nv_bfloat16* __restrict__ Xb, float* __restrict__ exr) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float yerr = __fmul_ru(0x1.0p-23f, __fadd_ru(1.f, __fmul_ru((float)(d + 8), 0x1.0p-30f)));
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
-    const float* x = X + i * d;
-    double ss = 0.0;
-    for (int64_t t = lane; t < d; t += 32) ss = fma((double)x[t], (double)x[t], ss);
-    ss = warp_sum_f64(ss);
-    const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
     const float ri = rinv[i];
-    double e2 = 0.0;
+    float e2 = 0.f;
     for (int64_t t = lane; t < d; t += 32) {
-      const __nv_bfloat16 b = __float2bfloat16_rn(__fmul_rn(x[t], ri));
+      const float y = __fmul_rn(X[i * d + t], ri);
+      const __nv_bfloat16 b = __float2bfloat16_rn(y);
       Xb[i * d + t] = b;
-      const double df = (double)__bfloat162float(b) - (double)x[t] * inv;
-      e2 = fma(df, df, e2);
+      const float e = __fsub_rn(y, __bfloat162float(b));  // exact
+      e2 = __fmaf_ru(e, e, e2);
     }
-    e2 = warp_sum_f64(e2);
-    if (lane == 0) exr[i] = norm_up(e2, d);
+    e2 = warp_sum_up(e2);
+    if (lane == 0) exr[i] = __fadd_ru(__fsqrt_ru(e2), yerr);
   }
 }
 
-// ec_j = |bf16(c_j) - c_j| for every center (a warp each), reduced to
+// ec_j = |bf16(c_j) - c_j| for every center (a warp each; the differences
+// are exact in FP32, their squares summed rounding up), reduced to
 // E_c = max_j ec_j (float bits compare as unsigned for values >= 0); the
 // last block to finish writes ebc = {1 + 6u + E_c, E_c + 1.02 (d + 16) 2^-23}
 // rounded up -- the per-row bound's center terms: |c_j| <= 1 + 6u, and the
@@ -78,14 +73,14 @@ __global__ void __launch_bounds__(256) k_center_err(const float* __restrict__ Cr
   const int lane = threadIdx.x & 31;
   const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (j < k) {
-    double e2 = 0.0;
+    float e2 = 0.f;
     for (int64_t t = lane; t < d; t += 32) {
-      const double df = (double)__bfloat162float(Cb[j * d + t]) - (double)Cr[j * d + t];
-      e2 = fma(df, df, e2);
+      const float e = __fsub_rn(Cr[j * d + t], __bfloat162float(Cb[j * d + t]));  // exact
+      e2 = __fmaf_ru(e, e, e2);
     }
-    e2 = warp_sum_f64(e2);
+    e2 = warp_sum_up(e2);
     if (lane == 0) {
-      atomicMax(ebw, __float_as_uint(norm_up(e2, d)));
+      atomicMax(ebw, __float_as_uint(__fsqrt_ru(e2)));
       __threadfence();
     }
   }

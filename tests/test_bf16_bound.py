@@ -110,3 +110,21 @@ def test_bf16_emulation_matches_torch():
                         (1.0 + (np.arange(256) + 0.5) / 128.0) * 2.0 ** -3]).astype(np.float32)
     want = torch.from_numpy(a).to(torch.bfloat16).to(torch.float64).numpy()
     np.testing.assert_array_equal(bf16(a), want)
+
+
+@pytest.mark.parametrize("scale", [1.0, 3.7e-3, 2.9e4])
+def test_row_error_split(scale):
+    """The row term the library computes: with y = fl32(x * fl32(1/|x|)) (the
+    values it rounds to BF16), |bf16(y) - x/|x|| <= |bf16(y) - y| +
+    2^-23 (1 + (d + 8) 2^-30), on unit and on scaled rows."""
+    d = 384
+    X = (synth.vmf(500, d, 20, 40.0, seed=11) * np.float32(scale)).astype(np.float32)
+    X64 = X.astype(np.float64)
+    nrm = np.sqrt(np.einsum("ij,ij->i", X64, X64))
+    ri = (1.0 / nrm).astype(np.float32)
+    y = (X * ri[:, None]).astype(np.float32)
+    yb = bf16(y)
+    lhs = np.linalg.norm(yb - X64 / nrm[:, None], axis=1)
+    rhs = np.linalg.norm(yb - y.astype(np.float64), axis=1) + 2.0 ** -23 * (1 + (d + 8) * 2.0 ** -30)
+    assert np.all(lhs <= rhs)
+    assert np.all(rhs - lhs <= 2.0 ** -22)  # the added term is small against the BF16 error
