@@ -470,7 +470,7 @@ __global__ void k_dense_lower(int64_t n, const int32_t* __restrict__ a, float* _
 }
 
 // Precision form, first pass.  For each row (all, or the Hamerly survivors
-// w1) the BF16 top-8 is within eps_b of the exact similarities (v1 the best
+// w1) the BF16 top-8 is within eps_b = bf16_eps(row) of the exact ones (v1 the best
 // at j1, v2 the next); the canonical FP32 similarities are within delta_i of
 // exact.  If v1 - v2 > 2 (eps_b + delta_i) the FP32 standard variant
 // necessarily picks j1, so j1 is the label, and Hamerly's bounds become
