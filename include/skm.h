@@ -200,7 +200,8 @@ int skm_get_stats(skm_ctx* ctx, skm_stats* out);
  * u = 2^-24 (Cauchy-Schwarz on <xb, cb> - <x, c>; at most
  * 2^-7 + 2^-15 + (d + 16) 2^-23, the bound for the worst-case rounding).
  * Rows the last Hamerly assignment pruned keep older values.  Any pointer may
- * be NULL; vals/idx/eps live in out_space.  SKM_ESTATE otherwise. */
+ * be NULL; vals/idx/eps live in out_space.  SKM_ESTATE for other contexts, and
+ * before the first assignment or after skm_set_centers / skm_set_labels. */
 int skm_get_bf16_topk(skm_ctx* ctx, float* vals, int32_t* idx, float* eps, int32_t out_space);
 
 /* Batched form: nruns independent clusterings of different row blocks of

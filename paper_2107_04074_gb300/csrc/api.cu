@@ -831,15 +831,21 @@ int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
 
 int skm_get_bf16_topk(skm_ctx* c, float* vals, int32_t* idx, float* eps, int32_t space) {
   if (!c) return SKM_EINVAL;
-  if (c->layout != SKM_DENSE || c->precision != SKM_PREC_BF16) return SKM_ESTATE;
+  if (c->layout != SKM_DENSE || c->precision != SKM_PREC_BF16 || !c->have_bounds) return SKM_ESTATE;
   const cudaMemcpyKind kind = space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   if (eps) {
     float* out = eps;
     if (space == SKM_HOST) TRY(dalloc(c, &out, (size_t)c->n));
-    TRY(dense_bf16_eps(c, out));
+    int rc = dense_bf16_eps(c, out);
     if (space == SKM_HOST) {
-      SKM_CUDA_TRY(cudaMemcpyAsync(eps, out, sizeof(float) * c->n, cudaMemcpyDeviceToHost, c->st));
-      SKM_CUDA_TRY(cudaFreeAsync(out, c->st));
+      if (rc == SKM_OK &&
+          cudaMemcpyAsync(eps, out, sizeof(float) * c->n, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+        rc = SKM_ECUDA;
+      cudaFreeAsync(out, c->st);
+    }
+    if (rc != SKM_OK) {
+      (void)cudaGetLastError();
+      return rc;
     }
   }
   if (vals) SKM_CUDA_TRY(cudaMemcpyAsync(vals, c->topv, sizeof(float) * kTopK * c->n, kind, c->st));
