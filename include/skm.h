@@ -69,8 +69,10 @@ typedef enum { SKM_DEVICE = 0, SKM_HOST = 1 } skm_memspace;
 /* Arithmetic of the dense similarity bulk.  FP32: the plain FP32 GEMM (the
  * reference point).  BF16: the precision form -- a BF16 x BF16 -> FP32
  * tensor-core GEMM whose per-row top-2 decides a label when its margin
- * exceeds the proven error bound; the other rows are rechecked in FP32, so
- * the labels are those of the FP32 path. */
+ * exceeds the row's proven error bound (from the row's and the centers'
+ * actual BF16 rounding errors, see skm_get_bf16_topk); the other rows are
+ * rechecked in FP32 against the centers that can still win, so the labels
+ * are those of the FP32 path. */
 typedef enum { SKM_PREC_FP32 = 0, SKM_PREC_BF16 = 1 } skm_precision;
 
 /* Input vectors x(1..n) in R^d (Section 2: sparse rows stored as sorted
