@@ -46,3 +46,56 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
     assert lib.skm_init(ctypes.byref(h), ctypes.byref(d), 30, 0, None, 0, None, None) == skm.EINVAL  # k > n
     assert lib.skm_init(ctypes.byref(h), ctypes.byref(d), 3, 9, None, 0, None, None) == skm.EINVAL  # variant
     assert h.value is None
+
+
+def test_unsupported_combinations_rejected_without_the_gpu():
+    """Combinations the library does not offer are refused before any CUDA
+    call: dense rows with Elkan or Yin-Yang or non-FP32 values, the BF16
+    precision form with d not a multiple of 8, Elkan with k > 4096, and the
+    batched form with a variant other than standard / simplified Elkan or
+    with a malformed run table."""
+    import numpy as np
+    lib = skm.load()
+    h = ctypes.c_void_p()
+    buf = np.zeros(64, np.float32)
+    rp = np.zeros(11, np.int64)
+    ci = np.zeros(4, np.int32)
+
+    def data(layout, dtype=0, n=10, d=16):  # dtype 0: FP32, 1: FP16
+        return skm.skm_data(n=n, d=d, layout=layout, dtype=dtype, memspace=skm.HOST, reserved=0,
+                            row_ptr=rp.ctypes.data if layout == skm.CSR else None,
+                            col_idx=ci.ctypes.data if layout == skm.CSR else None, values=buf.ctypes.data)
+
+    def init(x, k, variant, opt=None):
+        rc = lib.skm_init(ctypes.byref(h), ctypes.byref(x), k, variant, None, 0,
+                          ctypes.byref(opt) if opt is not None else None, None)
+        assert h.value is None
+        return rc
+
+    V = skm.VARIANTS
+    assert init(data(skm.DENSE), 3, V["elkan"]) == skm.EUNSUPPORTED
+    assert init(data(skm.DENSE), 3, V["simp_elkan"]) == skm.EUNSUPPORTED
+    assert init(data(skm.DENSE), 3, V["yinyang"]) == skm.EUNSUPPORTED
+    assert init(data(skm.DENSE, dtype=1), 3, V["standard"]) == skm.EUNSUPPORTED  # FP16 dense
+    opt = skm.skm_options()
+    lib.skm_default_options(ctypes.byref(opt))
+    opt.precision = skm.PREC_BF16
+    assert init(data(skm.DENSE, d=12), 3, V["standard"], opt) == skm.EUNSUPPORTED  # d % 8 != 0
+    assert init(data(skm.CSR, n=5000), 4097, V["elkan"]) == skm.EUNSUPPORTED
+
+    x = data(skm.CSR)
+    ks = np.array([2, 3], np.int32)
+
+    def batch(run_rows, ks, variant):
+        run_rows = np.asarray(run_rows, np.int64)
+        rc = lib.skm_batch_init(ctypes.byref(h), ctypes.byref(x), run_rows.ctypes.data, ks.ctypes.data, len(ks),
+                                variant, None, 0, None, None)
+        assert h.value is None
+        return rc
+
+    assert batch([0, 4, 10], ks, V["hamerly"]) == skm.EUNSUPPORTED
+    assert batch([0, 4, 10], ks, V["elkan"]) == skm.EUNSUPPORTED
+    assert batch([0, 4, 9], ks, V["standard"]) == skm.EINVAL      # does not end at n
+    assert batch([1, 4, 10], ks, V["standard"]) == skm.EINVAL     # does not start at 0
+    assert batch([0, 2, 10], np.array([3, 3], np.int32), V["standard"]) == skm.EINVAL  # k > rows of the run
+    assert batch([0, 4, 10], np.array([0, 3], np.int32), V["standard"]) == skm.EINVAL  # k < 1
