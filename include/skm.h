@@ -82,7 +82,9 @@ typedef enum { SKM_PREC_FP32 = 0, SKM_PREC_BF16 = 1 } skm_precision;
  *          values[nnz] of type dtype.
  *   DENSE: values[n*d] row-major FP32; row_ptr, col_idx unused.  Dense rows
  *          support the standard and Hamerly variants (SKM_EUNSUPPORTED for
- *          Elkan); precision BF16 needs d a multiple of 8 and d <= 448.
+ *          Elkan); precision BF16 needs d a multiple of 8 (the tensor maps
+ *          want 16-byte rows; any such d works, the K loop runs ceil(d/64)
+ *          blocks of 64 with the tail read as zeros).
  * memspace says where all three pointers live. */
 typedef struct {
   int64_t n;
@@ -281,8 +283,9 @@ const char* skm_strerror(int status);
  * code running inside another framework's memory pool or under a fixed
  * memory budget, or a service that must not allocate after start-up).
  *   x:        CSR data in DEVICE memory (not checked beyond what the kernel
- *             can see: a row with a column index outside [0,d) or a zero norm
- *             gets label -1).
+ *             can see: a row with a column index outside [0,d), a zero norm or
+ *             a non-finite value gets label -1, and so does a row whose
+ *             similarities are all NaN, e.g. against NaN centers).
  *   centers:  DEVICE float[k*d], row-major unit centers c(j).
  *   labels:   DEVICE int32[n], in: current labels (-1 = none), out: the new
  *             labels a(i) = argmax_j <x(i), c(j)> under the library's tie rule
@@ -290,7 +293,9 @@ const char* skm_strerror(int status);
  *             same centers and labels.
  *   n_changed: HOST, may be NULL; non-NULL synchronises the stream, returns
  *             the number of changed labels, and makes the call return
- *             SKM_EINVAL if some row was malformed.
+ *             SKM_EINVAL if some row got label -1 for the reasons above.
+ *             With NULL the call only enqueues its work: malformed rows then
+ *             show only as label -1.
  * Scratch lives in a static device array of 16 MiB (plus 16 bytes) that every
  * GPU loading the library holds until exit: d * round_up(k, 8) must not
  * exceed 4,194,304, else SKM_ETOOBIG.  The first call on a device looks up the

@@ -53,24 +53,31 @@ int scratch_for_current_device(float** out) {
   return SKM_OK;
 }
 
-// row-major k x d centers -> term-major d x kst (padding columns zeroed)
+// row-major k x d centers -> term-major d x kst (padding columns zeroed);
+// the grid walks the center tiles (y) with a stride, so any kst fits.
 __global__ void k_na_transpose(const float* __restrict__ C, int64_t d, int32_t k, int64_t kst, float* __restrict__ Ct) {
   __shared__ float tile[32][33];
-  const int64_t t0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int64_t j = j0 + r, t = t0 + threadIdx.x;
-    tile[r][threadIdx.x] = (j < k && t < d) ? C[j * d + t] : 0.f;
-  }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int64_t t = t0 + r, j = j0 + threadIdx.x;
-    if (t < d && j < kst) Ct[t * kst + j] = tile[threadIdx.x][r];
+  const int64_t t0 = (int64_t)blockIdx.x * 32;
+  for (int64_t j0 = (int64_t)blockIdx.y * 32; j0 < kst; j0 += (int64_t)gridDim.y * 32) {
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t j = j0 + r, t = t0 + threadIdx.x;
+      tile[r][threadIdx.x] = (j < k && t < d) ? C[j * d + t] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t t = t0 + r, j = j0 + threadIdx.x;
+      if (t < d && j < kst) Ct[t * kst + j] = tile[threadIdx.x][r];
+    }
+    __syncthreads();
   }
 }
 
 // Warp per row: 1/|x_i| computed in the row's own warp, then all k
 // similarities and the argmax under the tie rule.  A row with a column index
-// outside [0, d) or a zero norm gets label -1 and raises the error counter.
+// outside [0, d), a zero or non-finite norm (a NaN or an infinite value), or
+// one whose similarities leave no best center (NaN centers) gets label -1 and
+// raises the error counter.  The row is checked before any center value is
+// gathered, so a bad column index is never dereferenced.
 template <typename VT, int NT>
 __global__ void __launch_bounds__(256) k_na_rows_top2(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                       const VT* __restrict__ val, int64_t n, int64_t d,
@@ -92,7 +99,7 @@ __global__ void __launch_bounds__(256) k_na_rows_top2(const int64_t* __restrict_
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(SKM_FULL_MASK, ss, o);
-    bad = __any_sync(SKM_FULL_MASK, bad) || !(ss > 0.0) || e < b;
+    bad = __any_sync(SKM_FULL_MASK, bad) || !(ss > 0.0) || !isfinite(ss) || e < b;
     const int32_t cur = a[i];
     if (bad) {
       if (lane == 0) {
@@ -161,10 +168,13 @@ __global__ void __launch_bounds__(256) k_na_rows_top2(const int64_t* __restrict_
       }
       vcur = fmaxf(vcur, __shfl_xor_sync(SKM_FULL_MASK, vcur, o));
     }
-    const int32_t nb = (cur >= 0 && cur < k && vcur == v1) ? cur : j1;
+    // no finite maximum (every similarity NaN): no label
+    const bool none = (j1 == INT_MAX);
+    const int32_t nb = none ? -1 : (cur >= 0 && cur < k && vcur == v1) ? cur : j1;
     if (lane == 0) {
       a[i] = nb;
       my_changed += (nb != cur);
+      my_err += none ? 1 : 0;
     }
   }
   if (lane == 0) {
@@ -203,8 +213,8 @@ extern "C" int skm_assign_noalloc(const skm_data* x, int32_t k, const float* cen
     return SKM_EINVAL;
   if (x->dtype < SKM_F32 || x->dtype > SKM_BF16) return SKM_EINVAL;
   if (x->d > INT32_MAX || x->n > INT32_MAX) return SKM_ETOOBIG;
-  const int64_t kst = (k + 7) / 8 * 8;
-  if (x->d * kst > kMaxCenterFloats) return SKM_ETOOBIG;
+  const int64_t kst = ((int64_t)k + 7) / 8 * 8;
+  if (x->d > kMaxCenterFloats || x->d * kst > kMaxCenterFloats) return SKM_ETOOBIG;
   float* base = nullptr;
   int rc = scratch_for_current_device(&base);
   if (rc != SKM_OK) return rc;
@@ -216,7 +226,8 @@ extern "C" int skm_assign_noalloc(const skm_data* x, int32_t k, const float* cen
   SKM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   // the counters keep the previous call's values: clear them
   SKM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st));
-  dim3 g((unsigned)((x->d + 31) / 32), (unsigned)((kst + 31) / 32));
+  const int64_t gy = (kst + 31) / 32;
+  dim3 g((unsigned)((x->d + 31) / 32), (unsigned)(gy < 65535 ? gy : 65535));
   k_na_transpose<<<g, dim3(32, 8), 0, st>>>(centers, x->d, k, kst, Ct);
   skm::note_launch();
   if (cudaPeekAtLastError() != cudaSuccess) {

@@ -138,20 +138,24 @@ def bound_bytes(variant, n: int, k: int) -> int:
     return out.value
 
 
-def assign_noalloc(n: int, d: int, row_ptr, col_idx, values, k: int, centers, labels, stream=None) -> int:
+def assign_noalloc(n: int, d: int, row_ptr, col_idx, values, k: int, centers, labels, stream=None,
+                   count: bool = True):
     """Standard assignment without device allocation (skm_assign_noalloc).
 
     All arrays are torch CUDA tensors; labels (int32[n]) is updated in place.
-    Returns the number of changed labels (synchronises)."""
+    count=True: returns the number of changed labels (synchronises; a malformed
+    row raises SkmError EINVAL).  count=False: passes no host output, so the
+    call only enqueues its kernels and returns None."""
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
     data = skm_data(n=n, d=d, layout=CSR, dtype=_dtype_code(values.dtype), memspace=DEVICE, reserved=0,
                     row_ptr=_ptr(row_ptr), col_idx=_ptr(col_idx), values=_ptr(values))
     out = ctypes.c_int64(0)
-    _check(load().skm_assign_noalloc(ctypes.byref(data), int(k), _ptr(centers), _ptr(labels), ctypes.byref(out),
-                                     ctypes.c_void_p(stream)), "skm_assign_noalloc")
-    return out.value
+    _check(load().skm_assign_noalloc(ctypes.byref(data), int(k), _ptr(centers), _ptr(labels),
+                                     ctypes.byref(out) if count else None, ctypes.c_void_p(stream)),
+           "skm_assign_noalloc")
+    return out.value if count else None
 
 
 def _ptr(x):
