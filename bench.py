@@ -166,7 +166,7 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
-def kernel_bytes(name, it_rows, n, d, k, nnz, variant, full_sum=True):
+def kernel_bytes(name, it_rows, n, d, k, nnz, variant, full_sum=True, u_width=4):
     """Compulsory (algorithmic) bytes of one launch: what any implementation
     must move between HBM and the SMs for that step, given the rows it treats.
     it_rows: rows treated by the launch (all rows, the recompute list, ...)."""
@@ -174,12 +174,12 @@ def kernel_bytes(name, it_rows, n, d, k, nnz, variant, full_sum=True):
     elk = variant in ("elkan", "simp_elkan")
     row = 8 + 8 * avg + 4 + 4 + 4 + 4  # row_ptr, (col, val) entries, label r/w, 1/|x|, delta
     if name in ("k_rows_top2", "k_rows_top2(list)"):
-        out = (4 * k if elk else 0) + (8 if variant != "standard" else 0)
+        out = (u_width * k if elk else 0) + (8 if variant != "standard" else 0)
         return int(it_rows * (row + out + (4 if name.endswith("(list)") else 0)) + 4 * d * k)
     if name == "k_elk_bounds":
-        return int(8 * n * k + 16 * n)
+        return int(elk_bound_bytes(n, k, u_width))
     if name == "k_elk_recompute":
-        return int(it_rows * (4 * k * (2 if variant == "elkan" else 1) + row + 4))
+        return int(it_rows * ((u_width + (4 if variant == "elkan" else 0)) * k + row + 4))
     if name == "k_center_sum":  # only a full recomputation moves data (else the kernel returns at once)
         return int(8 * nnz + 8 * d * k + 4 * n) if full_sum else 0
     if name == "k_ham_bounds":
@@ -279,6 +279,7 @@ def run_ours(args, rank, world, local):
     flush.fill_(1.0)
     km.reset(init)
     prof_ms, prof_n, prof_bytes, prof_gather = {}, {}, {}, {}
+    u_width = elk_u_width(skm, n, k)
     upd = {"full": [0.0, 0], "incremental": [0.0, 0]}  # center update: ms, count
     for it in range(MAX_ITERS):
         km.profile(True)
@@ -299,7 +300,7 @@ def run_ours(args, rank, world, local):
         for nm, (ms_k, cnt_k) in list(pa.items()) + list(pu.items()):
             prof_ms[nm] = prof_ms.get(nm, 0.0) + ms_k
             prof_n[nm] = prof_n.get(nm, 0) + cnt_k
-            b = kernel_bytes(nm, rows_of.get(nm, n), n, d, k, nnz, variant, full_sum)
+            b = kernel_bytes(nm, rows_of.get(nm, n), n, d, k, nnz, variant, full_sum, u_width)
             if b is not None:
                 prof_bytes[nm] = prof_bytes.get(nm, 0) + b * cnt_k
             gb = gather_bytes(nm, rows_of.get(nm, n), n, k, nnz)
@@ -344,8 +345,8 @@ def run_ours(args, rank, world, local):
             gpl = prof_gather[top_name] / prof_n[top_name]
             roof["gathered_bytes_per_launch"] = int(gpl)
             roof["gather_GBps"] = round(gpl / avg_s / 1e9, 1)
-            roof["note"] = ("bound by the L1/L2 gathers of center slices (ncu: L1 throughput ~71% of peak, "
-                            "profiles/k_rows_top2_rcv1.md), not by HBM")
+            roof["note"] = ("bound by the L1/L2 gathers of center slices (ncu: L1 throughput ~71% of peak), "
+                            "not by HBM")
     kernel_share = {}
     for nm in sorted(prof_ms, key=lambda x: -prof_ms[x]):
         e = {"ms": round(prof_ms[nm], 3), "launches": prof_n[nm], "share": round(prof_ms[nm] / tot_prof, 4)}
@@ -415,7 +416,8 @@ def run_ours(args, rank, world, local):
         # --workload embed / batch); a failure there is reported, not fatal
         del km, km_std, rp, col, val, flush
         torch.cuda.empty_cache()
-        for key, fn in (("precision_form", summarize_embed), ("batched_form", summarize_batch)):
+        for key, fn in (("precision_form", summarize_embed), ("batched_form", summarize_batch),
+                        ("large_sparse", summarize_large)):
             try:
                 out[key] = fn(args, rank, world, local)
             except Exception as ex:  # noqa: BLE001
@@ -430,6 +432,9 @@ def summarize_embed(args, rank, world, local):
     keep = ("iters", "iters_per_s")
     return {"workload": r["workload"], "labels_identical_across_paths": r["labels_identical_across_paths"],
             "iters_per_s": {k: v["iters_per_s"] for k, v in p.items()},
+            "ms_median_min_max": {k: [v["ms"]] + v["ms_min_max"] for k, v in p.items()},
+            "repeats": p["standard/bf16"]["repeats"],
+            "error_vs_fp64_oracle": r["error_vs_fp64_oracle"],
             "speedup_bf16_vs_fp32_standard": r["speedup_bf16_vs_fp32_standard"],
             "roofline": r["bf16_gemm_roofline"],
             "rows_candidate_recheck_first_last": [p["standard/bf16"]["rows_candidate_recheck_per_iter"][0],
@@ -472,10 +477,72 @@ def trace_run(km, init, n, k):
     return {"trace": rows, "n": n, "k": k}
 
 
+def oracle_assign_rows(Xs, rows, C, prev, threads=None):
+    """The FP64 oracle's assignment of the dense rows Xs[rows] from centers C
+    (teacher-forced: prev holds their current labels), on contiguous blocks of
+    the sample in parallel host threads.  Returns (labels, top-2 gaps)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    P = threads or os.cpu_count() or 1
+    cuts = np.linspace(0, len(rows), P + 1).astype(np.int64)
+    C64 = np.ascontiguousarray(C, dtype=np.float64)
+
+    def one(q):
+        sub = oracle.Data.from_dense(Xs[rows[cuts[q]:cuts[q + 1]]])
+        lab, _, _, _, gap = oracle.assign(sub, oracle.rinv(sub), C64, prev[cuts[q]:cuts[q + 1]])
+        return lab, gap
+
+    with ThreadPoolExecutor(max_workers=P) as pool:
+        outs = list(pool.map(one, range(P)))
+    return np.concatenate([o[0] for o in outs]), np.concatenate([o[1] for o in outs])
+
+
+def embed_error_vs_oracle(skm, Xd, Xs, k, init, iters, precision, nsample=20000, check_at=(1, 2, 5, 10, 20)):
+    """Per-result error of a dense path against the FP64 oracle, teacher-forced
+    at the listed iterations: label mismatches on a seeded sample of rows (the
+    oracle assigns them from the GPU's centers and previous labels; mismatches
+    at FP64 top-2 gaps below 1e-6 are counted apart as near-ties), and after
+    the update the largest center error |c_gpu - c_oracle| and the objective's
+    relative error (the oracle updates from the GPU's labels over all rows)."""
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(77))
+    rows = np.sort(rng.choice(len(Xs), size=min(nsample, len(Xs)), replace=False))
+    X = oracle.Data.from_dense(Xs)
+    ri = oracle.rinv(X)
+    km = skm.KMeans.dense(Xd, k, variant="standard", init_rows=init, precision=precision)
+    prev = np.full(len(Xs), -1, np.int32)
+    out = []
+    for t in range(1, iters + 1):
+        C = km.centers()
+        ch = km.assign()
+        lab = km.labels()
+        if t in check_at:
+            want, gap = oracle_assign_rows(Xs, rows, C, prev[rows])
+            diff = want != lab[rows]
+            e = {"iteration": t, "rows": int(len(rows)), "label_mismatches": int(np.sum(diff & (gap >= 1e-6))),
+                 "near_ties": int(np.sum(diff & (gap < 1e-6)))}
+        if ch == 0:
+            if t in check_at:
+                out.append(e)
+            break
+        J = km.update_centers()
+        if t in check_at:
+            Co, _, Jo = oracle.update(X, ri, lab, C.astype(np.float64))
+            e["center_max_err"] = float(np.max(np.linalg.norm(km.centers().astype(np.float64) - Co, axis=1)))
+            e["objective_rel_err"] = float(abs(J - Jo) / abs(Jo))
+            out.append(e)
+        prev = lab
+    km.close()
+    return out
+
+
 def run_embed(args, rank, world, local):
     """Precision form on dense embeddings: n = 1e6 unit rows in d = 384 from a
     mixture of 1000 vMF(kappa = 40) components, k = 1000; FP32 GEMM vs the
-    BF16 tensor-core bulk with FP32 recheck, standard and Hamerly."""
+    BF16 tensor-core bulk with FP32 recheck, standard and Hamerly.  Each path
+    is timed over `embed_repeats` runs (L2 flushed before each), and the BF16
+    path's results are compared with the FP64 oracle."""
     import torch
     from paper_2107_04074_gb300 import skm
 
@@ -491,15 +558,18 @@ def run_embed(args, rank, world, local):
         km = skm.KMeans.dense(X, k, variant=variant, init_rows=init, precision=prec, stream=stream.cuda_stream)
         km.reset(init)
         km.run(2)  # warm-up
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        km.reset(init)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        it, J = km.run(iters)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        times = []
+        for _ in range(max(1, args.embed_repeats)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            km.reset(init)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, J = km.run(iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.median(times))
         labels[(variant, prec)] = km.labels()
         # per-iteration recheck counts and kernel times (separate, profiled run)
         km.reset(init)
@@ -520,12 +590,13 @@ def run_embed(args, rank, world, local):
             km.update_centers()
         km.close()
         entry = {"iters": it, "ms": round(ms, 3), "iters_per_s": round(it / (ms / 1e3), 3), "objective": J,
+                 "repeats": len(times), "ms_min_max": [round(min(times), 3), round(max(times), 3)],
                  "rows_whole_row_recheck_per_iter": rech,
                  "rows_candidate_recheck_per_iter": cand,
                  "kernels_ms": {nm: round(v[0], 3) for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
         if "k_bf16_topk" in prof:
             t_ms, c = prof["k_bf16_topk"]
-            flops = 2.0 * n * ((k + 255) // 256 * 256) * d
+            flops = 2.0 * n * k * d  # the method's work; the kernel also multiplies padding centers up to 1024
             entry["bf16_gemm_us_per_launch"] = round(t_ms / c * 1e3, 1)
             entry["bf16_gemm_tflops"] = round(flops / (t_ms / c / 1e3) / 1e12, 1)
         res[f"{variant}/{prec}"] = entry
@@ -537,12 +608,18 @@ def run_embed(args, rank, world, local):
         peak = 1900.0
     g = res["standard/bf16"]
     traffic = recorded_traffic("k_bf16_topk", "vmf-n1e6-d384-k1000") if n == 1_000_000 else None
+    errors = {}
+    if not args.no_oracle_check:
+        for prec in ("bf16", "fp32"):
+            errors[prec] = embed_error_vs_oracle(skm, X, Xs, k, init, iters, prec)
     return {"workload": f"vmf-embeddings n={n} d={d} k={k} kappa=40 ({iters} iterations max)",
             "labels_identical_across_paths": same, "paths": res,
             "speedup_bf16_vs_fp32_standard": round(g["iters_per_s"] / res["standard/fp32"]["iters_per_s"], 2),
+            "error_vs_fp64_oracle": errors,
             "bf16_gemm_roofline": {"kernel": "k_bf16_topk", "bound": "tensor", "achieved": g.get("bf16_gemm_tflops"),
                                    "peak": peak, "unit": "TFLOP/s", "peak_source": "measured (burst)",
                                    "frac": round(g.get("bf16_gemm_tflops", 0) / peak, 4), "traffic": traffic,
+                                   "flops_per_launch": 2 * n * k * d,
                                    "traffic_note": "ncu DRAM bytes of an n=2e5 launch scaled by rows"}}
 
 
@@ -658,12 +735,44 @@ def sampled_parity(km, csr, sample, prev, C):
     return int(len(sample)), int(np.sum(diff & (gap >= 1e-6))), int(np.sum(diff & (gap < 1e-6)))
 
 
+def elk_bound_bytes(n, k, u_width=4):
+    """Algorithmic bytes of one Elkan bound launch: the n x k upper bounds of
+    u_width bytes each read and written once, plus per point l read and
+    written, a(i), delta_i and the row length (16 B)."""
+    return 2 * u_width * n * k + 16 * n
+
+
+def elk_u_width(skm, n, k):
+    """Stored bytes per Elkan upper bound, from skm_bound_bytes (4n + w n k)."""
+    return (skm.bound_bytes("elkan", n, k) - 4 * n) // (n * k)
+
+
+def profiled_run(km, iters):
+    """One eager run with per-kernel CUDA events (not a timed value): per kernel
+    its summed ms and launches."""
+    prof = {}
+    for _ in range(iters):
+        km.profile(True)
+        ch = km.assign()
+        if ch:
+            km.update_centers()
+        for nm, (t, c) in km.profile_read().items():
+            prof.setdefault(nm, [0.0, 0])
+            prof[nm][0] += t
+            prof[nm][1] += c
+        km.profile(False)
+        if ch == 0:
+            break
+    return prof
+
+
 def run_large(args, rank, world, local):
     """Large sparse workload: n = 4e6 rows, d = 2e5, nnz/row lognormal(200,
     0.9) clipped to [10, 5000] (~8e8 nnz), Zipf(1.05), FP16 values, k = 1000,
-    30 iterations; Elkan, Hamerly and standard at identical labels, with the
-    first and last assignments of the Elkan run checked against the FP64
-    oracle on 2000 sampled rows."""
+    30 iterations; Elkan, Simplified Elkan, Hamerly and standard at identical
+    labels, with the first and last assignments of the Elkan run checked
+    against the FP64 oracle on 2000 sampled rows, and the Elkan bound kernel's
+    HBM rate (its n x k bound array, 16 GB, is far larger than L2)."""
     import torch
     from paper_2107_04074_gb300 import skm
 
@@ -681,8 +790,15 @@ def run_large(args, rank, world, local):
     Xd = [torch.from_numpy(a).to(dev) for a in (csr.row_ptr, csr.col, csr.val)]
     rng = np.random.Generator(np.random.PCG64(55))
     sample = np.sort(rng.choice(csr.n, size=min(2000, csr.n), replace=False))
-    res, labels = {}, {}
-    for variant in ("elkan", "hamerly", "standard"):
+    try:
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        peak_src = "measured"
+    except (OSError, KeyError, ValueError):
+        hbm_peak, peak_src = 6800.0, "fallback"
+    res, labels, bound_roof = {}, {}, {}
+    sampler = ClockSampler(local)
+    sampler.start()
+    for variant in ("elkan", "simp_elkan", "hamerly", "standard"):
         km = skm.KMeans(csr.n, csr.d, *Xd, k, variant=variant, init_rows=init, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -694,6 +810,22 @@ def run_large(args, rank, world, local):
         labels[variant] = km.labels()
         res[variant] = {"iterations": it, "ms": round(ms, 1), "iters_per_s": round(it / (ms / 1e3), 3),
                         "sims_evaluated": km.stats().total_sims, "objective": J}
+        if variant in ("elkan", "simp_elkan"):
+            km.reset(init)
+            prof = profiled_run(km, iters)
+            tot = sum(v[0] for v in prof.values()) or 1.0
+            res[variant]["kernel_time_share"] = {
+                nm: {"ms": round(v[0], 2), "launches": v[1], "share": round(v[0] / tot, 4)}
+                for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]}
+            if "k_elk_bounds" in prof:
+                t_ms, c = prof["k_elk_bounds"]
+                ab = elk_bound_bytes(csr.n, k, elk_u_width(skm, csr.n, k))
+                ach = ab / (t_ms / c / 1e3) / 1e9
+                bound_roof[variant] = {"kernel": "k_elk_bounds", "bound": "hbm", "achieved": round(ach, 1),
+                                       "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                                       "peak_source": peak_src, "avg_launch_us": round(t_ms / c * 1e3, 1),
+                                       "launches": c, "algorithmic_bytes_per_launch": int(ab),
+                                       "traffic": recorded_traffic("k_elk_bounds", "large-n4e6-k1000")}
         if variant == "elkan":
             # teacher-forced oracle checks of the first and the last assignment
             km.reset(init)
@@ -711,26 +843,74 @@ def run_large(args, rank, world, local):
                     km.update_centers()
             res[variant]["oracle_sample"] = checks
         km.close()
+    clocks = sampler.stop()
     same = all(np.array_equal(v, labels["standard"]) for v in labels.values())
+    std = res["standard"]["iters_per_s"]
     return {"workload": f"large sparse n={csr.n} d={csr.d} nnz={csr.nnz} (FP16 values) k={k} "
                         f"{iters} iterations", "generate_s": round(gen_s, 1), "labels_identical": same,
-            "variants": res,
-            "speedup_elkan_vs_standard": round(res["elkan"]["iters_per_s"] / res["standard"]["iters_per_s"], 2),
-            "speedup_hamerly_vs_standard": round(res["hamerly"]["iters_per_s"] / res["standard"]["iters_per_s"], 2)}
+            "variants": res, "bound_kernel_roofline": bound_roof, "clocks": clocks,
+            "speedup_vs_standard": {v: round(res[v]["iters_per_s"] / std, 3) for v in res if v != "standard"}}
+
+
+def summarize_large(args, rank, world, local):
+    a = argparse.Namespace(**vars(args))
+    a.large_frac = 1.0
+    return run_large(a, rank, world, local)
+
+
+def csr_slice(csr, a, b):
+    """Rows [a, b) of a CSR as their own CSR (views of the arrays)."""
+    rp = csr.row_ptr[a:b + 1] - csr.row_ptr[a]
+    return synth.CSR(b - a, csr.d, rp, csr.col[csr.row_ptr[a]:csr.row_ptr[b]],
+                     csr.val[csr.row_ptr[a]:csr.row_ptr[b]])
+
+
+def oracle_standard_all_cores(csr, init, iters=2, threads=None):
+    """The FP64 oracle's standard iterations with one host thread per core:
+    its assignment runs on contiguous row blocks in parallel (the oracle's C
+    code releases the interpreter lock; its arithmetic is untouched), then its
+    center update over all rows.  Returns (iterations/s, threads, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    P = threads or os.cpu_count() or 1
+    X = oracle.Data.from_csr(csr)
+    ri = oracle.rinv(X)
+    C = oracle.unit_rows(X, init)
+    cuts = np.linspace(0, csr.n, P + 1).astype(np.int64)
+    parts = [oracle.Data.from_csr(csr_slice(csr, int(a), int(b))) for a, b in zip(cuts[:-1], cuts[1:])]
+    ris = [ri[a:b] for a, b in zip(cuts[:-1], cuts[1:])]
+    lab = np.full(csr.n, -1, np.int32)
+    with ThreadPoolExecutor(max_workers=P) as pool:
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            outs = list(pool.map(lambda q: oracle.assign(parts[q], ris[q], C, lab[cuts[q]:cuts[q + 1]])[0],
+                                 range(P)))
+            lab = np.concatenate(outs)
+            C, _, _ = oracle.update(X, ri, lab, C)
+        dt = time.perf_counter() - t0
+    return iters / dt, P, dt
 
 
 def cpu_baseline(csr, init, variant, iters=3):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample: the
-    first `iters` iterations of the same run on the full data."""
+    first `iters` iterations of the same run on the full data; beside it the
+    oracle's standard iterations on all host cores."""
     import oracle
     X = oracle.Data.from_csr(csr)
     C0 = oracle.unit_rows(X, init)
     t0 = time.perf_counter()
     tr = oracle.run(X, C0, variant, max_iters=iters)
     dt = time.perf_counter() - t0
+    v_all, P, dt_all = oracle_standard_all_cores(csr, init)
     return {"value": round(tr.iters / dt, 4), "unit": "Lloyd iterations/s", "cores": 1, "kind": "oracle",
             "sample": f"first {tr.iters} {variant} iterations of the same run on the full data "
-                      f"(early iterations prune least), {dt:.1f} s"}
+                      f"(early iterations prune least), {dt:.1f} s",
+            "host_cpu_count": os.cpu_count(),
+            "all_cores": {"value": round(v_all, 4), "unit": "Lloyd iterations/s", "cores": P, "kind": "oracle",
+                          "variant": "standard",
+                          "sample": f"first 2 standard iterations on the full data, assignment parallel over "
+                                    f"row blocks ({P} threads), {dt_all:.1f} s"}}
 
 
 def run_reference(args, rank, world):
@@ -785,6 +965,9 @@ def main():
     ap.add_argument("--large-frac", type=float, default=1.0, help="fraction of the large workload's rows")
     ap.add_argument("--embed-n", type=int, default=1_000_000)
     ap.add_argument("--embed-iters", type=int, default=20)
+    ap.add_argument("--embed-repeats", type=int, default=5)
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the precision form's per-result comparison with the FP64 oracle")
     ap.add_argument("--trace", action="store_true",
                     help="print a per-iteration table (labels changed, similarities, survivors, kernel ms) and exit")
     args = ap.parse_args()

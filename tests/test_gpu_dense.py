@@ -82,7 +82,22 @@ def test_precision_form_labels_equal_fp32_path():
             np.testing.assert_array_equal(a, b)
 
 
-def test_bf16_error_bound_holds():
+@pytest.mark.parametrize("d", [768, 1024])
+def test_precision_form_wide_embeddings(d):
+    """Embedding widths 768 and 1024 (12 and 16 K blocks of the tensor-core
+    loop): the BF16 bulk is teacher-forced against the FP64 oracle step by
+    step, and its label sequence equals the FP32 path's."""
+    Xs = synth.vmf(3001, d, 40, 80.0, seed=43)
+    init = synth.init_rows(len(Xs), 37, 43)
+    seq_b, st = _teacher_forced_dense(Xs, 37, "standard", "bf16", init, 8)
+    seq_f, _ = _teacher_forced_dense(Xs, 37, "standard", "fp32", init, 8)
+    assert len(seq_b) == len(seq_f)
+    for a, b in zip(seq_b, seq_f):
+        np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("d", [384, 1024])
+def test_bf16_error_bound_holds(d):
     """Every BF16 similarity of the candidate list is within its row's bound
     eps_i of the exact FP64 one, the list is descending with distinct centers,
     and every center outside it is at most v8 + eps_i exactly (the facts the
@@ -91,7 +106,7 @@ def test_bf16_error_bound_holds():
     well below it.  Lists may end in entries with center -1 that carry a
     bound instead of a center; a row whose candidate buffer overflowed is all
     -1 / +inf (it gets a whole-row recheck) and must be rare."""
-    Xs = synth.vmf(4000, 384, 100, 40.0, seed=9)
+    Xs = synth.vmf(4000, d, 100, 40.0 * d / 384, seed=9)
     init = synth.init_rows(len(Xs), 256, 9)
     km = skm.KMeans.dense(torch.from_numpy(Xs).cuda(), 256, variant="standard", init_rows=init, precision="bf16")
     Xn = Xs.astype(np.float64) / np.linalg.norm(Xs.astype(np.float64), axis=1, keepdims=True)
@@ -194,6 +209,6 @@ def test_dense_host_input_and_rejections():
     np.testing.assert_array_equal(a.labels(), b.labels())
     with pytest.raises(skm.SkmError):
         skm.KMeans.dense(torch.from_numpy(Xs).cuda(), 7, variant="elkan", init_rows=init)
-    odd = synth.vmf(100, 500, 3, 20.0, seed=3)  # d = 500 > 448: no BF16 bulk
+    odd = synth.vmf(100, 500, 3, 20.0, seed=3)  # d = 500 is not a multiple of 8: no BF16 bulk
     with pytest.raises(skm.SkmError):
         skm.KMeans.dense(torch.from_numpy(odd).cuda(), 3, precision="bf16")

@@ -1,12 +1,8 @@
 """Parity at the workloads' full sizes, in the configurations bench.py times,
 on sampled rows the FP64 oracle can afford: teacher-forced assignments (the
 oracle assigns the sampled rows from the GPU's centers and previous labels)
-must give the GPU's labels except below the 1e-6 similarity gap.
-
-The 8e8-nonzero workload runs here at a tenth of its rows; set
-SKM_FULL_SCALE=1 to run it at full size (minutes)."""
-import os
-
+must give the GPU's labels except below the 1e-6 similarity gap.  Every
+workload runs at its full size, the 8e8-nonzero one included."""
 import numpy as np
 import pytest
 
@@ -124,25 +120,26 @@ def test_batch_full_size():
     g.close()
 
 
-@pytest.mark.parametrize("frac", [0.1] + ([1.0] if os.environ.get("SKM_FULL_SCALE") == "1" else []))
-def test_large_sparse(frac):
-    """n = 4e6 x frac rows, d = 2e5, ~200 nnz/row, FP16 values, k = 1000:
-    Elkan with sampled parity at the first and third assignments, and the
-    same labels as Hamerly and the standard variant after 5 iterations."""
-    cfg = synth.scaled(synth.CSR_LARGE, n=int(synth.CSR_LARGE.n * frac))
-    csr = synth.tfidf(cfg)
-    init = synth.init_rows(csr.n, 1000, cfg.seed)
+def test_large_sparse_full_size():
+    """n = 4e6 rows, d = 2e5, ~200 nnz/row (8e8 non-zeros), FP16 values,
+    k = 1000, 30 iterations: Elkan keeps n * 1000 FP32 bounds (16 GB, 4e9
+    elements, past signed 32-bit indexing).  Sampled parity at the first and the last
+    assignment; Hamerly and the standard variant reach the same labels after
+    the same 30 iterations."""
+    csr = synth.tfidf(synth.CSR_LARGE)
+    assert csr.nnz > 7.5e8 and csr.n * 1000 > 2 ** 31
+    init = synth.init_rows(csr.n, 1000, synth.CSR_LARGE.seed)
     dev = [torch.from_numpy(a).cuda() for a in (csr.row_ptr, csr.col, csr.val)]
+    iters = 30
     km = skm.KMeans(csr.n, csr.d, *dev, 1000, variant="elkan", init_rows=init)
-    _teacher_forced_sparse(km, csr, 5, {0, 2})
+    it = _teacher_forced_sparse(km, csr, iters, {0, iters - 1})
     ref = km.labels()
+    sims_elkan = km.stats().total_sims
     km.close()
+    assert sims_elkan < it * csr.n * 1000
     for variant in ("hamerly", "standard"):
         o = skm.KMeans(csr.n, csr.d, *dev, 1000, variant=variant, init_rows=init)
-        for t in range(5):
-            ch = o.assign()
-            if ch == 0 or t == 4:
-                break
-            o.update_centers()
+        it_o, _ = o.run(iters)
+        assert it_o == it
         np.testing.assert_array_equal(o.labels(), ref)
         o.close()
