@@ -436,7 +436,12 @@ def summarize_embed(args, rank, world, local):
             "repeats": p["standard/bf16"]["repeats"],
             "error_vs_fp64_oracle": r["error_vs_fp64_oracle"],
             "speedup_bf16_vs_fp32_standard": r["speedup_bf16_vs_fp32_standard"],
+            "speedup_fp8_vs_fp32_standard": r["speedup_fp8_vs_fp32_standard"],
             "roofline": r["bf16_gemm_roofline"],
+            "fp8_roofline": r["fp8_gemm_roofline"],
+            "ambiguous_fraction_first_last": {kk: [v["ambiguous_fraction_per_iter"][0],
+                                                   v["ambiguous_fraction_per_iter"][-1]]
+                                              for kk, v in p.items() if "ambiguous_fraction_per_iter" in v},
             "rows_candidate_recheck_first_last": [p["standard/bf16"]["rows_candidate_recheck_per_iter"][0],
                                                   p["standard/bf16"]["rows_candidate_recheck_per_iter"][-1]],
             "note": "BF16 tcgen05 bulk with candidate selection, FP32 recheck; see --workload embed"} \
@@ -554,7 +559,8 @@ def run_embed(args, rank, world, local):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     res, labels = {}, {}
-    for variant, prec in (("standard", "fp32"), ("standard", "bf16"), ("hamerly", "fp32"), ("hamerly", "bf16")):
+    for variant, prec in (("standard", "fp32"), ("standard", "bf16"), ("hamerly", "fp32"), ("hamerly", "bf16"),
+                          ("standard", "fp8"), ("hamerly", "fp8")):
         km = skm.KMeans.dense(X, k, variant=variant, init_rows=init, precision=prec, stream=stream.cuda_stream)
         km.reset(init)
         km.run(2)  # warm-up
@@ -594,11 +600,16 @@ def run_embed(args, rank, world, local):
                  "rows_whole_row_recheck_per_iter": rech,
                  "rows_candidate_recheck_per_iter": cand,
                  "kernels_ms": {nm: round(v[0], 3) for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
-        if "k_bf16_topk" in prof:
-            t_ms, c = prof["k_bf16_topk"]
-            flops = 2.0 * n * k * d  # the method's work; the kernel also multiplies padding centers up to 1024
-            entry["bf16_gemm_us_per_launch"] = round(t_ms / c * 1e3, 1)
-            entry["bf16_gemm_tflops"] = round(flops / (t_ms / c / 1e3) / 1e12, 1)
+        for kn, tag in (("k_bf16_topk", "bf16"), ("k_fp8_topk", "fp8")):
+            if kn in prof:
+                t_ms, c = prof[kn]
+                flops = 2.0 * n * k * d  # the method's work; the kernel also multiplies padding centers up to 1024
+                entry[f"{tag}_gemm_us_per_launch"] = round(t_ms / c * 1e3, 1)
+                entry[f"{tag}_gemm_tflops"] = round(flops / (t_ms / c / 1e3) / 1e12, 1)
+        if prec != "fp32":
+            # rows whose reduced-precision top-2 did not decide the label (the
+            # whole-row rechecks are a subset of them)
+            entry["ambiguous_fraction_per_iter"] = [round(b / n, 4) for b in cand]
         res[f"{variant}/{prec}"] = entry
     ref = labels[("standard", "fp32")]
     same = all(np.array_equal(v, ref) for v in labels.values())
@@ -610,12 +621,20 @@ def run_embed(args, rank, world, local):
     traffic = recorded_traffic("k_bf16_topk", "vmf-n1e6-d384-k1000") if n == 1_000_000 else None
     errors = {}
     if not args.no_oracle_check:
-        for prec in ("bf16", "fp32"):
+        for prec in ("bf16", "fp8", "fp32"):
             errors[prec] = embed_error_vs_oracle(skm, X, Xs, k, init, iters, prec)
     return {"workload": f"vmf-embeddings n={n} d={d} k={k} kappa=40 ({iters} iterations max)",
             "labels_identical_across_paths": same, "paths": res,
             "speedup_bf16_vs_fp32_standard": round(g["iters_per_s"] / res["standard/fp32"]["iters_per_s"], 2),
+            "speedup_fp8_vs_fp32_standard": round(res["standard/fp8"]["iters_per_s"] /
+                                                  res["standard/fp32"]["iters_per_s"], 2),
             "error_vs_fp64_oracle": errors,
+            "fp8_gemm_roofline": {"kernel": "k_fp8_topk", "bound": "tensor",
+                                  "achieved": res["standard/fp8"].get("fp8_gemm_tflops"), "peak": 2 * peak,
+                                  "unit": "TFLOP/s",
+                                  "peak_source": "2 x the measured BF16 burst peak (nominal FP8:BF16 ratio)",
+                                  "frac": round(res["standard/fp8"].get("fp8_gemm_tflops", 0) / (2 * peak), 4),
+                                  "traffic": None, "flops_per_launch": 2 * n * k * d},
             "bf16_gemm_roofline": {"kernel": "k_bf16_topk", "bound": "tensor", "achieved": g.get("bf16_gemm_tflops"),
                                    "peak": peak, "unit": "TFLOP/s", "peak_source": "measured (burst)",
                                    "frac": round(g.get("bf16_gemm_tflops", 0) / peak, 4), "traffic": traffic,

@@ -72,8 +72,13 @@ typedef enum { SKM_DEVICE = 0, SKM_HOST = 1 } skm_memspace;
  * exceeds the row's proven error bound (from the row's and the centers'
  * actual BF16 rounding errors, see skm_get_bf16_topk); the other rows are
  * rechecked in FP32 against the centers that can still win, so the labels
- * are those of the FP32 path. */
-typedef enum { SKM_PREC_FP32 = 0, SKM_PREC_BF16 = 1 } skm_precision;
+ * are those of the FP32 path.  FP8: the same with FP8-E4M3 operands
+ * (E4M3 x E4M3 -> FP32): each unit row is scaled by its own power of two
+ * 2^e_i (its largest entry lands in [128, 256)) and every center by 2^8
+ * before rounding, so the accumulator times 2^-(e_i + 8) is the similarity,
+ * exactly; E4M3 keeps 4 significant bits, so the error bound is about 16x
+ * the BF16 one and most rows are rechecked. */
+typedef enum { SKM_PREC_FP32 = 0, SKM_PREC_BF16 = 1, SKM_PREC_FP8 = 2 } skm_precision;
 
 /* Input vectors x(1..n) in R^d (Section 2: sparse rows stored as sorted
  * (index, value) pairs; dense rows as plain arrays).
@@ -82,9 +87,10 @@ typedef enum { SKM_PREC_FP32 = 0, SKM_PREC_BF16 = 1 } skm_precision;
  *          values[nnz] of type dtype.
  *   DENSE: values[n*d] row-major FP32; row_ptr, col_idx unused.  Dense rows
  *          support the standard and Hamerly variants (SKM_EUNSUPPORTED for
- *          Elkan); precision BF16 needs d a multiple of 8 (the tensor maps
- *          want 16-byte rows; any such d works, the K loop runs ceil(d/64)
- *          blocks of 64 with the tail read as zeros).
+ *          Elkan); precision BF16 needs d a multiple of 8 and FP8 a
+ *          multiple of 16 (the tensor maps want 16-byte rows; any such d
+ *          works: the K loop runs blocks of 128 bytes with the tail read as
+ *          zeros).
  * memspace says where all three pointers live. */
 typedef struct {
   int64_t n;
@@ -193,8 +199,8 @@ int skm_get_bounds(skm_ctx* ctx, float* l, float* u, int32_t out_space);
 
 int skm_get_stats(skm_ctx* ctx, skm_stats* out);
 
-/* Diagnostic for the precision form (dense rows, precision BF16): the BF16
- * tensor-core result of the last assignment, per row the 8 largest BF16
+/* Diagnostic for the precision form (dense rows, precision BF16 or FP8): the
+ * tensor-core result of the last assignment, per row the 8 largest BF16 (FP8)
  * similarities in descending order (vals, float[n*8]) and their centers
  * (idx, int32[n*8]; equal values: lower center first; -1 / -inf past k),
  * and per row the error bound eps (float[n]) that every BF16 similarity of
@@ -203,6 +209,8 @@ int skm_get_stats(skm_ctx* ctx, skm_stats* out);
  * with x_i the unit row, xb_i its BF16 copy, E_c = max_j |bf16(c_j) - c_j| and
  * u = 2^-24 (Cauchy-Schwarz on <xb, cb> - <x, c>; at most
  * 2^-7 + 2^-15 + (d + 16) 2^-23, the bound for the worst-case rounding).
+ * FP8: the same form with xb_i = e4m3(2^e_i x_i) 2^-e_i, cb_j =
+ * e4m3(2^8 c_j) 2^-8 and 1.25 in place of 1.02.
  * Rows the last Hamerly assignment pruned keep older values.  Any pointer may
  * be NULL; vals/idx/eps live in out_space.  SKM_ESTATE for other contexts, and
  * before the first assignment or after skm_set_centers / skm_set_labels. */

@@ -199,7 +199,7 @@ void release(skm_ctx* c) {
                   c->ub,     c->w1,      c->w2,    c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark,
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
                   c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n,
-                  c->exr,    c->ebc,     c->ebw};
+                  c->exr,    c->ebc,     c->ebw,   c->rsc};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -332,12 +332,21 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
     TRY(dalloc(c, &c->loff, (size_t)(k + 1)));
     TRY(dalloc(c, &c->lcursor, (size_t)k));
     TRY(dalloc(c, &c->lmembers, (size_t)n));
-    if (c->precision == SKM_PREC_BF16) {
-      __nv_bfloat16 *xb = nullptr, *cb = nullptr;
-      TRY(dalloc(c, &xb, (size_t)(n * d)));
-      c->Xb = xb;
-      TRY(dalloc(c, &cb, (size_t)(c->kpad * d)));
-      c->Cb = cb;
+    if (c->precision != SKM_PREC_FP32) {
+      if (c->precision == SKM_PREC_FP8) {
+        uint8_t *xq = nullptr, *cq = nullptr;
+        TRY(dalloc(c, &xq, (size_t)(n * d)));
+        c->Xb = xq;
+        TRY(dalloc(c, &cq, (size_t)(c->kpad * d)));
+        c->Cb = cq;
+        TRY(dalloc(c, &c->rsc, (size_t)n));
+      } else {
+        __nv_bfloat16 *xb = nullptr, *cb = nullptr;
+        TRY(dalloc(c, &xb, (size_t)(n * d)));
+        c->Xb = xb;
+        TRY(dalloc(c, &cb, (size_t)(c->kpad * d)));
+        c->Cb = cb;
+      }
       TRY(dalloc(c, &c->topv, (size_t)(n * kTopK)));
       TRY(dalloc(c, &c->topi, (size_t)(n * kTopK)));
       TRY(dalloc(c, &c->cand, (size_t)(n * 2 * 16)));
@@ -352,7 +361,7 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
       TRY(dalloc(c, &c->ebc, (size_t)2));
       TRY(dalloc(c, &c->ebw, (size_t)2));
       SKM_CUDA_TRY(cudaMemsetAsync(c->ebw, 0, sizeof(unsigned) * 2, c->st));
-      TRY(dense_prep_bf16(c));
+      TRY(c->precision == SKM_PREC_FP8 ? dense_prep_fp8(c) : dense_prep_bf16(c));
     }
   }
   // ---- labels, bounds, worklists
@@ -422,7 +431,12 @@ int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const
       delete c;
       return SKM_EUNSUPPORTED;
     }
-    if (c->opt.precision == SKM_PREC_BF16 && !bf16_mma_supported(x->d)) {
+    if (c->opt.precision < SKM_PREC_FP32 || c->opt.precision > SKM_PREC_FP8) {
+      delete c;
+      return SKM_EINVAL;
+    }
+    if ((c->opt.precision == SKM_PREC_BF16 && !bf16_mma_supported(x->d)) ||
+        (c->opt.precision == SKM_PREC_FP8 && !fp8_mma_supported(x->d))) {
       delete c;
       return SKM_EUNSUPPORTED;
     }
@@ -582,7 +596,7 @@ int assign_dense(skm_ctx* c) {
   TRY(dense_refresh_centers(c));
   const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
   const bool first = !c->have_bounds;
-  if (c->precision == SKM_PREC_BF16) {
+  if (c->precision != SKM_PREC_FP32) {
     // the precision form keeps Hamerly's l (and u) for every variant: l seeds
     // the candidate threshold of the tensor-core pass
     const int32_t* list = nullptr;
@@ -831,7 +845,7 @@ int skm_get_bounds(skm_ctx* c, float* l, float* u, int32_t space) {
 
 int skm_get_bf16_topk(skm_ctx* c, float* vals, int32_t* idx, float* eps, int32_t space) {
   if (!c) return SKM_EINVAL;
-  if (c->layout != SKM_DENSE || c->precision != SKM_PREC_BF16 || !c->have_bounds) return SKM_ESTATE;
+  if (c->layout != SKM_DENSE || c->precision == SKM_PREC_FP32 || !c->have_bounds) return SKM_ESTATE;
   const cudaMemcpyKind kind = space == SKM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   if (eps) {
     float* out = eps;

@@ -7,7 +7,10 @@
 // k_dense_tighten and the FP32 recheck, so all paths agree bit for bit.
 //
 //   k_dense_bf16        unit rows rounded to BF16 (A operand of k_bf16_topk)
+//   k_dense_fp8         unit rows scaled by a power of two and rounded to
+//                       FP8-E4M3 (the A operand of the FP8 form)
 //   k_dense_centers     term-major FP32 centers -> row-major FP32 and BF16
+//                       (or FP8-E4M3 of 2^8 c)
 //   k_dense_top2        FP32 GEMM + fused top-2 (plain FP32 path, whole rows
 //                       for Hamerly, recheck of ambiguous rows)
 //   k_dense_classify    precision form: the BF16 top-2 decides the label when its
@@ -18,6 +21,8 @@
 //   k_label_*, k_dense_cluster_sum, k_dense_delta
 //                       exact fixed-point cluster sums: full (rows sorted by
 //                       label) or only the rows whose label changed
+#include <cuda_fp8.h>
+
 #include <climits>
 
 #include "skm_internal.cuh"
@@ -59,6 +64,55 @@ __global__ void k_dense_bf16(const float* __restrict__ X, const float* __restric
   }
 }
 
+// E4M3 rounding (to nearest even; no saturation is reached: callers keep
+// |v| < 256) and its exact value as FP32.
+__device__ __forceinline__ uint8_t to_e4m3(float v) {
+  return (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float from_e4m3(uint8_t q) {
+  return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
+}
+
+// Xq = e4m3(y_i 2^e_i), y_i = fl(x_i * rinv_i) (a warp per row), with the
+// power of two 2^e_i chosen from the row's largest |y|, m in [2^q, 2^(q+1)):
+// e_i = 7 - q puts every scaled entry below 256 (no saturation) and the
+// largest at or above 128.  rsc_i = 2^-(e_i + 8) turns an accumulator of the
+// row against centers scaled by 2^8 back into a similarity, exactly.
+// exr_i >= |Xq_i 2^-e_i - x_i/|x_i||: y - e4m3(y 2^e) 2^-e is exact in FP32
+// (the difference between a float and its rounding to a coarser
+// power-of-two grid), its squares are summed rounding up, and y's own error
+// is added as in k_dense_bf16.
+__global__ void k_dense_fp8(const float* __restrict__ X, const float* __restrict__ rinv, int64_t n, int64_t d,
+                            uint8_t* __restrict__ Xq, float* __restrict__ exr, float* __restrict__ rsc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float yerr = __fmul_ru(0x1.0p-23f, __fadd_ru(1.f, __fmul_ru((float)(d + 8), 0x1.0p-30f)));
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const float ri = rinv[i];
+    float m = 0.f;
+    for (int64_t t = lane; t < d; t += 32) m = fmaxf(m, fabsf(__fmul_rn(X[i * d + t], ri)));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(SKM_FULL_MASK, m, o));
+    // unit rows: m >= 1/sqrt(d) is a normal float, q = its exponent
+    const int q = (int)((__float_as_uint(m) >> 23) & 0xFF) - 127;
+    const int e = 7 - q;
+    const float sc = ldexpf(1.f, e), isc = ldexpf(1.f, -e);
+    float e2 = 0.f;
+    for (int64_t t = lane; t < d; t += 32) {
+      const float y = __fmul_rn(X[i * d + t], ri);
+      const uint8_t b = to_e4m3(__fmul_rn(y, sc));  // y * 2^e is exact
+      Xq[i * d + t] = b;
+      const float err = __fsub_rn(y, __fmul_rn(from_e4m3(b), isc));  // exact
+      e2 = __fmaf_ru(err, err, e2);
+    }
+    e2 = warp_sum_up(e2);
+    if (lane == 0) {
+      exr[i] = __fadd_ru(__fsqrt_ru(e2), yerr);
+      rsc[i] = ldexpf(1.f, -(e + 8));
+    }
+  }
+}
+
 // ec_j = |bf16(c_j) - c_j| for every center (a warp each; the differences
 // are exact in FP32, their squares summed rounding up), reduced to
 // E_c = max_j ec_j (float bits compare as unsigned for values >= 0); the
@@ -97,6 +151,41 @@ __global__ void __launch_bounds__(256) k_center_err(const float* __restrict__ Cr
   }
 }
 
+// The same for the FP8 centers e4m3(2^8 c_j): ec_j = |e4m3(2^8 c_j) 2^-8 - c_j|
+// (exact differences); the accumulation term uses 1.25 >= (1 + ex_i)(1 + 6u +
+// E_c): an E4M3 rounding of a normal value errs by at most 2^-4 of it, and a
+// subnormal one (scaled magnitude below 2^-6) by at most 2^-10 of the scale,
+// so ex_i, E_c < 0.063 for unit rows and centers.
+__global__ void __launch_bounds__(256) k_center_err_fp8(const float* __restrict__ Cr, const uint8_t* __restrict__ Cq,
+                                                        int64_t d, int32_t k, unsigned* __restrict__ ebw,
+                                                        float* __restrict__ ebc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j < k) {
+    float e2 = 0.f;
+    for (int64_t t = lane; t < d; t += 32) {
+      const float e = __fsub_rn(Cr[j * d + t], __fmul_rn(from_e4m3(Cq[j * d + t]), 0x1.0p-8f));  // exact
+      e2 = __fmaf_ru(e, e, e2);
+    }
+    e2 = warp_sum_up(e2);
+    if (lane == 0) {
+      atomicMax(ebw, __float_as_uint(__fsqrt_ru(e2)));
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ebw + 1, 1u) == gridDim.x - 1) {
+      __threadfence();
+      const double ec = (double)__uint_as_float(atomicExch(ebw, 0u));
+      ebc[0] = __double2float_ru(__dadd_ru(1.0 + 6.0 * 0x1.0p-24, ec));
+      ebc[1] = __double2float_ru(__dadd_ru(ec, ((double)d + 16.0) * 0x1.0p-23 * 1.25));
+      atomicExch(ebw + 1, 0u);
+    }
+  }
+}
+
 __global__ void k_bf16_eps_rows(const float* __restrict__ exr, const float* __restrict__ ebc, int64_t n,
                                 float* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -104,9 +193,10 @@ __global__ void k_bf16_eps_rows(const float* __restrict__ exr, const float* __re
 }
 
 // Ct (d x kst, term-major) -> Cr (k x d FP32) and Cb (kpad x d BF16, zero
-// rows past k), through 32 x 32 shared tiles.
+// rows past k) or Cq (kpad x d FP8-E4M3 of 2^8 c), through 32 x 32 shared
+// tiles.
 __global__ void k_dense_centers(const float* __restrict__ Ct, int64_t d, int32_t k, int64_t kst, int32_t kpad,
-                                float* __restrict__ Cr, __nv_bfloat16* __restrict__ Cb) {
+                                float* __restrict__ Cr, __nv_bfloat16* __restrict__ Cb, uint8_t* __restrict__ Cq) {
   __shared__ float tile[32][33];
   const int64_t t0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -120,6 +210,7 @@ __global__ void k_dense_centers(const float* __restrict__ Ct, int64_t d, int32_t
       const float v = tile[threadIdx.x][r];
       if (j < k) Cr[j * d + t] = v;
       if (Cb) Cb[j * d + t] = __float2bfloat16_rn(v);
+      if (Cq) Cq[j * d + t] = to_e4m3(__fmul_rn(v, 0x1.0p8f));
     }
   }
 }
@@ -890,6 +981,14 @@ int dense_prep_bf16(skm_ctx* c) {
 }
 
 // out[i] = the row's current BF16 error bound (device memory, n floats).
+int dense_prep_fp8(skm_ctx* c) {
+  SKM_PROF_BEGIN(c, "k_dense_fp8");
+  k_dense_fp8<<<grid_cap(c->n, 8, c->nsm), 256, 0, c->st>>>((const float*)c->val, c->rinv, c->n, c->d,
+                                                            (uint8_t*)c->Xb, c->exr, c->rsc);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
 int dense_bf16_eps(skm_ctx* c, float* out) {
   SKM_PROF_BEGIN(c, "k_bf16_eps_rows");
   k_bf16_eps_rows<<<grid_cap(c->n, 256, c->nsm), 256, 0, c->st>>>(c->exr, c->ebc, c->n, out);
@@ -899,10 +998,18 @@ int dense_bf16_eps(skm_ctx* c, float* out) {
 
 int dense_refresh_centers(skm_ctx* c) {
   dim3 g((unsigned)((c->d + 31) / 32), (unsigned)((c->kpad + 31) / 32));
+  const bool fp8 = c->precision == SKM_PREC_FP8;
   SKM_PROF_BEGIN(c, "k_dense_centers");
-  k_dense_centers<<<g, dim3(32, 8), 0, c->st>>>(c->Ct, c->d, c->k, c->kst, c->kpad, c->Cr, (__nv_bfloat16*)c->Cb);
+  k_dense_centers<<<g, dim3(32, 8), 0, c->st>>>(c->Ct, c->d, c->k, c->kst, c->kpad, c->Cr,
+                                                fp8 ? nullptr : (__nv_bfloat16*)c->Cb,
+                                                fp8 ? (uint8_t*)c->Cb : nullptr);
   SKM_LAUNCHED(c);
-  if (c->Cb) {
+  if (c->Cb && fp8) {
+    SKM_PROF_BEGIN(c, "k_center_err");
+    k_center_err_fp8<<<(unsigned)((c->k + 7) / 8), 256, 0, c->st>>>(c->Cr, (const uint8_t*)c->Cb, c->d, c->k,
+                                                                   c->ebw, c->ebc);
+    SKM_LAUNCHED(c);
+  } else if (c->Cb) {
     SKM_PROF_BEGIN(c, "k_center_err");
     k_center_err<<<(unsigned)((c->k + 7) / 8), 256, 0, c->st>>>(c->Cr, (const __nv_bfloat16*)c->Cb, c->d, c->k,
                                                               c->ebw, c->ebc);

@@ -1,15 +1,20 @@
 // Dense similarity bulk on the 5th-generation tensor cores (precision form):
-// S^b = X_b * C_b^T with BF16 operands and FP32 accumulation in tensor memory,
-// fused with the selection of each row's recheck candidates.
+// S^b = X_b * C_b^T with BF16 operands (kind::f16) or FP8-E4M3 operands
+// (kind::f8f6f4) and FP32 accumulation in tensor memory, fused with the
+// selection of each row's recheck candidates.  FP8 operands carry power-of-two
+// scales (per row for the data, 2^8 for every center), so the epilogue turns
+// an accumulator into a similarity by one exact multiplication per value.
 //
 // One CTA per SM, persistent over tiles of 128 rows.  Warp roles:
 //   warp 0  TMA producer: per (center tile, K block) one stage of a 4-stage
-//           ring holding the row tile's 128 x 64 slice of A and the 256 x 64
-//           slice of the centers B, 128-byte swizzled (A comes from L2 after
-//           the first center tile);
+//           ring holding the row tile's 128 x 128-byte slice of A and the
+//           256 x 128-byte slice of the centers B (64 BF16 or 128 FP8
+//           elements of K), 128-byte swizzled (A comes from L2 after the
+//           first center tile);
 //   warp 1  allocates 512 TMEM columns; one lane issues tcgen05.mma
-//           (M = 128, N = 256, K = 16 per instruction) into one of two
-//           256-column accumulators, and tcgen05.commit to the barriers;
+//           (M = 128, N = 256, K = 32 bytes per instruction: 16 BF16 or 32
+//           FP8 elements) into one of two 256-column accumulators, and
+//           tcgen05.commit to the barriers;
 //   warps 2-9  epilogue, two groups of four: group g drains accumulator g
 //           (tcgen05.ld of the warp's 32-lane TMEM quarter) while the other
 //           group drains the other one.
@@ -39,12 +44,12 @@ namespace {
 
 constexpr int kBM = 128;          // rows per tile (UMMA M)
 constexpr int kBN = 256;          // centers per accumulator (UMMA N)
-constexpr int kBK = 64;           // K elements per 128-byte swizzled row
+constexpr int kRowBytes = 128;    // K bytes per 128-byte swizzled row of a stage
 constexpr int kStages = 4;        // A + B ring
 constexpr int kCap = 16;          // appended values a row's buffer holds per group
 constexpr int kThreads = 320;     // 2 + 8 warps
-constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KB per stage
-constexpr uint32_t kBBytes = kBN * kBK * 2;  // 32 KB per stage
+constexpr uint32_t kABytes = kBM * kRowBytes;  // 16 KB per stage
+constexpr uint32_t kBBytes = kBN * kRowBytes;  // 32 KB per stage
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint64_t kTimeoutNs = 1000000000ull;
 
@@ -126,18 +131,30 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+// Instruction descriptors, D = F32, A and B K-major: kind::f16 with
+// A = B = BF16 (type code 1), kind::f8f6f4 with A = B = E4M3 (type code 0).
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-          tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <bool FP8>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accumulate) {
+  if (FP8)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, "
+        "p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -222,14 +239,18 @@ __device__ __forceinline__ int compact_buf(uint2* b, int nap, float thr) {
   return w;
 }
 
-// Per row and group: the BF16 similarities above the group's final
-// threshold (with their centers), or an overflow mark.
+// Per row and group: the reduced-precision similarities above the group's
+// final threshold (with their centers), or an overflow mark.  FP8: rsc[row]
+// is the exact power of two 1 / (row scale * center scale) that turns the
+// row's accumulators into similarities.
+template <bool FP8>
 __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant__ CUtensorMap mapA,
                                                           const __grid_constant__ CUtensorMap mapB, int64_t n,
                                                           int32_t k, int nkb, int nnt, const float* __restrict__ lb,
                                                           const float* __restrict__ dlt, const float* __restrict__ exr,
-                                                          const float* __restrict__ ebc, int use_thr,
-                                                          uint2* __restrict__ cand, uint8_t* __restrict__ cand_n,
+                                                          const float* __restrict__ ebc, const float* __restrict__ rsc,
+                                                          int use_thr, uint2* __restrict__ cand,
+                                                          uint8_t* __restrict__ cand_n,
                                                           unsigned long long* __restrict__ cnt) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of the swizzled tiles
@@ -239,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
   MmaShared* sh = reinterpret_cast<MmaShared*>(buf + 2 * kCap * kBM);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = (n + kBM - 1) / kBM;
-  const uint32_t idesc = idesc_bf16(kBM, kBN);
+  const uint32_t idesc = FP8 ? idesc_e4m3(kBM, kBN) : idesc_bf16(kBM, kBN);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -278,8 +299,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
             if (!ok) break;
             unsigned char* st = St + (size_t)s * kStageBytes;
             mbar_expect_tx(&sh->full[s], kStageBytes);
-            tma_load_2d(&mapA, &sh->full[s], st, kb * kBK, (int)(tile * kBM));
-            tma_load_2d(&mapB, &sh->full[s], st + kABytes, kb * kBK, nt * kBN);
+            // x = the first K element of the block: 128 bytes per block, so
+            // x times the element size is a multiple of 16 bytes
+            const int kx = kb * (FP8 ? kRowBytes : kRowBytes / 2);
+            tma_load_2d(&mapA, &sh->full[s], st, kx, (int)(tile * kBM));
+            tma_load_2d(&mapB, &sh->full[s], st + kABytes, kx, nt * kBN);
           }
     }
   } else if (warp == 1) {
@@ -301,8 +325,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
             const uint32_t a_addr = smem_u32(St + (size_t)s * kStageBytes);
             const uint32_t b_addr = a_addr + kABytes;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)
-              umma_bf16(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
+            for (int kk = 0; kk < kRowBytes / 32; ++kk)
+              umma<FP8>(d_tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
                         (kb > 0 || kk > 0) ? 1u : 0u);
             umma_commit(&sh->empty[s]);  // the stage is free once these MMAs are done
           }
@@ -322,8 +346,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
       const int64_t row = tile * kBM + r_in_tile;
       const bool valid = row < n;
-      float tau = -INFINITY, W2 = 0.f;
+      float tau = -INFINITY, W2 = 0.f, f = 1.f;
       if (valid) {
+        if (FP8) f = rsc[row];
         const float eps_b = bf16_eps(exr, ebc, row);
         W2 = __fadd_ru(__fmul_ru(2.f, __fadd_ru(eps_b, dlt[row])), 0x1.0p-20f);
         if (use_thr) tau = __fsub_rd(__fsub_rd(__fsub_rd(lb[row], eps_b), W2), 0x1.0p-20f);
@@ -341,6 +366,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bf16_topk(const __grid_constant
           if (jb >= k) break;  // the same for the whole warp
           uint32_t r[64];
           tmem_ld32x2(tmem + ((uint32_t)(quarter * 32) << 16) + b * kBN + c * 64, r);
+          if (FP8) {  // accumulators -> similarities (exact: f is a power of two)
+#pragma unroll
+            for (int q = 0; q < 64; ++q) r[q] = __float_as_uint(__fmul_rn(__uint_as_float(r[q]), f));
+          }
           if (jb + 64 > k) {  // last chunk: columns past k belong to padding centers
 #pragma unroll
             for (int q = 0; q < 64; ++q)
@@ -479,15 +508,17 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-// rows x cols BF16, row-major (cols contiguous); boxes of 64 columns x box_rows.
-int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows) {
+// rows x cols of BF16 (esize 2) or FP8 (esize 1), row-major (cols
+// contiguous); boxes of 128 bytes of columns x box_rows.
+int make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows, int esize) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = get_encode();
   if (!enc) return SKM_EUNSUPPORTED;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * esize};
+  const cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esize), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  const CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                         const_cast<void*>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SKM_OK : SKM_EINVAL;
@@ -501,26 +532,36 @@ size_t bf16_mma_smem_bytes() {
 
 // rows of 16-byte multiples for the tensor maps
 int bf16_mma_supported(int64_t d) { return d % 8 == 0; }
+int fp8_mma_supported(int64_t d) { return d % 16 == 0; }
 
-// Xb: n x d BF16 (unit rows); Cb: (ceil(k/256)*256) x d BF16 (zero rows past k).
-// Columns past d read as zeros (the tensor map's out-of-bounds fill).
-// use_thr: lb holds a lower bound on every row's best exact similarity.
+// Xb: n x d BF16 or FP8 (scaled unit rows); Cb: (ceil(k/256)*256) x d of the
+// same type (zero rows past k).  Columns past d read as zeros (the tensor
+// map's out-of-bounds fill).  use_thr: lb holds a lower bound on every row's
+// best exact similarity.
 int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* topv, int32_t* topi) {
-  if (!bf16_mma_supported(c->d)) return SKM_EUNSUPPORTED;
+  const bool fp8 = c->precision == SKM_PREC_FP8;
+  if (fp8 ? !fp8_mma_supported(c->d) : !bf16_mma_supported(c->d)) return SKM_EUNSUPPORTED;
+  const int esize = fp8 ? 1 : 2;
   CUtensorMap mA, mB;
   const int nnt = (c->k + kBN - 1) / kBN;
-  int rc = make_map(&mA, Xb, c->n, c->d, kBM);
+  int rc = make_map(&mA, Xb, c->n, c->d, kBM, esize);
   if (rc) return rc;
-  rc = make_map(&mB, Cb, (int64_t)nnt * kBN, c->d, kBN);
+  rc = make_map(&mB, Cb, (int64_t)nnt * kBN, c->d, kBN, esize);
   if (rc) return rc;
   const size_t smem = bf16_mma_smem_bytes();
-  SKM_CUDA_TRY(cudaFuncSetAttribute(k_bf16_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const void* kern = fp8 ? (const void*)k_bf16_topk<true> : (const void*)k_bf16_topk<false>;
+  SKM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t ntiles = (c->n + kBM - 1) / kBM;
   const int grid = (int)(ntiles < c->nsm ? ntiles : c->nsm);
-  const int nkb = (int)((c->d + kBK - 1) / kBK);
-  SKM_PROF_BEGIN(c, "k_bf16_topk");
-  k_bf16_topk<<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->exr, c->ebc,
-                                               use_thr, c->cand, c->cand_n, c->cnt);
+  const int kblk = kRowBytes / esize;  // K elements per block
+  const int nkb = (int)((c->d + kblk - 1) / kblk);
+  SKM_PROF_BEGIN(c, fp8 ? "k_fp8_topk" : "k_bf16_topk");
+  if (fp8)
+    k_bf16_topk<true><<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->exr, c->ebc,
+                                                       c->rsc, use_thr, c->cand, c->cand_n, c->cnt);
+  else
+    k_bf16_topk<false><<<grid, kThreads, smem, c->st>>>(mA, mB, c->n, c->k, nkb, nnt, c->lb, c->dlt, c->exr,
+                                                        c->ebc, nullptr, use_thr, c->cand, c->cand_n, c->cnt);
   SKM_LAUNCHED(c);
   SKM_PROF_BEGIN(c, "k_topk_merge");
   const int64_t gm = (c->n + 255) / 256, gcap = (int64_t)c->nsm * 16;

@@ -370,9 +370,10 @@ struct skm_ctx {
   float* exr;         // [n] |bf16(x_i/|x_i|) - x_i/|x_i||, rounded up (precision form)
   float* ebc;         // [2] {1 + 6u + E_c, E_c + accumulation term}, E_c = max_j |bf16(c_j) - c_j|
   unsigned* ebw;      // [2] k_center_err's running max (float bits) and block counter; zero between launches
-  void* Xb;           // [n x d] BF16 unit rows
+  void* Xb;           // [n x d] BF16 unit rows, or FP8-E4M3 rows scaled by 2^e_i
+  float* rsc;         // [n] FP8: 2^-(e_i + 8), accumulator -> similarity
   float* Cr;          // [k x d] FP32 centers, row-major
-  void* Cb;           // [kpad x d] BF16 centers
+  void* Cb;           // [kpad x d] BF16 centers, or FP8-E4M3 of 2^8 c
   float* topv;        // [n x 8] best BF16 similarities per row, descending
   int32_t* topi;      // [n x 8] their centers
   uint2* cand;        // [2 x 16 x n] the tensor kernel's per-group lists (value bits, center)
@@ -433,6 +434,7 @@ int finish_update(skm_ctx* c);
 
 // dense rows (k_dense.cu, k_mma.cu)
 int dense_prep_bf16(skm_ctx* c);
+int dense_prep_fp8(skm_ctx* c);
 int dense_refresh_centers(skm_ctx* c);
 int dense_bf16_eps(skm_ctx* c, float* out);
 int dense_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt);
@@ -440,6 +442,7 @@ int dense_classify(skm_ctx* c, bool hamerly, const int32_t* list, const unsigned
 int dense_tighten(skm_ctx* c);
 int dense_center_sums(skm_ctx* c);
 int bf16_mma_supported(int64_t d);
+int fp8_mma_supported(int64_t d);
 constexpr int kTopK = 8;  // BF16 candidates kept per row
 int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* topv, int32_t* topi);
 int dense_lower(skm_ctx* c);

@@ -20,7 +20,7 @@ STANDARD, HAMERLY, ELKAN, SIMP_HAMERLY, SIMP_ELKAN, YINYANG = 0, 1, 2, 3, 4, 5
 VARIANTS = {"standard": STANDARD, "hamerly": HAMERLY, "elkan": ELKAN, "simp_hamerly": SIMP_HAMERLY,
             "simp_elkan": SIMP_ELKAN, "yinyang": YINYANG}
 F32, F16, BF16 = 0, 1, 2
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 CSR, DENSE = 0, 1
 DEVICE, HOST = 0, 1
 
@@ -210,7 +210,7 @@ class KMeans:
         opt = skm_options()
         lib.skm_default_options(ctypes.byref(opt))
         opt.hamerly_tight = 1 if hamerly_tight else 0
-        opt.precision = {"fp32": PREC_FP32, "bf16": PREC_BF16}[precision]
+        opt.precision = {"fp32": PREC_FP32, "bf16": PREC_BF16, "fp8": PREC_FP8}[precision]
         opt.row_threshold = int(row_threshold)
         opt.graph = 1 if graph else 0
         opt.graph_check = int(graph_check)

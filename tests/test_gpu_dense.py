@@ -50,7 +50,7 @@ def emb():
 
 
 @pytest.mark.parametrize("variant", ["standard", "hamerly", "simp_hamerly"])
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_dense_teacher_forced(emb, variant, precision):
     init = synth.init_rows(len(emb), 37, 5)
     _teacher_forced_dense(emb, 37, variant, precision, init, 15)
@@ -64,7 +64,7 @@ def test_precision_form_labels_equal_fp32_path():
     Xd = torch.from_numpy(Xs).cuda()
     seqs = {}
     for v in ("standard", "hamerly"):
-        for p in ("fp32", "bf16"):
+        for p in ("fp32", "bf16", "fp8"):
             km = skm.KMeans.dense(Xd, 300, variant=v, init_rows=init, precision=p)
             labs = []
             for _ in range(12):
@@ -155,14 +155,15 @@ def _label_runs(Xs, k, init, iters, keys):
             if ch == 0:
                 break
             km.update_centers()
-        if p == "bf16":
+        if p != "fp32":
             stats[(v, p)] = (sts, km.bf16_topk())
         seqs[(v, p)] = labs
         km.close()
     return seqs, stats
 
 
-KEYS = [("standard", "fp32"), ("standard", "bf16"), ("hamerly", "bf16"), ("simp_hamerly", "bf16")]
+KEYS = [("standard", "fp32"), ("standard", "bf16"), ("hamerly", "bf16"), ("simp_hamerly", "bf16"),
+        ("standard", "fp8"), ("hamerly", "fp8")]
 
 
 @pytest.mark.parametrize("k", [5, 8, 9])
@@ -212,3 +213,90 @@ def test_dense_host_input_and_rejections():
     odd = synth.vmf(100, 500, 3, 20.0, seed=3)  # d = 500 is not a multiple of 8: no BF16 bulk
     with pytest.raises(skm.SkmError):
         skm.KMeans.dense(torch.from_numpy(odd).cuda(), 3, precision="bf16")
+
+
+def _e4m3(y):
+    """Nearest E4M3 value (ties to even), as FP64 (the emulation pinned
+    against PyTorch in test_fp8_bound.py)."""
+    y = np.asarray(y, dtype=np.float64)
+    ay = np.abs(y)
+    e = np.maximum(np.floor(np.log2(np.where(ay > 0, ay, 1.0))), -6.0)
+    q = 2.0 ** (e - 3)
+    return np.clip(np.round(y / q) * q, -448.0, 448.0)
+
+
+def _unit32(M):
+    M = np.asarray(M, dtype=np.float32)
+    ss = np.einsum("ij,ij->i", M.astype(np.float64), M.astype(np.float64))
+    return (M * (1.0 / np.sqrt(ss)).astype(np.float32)[:, None]).astype(np.float32)
+
+
+def test_fp8_error_bound_holds():
+    """FP8 form: every listed E4M3 similarity is within its row's bound eps_i
+    of the exact FP64 one, every center left out is at most v8 + eps_i, and
+    eps_i lies near the E4M3 rounding scale (about 16x the BF16 bound)."""
+    Xs = synth.vmf(4000, 384, 100, 40.0, seed=9)
+    init = synth.init_rows(len(Xs), 256, 9)
+    km = skm.KMeans.dense(torch.from_numpy(Xs).cuda(), 256, variant="standard", init_rows=init, precision="fp8")
+    Xn = Xs.astype(np.float64) / np.linalg.norm(Xs.astype(np.float64), axis=1, keepdims=True)
+    for it in range(3):
+        C = km.centers().astype(np.float64)
+        km.assign()
+        tv, ti, eps = km.bf16_topk()
+        km.update_centers()
+        eps = eps.astype(np.float64)
+        assert np.all(eps > 0.005) and np.all(eps < 0.15), (eps.min(), eps.max())
+        S = Xn @ (C / np.linalg.norm(C, axis=1, keepdims=True)).T
+        over = ti[:, 0] < 0
+        tv, ti, S, eps = tv[~over], ti[~over], S[~over], eps[~over]
+        real = ti >= 0
+        exact = np.take_along_axis(S, np.where(real, ti, 0).astype(np.int64), axis=1)
+        err = np.where(real, np.abs(tv.astype(np.float64) - exact), 0.0)
+        assert np.all(err <= eps[:, None]), (err.max(), eps.min())
+        outside = S.copy()
+        for r in range(len(tv)):
+            outside[r, ti[r][real[r]]] = -np.inf
+        assert np.all(outside.max(axis=1) <= tv[:, 7].astype(np.float64) + eps)
+    km.close()
+
+
+def test_fp8_tensor_core_sums_the_exact_products():
+    """The FP8 similarities the tensor cores return are the FP32-accumulated
+    sums of the exact E4M3 products, unscaled exactly: against the sums of the
+    same quantised operands in FP64 they differ by at most (d + 16) 2^-23
+    times the sum of |products| (reading TC of the bound).  The rows are built
+    so that large partial sums cancel: rows 2.. are (+a..., -a..., small
+    entries) and the two centers (rows 0 and 1) are (a..., a..., small
+    entries), so each of those similarities is a small sum left after
+    products of 64 x 64 entries cancel; an accumulator that kept fewer bits
+    than FP32 would lose the small products and fail here."""
+    d, n = 256, 64
+    rng = np.random.default_rng(17)
+    M = np.zeros((n, d), np.float64)
+    M[:, :64] = 1.0
+    M[:, 64:128] = -1.0
+    M[:2, 64:128] = 1.0
+    M[:, 128:] = rng.uniform(-2.0 ** -5, 2.0 ** -5, size=(n, 128))
+    Y = _unit32(M)
+    km = skm.KMeans.dense(torch.from_numpy(Y).cuda(), 2, variant="standard", init_rows=np.array([0, 1]),
+                          precision="fp8")
+    C = km.centers()  # unit rows 0 and 1 (FP32)
+    km.assign()
+    tv, ti, _ = km.bf16_topk()
+    km.close()
+    e = 7 - np.floor(np.log2(np.abs(Y.astype(np.float64)).max(axis=1))).astype(np.int64)
+    s = np.ldexp(1.0, e)[:, None]
+    Xq = _e4m3(Y.astype(np.float64) * s)                   # scaled row operands
+    Cq = _e4m3(C.astype(np.float64) * 256.0)              # scaled center operands
+    P = Xq @ Cq.T                                           # exact sums of the products
+    A = np.abs(Xq) @ np.abs(Cq).T
+    got = np.full((n, 2), np.nan)
+    for r in range(n):
+        for q in range(8):
+            if ti[r, q] >= 0:
+                got[r, ti[r, q]] = tv[r, q] * s[r, 0] * 256.0  # back to the accumulator's units
+    have = ~np.isnan(got)
+    assert have[2:].all()  # both centers are candidates of every test row
+    assert np.all(np.abs(P[2:]) < 0.01 * A[2:])  # the large products do cancel
+    tol = (d + 16) * 2.0 ** -23 * A
+    assert np.all(np.abs(got[have] - P[have]) <= tol[have]), np.max(np.abs(got - P)[have] / A[have])
