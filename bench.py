@@ -452,7 +452,8 @@ def summarize_batch(args, rank, world, local):
     a = argparse.Namespace(**vars(args))
     a.steps, a.warmup = 2, 1
     r = run_batch(a, rank, world, local)
-    r.pop("kernel_time_share", None)
+    for v in r["variants"].values():
+        v.pop("kernel_time_share", None)
     r["note"] = "see --workload batch"
     return r
 
@@ -645,10 +646,10 @@ def run_embed(args, rank, world, local):
 def run_batch(args, rank, world, local):
     """Batched form: 64 independent runs (n_r lognormal over [5e3, 2e5],
     d = 2e4, k_r uniform over {10, 50, 100, 250, 500}, at most 50 iterations
-    each) in one context -- simplified Elkan, one launch per phase for all
-    runs, the iteration replayed as a CUDA graph, launch shape autotuned --
-    against the plain FP32 standard variant run by run (one context each, one
-    after the other), at identical labels."""
+    each) in one context -- Elkan bounds (and Simplified Elkan beside it), one
+    launch per phase for all runs, the iteration replayed as a CUDA graph,
+    launch shape autotuned -- against the plain FP32 standard variant run by
+    run (one context each, one after the other), at identical labels."""
     import tempfile
 
     import torch
@@ -665,49 +666,49 @@ def run_batch(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     Xd = [torch.from_numpy(a).to(dev) for a in (X.row_ptr, X.col, X.val)]
-    b = skm.Batch(X.n, X.d, *Xd, run_rows, ks, variant="simp_elkan", init_rows=init_all, graph=True,
-                  stream=stream.cuda_stream)
     cache = os.path.join(tempfile.gettempdir(), "skm_autotune.txt")
-    t0 = time.perf_counter()
-    from_cache = b.autotune(cache, iters=3)
-    tune_s = time.perf_counter() - t0
-    for _ in range(args.warmup):
-        b.reset(init_all)
-        b.run(iters)
     sampler = ClockSampler(local)
     sampler.start()
-    ms_b, its = 0.0, []
-    l0 = skm.kernel_launches()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+    per_variant, lab_b = {}, {}
+    for variant in ("elkan", "simp_elkan"):
+        b = skm.Batch(X.n, X.d, *Xd, run_rows, ks, variant=variant, init_rows=init_all, graph=True,
+                      stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        from_cache = b.autotune(cache, iters=3)
+        tune_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            b.reset(init_all)
+            b.run(iters)
+        ms_b, its = 0.0, []
+        l0 = skm.kernel_launches()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.reset(init_all)
+            it, J = b.run(iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_b += e0.elapsed_time(e1)
+            its.append(it)
+        launches = skm.kernel_launches() - l0
+        lab_b[variant] = b.labels()
+        sims = b.stats().total_sims
+        # kernel shares of one eager run with per-kernel events
         b.reset(init_all)
-        it, J = b.run(iters)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_b += e0.elapsed_time(e1)
-        its.append(it)
-    launches = skm.kernel_launches() - l0
+        prof = profiled_run(b, iters)
+        b.close()
+        per_step = ms_b / args.steps
+        tot = sum(v[0] for v in prof.values()) or 1.0
+        per_variant[variant] = {
+            "batch_ms_per_step": round(per_step, 3), "batch_iterations": its[-1],
+            "run_iterations_per_s": round(nruns * its[-1] / (per_step / 1e3), 1),
+            "sims_evaluated": sims, "gpu_launches_per_step": int(launches / args.steps),
+            "autotune": {"from_cache": from_cache, "seconds": round(tune_s, 2)},
+            "kernel_time_share": {nm: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)}
+                                  for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:12]}}
     clocks = sampler.stop()
-    lab_b = b.labels()
-    # kernel shares of one eager run with per-kernel events
-    b.reset(init_all)
-    prof = {}
-    for _ in range(iters):
-        b.profile(True)
-        ch = b.assign()
-        if ch:
-            b.update_centers()
-        for nm, (t, c) in b.profile_read().items():
-            prof.setdefault(nm, [0.0, 0])
-            prof[nm][0] += t
-            prof[nm][1] += c
-        b.profile(False)
-        if ch == 0:
-            break
-    b.close()
     # the plain FP32 standard variant, run by run (contexts built outside the timing)
     ms_s, it_s, lab_s = 0.0, 0, []
     for r, p in enumerate(parts):
@@ -725,20 +726,16 @@ def run_batch(args, rank, world, local):
         it_s += it
         lab_s.append(km.labels())
         km.close()
-    same = bool(np.array_equal(lab_b, np.concatenate(lab_s)))
-    per_step = ms_b / args.steps
-    tot = sum(v[0] for v in prof.values()) or 1.0
+    ref = np.concatenate(lab_s)
+    for v, e in per_variant.items():
+        e["labels_identical_to_standard"] = bool(np.array_equal(lab_b[v], ref))
+        e["speedup_vs_sequential_standard"] = round(ms_s / e["batch_ms_per_step"], 2)
+    head = per_variant["elkan"]
     return {"workload": f"{nruns} sparse TF-IDF runs, n_r in [5e3, 2e5] (sum {X.n}, {X.nnz} nnz), d=20000, "
                         f"k_r in {{10,50,100,250,500}} (sum {int(ks.sum())}), at most {iters} iterations each",
-            "batch_ms_per_step": round(per_step, 3), "batch_iterations": its[-1],
-            "run_iterations_per_s": round(nruns * its[-1] / (per_step / 1e3), 1),
+            "variant": "elkan", **{kk: vv for kk, vv in head.items() if kk != "kernel_time_share"},
             "sequential_standard_ms": round(ms_s, 3), "sequential_standard_run_iterations": it_s,
-            "speedup_vs_sequential_standard": round(ms_s / per_step, 2),
-            "labels_identical_to_standard": same, "gpu_launches_per_step": int(launches / args.steps),
-            "autotune": {"from_cache": from_cache, "seconds": round(tune_s, 2)},
-            "clocks": clocks,
-            "kernel_time_share": {nm: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)}
-                                  for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:12]}}
+            "variants": per_variant, "clocks": clocks}
 
 
 def sampled_parity(km, csr, sample, prev, C):

@@ -199,7 +199,7 @@ void release(skm_ctx* c) {
                   c->ub,     c->w1,      c->w2,    c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark,
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
                   c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n,
-                  c->exr,    c->ebc,     c->ebw,   c->rsc};
+                  c->exr,    c->ebc,     c->ebw,   c->rsc,    c->gdbeg,  c->gdcnt,  c->gtask};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -300,12 +300,23 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   TRY(dalloc(c, &c->pdn, (size_t)kst));
   TRY(dalloc(c, &c->pup, (size_t)kst));
   TRY(dalloc(c, &c->qup, (size_t)kst));
-  TRY(dalloc(c, &c->hsel, HSEL_N));
+  TRY(dalloc(c, &c->hsel, (size_t)HSEL_N * (c->nruns > 0 ? c->nruns : 1)));
   const bool full = (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY);
   const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
   const bool yy = (c->variant == SKM_YINYANG);
   const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY) || c->layout == SKM_DENSE || yy;
-  if (full) {
+  if (full && c->nruns > 0) {
+    // a batch: each run's k x kst block of cc and of the Gram (FP64), and the
+    // per-run plan of the Gram tasks
+    const auto& R = *static_cast<std::vector<RunDesc>*>(c->hruns);
+    const int64_t blk = R.back().ccoff + (int64_t)R.back().k * R.back().kst;
+    TRY(dalloc(c, &c->cc, (size_t)blk));
+    TRY(dalloc(c, &c->sc, (size_t)k));
+    TRY(dalloc(c, &c->G, (size_t)blk));
+    TRY(dalloc(c, &c->gdbeg, (size_t)c->nruns));
+    TRY(dalloc(c, &c->gdcnt, (size_t)c->nruns));
+    TRY(dalloc(c, &c->gtask, (size_t)c->nruns + 1));
+  } else if (full) {
     // enough d-splits of the Gram (64 x 64 tiles) for ~4 blocks per SM, each
     // split >= 256 terms
     const int64_t tk = (k + 63) / 64, tiles = tk * (tk + 1) / 2;
@@ -462,14 +473,14 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
   if (!x || !run_rows || !ks || nruns < 1 || x->n < 1 || x->d < 1 || x->reserved != 0) return SKM_EINVAL;
   if (x->layout != SKM_CSR) return SKM_EUNSUPPORTED;
   if (variant < SKM_STANDARD || variant > SKM_YINYANG) return SKM_EINVAL;
-  if (variant != SKM_STANDARD && variant != SKM_SIMP_ELKAN) return SKM_EUNSUPPORTED;
+  if (variant == SKM_YINYANG) return SKM_EUNSUPPORTED;
   if (x->dtype < SKM_F32 || x->dtype > SKM_BF16) return SKM_EINVAL;
   if (x->memspace != SKM_DEVICE && x->memspace != SKM_HOST) return SKM_EINVAL;
   if (!x->values || !x->row_ptr || !x->col_idx) return SKM_EINVAL;
   if (x->d > INT32_MAX || x->n > INT32_MAX || (int64_t)nruns * x->d > INT32_MAX) return SKM_EUNSUPPORTED;
   if (run_rows[0] != 0 || run_rows[nruns] != x->n) return SKM_EINVAL;
   std::vector<RunDesc> R((size_t)nruns);
-  int64_t koff = 0, uoff = 0;
+  int64_t koff = 0, uoff = 0, ccoff = 0;
   int32_t kmax = 0;
   for (int32_t r = 0; r < nruns; ++r) {
     const int64_t nr = run_rows[r + 1] - run_rows[r];
@@ -482,10 +493,12 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
     d.kst = (ks[r] + 7) / 8 * 8;
     d.koff = (int32_t)koff;
     d.uoff = uoff;
+    d.ccoff = ccoff;
     int32_t cap = opt && opt->row_threshold > 0 ? opt->row_threshold : (ks[r] + 7) / 8;
     d.cap = cap > 7 ? 7 : cap;
     koff += d.kst;
     uoff += nr * d.kst;
+    ccoff += (int64_t)d.k * d.kst;
     if (d.kst > kmax) kmax = d.kst;
   }
   if (koff > INT32_MAX / 2) return SKM_EUNSUPPORTED;

@@ -248,16 +248,17 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
 
 // ------------------------------------------------------------- Hamerly
 
-template <bool FULL>
+// Thread per point.  A batch keeps one drift summary per run (the other
+// centers of a point are those of its run), read through row_run.
+template <bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_ham_bounds(int64_t n, const int32_t* __restrict__ a,
                                                        float* __restrict__ lb, float* __restrict__ ub,
                                                        const float* __restrict__ dlt, const float* __restrict__ pdn,
                                                        const float* __restrict__ pup, const float* __restrict__ qup,
                                                        const float* __restrict__ hsel, const float* __restrict__ sc,
-                                                       int tight, int moved, int32_t* __restrict__ w1,
-                                                       unsigned long long* __restrict__ cnt) {
+                                                       const int32_t* __restrict__ row_run, int tight, int moved,
+                                                       int32_t* __restrict__ w1, unsigned long long* __restrict__ cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int jmin_d = (int)hsel[0], jmin_u = (int)hsel[3], jmax_q = (int)hsel[6];
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t i = base + threadIdx.x;
     bool take = false;
@@ -266,9 +267,11 @@ __global__ void __launch_bounds__(kBlock) k_ham_bounds(int64_t n, const int32_t*
       float l = lb[i], u = ub[i];
       if (moved) {
         // p'(a) = min_{j != a} p(j): the worst drift among the other centers
-        const float pdm = (ai == jmin_d) ? hsel[2] : hsel[1];
-        const float pum = (ai == jmin_u) ? hsel[5] : hsel[4];
-        const float qm = (ai == jmax_q) ? hsel[8] : hsel[7];
+        const float* hs = BATCH ? hsel + (int64_t)HSEL_N * row_run[i] : hsel;
+        const int jmin_d = (int)hs[0], jmin_u = (int)hs[3], jmax_q = (int)hs[6];
+        const float pdm = (ai == jmin_d) ? hs[2] : hs[1];
+        const float pum = (ai == jmin_u) ? hs[5] : hs[4];
+        const float qm = (ai == jmax_q) ? hs[8] : hs[7];
         l = bound_l(l, pdn[ai], pup[ai], qup[ai]);
         u = bound_u_hamerly(u, pdm, pum, qm, tight);
         lb[i] = l;
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
       const float L = __shfl_sync(SKM_FULL_MASK, my_L, r);
       const bool skip_pt = __shfl_sync(SKM_FULL_MASK, (int)my_skip, r) != 0;
       float* urow = ub + rg.ubase;
-      const float* ccrow = cc + (int64_t)ai * kst;
+      const float* ccrow = cc + rg.ccoff + (int64_t)ai * rg.kst;
       const float* pdr = pdn + rg.koff;
       const float* pur = pup + rg.koff;
       const float* qr = qup + rg.koff;
@@ -644,7 +647,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     const float dl = dlt[i];
     const float L = __fsub_rd(lb[i], 2.f * dl);
     float* urow = ub + rg.ubase;
-    const int m = elk_candidates<FULL>(urow, cc + (int64_t)ai * kst, ai, L, rg.k, gmask, gl, sj);
+    const int m = elk_candidates<FULL>(urow, cc + rg.ccoff + (int64_t)ai * rg.kst, ai, L, rg.k, gmask, gl, sj);
     if (m > 7) {  // not expected (the bound kernel routes such points), handled anyway
       if (gl == 0) {
         const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
@@ -708,7 +711,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
     const float L = __fsub_rd(lb[i], 2.f * dl);
     float* urow = ub + rg.ubase;
     int m = 0;
-    if (lane < 8) m = elk_candidates<FULL>(urow, cc + (int64_t)ai * kst, ai, L, rg.k, 0xFFu, lane, sj);
+    if (lane < 8) m = elk_candidates<FULL>(urow, cc + rg.ccoff + (int64_t)ai * rg.kst, ai, L, rg.k, 0xFFu, lane, sj);
     m = __shfl_sync(SKM_FULL_MASK, m, 0);
     __syncwarp();
     if (m > 7) {
@@ -861,19 +864,29 @@ int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long
   return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows);
 }
 
+// Hamerly's bound pass (k_ham_bounds for the context's variant and form).
+int ham_bounds_launch(skm_ctx* c) {
+  const bool full = (c->variant == SKM_HAMERLY), batch = c->nruns > 0;
+#define SKM_HAMB(F, B)                                                                                            \
+  k_ham_bounds<F, B><<<persistent_grid(c, (const void*)k_ham_bounds<F, B>), kBlock, 0, c->st>>>(                  \
+      c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel, c->sc, c->row_run, c->opt.hamerly_tight, \
+      c->moved, c->w1, c->cnt)
+  SKM_PROF_BEGIN(c, "k_ham_bounds");
+  if (full && batch) SKM_HAMB(true, true);
+  else if (full) SKM_HAMB(true, false);
+  else if (batch) SKM_HAMB(false, true);
+  else SKM_HAMB(false, false);
+#undef SKM_HAMB
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
 template <typename VT>
 int hamerly_step_t(skm_ctx* c) {
   const bool full = (c->variant == SKM_HAMERLY);
-  const int g = persistent_grid(c, full ? (const void*)k_ham_bounds<true> : (const void*)k_ham_bounds<false>);
-  SKM_PROF_BEGIN(c, "k_ham_bounds");
-  if (full) {
-    k_ham_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
-                                                c->sc, c->opt.hamerly_tight, c->moved, c->w1, c->cnt);
-  } else {
-    k_ham_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
-                                                 c->sc, c->opt.hamerly_tight, c->moved, c->w1, c->cnt);
-  }
-  SKM_LAUNCHED(c);
+  const int rc = ham_bounds_launch(c);
+  if (rc) return rc;
+  const int g = persistent_grid(c, full ? (const void*)k_ham_tighten<VT, true> : (const void*)k_ham_tighten<VT, false>);
   const VT* v = (const VT*)c->val;
   SKM_PROF_BEGIN(c, "k_ham_tighten");
   if (full) {
@@ -901,7 +914,8 @@ int elkan_step_t(skm_ctx* c) {
                                               c->dlt,                                                              \
                                               c->pdn, c->pup, c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1,   \
                                               c->w2, c->cnt)
-  if (batch) SKM_ELKB(false, true);
+  if (batch && full) SKM_ELKB(true, true);
+  else if (batch) SKM_ELKB(false, true);
   else if (full) SKM_ELKB(true, false);
   else SKM_ELKB(false, false);
 #undef SKM_ELKB
@@ -912,7 +926,8 @@ int elkan_step_t(skm_ctx* c) {
   k_elk_recompute<VT, F, B><<<persistent_grid(c, (const void*)k_elk_recompute<VT, F, B>), kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,     \
                                                      c->row_run, c->runs, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, \
                                                      c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
-  if (batch) SKM_ELKR(false, true);
+  if (batch && full) SKM_ELKR(true, true);
+  else if (batch) SKM_ELKR(false, true);
   else if (full) SKM_ELKR(true, false);
   else SKM_ELKR(false, false);
 #undef SKM_ELKR
@@ -923,7 +938,8 @@ int elkan_step_t(skm_ctx* c) {
                                    c->st>>>(                                                                   \
       c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->row_run, c->runs, c->w1 + (c->n - 1),         \
       c->cnt + C_W1L, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
-  if (batch) SKM_ELKL(false, true);
+  if (batch && full) SKM_ELKL(true, true);
+  else if (batch) SKM_ELKL(false, true);
   else if (full) SKM_ELKL(true, false);
   else SKM_ELKL(false, false);
 #undef SKM_ELKL
@@ -951,19 +967,7 @@ int yinyang_step_t(skm_ctx* c) {
 
 }  // namespace
 
-int hamerly_bounds_only(skm_ctx* c) {
-  const int g = persistent_grid(
-      c, c->variant == SKM_HAMERLY ? (const void*)k_ham_bounds<true> : (const void*)k_ham_bounds<false>);
-  SKM_PROF_BEGIN(c, "k_ham_bounds");
-  if (c->variant == SKM_HAMERLY)
-    k_ham_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
-                                                c->sc, c->opt.hamerly_tight, c->moved, c->w1, c->cnt);
-  else
-    k_ham_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel,
-                                                 c->sc, c->opt.hamerly_tight, c->moved, c->w1, c->cnt);
-  SKM_LAUNCHED(c);
-  return SKM_OK;
-}
+int hamerly_bounds_only(skm_ctx* c) { return ham_bounds_launch(c); }
 
 int assign_full(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
   switch (c->dtype) {

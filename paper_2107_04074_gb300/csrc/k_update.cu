@@ -30,6 +30,10 @@
 //                       chunks): all tiles when many clusters moved, else only
 //                       the rows of the (at most 64) dirty clusters; then cc
 //                       and s.
+//   k_hsel_runs, k_gram_plan, k_gram_batch, k_gram_final_batch
+//                       a batch of runs: Hamerly's worst-drift summary per run,
+//                       and each run's own (block-diagonal) Gram entries of its
+//                       dirty centers, then its cc rows and s.
 #include <cfloat>
 #include <climits>
 
@@ -652,6 +656,265 @@ __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ G
   if (threadIdx.x == 0) sc[i] = sh[0];
 }
 
+// ---------------------------------------------------------------- batches
+
+// Block per run: Hamerly's worst-drift summary over the run's own centers
+// koff .. koff + k - 1 (global ids), the rule of k_hsel_obj.
+__global__ void __launch_bounds__(256) k_hsel_runs(const float* __restrict__ pdn, const float* __restrict__ pup,
+                                                   const float* __restrict__ qup, const RunDesc* __restrict__ runs,
+                                                   float* __restrict__ hsel) {
+  const RunDesc R = runs[blockIdx.x];
+  __shared__ float s_pd[256], s_pu[256], s_q[256], s_pd2[256], s_pu2[256], s_q2[256];
+  __shared__ int s_jd[256], s_ju[256], s_jq[256];
+  float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
+  int jd = INT_MAX, ju = INT_MAX, jq = INT_MAX;
+  for (int j = R.koff + threadIdx.x; j < R.koff + R.k; j += blockDim.x) {
+    const float x = pdn[j], y = pup[j], z = qup[j];
+    if (x < bd) { bd2 = bd; bd = x; jd = j; } else if (x < bd2) bd2 = x;
+    if (y < bu) { bu2 = bu; bu = y; ju = j; } else if (y < bu2) bu2 = y;
+    if (z > bq) { bq2 = bq; bq = z; jq = j; } else if (z > bq2) bq2 = z;
+  }
+  s_pd[threadIdx.x] = bd; s_pd2[threadIdx.x] = bd2; s_jd[threadIdx.x] = jd;
+  s_pu[threadIdx.x] = bu; s_pu2[threadIdx.x] = bu2; s_ju[threadIdx.x] = ju;
+  s_q[threadIdx.x] = bq; s_q2[threadIdx.x] = bq2; s_jq[threadIdx.x] = jq;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const int a = threadIdx.x, b = threadIdx.x + o;
+      if (s_pd[b] < s_pd[a] || (s_pd[b] == s_pd[a] && s_jd[b] < s_jd[a])) {
+        s_pd2[a] = fminf(s_pd2[b], s_pd[a]);
+        s_pd[a] = s_pd[b];
+        s_jd[a] = s_jd[b];
+      } else {
+        s_pd2[a] = fminf(s_pd2[a], s_pd[b]);
+      }
+      if (s_pu[b] < s_pu[a] || (s_pu[b] == s_pu[a] && s_ju[b] < s_ju[a])) {
+        s_pu2[a] = fminf(s_pu2[b], s_pu[a]);
+        s_pu[a] = s_pu[b];
+        s_ju[a] = s_ju[b];
+      } else {
+        s_pu2[a] = fminf(s_pu2[a], s_pu[b]);
+      }
+      if (s_q[b] > s_q[a] || (s_q[b] == s_q[a] && s_jq[b] < s_jq[a])) {
+        s_q2[a] = fmaxf(s_q2[b], s_q[a]);
+        s_q[a] = s_q[b];
+        s_jq[a] = s_jq[b];
+      } else {
+        s_q2[a] = fmaxf(s_q2[a], s_q[b]);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const bool one = (R.k == 1);
+    float* h = hsel + (int64_t)HSEL_N * blockIdx.x;
+    h[0] = (float)s_jd[0];
+    h[1] = s_pd[0];
+    h[2] = one ? 1.f : s_pd2[0];
+    h[3] = (float)s_ju[0];
+    h[4] = s_pu[0];
+    h[5] = one ? 1.f : s_pu2[0];
+    h[6] = (float)s_jq[0];
+    h[7] = s_q[0];
+    h[8] = one ? 0.f : s_q2[0];
+  }
+}
+
+// First position p in the ascending list[0..len) with list[p] >= v.
+__device__ __forceinline__ int lower_pos(const int32_t* __restrict__ list, int len, int32_t v) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (list[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// One block: per run the range of its real dirty centers in the ascending
+// dirty list (dbeg, dcnt) and its tile count ceil(dcnt / 64) * ceil(k / 64);
+// task_off = the exclusive prefix over runs (task_off[nruns] = total).
+__global__ void __launch_bounds__(1024) k_gram_plan(const int32_t* __restrict__ dlist,
+                                                    const unsigned long long* __restrict__ cnt,
+                                                    const RunDesc* __restrict__ runs, int32_t nruns,
+                                                    int32_t* __restrict__ dbeg, int32_t* __restrict__ dcnt,
+                                                    int64_t* __restrict__ task_off) {
+  __shared__ long long part[1024];
+  const int nd = (int)cnt[C_NDIRTY];
+  const int per = (nruns + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int r0 = (int)threadIdx.x * per, r1 = min(nruns, r0 + per);
+  long long mine = 0;
+  for (int r = r0; r < r1; ++r) {
+    const int lo = lower_pos(dlist, nd, runs[r].koff), hi = lower_pos(dlist, nd, runs[r].koff + runs[r].k);
+    dbeg[r] = lo;
+    dcnt[r] = hi - lo;
+    mine += (long long)((hi - lo + kGT - 1) / kGT) * ((runs[r].k + kGT - 1) / kGT);
+  }
+  part[threadIdx.x] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long s = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const long long v = part[t];
+      part[t] = s;
+      s += v;
+    }
+    task_off[nruns] = s;
+  }
+  __syncthreads();
+  long long s = part[threadIdx.x];
+  for (int r = r0; r < r1; ++r) {
+    task_off[r] = s;
+    s += (long long)((dcnt[r] + kGT - 1) / kGT) * ((runs[r].k + kGT - 1) / kGT);
+  }
+}
+
+// Persistent blocks over the batch's Gram tasks: a task is (run, block of <= 64
+// dirty centers of the run, tile of 64 of the run's centers).  Its 64 x 64
+// dot products over all d terms (threads own 4 x 4, FP32 products summed over
+// 256 terms, then in FP64 -- the chunking of k_gram_part, so the error bound
+// eg holds) are written to both G[i][j] and G[j][i] of the run's block: a
+// moved center changes its row and its column.  When i and j both moved,
+// both tasks compute the same value (the same products in the same order).
+__global__ void __launch_bounds__(256) k_gram_batch(const float* __restrict__ Ct, int64_t d, int64_t K,
+                                                    const RunDesc* __restrict__ runs, int32_t nruns,
+                                                    const int32_t* __restrict__ dlist,
+                                                    const int32_t* __restrict__ dbeg,
+                                                    const int32_t* __restrict__ dcnt,
+                                                    const int64_t* __restrict__ task_off, double* __restrict__ G) {
+  __shared__ __align__(16) float A[32][kGT], B[32][kGT];
+  __shared__ int rows_g[kGT];
+  const int64_t total = task_off[nruns];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int64_t task = blockIdx.x; task < total; task += gridDim.x) {
+    int lo = 0, hi = nruns - 1;  // the run: last r with task_off[r] <= task
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (task_off[mid] <= task) lo = mid;
+      else hi = mid - 1;
+    }
+    const RunDesc R = runs[lo];
+    const int64_t t_in = task - task_off[lo];
+    const int nj = (R.k + kGT - 1) / kGT;
+    const int db = (int)(t_in / nj), j0 = (int)(t_in % nj) * kGT;  // j0: local
+    const int nrow = min(kGT, dcnt[lo] - db * kGT);
+    __syncthreads();  // the previous task's readers of rows_g are done
+    if (tid < kGT) rows_g[tid] = tid < nrow ? dlist[dbeg[lo] + db * kGT + tid] : -1;
+    __syncthreads();
+    double acc64[4][4];
+    float acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        acc64[x][y] = 0.0;
+        acc[x][y] = 0.f;
+      }
+    int steps = 0;
+    for (int64_t t0 = 0; t0 < d; t0 += 32) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = tid + 256 * h;
+        const int r = q >> 4, c4 = (q & 15) * 4;
+        const int64_t t = t0 + r;
+        float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+        if (t < d) {
+          const float* row = Ct + t * K;
+          va.x = rows_g[c4 + 0] >= 0 ? row[rows_g[c4 + 0]] : 0.f;
+          va.y = rows_g[c4 + 1] >= 0 ? row[rows_g[c4 + 1]] : 0.f;
+          va.z = rows_g[c4 + 2] >= 0 ? row[rows_g[c4 + 2]] : 0.f;
+          va.w = rows_g[c4 + 3] >= 0 ? row[rows_g[c4 + 3]] : 0.f;
+          // the run's slice is kst wide (a multiple of 8): 16-byte loads stay inside it
+          if (j0 + c4 < R.kst) vb = *reinterpret_cast<const float4*>(row + R.koff + j0 + c4);
+        }
+        *reinterpret_cast<float4*>(&A[r][c4]) = va;
+        *reinterpret_cast<float4*>(&B[r][c4]) = vb;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) {
+        const float4 av = *reinterpret_cast<const float4*>(&A[r][ty * 4]);
+        const float4 bv = *reinterpret_cast<const float4*>(&B[r][tx * 4]);
+        const float ar[4] = {av.x, av.y, av.z, av.w}, br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = __fmaf_rn(ar[x], br[y], acc[x][y]);
+      }
+      __syncthreads();
+      if (++steps == 8) {
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            acc64[x][y] += (double)acc[x][y];
+            acc[x][y] = 0.f;
+          }
+        steps = 0;
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int ri = ty * 4 + x, jl = j0 + tx * 4 + y;
+        if (ri < nrow && jl < R.k) {
+          const int il = rows_g[ri] - R.koff;
+          const double g = acc64[x][y] + (double)acc[x][y];
+          G[R.ccoff + (int64_t)il * R.kst + jl] = g;
+          G[R.ccoff + (int64_t)jl * R.kst + il] = g;
+        }
+      }
+  }
+}
+
+// Block per global center i of a batch: its run's cc row (the rule of
+// k_gram_final on the run's block of G) and s(i).  A run's padding centers
+// (local ids k .. kst - 1) label no row, so their rows are skipped; their
+// columns get cc = 1.
+__global__ void __launch_bounds__(256) k_gram_final_batch(const double* __restrict__ G,
+                                                          const RunDesc* __restrict__ runs, int32_t nruns,
+                                                          const double* __restrict__ cnorm, double eg,
+                                                          float* __restrict__ cc, float* __restrict__ sc) {
+  __shared__ float sh[256];
+  const int i = blockIdx.x;
+  int lo = 0, hi = nruns - 1;  // the run: last r with koff <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (runs[mid].koff <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  const RunDesc R = runs[lo];
+  const int il = i - R.koff;
+  if (il >= R.k) {
+    if (threadIdx.x == 0) sc[i] = 1.f;
+    return;
+  }
+  float best = -1.f;
+  for (int j = threadIdx.x; j < R.kst; j += blockDim.x) {
+    float* out = cc + R.ccoff + (int64_t)il * R.kst + j;
+    if (j >= R.k) {
+      *out = 1.f;
+      continue;
+    }
+    const double g = G[R.ccoff + (int64_t)il * R.kst + j];
+    const double den = cnorm[i] * cnorm[R.koff + j];
+    double gh = (den > 0.0 ? g / den : 0.0) + eg;
+    double h = 0.5 * (gh + 1.0);
+    h = h < 0.0 ? 0.0 : (h > 1.0 ? 1.0 : h);
+    const float v = fminf(__double2float_ru(sqrt(h) * (1.0 + 0x1.0p-50)), 1.f);
+    *out = v;
+    if (j != il) best = fmaxf(best, v);
+  }
+  sh[threadIdx.x] = best;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sc[i] = sh[0];
+}
+
 inline unsigned grid_cap(int64_t items, int per_block, int nsm, int per_sm = 16) {
   int64_t g = (items + per_block - 1) / per_block;
   if (g > (int64_t)nsm * per_sm) g = (int64_t)nsm * per_sm;
@@ -739,8 +1002,34 @@ int finish_update(skm_ctx* c) {
   SKM_PROF_BEGIN(c, "k_hsel_obj");
   k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj, c->cnt);
   SKM_LAUNCHED(c);
+  const bool hamv = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
+  const bool full = (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY);
+  // |error| of an FP32 sum of 256 products <= gamma_256 |c_i||c_j|, plus
+  // the normalisation by FP64 norms of FP32 vectors.
+  const double eg = 260.0 * 0x1.0p-24 / (1.0 - 260.0 * 0x1.0p-24) + 1e-12;
+  if (c->nruns > 0) {
+    // a batch: per-run drift summaries, per-run (block-diagonal) Gram
+    if (hamv) {
+      SKM_PROF_BEGIN(c, "k_hsel_runs");
+      k_hsel_runs<<<(unsigned)c->nruns, 256, 0, c->st>>>(c->pdn, c->pup, c->qup, c->runs, c->hsel);
+      SKM_LAUNCHED(c);
+    }
+    if (full) {
+      SKM_PROF_BEGIN(c, "k_gram_plan");
+      k_gram_plan<<<1, 1024, 0, c->st>>>(c->dlist, c->cnt, c->runs, c->nruns, c->gdbeg, c->gdcnt, c->gtask);
+      SKM_LAUNCHED(c);
+      SKM_PROF_BEGIN(c, "k_gram_batch");
+      k_gram_batch<<<(unsigned)(c->nsm * 4), 256, 0, c->st>>>(c->Ct, c->d, c->kst, c->runs, c->nruns, c->dlist,
+                                                              c->gdbeg, c->gdcnt, c->gtask, c->G);
+      SKM_LAUNCHED(c);
+      SKM_PROF_BEGIN(c, "k_gram_final");
+      k_gram_final_batch<<<(unsigned)k, 256, 0, c->st>>>(c->G, c->runs, c->nruns, cnorm, eg, c->cc, c->sc);
+      SKM_LAUNCHED(c);
+    }
+    return SKM_OK;
+  }
   // ---- center-center bounds (full variants)
-  if (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY) {
+  if (full) {
     const int32_t row_max = c->grow_max;
     const int64_t per = (c->d + c->gsplit - 1) / c->gsplit;
     const unsigned tk = (unsigned)((k + kGT - 1) / kGT);
@@ -760,9 +1049,6 @@ int finish_update(skm_ctx* c) {
     k_gram_rows_reduce<<<grid_cap((int64_t)row_max * k, 256, c->nsm), 256, 0, c->st>>>(c->rpart, c->gsplit, k,
                                                                                        c->dlist, c->cnt, row_max, c->G);
     SKM_LAUNCHED(c);
-    // |error| of an FP32 sum of 256 products <= gamma_256 |c_i||c_j|, plus
-    // the normalisation by FP64 norms of FP32 vectors.
-    const double eg = 260.0 * 0x1.0p-24 / (1.0 - 260.0 * 0x1.0p-24) + 1e-12;
     SKM_PROF_BEGIN(c, "k_gram_final");
     k_gram_final<<<k, 256, 0, c->st>>>(c->G, k, c->kst, cnorm, eg, c->cc, c->sc);
     SKM_LAUNCHED(c);

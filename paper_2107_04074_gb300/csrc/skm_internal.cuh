@@ -260,18 +260,20 @@ constexpr int kLogCap = 256;  // iterations a graph replay logs between host rea
 // One run of a batch (many independent clusterings in one context): rows
 // [row0, row0 + n) of the concatenated data, centers koff .. koff + k - 1 in
 // global numbering (the run's slice of the term-major arrays is kst wide, a
-// multiple of 8, so koff is too), Elkan bound rows of kst floats from uoff.
-// Labels are global center ids.
+// multiple of 8, so koff is too), Elkan bound rows of kst floats from uoff,
+// and (full variants) its block of center-center bounds and Gram entries,
+// k rows of kst, from ccoff.  Labels are global center ids.
 struct RunDesc {
-  int64_t row0, n, uoff;
+  int64_t row0, n, uoff, ccoff;
   int32_t koff, k, kst, cap;
 };
 
 // Where a row's centers and bounds live: its run's slice, or for a single
-// run the whole center range.
+// run the whole center range (ccoff: the first center-center row; kst: the
+// row stride of the bound and center-center rows).
 struct RowGeom {
-  int64_t ubase;
-  int32_t koff, k, cap;
+  int64_t ubase, ccoff;
+  int32_t koff, k, cap, kst;
 };
 template <bool BATCH>
 __device__ __forceinline__ RowGeom row_geom(int64_t i, int32_t k, int64_t kst, int32_t cap,
@@ -280,15 +282,19 @@ __device__ __forceinline__ RowGeom row_geom(int64_t i, int32_t k, int64_t kst, i
   RowGeom g;
   if (!BATCH) {
     g.ubase = i * kst;
+    g.ccoff = 0;
     g.koff = 0;
     g.k = k;
     g.cap = cap;
+    g.kst = (int32_t)kst;
   } else {
     const RunDesc& R = runs[row_run[i]];
     g.ubase = R.uoff + (i - R.row0) * (int64_t)R.kst;
+    g.ccoff = R.ccoff;
     g.koff = R.koff;
     g.k = R.k;
     g.cap = R.cap;
+    g.kst = R.kst;
   }
   return g;
 }
@@ -357,11 +363,14 @@ struct skm_ctx {
   float* pup;   // [kst] drift cosine upper bound
   float* qup;   // [kst] drift sine upper bound
   float* gdrift;  // [3 ng] Yin-Yang: per group of 8 centers min pd, max pu, max q
-  float* hsel;  // [HSEL_N] Hamerly drift summary
-  float* cc;    // [k * kst] center-center bounds (full variants)
+  float* hsel;  // [HSEL_N] Hamerly drift summary (a batch: one per run)
+  float* cc;    // [k * kst] center-center bounds (full variants; a batch: per run from ccoff)
   float* sc;    // [k] s(j)
   double* gpart;  // Gram partials (all tiles)
-  double* G;      // [k * k] Gram, upper triangle
+  double* G;      // [k * k] Gram, upper triangle (a batch: each run's k x kst block from ccoff, both triangles)
+  int32_t* gdbeg;   // batch Gram plan: per run the first of its dirty centers in dlist
+  int32_t* gdcnt;   // ... and their number
+  int64_t* gtask;   // [nruns + 1] exclusive prefix of the runs' tile counts
   double* rpart;  // Gram partials of dirty rows
   int32_t gsplit, rsplit, grow_max;
   // dense rows (layout SKM_DENSE)

@@ -51,9 +51,9 @@ def test_init_rejects_bad_arguments_without_touching_the_gpu():
 def test_unsupported_combinations_rejected_without_the_gpu():
     """Combinations the library does not offer are refused before any CUDA
     call: dense rows with Elkan or Yin-Yang or non-FP32 values, the BF16
-    precision form with d not a multiple of 8, Elkan with k > 4096, and the
-    batched form with a variant other than standard / simplified Elkan or
-    with a malformed run table."""
+    precision form with d not a multiple of 8 (FP8: 16) or an unknown
+    precision, Elkan with k > 4096, and the batched form with Yin-Yang bounds
+    or with a malformed run table."""
     import numpy as np
     lib = skm.load()
     h = ctypes.c_void_p()
@@ -81,6 +81,10 @@ def test_unsupported_combinations_rejected_without_the_gpu():
     lib.skm_default_options(ctypes.byref(opt))
     opt.precision = skm.PREC_BF16
     assert init(data(skm.DENSE, d=12), 3, V["standard"], opt) == skm.EUNSUPPORTED  # d % 8 != 0
+    opt.precision = skm.PREC_FP8
+    assert init(data(skm.DENSE, d=24), 3, V["standard"], opt) == skm.EUNSUPPORTED  # d % 16 != 0
+    opt.precision = 7
+    assert init(data(skm.DENSE, d=32), 3, V["standard"], opt) == skm.EINVAL  # no such precision
     assert init(data(skm.CSR, n=5000), 4097, V["elkan"]) == skm.EUNSUPPORTED
 
     x = data(skm.CSR)
@@ -93,8 +97,7 @@ def test_unsupported_combinations_rejected_without_the_gpu():
         assert h.value is None
         return rc
 
-    assert batch([0, 4, 10], ks, V["hamerly"]) == skm.EUNSUPPORTED
-    assert batch([0, 4, 10], ks, V["elkan"]) == skm.EUNSUPPORTED
+    assert batch([0, 4, 10], ks, V["yinyang"]) == skm.EUNSUPPORTED
     assert batch([0, 4, 9], ks, V["standard"]) == skm.EINVAL      # does not end at n
     assert batch([1, 4, 10], ks, V["standard"]) == skm.EINVAL     # does not start at 0
     assert batch([0, 2, 10], np.array([3, 3], np.int32), V["standard"]) == skm.EINVAL  # k > rows of the run

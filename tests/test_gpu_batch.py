@@ -43,7 +43,10 @@ def _single(part, k, init, variant, **kw):
     return skm.KMeans(part.n, part.d, dev[0], dev[1], dev[2], int(k), variant=variant, init_rows=init, **kw), dev
 
 
-@pytest.mark.parametrize("variant", ["standard", "simp_elkan"])
+BATCH_VARIANTS = ["standard", "hamerly", "simp_hamerly", "elkan", "simp_elkan"]
+
+
+@pytest.mark.parametrize("variant", BATCH_VARIANTS)
 def test_batch_equals_single_runs(small_batch, variant):
     parts, X, run_rows, ks, inits = small_batch
     b, keep = _batch(X, run_rows, ks, inits, variant)
@@ -69,11 +72,12 @@ def test_batch_equals_single_runs(small_batch, variant):
     b.close()
 
 
-def test_batch_runs_match_oracle(small_batch):
+@pytest.mark.parametrize("variant", ["simp_elkan", "elkan", "hamerly"])
+def test_batch_runs_match_oracle(small_batch, variant):
     """Teacher-forced: every run's assignment from the batch's centers equals
     the FP64 oracle's (up to near-ties), and its center update matches."""
     parts, X, run_rows, ks, inits = small_batch
-    b, keep = _batch(X, run_rows, ks, inits, "simp_elkan")
+    b, keep = _batch(X, run_rows, ks, inits, variant)
     data = [oracle.Data.from_csr(p) for p in parts]
     ris = [oracle.rinv(dd) for dd in data]
     prev = [np.full(p.n, -1, np.int32) for p in parts]
@@ -94,7 +98,7 @@ def test_batch_runs_match_oracle(small_batch):
     b.close()
 
 
-@pytest.mark.parametrize("variant", ["standard", "simp_elkan"])
+@pytest.mark.parametrize("variant", BATCH_VARIANTS)
 def test_graph_replay_equals_eager(small_batch, variant):
     parts, X, run_rows, ks, inits = small_batch
     eager, k1 = _batch(X, run_rows, ks, inits, variant)
@@ -151,9 +155,8 @@ def test_autotune_and_cache(small_batch, tmp_path):
 def test_batch_rejections(small_batch):
     parts, X, run_rows, ks, inits = small_batch
     dev = [torch.from_numpy(a).cuda() for a in (X.row_ptr, X.col, X.val)]
-    for variant in ("hamerly", "elkan", "simp_hamerly", "yinyang"):
-        with pytest.raises(skm.SkmError):
-            skm.Batch(X.n, X.d, *dev, run_rows, ks, variant=variant)
+    with pytest.raises(skm.SkmError):
+        skm.Batch(X.n, X.d, *dev, run_rows, ks, variant="yinyang")
     bad = ks.copy()
     bad[0] = parts[0].n + 1
     with pytest.raises(skm.SkmError):
@@ -171,3 +174,30 @@ def test_batch_rejections(small_batch):
     lab = b.run_labels()
     assert all(l.min() >= 0 and l.max() < k for l, k in zip(lab, ks))
     b.close()
+
+
+@pytest.mark.parametrize("variant", ["elkan", "hamerly"])
+def test_batch_full_variants_prune_with_center_bounds(small_batch, variant):
+    """The full variants' per-run center-center bounds do prune: over a whole
+    run the batch computes no more exact similarities than its simplified
+    variant (same labels), and about as many as the runs alone (their Gram
+    sums the same products in other chunks, so the bounds may differ in the
+    last bits and prune a few pairs differently)."""
+    parts, X, run_rows, ks, inits = small_batch
+    simp = "simp_" + variant
+    sims = {}
+    for v in (variant, simp):
+        b, keep = _batch(X, run_rows, ks, inits, v)
+        it, _ = b.run(40)
+        sims[v] = (it, b.stats().total_sims, b.labels())
+        b.close()
+    assert sims[variant][0] == sims[simp][0]
+    np.testing.assert_array_equal(sims[variant][2], sims[simp][2])
+    assert sims[variant][1] <= sims[simp][1]
+    single = 0
+    for p, k, ini in zip(parts, ks, inits):
+        s, keep = _single(p, k, ini, variant)
+        s.run(40)
+        single += s.stats().total_sims
+        s.close()
+    assert abs(sims[variant][1] - single) <= 0.02 * single
