@@ -261,6 +261,21 @@ int skm_autotune(skm_ctx* ctx, const char* cache_path, int32_t iters, int32_t* f
  * be NULL) receives them.  SKM_EUNSUPPORTED for a batch. */
 int skm_seed_kmeanspp(skm_ctx* ctx, const double* u, int64_t* rows_out);
 
+/* skm_seed_kmeanspp followed by the first assignment, which costs no extra
+ * pass: the bound pre-initialisation that Section 5.6 remarks on and Section 7
+ * names as future work.  The seeding computes every row's similarity to each
+ * center it chooses (the last one included) with the assignment kernels'
+ * arithmetic, so it keeps per row the best center, the best and second best
+ * similarity and, for Elkan, every u(i,j); the labels and bounds are then
+ * exactly those skm_assign would leave after skm_seed_kmeanspp (l = s1 - delta
+ * rounded down, Hamerly's u = s2 + delta, Elkan's u(i,j) = s_ij + delta
+ * rounded up), and the next call is skm_update_centers (skm_run begins with an
+ * assignment, so call skm_update_centers before it).  n_changed (host, may
+ * be NULL; non-NULL synchronises) receives n, as for a first assignment, and
+ * skm_get_stats counts n k similarities for it.  SKM_EUNSUPPORTED for a batch
+ * and for Yin-Yang bounds; u and rows_out as skm_seed_kmeanspp. */
+int skm_seed_kmeanspp_assign(skm_ctx* ctx, const double* u, int64_t* rows_out, int64_t* n_changed);
+
 /* Self-test of the failure path of every device-side wait (the tensor-core
  * kernel's barrier waits): launches one warp that waits on a barrier nothing
  * completes, with the given limit (1 ns .. 2 s).  Returns SKM_ETIMEOUT when

@@ -21,6 +21,10 @@ Functions and the passages they follow:
 * ``u_hamerly``       Eq. (eqn:u-hamerly-2) under rule HG (Section 5.3)
 * ``run``             full runs of the five variants (Sections 5, 5.1-5.4) and of
                       Yin-Yang group bounds (Section 5.5)
+* ``kmeanspp``        spherical k-means++ seeding (Section 5.6)
+* ``kmeanspp_bounds`` the same, with the first assignment and the bounds
+                      pre-initialised from the seeding's similarities
+                      (Section 5.6's remark, Section 7's outlook)
 
 The rule letters (T, E, CL, HG, V, D, M) are defined in the header of
 ``skm_oracle.c``.
@@ -92,6 +96,8 @@ def _lib():
             lib.sko_run.restype = ci
             lib.sko_kmeanspp.argtypes = data + [ip, i64, ip, ip]
             lib.sko_kmeanspp.restype = ci
+            lib.sko_kmeanspp_bounds.argtypes = data + [ip, i64, ip, ip, ip, ip, ip, ip]
+            lib.sko_kmeanspp_bounds.restype = ci
             _LIB = lib
     return _LIB
 
@@ -161,6 +167,23 @@ def kmeanspp(X: Data, ri: np.ndarray, u) -> np.ndarray:
     rows = np.empty(len(u), dtype=np.int64)
     _lib().sko_kmeanspp(*X.args(), _p(ri), len(u), _p(u), _p(rows))
     return rows
+
+
+def kmeanspp_bounds(X: Data, ri: np.ndarray, u, with_sims: bool = False):
+    """Spherical k-means++ seeding (Section 5.6) with the bound
+    pre-initialisation of Section 5.6's remark and Section 7's outlook: the
+    seeding's own similarities give the first assignment from the seeded
+    centers.  Returns (rows, labels, s_best, s_second, S) -- S the n x k
+    similarities (Elkan's initial upper bounds) when with_sims, else None."""
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    k = len(u)
+    rows = np.empty(k, dtype=np.int64)
+    lab = np.empty(X.n, dtype=np.int32)
+    s1 = np.empty(X.n)
+    s2 = np.empty(X.n)
+    S = np.empty((X.n, k)) if with_sims else None
+    _lib().sko_kmeanspp_bounds(*X.args(), _p(ri), k, _p(u), _p(rows), _p(lab), _p(s1), _p(s2), _p(S))
+    return rows, lab, s1, s2, S
 
 
 def assign(X: Data, ri: np.ndarray, C: np.ndarray, a: np.ndarray | None = None):

@@ -21,7 +21,9 @@
  *     (5.3), Hamerly's center test and Simplified Hamerly (5.4), each walked
  *     point by point in the paper's order;
  *   - spherical k-means++ seeding (Section 5.6): the first center uniform,
- *     the others drawn proportional to 1 - max_c <x(i), c>;
+ *     the others drawn proportional to 1 - max_c <x(i), c>; and the bound
+ *     pre-initialisation from the seeding's similarities (Section 5.6 and
+ *     the outlook of Section 7);
  *   - Yin-Yang group bounds (Section 5.5 names them without a cosine form;
  *     reading YY below).
  *
@@ -516,9 +518,21 @@ int sko_run(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32
  * are added), each row weighs 1 - m_i, quantised to q_i = round((1 - m_i) 2^40)
  * (0 if negative); with W = sum q_i and T = floor(u[j] W) the next center is
  * the first row whose running sum of q exceeds T, or, if W = 0, the first row
- * not chosen yet.  Writes the k chosen rows; returns 0. */
-int sko_kmeanspp(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32_t* col,
-                 const double* val, const double* rinv, int64_t k, const double* u, int64_t* rows) {
+ * not chosen yet.  Writes the k chosen rows; returns 0.
+ *
+ * Bound pre-initialisation (the remark of Section 5.6 and the outlook of
+ * Section 7: the similarities the seeding computes can initialise the
+ * bounds): when a is not NULL the similarities to the last center are
+ * computed as well, and each row keeps, over the centers in the order they
+ * were chosen, its best similarity s1 (at the lowest index among equal
+ * values, rule T with no current label), that index a(i), and its second
+ * best s2 (the largest of the others; -inf with k = 1); S (n x k, may be
+ * NULL) receives every similarity.  That is the first assignment from the
+ * seeded centers, with Hamerly's bounds l = s1, u = s2 and Elkan's
+ * u(i,j) = S[i][j], without a separate pass over the data. */
+static int kmeanspp_impl(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32_t* col,
+                         const double* val, const double* rinv, int64_t k, const double* u, int64_t* rows,
+                         int32_t* a, double* s1, double* s2, double* S) {
   sko_data X = {n, d, dense, row_ptr, col, val};
   double* c = (double*)malloc(sizeof(double) * (size_t)d);
   double* m = (double*)malloc(sizeof(double) * (size_t)n);
@@ -533,14 +547,29 @@ int sko_kmeanspp(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const 
     } else {
       for (int64_t p = row_ptr[r]; p < row_ptr[r + 1]; ++p) c[col[p]] = val[p] * rinv[r];
     }
-    if (j + 1 == k) break;
+    if (j + 1 == k && !a) break;
     long long W = 0;
     for (int64_t i = 0; i < n; ++i) {
       const double s = sim(&X, rinv, i, c);
       m[i] = (j == 0 || s > m[i]) ? s : m[i];
       long long q = llround((1.0 - m[i]) * 0x1.0p40);
       W += q > 0 ? q : 0;
+      if (a) {
+        if (S) S[i * k + j] = s;
+        if (j == 0) {
+          a[i] = 0;
+          s1[i] = s;
+          s2[i] = -INFINITY;
+        } else if (s > s1[i]) {
+          s2[i] = s1[i];
+          s1[i] = s;
+          a[i] = (int32_t)j;
+        } else if (s > s2[i]) {
+          s2[i] = s;
+        }
+      }
     }
+    if (j + 1 == k) break;
     int64_t next = -1;
     if (W > 0) {
       long long T = (long long)(u[j + 1] * (double)W);
@@ -563,4 +592,15 @@ int sko_kmeanspp(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const 
   free(c);
   free(m);
   return 0;
+}
+
+int sko_kmeanspp(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32_t* col,
+                 const double* val, const double* rinv, int64_t k, const double* u, int64_t* rows) {
+  return kmeanspp_impl(n, d, dense, row_ptr, col, val, rinv, k, u, rows, NULL, NULL, NULL, NULL);
+}
+
+int sko_kmeanspp_bounds(int64_t n, int64_t d, int dense, const int64_t* row_ptr, const int32_t* col,
+                        const double* val, const double* rinv, int64_t k, const double* u, int64_t* rows,
+                        int32_t* a, double* s1, double* s2, double* S) {
+  return kmeanspp_impl(n, d, dense, row_ptr, col, val, rinv, k, u, rows, a, s1, s2, S);
 }

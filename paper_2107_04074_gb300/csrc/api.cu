@@ -1055,6 +1055,41 @@ int skm_seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_out) {
   return SKM_OK;
 }
 
+int skm_seed_kmeanspp_assign(skm_ctx* c, const double* u, int64_t* rows_out, int64_t* n_changed) {
+  if (!c || !u) return SKM_EINVAL;
+  if (c->nruns > 0 || c->variant == SKM_YINYANG) return SKM_EUNSUPPORTED;
+  for (int32_t j = 0; j < c->k; ++j)
+    if (!(u[j] >= 0.0 && u[j] < 1.0)) return SKM_EINVAL;
+  const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
+  const bool ham = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
+  SeedFirst first = {elk ? 1 : 0, c->lb ? 1 : 0, (c->ub && !elk) ? 1 : 0, nullptr, nullptr, nullptr};
+  std::vector<int64_t> rows((size_t)c->k);
+  TRY(seed_kmeanspp(c, u, rows.data(), &first));
+  {
+    std::unordered_set<int64_t> seen;
+    for (int64_t r : rows)
+      if (r < 0 || r >= c->n || !seen.insert(r).second) return SKM_ECUDA;  // not reachable
+  }
+  TRY(start_from_rows(c, rows));
+  // the assignment the seeding made: its counters start from zero, as in skm_assign
+  SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_ERR, c->st));
+  TRY(seed_finish(c, &first));
+  c->have_bounds = c->layout == SKM_DENSE ? (ham || c->precision != SKM_PREC_FP32) : (c->variant != SKM_STANDARD);
+  c->moved = 0;
+  c->chg_fresh = 1;
+  c->cnt_clear = 0;
+  c->stats.iterations = 1;
+  if (rows_out) std::memcpy(rows_out, rows.data(), sizeof(int64_t) * rows.size());
+  if (n_changed) {
+    TRY(read_counters(c));
+    c->stats.total_sims += c->stats.last_sims;
+    *n_changed = c->stats.last_changed;
+  } else {
+    c->stats.last_changed = -1;
+  }
+  return SKM_OK;
+}
+
 int skm_selftest_wait(int64_t timeout_ns, void* stream) {
   if (timeout_ns < 1 || timeout_ns > 2000000000ll) return SKM_EINVAL;
   return wait_selftest(timeout_ns, (cudaStream_t)stream);

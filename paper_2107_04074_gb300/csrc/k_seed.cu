@@ -19,6 +19,13 @@
 //   k_seed_sims    m_i = max(m_i, <x_i, c_j>), q_i, block sums (dense rows: a
 //                  warp per row; CSR rows: k_seed_sims_lane, a lane per row)
 //   k_seed_pick    one block: W, T, the chosen row for column j + 1
+//   k_seed_finish  bound pre-initialisation (the remark of Section 5.6 and
+//                  the outlook of Section 7): the seeding's similarities are
+//                  those of the first assignment from the seeded centers, so
+//                  the similarity passes also keep each row's best center,
+//                  its best and second best similarity and (Elkan) every
+//                  u(i,j), and this kernel installs the labels and bounds --
+//                  the first assignment without another pass over the data.
 #include <climits>
 
 #include "skm_internal.cuh"
@@ -78,12 +85,41 @@ __device__ __forceinline__ float warp_dot_dense_col(const VT* __restrict__ x, in
   return acc;
 }
 
+// What the similarity passes keep for the first assignment (all pointers
+// NULL: plain seeding).  Over the centers in the order they are chosen, each
+// row keeps its best similarity (m, the seeding's own maximum), the lowest
+// center index reaching it (best) and the second best (second, the largest
+// of the others: equal to m on a tie); Elkan's u(i,j) = s_ij + delta_i
+// rounded up goes to uelk (row stride ustride).
+struct SeedTrack {
+  int32_t* best;
+  float* second;
+  float* uelk;
+  int64_t ustride;
+  const float* dlt;
+};
+
+__device__ __forceinline__ void seed_track(const SeedTrack& tr, int64_t i, int j, float sim, float m_old) {
+  if (!tr.best) return;
+  if (j == 0) {
+    tr.best[i] = 0;
+    tr.second[i] = -INFINITY;
+  } else if (sim > m_old) {
+    tr.second[i] = m_old;
+    tr.best[i] = j;
+  } else if (sim > tr.second[i]) {
+    tr.second[i] = sim;
+  }
+  if (tr.uelk) tr.uelk[i * tr.ustride + j] = __fadd_ru(sim, tr.dlt[i]);
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(256) k_seed_sims(int64_t n, int64_t d, int dense, const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ col, const VT* __restrict__ val,
                                                    const float* __restrict__ rinv, const float* __restrict__ Ct,
                                                    int64_t kst, int jc, int j, float* __restrict__ m,
-                                                   long long* __restrict__ q, long long* __restrict__ bsum) {
+                                                   long long* __restrict__ q, long long* __restrict__ bsum,
+                                                   SeedTrack tr) {
   __shared__ long long wsum[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long s = 0;
@@ -95,6 +131,7 @@ __global__ void __launch_bounds__(256) k_seed_sims(int64_t n, int64_t d, int den
     else dot = warp_dot_one<VT>(rp[i], rp[i + 1], col, val, Ct, kst, jc);
     const float sim = __fmul_rn(dot, rinv[i]);
     if (lane == 0) {
+      seed_track(tr, i, j, sim, m[i]);
       const float mi = j == 0 ? sim : fmaxf(m[i], sim);
       m[i] = mi;
       long long qi = __double2ll_rn((1.0 - (double)mi) * 0x1.0p40);
@@ -125,7 +162,7 @@ __global__ void __launch_bounds__(256) k_seed_sims_lane(int64_t n, const int64_t
                                                         const float* __restrict__ rinv,
                                                         const float* __restrict__ cvec, int j,
                                                         float* __restrict__ m, long long* __restrict__ q,
-                                                        long long* __restrict__ bsum) {
+                                                        long long* __restrict__ bsum, SeedTrack tr) {
   __shared__ long long wsum[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * kSeedRowsLane + threadIdx.x;
@@ -149,6 +186,7 @@ __global__ void __launch_bounds__(256) k_seed_sims_lane(int64_t n, const int64_t
     }
     for (; p < e; ++p) acc = __fmaf_rn(to_f32(val[p]), __ldg(cvec + __ldg(col + p)), acc);
     const float sim = __fmul_rn(acc, rinv[i]);
+    seed_track(tr, i, j, sim, m[i]);
     const float mi = j == 0 ? sim : fmaxf(m[i], sim);
     m[i] = mi;
     qi = __double2ll_rn((1.0 - (double)mi) * 0x1.0p40);
@@ -234,8 +272,32 @@ __global__ void __launch_bounds__(1024) k_seed_pick(const long long* __restrict_
   }
 }
 
+// Thread per row: the first assignment from the seeding's similarities, as
+// k_rows_top2 leaves it (no label was current, so every label changes):
+// a(i) = best, l(i) = s1 - delta rounded down, Hamerly's u(i) = s2 + delta
+// rounded up (-1 with one center); the counters count n changed labels and
+// n k similarities.
+__global__ void __launch_bounds__(256) k_seed_finish(int64_t n, int32_t k, const float* __restrict__ m,
+                                                     const int32_t* __restrict__ best,
+                                                     const float* __restrict__ second,
+                                                     const float* __restrict__ dlt, int32_t* __restrict__ a,
+                                                     float* __restrict__ lb, float* __restrict__ ub_one,
+                                                     unsigned long long* __restrict__ cnt) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    a[i] = best[i];
+    const float dl = dlt[i];
+    if (lb) lb[i] = __fsub_rd(m[i], dl);
+    if (ub_one) ub_one[i] = (k > 1) ? __fadd_ru(second[i], dl) : -1.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    cnt[C_CHANGED] = (unsigned long long)n;
+    cnt[C_SIMS] = (unsigned long long)n * (unsigned long long)k;
+  }
+}
+
 template <typename VT>
-int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
+int seed_t(skm_ctx* c, const double* u, int64_t* rows_host, SeedFirst* first) {
   const int64_t n = c->n, d = c->d, kst = c->kst;
   const int k = c->k;
   const int dense = c->layout == SKM_DENSE;
@@ -249,6 +311,16 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
   SKM_CUDA_TRY(cudaMallocAsync((void**)&q, sizeof(long long) * n, c->st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&bsum, sizeof(long long) * nblk, c->st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&rows, sizeof(int64_t) * k, c->st));
+  SeedTrack tr = {nullptr, nullptr, nullptr, 0, nullptr};
+  if (first) {
+    SKM_CUDA_TRY(cudaMallocAsync((void**)&tr.best, sizeof(int32_t) * n, c->st));
+    SKM_CUDA_TRY(cudaMallocAsync((void**)&tr.second, sizeof(float) * n, c->st));
+    if (first->elkan) {
+      tr.uelk = c->ub;
+      tr.ustride = kst;
+    }
+    tr.dlt = c->dlt;
+  }
   SKM_CUDA_TRY(cudaMemsetAsync(c->Ct, 0, sizeof(float) * d * kst, c->st));
   int64_t r0 = (int64_t)(u[0] * (double)n);
   if (r0 >= n) r0 = n - 1;
@@ -259,20 +331,30 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
   for (int j = 0; j < k; ++j) {
     k_seed_column<VT><<<1, 256, 0, c->st>>>(c->rp, c->col, v, c->rinv, n, d, dense, kst, j, rows, c->Ct, cvec);
     SKM_LAUNCH_CHECK();
-    if (j + 1 == k) break;
+    // the last center's similarities are needed only for the first assignment
+    if (j + 1 == k && !first) break;
     // the similarities to center j, read from its contiguous copy (the same
     // FP32 values as column j of Ct)
     if (dense)
       k_seed_sims<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, d, dense, c->rp, c->col, v, c->rinv, cvec, 1, 0, j, m,
-                                                         q, bsum);
+                                                         q, bsum, tr);
     else
-      k_seed_sims_lane<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, c->rp, c->col, v, c->rinv, cvec, j, m, q, bsum);
+      k_seed_sims_lane<VT><<<(unsigned)nblk, 256, 0, c->st>>>(n, c->rp, c->col, v, c->rinv, cvec, j, m, q, bsum,
+                                                              tr);
     SKM_LAUNCH_CHECK();
+    if (j + 1 == k) break;
     k_seed_pick<<<1, 1024, 0, c->st>>>(bsum, nblk, rpb, q, n, u[j + 1], rows, j + 1);
     SKM_LAUNCH_CHECK();
   }
   SKM_CUDA_TRY(cudaMemcpyAsync(rows_host, rows, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, c->st));
-  cudaFreeAsync(m, c->st);
+  if (first) {
+    // handed to seed_finish, which frees them
+    first->m = m;
+    first->best = tr.best;
+    first->second = tr.second;
+    m = nullptr;
+  }
+  if (m) cudaFreeAsync(m, c->st);
   cudaFreeAsync(cvec, c->st);
   cudaFreeAsync(q, c->st);
   cudaFreeAsync(bsum, c->st);
@@ -283,13 +365,31 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host) {
 
 }  // namespace
 
-int seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_host) {
+int seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_host, SeedFirst* first) {
   switch (c->dtype) {
-    case SKM_F32: return seed_t<float>(c, u, rows_host);
-    case SKM_F16: return seed_t<__half>(c, u, rows_host);
-    case SKM_BF16: return seed_t<__nv_bfloat16>(c, u, rows_host);
+    case SKM_F32: return seed_t<float>(c, u, rows_host, first);
+    case SKM_F16: return seed_t<__half>(c, u, rows_host, first);
+    case SKM_BF16: return seed_t<__nv_bfloat16>(c, u, rows_host, first);
   }
   return SKM_EINVAL;
+}
+
+// After the context restarted from the seeded rows: install the first
+// assignment kept by the seeding (labels; l for every variant that keeps
+// it; Hamerly's single u; Elkan's u(i,j) were written during the seeding)
+// and free the seeding's per-row buffers.
+int seed_finish(skm_ctx* c, SeedFirst* first) {
+  const int64_t g = (c->n + 255) / 256, gcap = (int64_t)c->nsm * 16;
+  SKM_PROF_BEGIN(c, "k_seed_finish");
+  k_seed_finish<<<(unsigned)(g < gcap ? g : gcap), 256, 0, c->st>>>(c->n, c->k, first->m, first->best,
+                                                                    first->second, c->dlt, c->a,
+                                                                    first->keep_l ? c->lb : nullptr,
+                                                                    first->keep_u ? c->ub : nullptr, c->cnt);
+  SKM_LAUNCHED(c);
+  cudaFreeAsync(first->m, c->st);
+  cudaFreeAsync(first->best, c->st);
+  cudaFreeAsync(first->second, c->st);
+  return SKM_OK;
 }
 
 }  // namespace skm

@@ -457,7 +457,18 @@ int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* to
 int dense_lower(skm_ctx* c);
 int dense_recheck_cands(skm_ctx* c, bool hamerly);
 int wait_selftest(int64_t timeout_ns, cudaStream_t st);
-int seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_host);
+// The first assignment kept by a seeding (seed_kmeanspp with first != NULL):
+// per row the best similarity, its center and the second best (device
+// buffers the seeding allocates and seed_finish frees); elkan: the seeding
+// also writes Elkan's bounds u(i,j) into the context's array.
+struct SeedFirst {
+  int elkan, keep_l, keep_u;
+  float* m;
+  int32_t* best;
+  float* second;
+};
+int seed_kmeanspp(skm_ctx* c, const double* u, int64_t* rows_host, SeedFirst* first = nullptr);
+int seed_finish(skm_ctx* c, SeedFirst* first);
 int yinyang_step(skm_ctx* c);
 
 }  // namespace skm

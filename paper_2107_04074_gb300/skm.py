@@ -29,7 +29,7 @@ EXPORTS = ["skm_default_options", "skm_init", "skm_reset", "skm_assign", "skm_up
            "skm_get_labels", "skm_get_centers", "skm_set_centers", "skm_set_labels", "skm_get_bounds",
            "skm_get_stats", "skm_bound_bytes", "skm_kernel_launches", "skm_profile", "skm_profile_read",
            "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_topk", "skm_batch_init",
-           "skm_autotune", "skm_selftest_wait", "skm_seed_kmeanspp"]
+           "skm_autotune", "skm_selftest_wait", "skm_seed_kmeanspp", "skm_seed_kmeanspp_assign"]
 
 
 class SkmError(RuntimeError):
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
         "skm_autotune": (ctypes.c_int, [P, ctypes.c_char_p, i32, P]),
         "skm_selftest_wait": (ctypes.c_int, [i64, P]),
         "skm_seed_kmeanspp": (ctypes.c_int, [P, P, P]),
+        "skm_seed_kmeanspp_assign": (ctypes.c_int, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -341,6 +342,18 @@ class KMeans:
         rows = np.empty(self.k, dtype=np.int64)
         _check(load().skm_seed_kmeanspp(self._h, _ptr(u), _ptr(rows)), "skm_seed_kmeanspp")
         return rows
+
+    def seed_kmeanspp_assign(self, u, sync: bool = True):
+        """Seeding plus the first assignment from the seeding's similarities
+        (skm_seed_kmeanspp_assign): returns (rows, labels changed or None)."""
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+        if u.shape != (self.k,):
+            raise ValueError("u must have k entries")
+        rows = np.empty(self.k, dtype=np.int64)
+        out = ctypes.c_int64(0)
+        _check(load().skm_seed_kmeanspp_assign(self._h, _ptr(u), _ptr(rows), ctypes.byref(out) if sync else None),
+               "skm_seed_kmeanspp_assign")
+        return rows, (out.value if sync else None)
 
     def autotune(self, cache_path=None, iters: int = 3) -> bool:
         """Pick the persistent kernels' launch shape (and the Elkan whole-row
