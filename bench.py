@@ -166,6 +166,38 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
+def measured_peaks(skm, torch):
+    """FP32 and FP64 FMA rates from the library's own microbenchmark
+    (skm_measure_peak), and the FP8-E4M3 GEMM rate of cuBLAS through
+    torch._scaled_mm (8192^3, best of 10; None where this PyTorch lacks it)."""
+    out = {"fp32_fma_tflops": round(skm.measure_peak("fp32"), 1),
+           "fp64_fma_tflops": round(skm.measure_peak("fp64"), 2)}
+    try:
+        N = 8192
+        a = torch.randn(N, N, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(N, N, device="cuda").to(torch.float8_e4m3fn).t()  # column-major operand
+        one = torch.tensor(1.0, device="cuda")
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        best = None
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out["fp8_gemm_tflops"] = round(2.0 * N ** 3 / (best / 1e3) / 1e12, 1)
+        del a, b
+    except Exception as ex:  # noqa: BLE001
+        out["fp8_gemm_tflops"] = None
+        out["fp8_note"] = f"{type(ex).__name__}: {ex}"[:160]
+    out["how"] = ("fp32/fp64: skm_measure_peak (independent FMA chains on every SM, CUDA events); "
+                  "fp8: torch._scaled_mm E4M3 8192^3 -> BF16, best of 10")
+    return out
+
+
 def kernel_bytes(name, it_rows, n, d, k, nnz, variant, full_sum=True, u_width=4):
     """Compulsory (algorithmic) bytes of one launch: what any implementation
     must move between HBM and the SMs for that step, given the rows it treats.
@@ -278,8 +310,9 @@ def run_ours(args, rank, world, local):
     # value), iteration by iteration so that each launch's rows are known
     flush.fill_(1.0)
     km.reset(init)
-    prof_ms, prof_n, prof_bytes, prof_gather = {}, {}, {}, {}
+    prof_ms, prof_n, prof_bytes, prof_gather, prof_flops = {}, {}, {}, {}, {}
     u_width = elk_u_width(skm, n, k)
+    peaks_meas = measured_peaks(skm, torch)
     upd = {"full": [0.0, 0], "incremental": [0.0, 0]}  # center update: ms, count
     for it in range(MAX_ITERS):
         km.profile(True)
@@ -306,6 +339,8 @@ def run_ours(args, rank, world, local):
             gb = gather_bytes(nm, rows_of.get(nm, n), n, k, nnz)
             if gb is not None:
                 prof_gather[nm] = prof_gather.get(nm, 0) + gb * cnt_k
+                # the similarity FMAs of a whole-row launch: 2 per entry and center
+                prof_flops[nm] = prof_flops.get(nm, 0) + 2 * rows_of.get(nm, n) * (nnz / n) * k * cnt_k
         if ch == 0:
             break
     km.close()
@@ -364,6 +399,13 @@ def run_ours(args, rank, world, local):
                 "traffic": recorded_traffic(top_name, "rcv1-like-k100"),
                 "avg_launch_us": round(avg_s * 1e6, 2), "launches": prof_n[top_name],
                 "algorithmic_bytes_per_launch": int(ab)}
+        if top_name in prof_flops and peaks_meas.get("fp32_fma_tflops"):
+            fpl = prof_flops[top_name] / prof_n[top_name]
+            ach_f = fpl / avg_s / 1e12
+            roof["fma_view"] = {"achieved": round(ach_f, 2), "peak": peaks_meas["fp32_fma_tflops"],
+                                "unit": "TFLOP/s", "frac": round(ach_f / peaks_meas["fp32_fma_tflops"], 4),
+                                "peak_source": "measured (skm_measure_peak FP32 FMA)",
+                                "flops_per_launch": int(fpl)}
         if top_name in prof_gather:
             gpl = prof_gather[top_name] / prof_n[top_name]
             roof["gathered_bytes_per_launch"] = int(gpl)
@@ -425,6 +467,7 @@ def run_ours(args, rank, world, local):
         "clocks": clocks,
         "roofline": roof,
         "kernel_time_share": kernel_share,
+        "measured_peaks": peaks_meas,
         "center_update": center_update,
         "kmeanspp_seeding": {"ms": seed_ms, "k": k, "rows": n, "variants": seeding,
                              "note": "host-timed, synchronised, best of 3: skm_seed_kmeanspp alone; followed by "
@@ -465,6 +508,7 @@ def summarize_embed(args, rank, world, local):
             "speedup_fp8_vs_fp32_standard": r["speedup_fp8_vs_fp32_standard"],
             "roofline": r["bf16_gemm_roofline"],
             "fp8_roofline": r["fp8_gemm_roofline"],
+            "fp32_roofline": r["fp32_gemm_roofline"],
             "ambiguous_fraction_first_last": {kk: [v["ambiguous_fraction_per_iter"][0],
                                                    v["ambiguous_fraction_per_iter"][-1]]
                                               for kk, v in p.items() if "ambiguous_fraction_per_iter" in v},
@@ -627,6 +671,9 @@ def run_embed(args, rank, world, local):
                  "rows_whole_row_recheck_per_iter": rech,
                  "rows_candidate_recheck_per_iter": cand,
                  "kernels_ms": {nm: round(v[0], 3) for nm, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+        if "k_dense_top2" in prof and prec == "fp32" and variant == "standard":
+            t_ms, c = prof["k_dense_top2"]
+            entry["fp32_gemm_tflops"] = round(2.0 * n * k * d / (t_ms / c / 1e3) / 1e12, 1)
         for kn, tag in (("k_bf16_topk", "bf16"), ("k_fp8_topk", "fp8")):
             if kn in prof:
                 t_ms, c = prof[kn]
@@ -646,21 +693,31 @@ def run_embed(args, rank, world, local):
         peak = 1900.0
     g = res["standard/bf16"]
     traffic = recorded_traffic("k_bf16_topk", "vmf-n1e6-d384-k1000") if n == 1_000_000 else None
+    pk = measured_peaks(skm, torch)
+    fp32_peak = pk["fp32_fma_tflops"]
+    if pk.get("fp8_gemm_tflops"):
+        fp8_peak, fp8_src = pk["fp8_gemm_tflops"], "measured (cuBLAS E4M3 GEMM via torch._scaled_mm, burst)"
+    else:
+        fp8_peak, fp8_src = 2 * peak, "2 x the measured BF16 burst peak (nominal FP8:BF16 ratio)"
+    f32 = res["standard/fp32"].get("fp32_gemm_tflops")
+    fp32_roof = {"kernel": "k_dense_top2", "bound": "alu", "achieved": f32, "peak": round(fp32_peak, 1),
+                 "unit": "TFLOP/s", "frac": round(f32 / fp32_peak, 4) if f32 else None,
+                 "peak_source": "measured (skm_measure_peak FP32 FMA)", "flops_per_launch": 2 * n * k * d}
     errors = {}
     if not args.no_oracle_check:
         for prec in ("bf16", "fp8", "fp32"):
             errors[prec] = embed_error_vs_oracle(skm, X, Xs, k, init, iters, prec)
     return {"workload": f"vmf-embeddings n={n} d={d} k={k} kappa=40 ({iters} iterations max)",
-            "labels_identical_across_paths": same, "paths": res,
+            "labels_identical_across_paths": same, "paths": res, "measured_peaks": pk,
             "speedup_bf16_vs_fp32_standard": round(g["iters_per_s"] / res["standard/fp32"]["iters_per_s"], 2),
             "speedup_fp8_vs_fp32_standard": round(res["standard/fp8"]["iters_per_s"] /
                                                   res["standard/fp32"]["iters_per_s"], 2),
             "error_vs_fp64_oracle": errors,
+            "fp32_gemm_roofline": fp32_roof,
             "fp8_gemm_roofline": {"kernel": "k_fp8_topk", "bound": "tensor",
-                                  "achieved": res["standard/fp8"].get("fp8_gemm_tflops"), "peak": 2 * peak,
-                                  "unit": "TFLOP/s",
-                                  "peak_source": "2 x the measured BF16 burst peak (nominal FP8:BF16 ratio)",
-                                  "frac": round(res["standard/fp8"].get("fp8_gemm_tflops", 0) / (2 * peak), 4),
+                                  "achieved": res["standard/fp8"].get("fp8_gemm_tflops"), "peak": fp8_peak,
+                                  "unit": "TFLOP/s", "peak_source": fp8_src,
+                                  "frac": round(res["standard/fp8"].get("fp8_gemm_tflops", 0) / fp8_peak, 4),
                                   "traffic": None, "flops_per_launch": 2 * n * k * d},
             "bf16_gemm_roofline": {"kernel": "k_bf16_topk", "bound": "tensor", "achieved": g.get("bf16_gemm_tflops"),
                                    "peak": peak, "unit": "TFLOP/s", "peak_source": "measured (burst)",

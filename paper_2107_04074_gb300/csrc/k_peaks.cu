@@ -1,0 +1,73 @@
+// Peak arithmetic rates of this GPU, measured rather than quoted: the FP32
+// and FP64 FMA roofs that the SIMT kernels of this library (the sparse
+// similarity gathers, the FP32 dense GEMM, the FP64 drift sums) are reported
+// against.  The paper has no counterpart; this is measurement support.
+//
+// Each thread runs 8 independent FMA chains (enough independent work to
+// cover the pipeline latency with 8 warps per scheduler), the grid fills
+// every SM 8 times over, and the chains' results are folded into one store
+// so that none of the work can be dropped.  Time = CUDA events around one
+// launch after a warm-up launch; rate = 2 FLOP per FMA.
+#include "skm_internal.cuh"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kUnroll = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_peak_fma(int iters, T b, T c, T* __restrict__ out) {
+  T a[kChains];
+#pragma unroll
+  for (int q = 0; q < kChains; ++q) a[q] = (T)(threadIdx.x + q) * (T)1e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+      for (int q = 0; q < kChains; ++q) a[q] = fma(a[q], b, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int q = 0; q < kChains; ++q) s += a[q];
+  if (s == (T)-1.2345) out[blockIdx.x] = s;  // never true for these inputs; keeps the chains live
+}
+
+template <typename T>
+int measure(int iters, double* tflops, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  SKM_CUDA_TRY(cudaGetDevice(&dev));
+  SKM_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  T* out = nullptr;
+  const unsigned grid = (unsigned)nsm * 8;
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&out, sizeof(T) * grid, st));
+  cudaEvent_t e0, e1;
+  SKM_CUDA_TRY(cudaEventCreate(&e0));
+  SKM_CUDA_TRY(cudaEventCreate(&e1));
+  const T b = (T)0.999999, c = (T)1e-7;
+  k_peak_fma<T><<<grid, 256, 0, st>>>(iters, b, c, out);  // warm-up
+  skm::note_launch();
+  SKM_CUDA_TRY(cudaEventRecord(e0, st));
+  k_peak_fma<T><<<grid, 256, 0, st>>>(iters, b, c, out);
+  skm::note_launch();
+  SKM_CUDA_TRY(cudaEventRecord(e1, st));
+  SKM_CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SKM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SKM_CUDA_TRY(cudaFreeAsync(out, st));
+  SKM_CUDA_TRY(cudaStreamSynchronize(st));
+  const double fmas = (double)grid * 256.0 * (double)iters * kUnroll * kChains;
+  *tflops = 2.0 * fmas / ((double)ms * 1e-3) / 1e12;
+  return SKM_OK;
+}
+
+}  // namespace
+
+extern "C" int skm_measure_peak(int32_t kind, double* tflops, void* stream) {
+  if (!tflops) return SKM_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (kind == SKM_PEAK_FP32_FMA) return measure<float>(4096, tflops, st);
+  if (kind == SKM_PEAK_FP64_FMA) return measure<double>(256, tflops, st);
+  return SKM_EINVAL;
+}

@@ -29,7 +29,7 @@ EXPORTS = ["skm_default_options", "skm_init", "skm_reset", "skm_assign", "skm_up
            "skm_get_labels", "skm_get_centers", "skm_set_centers", "skm_set_labels", "skm_get_bounds",
            "skm_get_stats", "skm_bound_bytes", "skm_kernel_launches", "skm_profile", "skm_profile_read",
            "skm_destroy", "skm_strerror", "skm_assign_noalloc", "skm_get_bf16_topk", "skm_batch_init",
-           "skm_autotune", "skm_selftest_wait", "skm_seed_kmeanspp", "skm_seed_kmeanspp_assign"]
+           "skm_autotune", "skm_selftest_wait", "skm_seed_kmeanspp", "skm_seed_kmeanspp_assign", "skm_measure_peak"]
 
 
 class SkmError(RuntimeError):
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         "skm_selftest_wait": (ctypes.c_int, [i64, P]),
         "skm_seed_kmeanspp": (ctypes.c_int, [P, P, P]),
         "skm_seed_kmeanspp_assign": (ctypes.c_int, [P, P, P, P]),
+        "skm_measure_peak": (ctypes.c_int, [i32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -126,6 +127,18 @@ def _check(code: int, what: str):
 def selftest_wait(timeout_ns: int, stream=None) -> int:
     """Status of a device wait on a barrier nothing completes (SKM_ETIMEOUT expected)."""
     return int(load().skm_selftest_wait(int(timeout_ns), ctypes.c_void_p(stream or 0)))
+
+
+PEAK_FP32_FMA, PEAK_FP64_FMA = 0, 1
+
+
+def measure_peak(kind: str, stream=None) -> float:
+    """Measured FMA rate of the current GPU in TFLOP/s (skm_measure_peak):
+    kind "fp32" or "fp64"."""
+    out = ctypes.c_double(0)
+    code = {"fp32": PEAK_FP32_FMA, "fp64": PEAK_FP64_FMA}[kind]
+    _check(load().skm_measure_peak(code, ctypes.byref(out), ctypes.c_void_p(stream or 0)), "skm_measure_peak")
+    return out.value
 
 
 def kernel_launches() -> int:

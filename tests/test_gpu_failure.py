@@ -40,3 +40,4 @@ def test_wait_times_out_and_context_survives(limit_ms):
 def test_wait_selftest_rejects_bad_limits():
     assert skm.selftest_wait(0) == skm.EINVAL
     assert skm.selftest_wait(3_000_000_000) == skm.EINVAL
+
