@@ -123,7 +123,15 @@ typedef struct {
   int32_t blocks_per_sm;   /* grid of the persistent bound/recompute kernels:
                               at most this many blocks per SM (0 = as many
                               as are resident at once); skm_autotune sets it */
-  int32_t reserved[5];
+  int32_t fused_update;    /* 0 (default): the center update's phases after
+                              the sums (dirty list, norms, normalisation,
+                              drift, objective) run as separate kernels; 1:
+                              as one cooperative launch whose blocks wait on
+                              one another at bounded grid barriers (a wait
+                              that gives up after 1 s makes the next
+                              skm_assign return SKM_ETIMEOUT; destroy the
+                              context then).  Results are bit-identical. */
+  int32_t reserved[4];
 } skm_options;
 
 /* Counters of the last assignment and of the run so far. */
@@ -276,11 +284,13 @@ int skm_seed_kmeanspp(skm_ctx* ctx, const double* u, int64_t* rows_out);
  * and for Yin-Yang bounds; u and rows_out as skm_seed_kmeanspp. */
 int skm_seed_kmeanspp_assign(skm_ctx* ctx, const double* u, int64_t* rows_out, int64_t* n_changed);
 
-/* Self-test of the failure path of every device-side wait (the tensor-core
- * kernel's barrier waits): launches one warp that waits on a barrier nothing
- * completes, with the given limit (1 ns .. 2 s).  Returns SKM_ETIMEOUT when
- * the wait gave up as it must (the GPU context stays usable), SKM_OK if the
- * wait completed (a defect), SKM_ECUDA on a CUDA error. */
+/* Self-test of the failure path of every device-side wait: the tensor-core
+ * kernel's barrier waits (one warp waits on an mbarrier nothing completes)
+ * and the grid barrier of the fused center update (a cooperative launch of
+ * two blocks, one of which never arrives), each with the given limit
+ * (1 ns .. 2 s).  Returns SKM_ETIMEOUT when both waits gave up as they must
+ * (the GPU context stays usable), SKM_OK if one completed (a defect),
+ * SKM_ECUDA on a CUDA error. */
 int skm_selftest_wait(int64_t timeout_ns, void* stream);
 
 /* Bytes of bound state a variant keeps for n points and k centers (labels

@@ -199,7 +199,7 @@ void release(skm_ctx* c) {
                   c->ub,     c->w1,      c->w2,    c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark,
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
                   c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n,
-                  c->exr,    c->ebc,     c->ebw,   c->rsc,    c->gdbeg,  c->gdcnt,  c->gtask};
+                  c->exr,    c->ebc,     c->ebw,   c->rsc,    c->gdbeg,  c->gdcnt,  c->gtask,  c->fbar};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -273,6 +273,8 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   // ---- counters and per-row data
   TRY(dalloc(c, &c->cnt, C_NUM));
   SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_NUM, c->st));
+  TRY(dalloc(c, &c->fbar, 2));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->fbar, 0, sizeof(unsigned long long) * 2, c->st));
   SKM_CUDA_TRY(cudaMallocHost((void**)&c->hcnt, sizeof(unsigned long long) * C_NUM));
   SKM_CUDA_TRY(cudaMallocHost((void**)&c->hobj, sizeof(double)));
   TRY(dalloc(c, &c->rinv, (size_t)n));
@@ -1092,7 +1094,12 @@ int skm_seed_kmeanspp_assign(skm_ctx* c, const double* u, int64_t* rows_out, int
 
 int skm_selftest_wait(int64_t timeout_ns, void* stream) {
   if (timeout_ns < 1 || timeout_ns > 2000000000ll) return SKM_EINVAL;
-  return wait_selftest(timeout_ns, (cudaStream_t)stream);
+  const int a = wait_selftest(timeout_ns, (cudaStream_t)stream);
+  if (a != SKM_OK && a != SKM_ETIMEOUT) return a;
+  const int b = barrier_selftest(timeout_ns, (cudaStream_t)stream);
+  if (b != SKM_OK && b != SKM_ETIMEOUT) return b;
+  // both waits must have given up
+  return (a == SKM_ETIMEOUT && b == SKM_ETIMEOUT) ? SKM_ETIMEOUT : SKM_OK;
 }
 
 void skm_destroy(skm_ctx* c) { release(c); }

@@ -208,18 +208,23 @@ __global__ void __launch_bounds__(256) k_center_delta(const int64_t* __restrict_
   }
 }
 
+// ------------------------------------------------------------------
+// The phases after the sums.  Each is a device routine so that the separate
+// kernels below and the fused cooperative kernel (k_finish_fused) run the
+// same arithmetic in the same order: their results are bit-identical.  Data
+// that another block may have written earlier in the fused launch is read
+// with __ldcg (from L2, past this SM's L1).
+
 // One block: the list of dirty clusters in ascending order (all clusters
 // after a full recompute), dmark[j] / dpos[j] for lookups, flags cleared.
-__global__ void __launch_bounds__(1024) k_dirty(int32_t k, int32_t* __restrict__ dflag, int32_t* __restrict__ dmark,
-                                                int32_t* __restrict__ dpos, int32_t* __restrict__ dlist,
-                                                unsigned long long* __restrict__ cnt, int s64_valid, int64_t n) {
-  __shared__ int wsum[32];
-  __shared__ int base;
-  const bool full = full_update(s64_valid, cnt, n);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) base = 0;
+// wsum: shared, one int per warp of the block.
+__device__ __forceinline__ void dev_dirty(int32_t k, int32_t* __restrict__ dflag, int32_t* __restrict__ dmark,
+                                          int32_t* __restrict__ dpos, int32_t* __restrict__ dlist,
+                                          unsigned long long* __restrict__ cnt, bool full, int* wsum, int* base) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (threadIdx.x == 0) *base = 0;
   __syncthreads();
-  for (int j0 = 0; j0 < k; j0 += 1024) {
+  for (int j0 = 0; j0 < k; j0 += blockDim.x) {
     const int j = j0 + threadIdx.x;
     const bool d = (j < k) && (full || dflag[j] != 0);
     const unsigned ball = __ballot_sync(SKM_FULL_MASK, d);
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(1024) k_dirty(int32_t k, int32_t* __restrict__
     __syncthreads();
     int before = 0;
     for (int w = 0; w < wid; ++w) before += wsum[w];
-    const int pos = base + before + __popc(ball & ((1u << lane) - 1u));
+    const int pos = *base + before + __popc(ball & ((1u << lane) - 1u));
     if (j < k) {
       dmark[j] = d ? 1 : 0;
       dpos[j] = d ? pos : -1;
@@ -237,30 +242,37 @@ __global__ void __launch_bounds__(1024) k_dirty(int32_t k, int32_t* __restrict__
     __syncthreads();
     if (threadIdx.x == 0) {
       int tot = 0;
-      for (int w = 0; w < 32; ++w) tot += wsum[w];
-      base += tot;
+      for (int w = 0; w < nwarp; ++w) tot += wsum[w];
+      *base += tot;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) cnt[C_NDIRTY] = (unsigned long long)base;
+  if (threadIdx.x == 0) cnt[C_NDIRTY] = (unsigned long long)*base;
 }
 
-// grid (ceil(d/kTB), ceil(k/32)), block (32, 8): thread (x, y) handles dirty
-// slot 32 blockIdx.y + x and terms t = y, y+8, ... of the block's range.
-// Squares summed in FP32 with a compensation term (Neumaier), accurate to
-// ~2u per thread; threads and blocks combine in FP64.
-__global__ void k_colnorm_part(const long long* __restrict__ S64, float inv, int64_t d, int64_t kst,
-                               const int32_t* __restrict__ dlist, const unsigned long long* __restrict__ cnt,
-                               double* __restrict__ red) {
-  __shared__ double sh[8][33];
-  const int nd = (int)cnt[C_NDIRTY];
-  const int slot = blockIdx.y * 32 + threadIdx.x;
-  if ((int)(blockIdx.y * 32) >= nd) return;
-  const int64_t t0 = (int64_t)blockIdx.x * kTB;
+__global__ void __launch_bounds__(1024) k_dirty(int32_t k, int32_t* __restrict__ dflag, int32_t* __restrict__ dmark,
+                                                int32_t* __restrict__ dpos, int32_t* __restrict__ dlist,
+                                                unsigned long long* __restrict__ cnt, int s64_valid, int64_t n) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  dev_dirty(k, dflag, dmark, dpos, dlist, cnt, full_update(s64_valid, cnt, n), wsum, &base);
+}
+
+// Tile (bx, by) of 256 terms x 32 dirty slots, threads (x, y) = (tid & 31,
+// tid >> 5) of 256: thread (x, y) handles dirty slot 32 by + x and terms
+// t = y, y+8, ... of the tile.  Squares summed in FP32 with a compensation
+// term (Neumaier), accurate to ~2u per thread; threads and tiles combine in
+// FP64.  sh: shared double[8][33].
+__device__ __forceinline__ void dev_colnorm_part(const long long* __restrict__ S64, float inv, int64_t d, int64_t kst,
+                                                 const int32_t* __restrict__ dlist, int nd, double* __restrict__ red,
+                                                 int bx, int by, double (*sh)[33]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int slot = by * 32 + tx;
+  const int64_t t0 = (int64_t)bx * kTB;
   float s = 0.f, comp = 0.f;
   if (slot < nd) {
-    const int j = dlist[slot];
-    for (int64_t t = t0 + threadIdx.y; t < min(d, t0 + kTB); t += 8) {
+    const int j = __ldcg(dlist + slot);
+    for (int64_t t = t0 + ty; t < min(d, t0 + kTB); t += 8) {
       const float v = from_fixed(S64[t * kst + j], inv);
       const float sq = __fmul_rn(v, v);
       const float err_sq = __fmaf_rn(v, v, -sq);  // exact low part of v*v
@@ -270,54 +282,75 @@ __global__ void k_colnorm_part(const long long* __restrict__ S64, float inv, int
       s = ns;
     }
   }
-  sh[threadIdx.y][threadIdx.x] = (double)s + (double)comp;
+  sh[ty][tx] = (double)s + (double)comp;
   __syncthreads();
-  if (threadIdx.y == 0 && slot < nd) {
+  if (ty == 0 && slot < nd) {
     double r = 0.0;
-    for (int y = 0; y < 8; ++y) r += sh[y][threadIdx.x];
-    red[(int64_t)blockIdx.x * kst + slot] = r;
+    for (int y = 0; y < 8; ++y) r += sh[y][tx];
+    red[(int64_t)bx * kst + slot] = r;
   }
+  __syncthreads();
 }
 
-// Block per dirty slot: |S_j| from the per-block partials in a fixed order.
-__global__ void __launch_bounds__(128) k_colnorm_final(const double* __restrict__ red, int64_t nblk, int64_t kst,
-                                                       const int32_t* __restrict__ dlist,
-                                                       const unsigned long long* __restrict__ cnt,
-                                                       double* __restrict__ nrm) {
-  __shared__ double sh[128];
-  const int slot = blockIdx.x;
-  if (slot >= (int)cnt[C_NDIRTY]) return;
+// grid (ceil(d/kTB), ceil(k/32)), block 256.
+__global__ void __launch_bounds__(256) k_colnorm_part(const long long* __restrict__ S64, float inv, int64_t d,
+                                                      int64_t kst, const int32_t* __restrict__ dlist,
+                                                      const unsigned long long* __restrict__ cnt,
+                                                      double* __restrict__ red) {
+  __shared__ double sh[8][33];
+  const int nd = (int)cnt[C_NDIRTY];
+  if ((int)(blockIdx.y * 32) >= nd) return;
+  dev_colnorm_part(S64, inv, d, kst, dlist, nd, red, blockIdx.x, blockIdx.y, sh);
+}
+
+// Dirty slot `slot`: |S_j| from the per-tile partials in a fixed order, by
+// the block's first 128 threads.  sh: shared double[128].
+__device__ __forceinline__ void dev_colnorm_final(const double* __restrict__ red, int64_t nblk, int64_t kst,
+                                                  const int32_t* __restrict__ dlist, int slot,
+                                                  double* __restrict__ nrm, double* sh) {
+  const bool on = threadIdx.x < 128;
   double s = 0.0;
-  for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) s += red[b * kst + slot];
-  sh[threadIdx.x] = s;
+  if (on)
+    for (int64_t b = threadIdx.x; b < nblk; b += 128) s += __ldcg(red + b * kst + slot);
+  if (on) sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = 64; o; o >>= 1) {
     if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) nrm[dlist[slot]] = sqrt(sh[0]);
+  if (threadIdx.x == 0) nrm[__ldcg(dlist + slot)] = sqrt(sh[0]);
+  __syncthreads();
 }
 
-// grid (ceil(d/kTB), ceil(k/32)), block (32, 8), dirty slots as above.  The
-// dirty centers are overwritten in place; red2 receives per block and slot
-// sum c^2, sum c'^2 and sum (c - c')^2 (FP32 per thread over 32 terms --
-// relative error <= 36u, covered by the slack of k_drift_final).
-__global__ void k_normalize_drift(const long long* __restrict__ S64, float inv, float* __restrict__ Ct,
-                                  const double* __restrict__ nrm, int64_t d, int64_t kst,
-                                  const int32_t* __restrict__ dlist, const unsigned long long* __restrict__ cnt,
-                                  double* __restrict__ red2) {
-  __shared__ double sh[3][8][33];
-  const int nd = (int)cnt[C_NDIRTY];
-  const int slot = blockIdx.y * 32 + threadIdx.x;
-  if ((int)(blockIdx.y * 32) >= nd) return;
-  const int64_t t0 = (int64_t)blockIdx.x * kTB;
+// Block per dirty slot.
+__global__ void __launch_bounds__(128) k_colnorm_final(const double* __restrict__ red, int64_t nblk, int64_t kst,
+                                                       const int32_t* __restrict__ dlist,
+                                                       const unsigned long long* __restrict__ cnt,
+                                                       double* __restrict__ nrm) {
+  __shared__ double sh[128];
+  if ((int)blockIdx.x >= (int)cnt[C_NDIRTY]) return;
+  dev_colnorm_final(red, nblk, kst, dlist, blockIdx.x, nrm, sh);
+}
+
+// Tile (bx, by), threads as dev_colnorm_part.  The dirty centers are
+// overwritten in place; red2 receives per tile and slot sum c^2, sum c'^2 and
+// sum (c - c')^2 (FP32 per thread over 32 terms -- relative error <= 36u,
+// covered by the slack of dev_drift_final).  sh: shared double[3][8][33].
+__device__ __forceinline__ void dev_normalize_drift(const long long* __restrict__ S64, float inv,
+                                                    float* __restrict__ Ct, const double* __restrict__ nrm,
+                                                    int64_t d, int64_t kst, const int32_t* __restrict__ dlist,
+                                                    int nd, double* __restrict__ red2, int bx, int by,
+                                                    double (*sh)[8][33]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int slot = by * 32 + tx;
+  const int64_t t0 = (int64_t)bx * kTB;
   float sn = 0.f, so = 0.f, sd = 0.f;
   if (slot < nd) {
-    const int j = dlist[slot];
-    const double nr = nrm[j];
+    const int j = __ldcg(dlist + slot);
+    const double nr = __ldcg(nrm + j);
     const bool empty = !(nr > 0.0);
     const float rn = empty ? 0.f : (float)(1.0 / nr);
-    for (int64_t t = t0 + threadIdx.y; t < min(d, t0 + kTB); t += 8) {
+    for (int64_t t = t0 + ty; t < min(d, t0 + kTB); t += 8) {
       float* cp = Ct + t * kst + j;
       const float co = *cp;
       const float cn = empty ? co : __fmul_rn(from_fixed(S64[t * kst + j], inv), rn);
@@ -328,56 +361,72 @@ __global__ void k_normalize_drift(const long long* __restrict__ S64, float inv, 
       sd = __fmaf_rn(df, df, sd);
     }
   }
-  sh[0][threadIdx.y][threadIdx.x] = sn;
-  sh[1][threadIdx.y][threadIdx.x] = so;
-  sh[2][threadIdx.y][threadIdx.x] = sd;
+  sh[0][ty][tx] = sn;
+  sh[1][ty][tx] = so;
+  sh[2][ty][tx] = sd;
   __syncthreads();
-  if (threadIdx.y == 0 && slot < nd) {
+  if (ty == 0 && slot < nd) {
     double r0 = 0.0, r1 = 0.0, r2 = 0.0;
     for (int y = 0; y < 8; ++y) {
-      r0 += sh[0][y][threadIdx.x];
-      r1 += sh[1][y][threadIdx.x];
-      r2 += sh[2][y][threadIdx.x];
+      r0 += sh[0][y][tx];
+      r1 += sh[1][y][tx];
+      r2 += sh[2][y][tx];
     }
-    double* o = red2 + ((int64_t)blockIdx.x * kst + slot) * 3;
+    double* o = red2 + ((int64_t)bx * kst + slot) * 3;
     o[0] = r0;
     o[1] = r1;
     o[2] = r2;
   }
+  __syncthreads();
 }
 
-// Block per center (grid kst).  Clean centers did not move: p = 1, sine 0.
-// Dirty ones: from N = |c|, N' = |c'| and D = |c - c'|^2 (relative error <= e,
-// e = 40u + d 2^-53):  1 - cos = (D - (N - N')^2) / (2 N N'), hence
+__global__ void __launch_bounds__(256) k_normalize_drift(const long long* __restrict__ S64, float inv,
+                                                         float* __restrict__ Ct, const double* __restrict__ nrm,
+                                                         int64_t d, int64_t kst, const int32_t* __restrict__ dlist,
+                                                         const unsigned long long* __restrict__ cnt,
+                                                         double* __restrict__ red2) {
+  __shared__ double sh[3][8][33];
+  const int nd = (int)cnt[C_NDIRTY];
+  if ((int)(blockIdx.y * 32) >= nd) return;
+  dev_normalize_drift(S64, inv, Ct, nrm, d, kst, dlist, nd, red2, blockIdx.x, blockIdx.y, sh);
+}
+
+// Center j (the block's first 128 threads).  Clean centers did not move:
+// p = 1, sine 0.  Dirty ones: from N = |c|, N' = |c'| and D = |c - c'|^2
+// (relative error <= e, e = 40u + d 2^-53):  1 - cos = (D - (N - N')^2) /
+// (2 N N'), hence
 //   q_up = D (1+4e) / (2 N N')                           >= 1 - cos
 //   q_dn = (D (1-e) - (|N-N'| + e)^2) / (2 N N' (1+3e))  <= 1 - cos
 // pd = rd(1 - q_up), pu = ru(1 - q_dn), q = ru(max sin over [q_dn, q_up]).
-__global__ void __launch_bounds__(128) k_drift_final(const double* __restrict__ red2, int64_t nblk, int32_t k,
-                                                     int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
-                                                     const int32_t* __restrict__ dpos, float* __restrict__ pdn,
-                                                     float* __restrict__ pup, float* __restrict__ qup,
-                                                     double* __restrict__ cnorm) {
-  __shared__ double sh[3][128];
-  const int j = blockIdx.x;
-  if (j >= k || !dmark[j]) {
+// sh: shared double[3][128].
+__device__ __forceinline__ void dev_drift_final(const double* __restrict__ red2, int64_t nblk, int32_t k,
+                                                int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
+                                                const int32_t* __restrict__ dpos, float* __restrict__ pdn,
+                                                float* __restrict__ pup, float* __restrict__ qup,
+                                                double* __restrict__ cnorm, int j, double (*sh)[128]) {
+  if (j >= k || !__ldcg(dmark + j)) {
     if (threadIdx.x == 0) {
       pdn[j] = 1.f;
       pup[j] = 1.f;
       qup[j] = 0.f;
     }
-    return;
+    return;  // the same for the whole block
   }
-  const int slot = dpos[j];
+  const bool on = threadIdx.x < 128;
+  const int slot = __ldcg(dpos + j);
   double sn = 0.0, so = 0.0, sd = 0.0;
-  for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) {
-    const double* r = red2 + (b * kst + slot) * 3;
-    sn += r[0];
-    so += r[1];
-    sd += r[2];
+  if (on)
+    for (int64_t b = threadIdx.x; b < nblk; b += 128) {
+      const double* r = red2 + (b * kst + slot) * 3;
+      sn += __ldcg(r);
+      so += __ldcg(r + 1);
+      sd += __ldcg(r + 2);
+    }
+  if (on) {
+    sh[0][threadIdx.x] = sn;
+    sh[1][threadIdx.x] = so;
+    sh[2][threadIdx.x] = sd;
   }
-  sh[0][threadIdx.x] = sn;
-  sh[1][threadIdx.x] = so;
-  sh[2][threadIdx.x] = sd;
   __syncthreads();
   for (int o = 64; o; o >>= 1) {
     if ((int)threadIdx.x < o) {
@@ -387,111 +436,323 @@ __global__ void __launch_bounds__(128) k_drift_final(const double* __restrict__ 
     }
     __syncthreads();
   }
-  if (threadIdx.x != 0) return;
-  sn = sh[0][0];
-  so = sh[1][0];
-  sd = sh[2][0];
-  const double e = 40.0 * 0x1.0p-24 + ((double)d + 8.0) * 0x1.0p-53;
-  const double N = sqrt(sn), No = sqrt(so);
-  cnorm[j] = N;
-  float pd, pu, q;
-  if (sd == 0.0) {
-    pd = 1.f;
-    pu = 1.f;
-    q = 0.f;
-  } else {
-    const double den = 2.0 * N * No;
-    const double qu = sd * (1.0 + 4.0 * e) / den;
-    const double dn = fabs(N - No) + e;
-    double qd = (sd * (1.0 - e) - dn * dn) / (den * (1.0 + 3.0 * e));
-    if (qd < 0.0) qd = 0.0;
-    double lo = 1.0 - qu, hi = 1.0 - qd;
-    lo = lo < -1.0 ? -1.0 : lo;
-    hi = hi > 1.0 ? 1.0 : hi;
-    pd = fmaxf(__double2float_rd(lo - 0x1.0p-60), -1.f);
-    pu = fminf(__double2float_ru(hi + 0x1.0p-60), 1.f);
-    double smax;
-    if (qd <= 1.0 && qu >= 1.0) smax = 1.0;
-    else if (qu < 1.0) smax = sqrt(qu * (2.0 - qu));
-    else smax = sqrt(qd * (2.0 - qd));
-    q = fminf(__double2float_ru(smax * (1.0 + 4.0 * e) + 0x1.0p-60), 1.f);
+  if (threadIdx.x == 0) {
+    sn = sh[0][0];
+    so = sh[1][0];
+    sd = sh[2][0];
+    const double e = 40.0 * 0x1.0p-24 + ((double)d + 8.0) * 0x1.0p-53;
+    const double N = sqrt(sn), No = sqrt(so);
+    cnorm[j] = N;
+    float pd, pu, q;
+    if (sd == 0.0) {
+      pd = 1.f;
+      pu = 1.f;
+      q = 0.f;
+    } else {
+      const double den = 2.0 * N * No;
+      const double qu = sd * (1.0 + 4.0 * e) / den;
+      const double dn = fabs(N - No) + e;
+      double qd = (sd * (1.0 - e) - dn * dn) / (den * (1.0 + 3.0 * e));
+      if (qd < 0.0) qd = 0.0;
+      double lo = 1.0 - qu, hi = 1.0 - qd;
+      lo = lo < -1.0 ? -1.0 : lo;
+      hi = hi > 1.0 ? 1.0 : hi;
+      pd = fmaxf(__double2float_rd(lo - 0x1.0p-60), -1.f);
+      pu = fminf(__double2float_ru(hi + 0x1.0p-60), 1.f);
+      double smax;
+      if (qd <= 1.0 && qu >= 1.0) smax = 1.0;
+      else if (qu < 1.0) smax = sqrt(qu * (2.0 - qu));
+      else smax = sqrt(qd * (2.0 - qd));
+      q = fminf(__double2float_ru(smax * (1.0 + 4.0 * e) + 0x1.0p-60), 1.f);
+    }
+    pdn[j] = pd;
+    pup[j] = pu;
+    qup[j] = q;
   }
-  pdn[j] = pd;
-  pup[j] = pu;
-  qup[j] = q;
+  __syncthreads();
 }
+
+// Block per center (grid kst).
+__global__ void __launch_bounds__(128) k_drift_final(const double* __restrict__ red2, int64_t nblk, int32_t k,
+                                                     int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
+                                                     const int32_t* __restrict__ dpos, float* __restrict__ pdn,
+                                                     float* __restrict__ pup, float* __restrict__ qup,
+                                                     double* __restrict__ cnorm) {
+  __shared__ double sh[3][128];
+  dev_drift_final(red2, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, blockIdx.x, sh);
+}
+
+// Shared memory of dev_hsel_obj: 1024 slots per quantity (a block of fewer
+// threads takes several slots per thread, so the sums run in the order of a
+// 1024-thread block whatever the block size).
+struct HselShared {
+  float pd[1024], pu[1024], q[1024], pd2[1024], pu2[1024], q2[1024];
+  int jd[1024], ju[1024], jq[1024];
+  double J[1024];
+};
 
 // One block: the objective J = sum_j |S_j| (fixed order) and Hamerly's
 // worst-drift summary -- argmin / min / second min of pd and of pu, argmax /
 // max / second max of q, lowest index on ties (Section 5.3: p' is the minimum
 // over the other centers, hence the second value for the argmin's members).
-__global__ void __launch_bounds__(1024) k_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
-                                                   const float* __restrict__ qup, const double* __restrict__ nrm,
-                                                   int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
-                                                   unsigned long long* __restrict__ cnt) {
-  // the last kernel of the update to read the assignment's counters has run:
-  // zero them for the next assignment (which then needs no memset)
+// Also zeroes the assignment counters for the next assignment: the last
+// reader of them (the update) is done.
+__device__ __forceinline__ void dev_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
+                                             const float* __restrict__ qup, const double* __restrict__ nrm,
+                                             int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
+                                             unsigned long long* __restrict__ cnt, HselShared& S) {
   if (threadIdx.x < C_ERR) cnt[threadIdx.x] = 0ull;
-  __shared__ float s_pd[1024], s_pu[1024], s_q[1024], s_pd2[1024], s_pu2[1024], s_q2[1024];
-  __shared__ int s_jd[1024], s_ju[1024], s_jq[1024];
-  __shared__ double s_J[1024];
-  float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
-  int jd = INT_MAX, ju = INT_MAX, jq = INT_MAX;
-  double J = 0.0;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    const float x = pdn[j], y = pup[j], z = qup[j];
-    if (x < bd) { bd2 = bd; bd = x; jd = j; } else if (x < bd2) bd2 = x;
-    if (y < bu) { bu2 = bu; bu = y; ju = j; } else if (y < bu2) bu2 = y;
-    if (z > bq) { bq2 = bq; bq = z; jq = j; } else if (z > bq2) bq2 = z;
-    J += nrm[j];
+  for (int v = threadIdx.x; v < 1024; v += blockDim.x) {
+    float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
+    int jd = INT_MAX, ju = INT_MAX, jq = INT_MAX;
+    double J = 0.0;
+    for (int j = v; j < k; j += 1024) {
+      const float x = __ldcg(pdn + j), y = __ldcg(pup + j), z = __ldcg(qup + j);
+      if (x < bd) { bd2 = bd; bd = x; jd = j; } else if (x < bd2) bd2 = x;
+      if (y < bu) { bu2 = bu; bu = y; ju = j; } else if (y < bu2) bu2 = y;
+      if (z > bq) { bq2 = bq; bq = z; jq = j; } else if (z > bq2) bq2 = z;
+      J += __ldcg(nrm + j);
+    }
+    S.pd[v] = bd; S.pd2[v] = bd2; S.jd[v] = jd;
+    S.pu[v] = bu; S.pu2[v] = bu2; S.ju[v] = ju;
+    S.q[v] = bq; S.q2[v] = bq2; S.jq[v] = jq;
+    S.J[v] = J;
   }
-  s_pd[threadIdx.x] = bd; s_pd2[threadIdx.x] = bd2; s_jd[threadIdx.x] = jd;
-  s_pu[threadIdx.x] = bu; s_pu2[threadIdx.x] = bu2; s_ju[threadIdx.x] = ju;
-  s_q[threadIdx.x] = bq; s_q2[threadIdx.x] = bq2; s_jq[threadIdx.x] = jq;
-  s_J[threadIdx.x] = J;
   __syncthreads();
-  for (int o = blockDim.x / 2; o; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      const int a = threadIdx.x, b = threadIdx.x + o;
-      if (s_pd[b] < s_pd[a] || (s_pd[b] == s_pd[a] && s_jd[b] < s_jd[a])) {
-        s_pd2[a] = fminf(s_pd2[b], s_pd[a]);
-        s_pd[a] = s_pd[b];
-        s_jd[a] = s_jd[b];
+  for (int o = 512; o; o >>= 1) {
+    for (int a = threadIdx.x; a < o; a += blockDim.x) {
+      const int b = a + o;
+      if (S.pd[b] < S.pd[a] || (S.pd[b] == S.pd[a] && S.jd[b] < S.jd[a])) {
+        S.pd2[a] = fminf(S.pd2[b], S.pd[a]);
+        S.pd[a] = S.pd[b];
+        S.jd[a] = S.jd[b];
       } else {
-        s_pd2[a] = fminf(s_pd2[a], s_pd[b]);
+        S.pd2[a] = fminf(S.pd2[a], S.pd[b]);
       }
-      if (s_pu[b] < s_pu[a] || (s_pu[b] == s_pu[a] && s_ju[b] < s_ju[a])) {
-        s_pu2[a] = fminf(s_pu2[b], s_pu[a]);
-        s_pu[a] = s_pu[b];
-        s_ju[a] = s_ju[b];
+      if (S.pu[b] < S.pu[a] || (S.pu[b] == S.pu[a] && S.ju[b] < S.ju[a])) {
+        S.pu2[a] = fminf(S.pu2[b], S.pu[a]);
+        S.pu[a] = S.pu[b];
+        S.ju[a] = S.ju[b];
       } else {
-        s_pu2[a] = fminf(s_pu2[a], s_pu[b]);
+        S.pu2[a] = fminf(S.pu2[a], S.pu[b]);
       }
-      if (s_q[b] > s_q[a] || (s_q[b] == s_q[a] && s_jq[b] < s_jq[a])) {
-        s_q2[a] = fmaxf(s_q2[b], s_q[a]);
-        s_q[a] = s_q[b];
-        s_jq[a] = s_jq[b];
+      if (S.q[b] > S.q[a] || (S.q[b] == S.q[a] && S.jq[b] < S.jq[a])) {
+        S.q2[a] = fmaxf(S.q2[b], S.q[a]);
+        S.q[a] = S.q[b];
+        S.jq[a] = S.jq[b];
       } else {
-        s_q2[a] = fmaxf(s_q2[a], s_q[b]);
+        S.q2[a] = fmaxf(S.q2[a], S.q[b]);
       }
-      s_J[a] += s_J[b];
+      S.J[a] += S.J[b];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     // with a single center there is no "other" center: no drift to account for
     const bool one = (k == 1);
-    hsel[0] = (float)s_jd[0];
-    hsel[1] = s_pd[0];
-    hsel[2] = one ? 1.f : s_pd2[0];
-    hsel[3] = (float)s_ju[0];
-    hsel[4] = s_pu[0];
-    hsel[5] = one ? 1.f : s_pu2[0];
-    hsel[6] = (float)s_jq[0];
-    hsel[7] = s_q[0];
-    hsel[8] = one ? 0.f : s_q2[0];
-    obj[0] = s_J[0];
+    hsel[0] = (float)S.jd[0];
+    hsel[1] = S.pd[0];
+    hsel[2] = one ? 1.f : S.pd2[0];
+    hsel[3] = (float)S.ju[0];
+    hsel[4] = S.pu[0];
+    hsel[5] = one ? 1.f : S.pu2[0];
+    hsel[6] = (float)S.jq[0];
+    hsel[7] = S.q[0];
+    hsel[8] = one ? 0.f : S.q2[0];
+    obj[0] = S.J[0];
   }
+}
+
+// The same results with 256 slots for the minima and maxima (which do not
+// depend on the order they are combined in: values, then the lowest index on
+// ties) and the 1024-slot order for J, for a 256-thread block.
+struct HselSmall {
+  float pd[256], pu[256], q[256], pd2[256], pu2[256], q2[256];
+  int jd[256], ju[256], jq[256];
+  double J[1024];
+};
+__device__ __forceinline__ void dev_hsel_obj_256(const float* __restrict__ pdn, const float* __restrict__ pup,
+                                                 const float* __restrict__ qup, const double* __restrict__ nrm,
+                                                 int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
+                                                 unsigned long long* __restrict__ cnt, HselSmall& S) {
+  if (threadIdx.x < C_ERR) cnt[threadIdx.x] = 0ull;
+  const int tid = threadIdx.x;
+  float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
+  int jd = INT_MAX, ju = INT_MAX, jq = INT_MAX;
+  for (int j = tid; j < k; j += 256) {
+    const float x = __ldcg(pdn + j), y = __ldcg(pup + j), z = __ldcg(qup + j);
+    if (x < bd) { bd2 = bd; bd = x; jd = j; } else if (x < bd2) bd2 = x;
+    if (y < bu) { bu2 = bu; bu = y; ju = j; } else if (y < bu2) bu2 = y;
+    if (z > bq) { bq2 = bq; bq = z; jq = j; } else if (z > bq2) bq2 = z;
+  }
+  S.pd[tid] = bd; S.pd2[tid] = bd2; S.jd[tid] = jd;
+  S.pu[tid] = bu; S.pu2[tid] = bu2; S.ju[tid] = ju;
+  S.q[tid] = bq; S.q2[tid] = bq2; S.jq[tid] = jq;
+  for (int v = tid; v < 1024; v += 256) {
+    double J = 0.0;
+    for (int j = v; j < k; j += 1024) J += __ldcg(nrm + j);
+    S.J[v] = J;
+  }
+  __syncthreads();
+  for (int o = 512; o; o >>= 1) {
+    for (int a = tid; a < o; a += 256) S.J[a] += S.J[a + o];
+    if (o < 256 && tid < o) {
+      const int a = tid, b = tid + o;
+      if (S.pd[b] < S.pd[a] || (S.pd[b] == S.pd[a] && S.jd[b] < S.jd[a])) {
+        S.pd2[a] = fminf(S.pd2[b], S.pd[a]);
+        S.pd[a] = S.pd[b];
+        S.jd[a] = S.jd[b];
+      } else {
+        S.pd2[a] = fminf(S.pd2[a], S.pd[b]);
+      }
+      if (S.pu[b] < S.pu[a] || (S.pu[b] == S.pu[a] && S.ju[b] < S.ju[a])) {
+        S.pu2[a] = fminf(S.pu2[b], S.pu[a]);
+        S.pu[a] = S.pu[b];
+        S.ju[a] = S.ju[b];
+      } else {
+        S.pu2[a] = fminf(S.pu2[a], S.pu[b]);
+      }
+      if (S.q[b] > S.q[a] || (S.q[b] == S.q[a] && S.jq[b] < S.jq[a])) {
+        S.q2[a] = fmaxf(S.q2[b], S.q[a]);
+        S.q[a] = S.q[b];
+        S.jq[a] = S.jq[b];
+      } else {
+        S.q2[a] = fmaxf(S.q2[a], S.q[b]);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const bool one = (k == 1);
+    hsel[0] = (float)S.jd[0];
+    hsel[1] = S.pd[0];
+    hsel[2] = one ? 1.f : S.pd2[0];
+    hsel[3] = (float)S.ju[0];
+    hsel[4] = S.pu[0];
+    hsel[5] = one ? 1.f : S.pu2[0];
+    hsel[6] = (float)S.jq[0];
+    hsel[7] = S.q[0];
+    hsel[8] = one ? 0.f : S.q2[0];
+    obj[0] = S.J[0];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
+                                                   const float* __restrict__ qup, const double* __restrict__ nrm,
+                                                   int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
+                                                   unsigned long long* __restrict__ cnt) {
+  __shared__ HselShared S;
+  dev_hsel_obj(pdn, pup, qup, nrm, k, hsel, obj, cnt, S);
+}
+
+// ------------------------------------------------------------------
+// All the phases above in one cooperative launch (every block resident at
+// once, so blocks may wait on one another), with grid barriers between the
+// phases that read what the previous one wrote:
+//   block 0: dirty list | tiles: partial norms | dirty slots: norms |
+//   tiles: normalise + drift partials | centers: drift | last block: J and
+//   Hamerly's summary.
+// Each barrier waits on a 64-bit counter that only grows (kFinishBars
+// arrivals per block per launch), so no reset is needed between launches or
+// graph replays: a block finds its launch's base by rounding the counter it
+// reads at the start down to a multiple of kFinishBars * gridDim.x (no block
+// can pass the first barrier before every block has started).  Every wait
+// gives up after one second, raises E_TIMEOUT and the blocks leave.
+constexpr int kFinishBars = 4;
+constexpr uint64_t kFinishTimeoutNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier number `which` (1-based) of this launch; false if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned long long base, int which,
+                                             unsigned long long* __restrict__ cnt, int* ok_sh,
+                                             uint64_t timeout_ns = kFinishTimeoutNs) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1ull);
+    const unsigned long long target = base + (unsigned long long)which * gridDim.x;
+    const uint64_t t0 = globaltimer_ns();
+    int ok = 1;
+    while (*reinterpret_cast<volatile unsigned long long*>(bar) < target) {
+      if (globaltimer_ns() - t0 > timeout_ns) {
+        ok = 0;
+        atomicOr(cnt + C_ERR, (unsigned long long)E_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    *ok_sh = ok;
+  }
+  __syncthreads();
+  return *ok_sh != 0;
+}
+
+// Self-test of the barrier's failure path: two cooperative blocks, block 1
+// never arrives, so block 0's wait must give up after timeout_ns and raise
+// E_TIMEOUT in flag[C_ERR].
+__global__ void k_barrier_selftest(unsigned long long* bar, uint64_t timeout_ns, unsigned long long* flag) {
+  __shared__ int ok_sh;
+  if (blockIdx.x != 0) return;
+  (void)grid_barrier(bar, 0, 1, flag, &ok_sh, timeout_ns);
+}
+
+__global__ void __launch_bounds__(256) k_finish_fused(int32_t k, int64_t kst, int64_t d, int64_t nblk, float inv,
+                                                      int s64_valid, int64_t n, int32_t* __restrict__ dflag,
+                                                      int32_t* __restrict__ dmark, int32_t* __restrict__ dpos,
+                                                      int32_t* __restrict__ dlist, const long long* __restrict__ S64,
+                                                      float* __restrict__ Ct, double* __restrict__ nrm,
+                                                      double* __restrict__ red, float* __restrict__ pdn,
+                                                      float* __restrict__ pup, float* __restrict__ qup,
+                                                      double* __restrict__ cnorm, float* __restrict__ hsel,
+                                                      double* __restrict__ obj, unsigned long long* __restrict__ cnt,
+                                                      unsigned long long* __restrict__ bar) {
+  __shared__ union {
+    double part[3][8][33];
+    double fin[3][128];
+    HselSmall hs;
+  } sm;
+  __shared__ int wsum[8];
+  __shared__ int base_sh, ok_sh, last_sh;
+  __shared__ unsigned long long bar0_sh;
+  if (threadIdx.x == 0) {
+    const unsigned long long per = (unsigned long long)kFinishBars * gridDim.x;
+    const unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(bar);
+    bar0_sh = v - v % per;
+  }
+  __syncthreads();
+  const unsigned long long b0 = bar0_sh;
+  const bool full = full_update(s64_valid, cnt, n);
+  if (blockIdx.x == 0) dev_dirty(k, dflag, dmark, dpos, dlist, cnt, full, wsum, &base_sh);
+  if (!grid_barrier(bar, b0, 1, cnt, &ok_sh)) return;
+  const int nd = (int)__ldcg(cnt + C_NDIRTY);
+  const int ngroups = (nd + 31) / 32;
+  const int64_t ntile = nblk * ngroups;
+  for (int64_t w = blockIdx.x; w < ntile; w += gridDim.x)
+    dev_colnorm_part(S64, inv, d, kst, dlist, nd, red, (int)(w % nblk), (int)(w / nblk), sm.part[0]);
+  if (!grid_barrier(bar, b0, 2, cnt, &ok_sh)) return;
+  for (int slot = blockIdx.x; slot < nd; slot += gridDim.x) dev_colnorm_final(red, nblk, kst, dlist, slot, nrm, sm.fin[0]);
+  if (!grid_barrier(bar, b0, 3, cnt, &ok_sh)) return;
+  for (int64_t w = blockIdx.x; w < ntile; w += gridDim.x)
+    dev_normalize_drift(S64, inv, Ct, nrm, d, kst, dlist, nd, red, (int)(w % nblk), (int)(w / nblk), sm.part);
+  if (!grid_barrier(bar, b0, 4, cnt, &ok_sh)) return;
+  for (int64_t j = blockIdx.x; j < kst; j += gridDim.x)
+    dev_drift_final(red, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, (int)j, sm.fin);
+  // the last block to get here writes J and Hamerly's summary
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long v = atomicAdd(bar + 1, 1ull);
+    last_sh = (v % gridDim.x) == gridDim.x - 1;
+    __threadfence();
+  }
+  __syncthreads();
+  if (last_sh) dev_hsel_obj_256(pdn, pup, qup, nrm, k, hsel, obj, cnt, sm.hs);
 }
 
 // The Gram by 64 x 64 tiles: grid (ceil(k/64), ceil(k/64), nsplit), block
@@ -973,35 +1234,106 @@ int update_centers(skm_ctx* c) {
   return finish_update(c);
 }
 
+int barrier_selftest(int64_t timeout_ns, cudaStream_t st) {
+  unsigned long long* buf = nullptr;  // [0] the barrier counter, [1 + C_ERR] the error word
+  SKM_CUDA_TRY(cudaMallocAsync((void**)&buf, sizeof(unsigned long long) * (2 + C_NUM), st));
+  SKM_CUDA_TRY(cudaMemsetAsync(buf, 0, sizeof(unsigned long long) * (2 + C_NUM), st));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SKM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_barrier_selftest, buf, (uint64_t)timeout_ns, buf + 1));
+  note_launch();
+  unsigned long long h = 0;
+  SKM_CUDA_TRY(cudaMemcpyAsync(&h, buf + 1 + C_ERR, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SKM_CUDA_TRY(cudaFreeAsync(buf, st));
+  SKM_CUDA_TRY(cudaStreamSynchronize(st));
+  return (h & E_TIMEOUT) ? SKM_ETIMEOUT : SKM_OK;
+}
+
+// Blocks of the fused finishing kernel: enough for its largest phase, at most
+// what is resident at once (its blocks wait on one another); 0 if it is not
+// asked for (opt.fused_update; on the RCV-1-like workload its four grid
+// barriers and serial dirty-list phase cost more than the launch gaps of the
+// separate kernels save: 2251 vs 2331 iterations/s) or this device cannot
+// launch cooperative kernels.
+int finish_fused_grid(const skm_ctx* c) {
+  if (!c->opt.fused_update) return 0;
+  static int per_sm = -1, coop = -1;
+  if (per_sm < 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
+      v = 0;
+    coop = v;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_finish_fused, 256, 0) != cudaSuccess) nb = 0;
+    (void)cudaGetLastError();
+    per_sm = nb;
+  }
+  if (!coop || per_sm < 1 || !c->fbar) return 0;
+  const int64_t want = reduction_blocks(c->d) * ((c->kst + 31) / 32);
+  int64_t g = (int64_t)c->nsm * per_sm;
+  if (want < g) g = want;
+  return (int)(g < 1 ? 1 : g);
+}
+
 // Dirty list, norms, new centers, drift and (full variants) the center-center
 // bounds, shared by the sparse and dense paths.
 int finish_update(skm_ctx* c) {
   const int k = c->k;
-  SKM_PROF_BEGIN(c, "k_dirty");
-  k_dirty<<<1, 1024, 0, c->st>>>(k, c->dflag, c->dmark, c->dpos, c->dlist, c->cnt, c->s64_valid, c->n);
-  SKM_LAUNCHED(c);
-  c->s64_valid = 1;
-  // ---- norms, new centers and drift of the dirty clusters
   const int64_t nblk = reduction_blocks(c->d);
-  dim3 grid((unsigned)nblk, (unsigned)((k + 31) / 32));
-  SKM_PROF_BEGIN(c, "k_colnorm_part");
-  k_colnorm_part<<<grid, dim3(32, 8), 0, c->st>>>(c->S64, c->fx_inv, c->d, c->kst, c->dlist, c->cnt, c->red);
-  SKM_LAUNCHED(c);
-  SKM_PROF_BEGIN(c, "k_colnorm_final");
-  k_colnorm_final<<<k, 128, 0, c->st>>>(c->red, nblk, c->kst, c->dlist, c->cnt, c->nrm);
-  SKM_LAUNCHED(c);
-  SKM_PROF_BEGIN(c, "k_normalize_drift");
-  k_normalize_drift<<<grid, dim3(32, 8), 0, c->st>>>(c->S64, c->fx_inv, c->Ct, c->nrm, c->d, c->kst, c->dlist,
-                                                     c->cnt, c->red);
-  SKM_LAUNCHED(c);
   double* cnorm = c->nrm + c->kst;  // second half of the norm buffer: |c(j)| of the centers
-  SKM_PROF_BEGIN(c, "k_drift_final");
-  k_drift_final<<<c->kst, 128, 0, c->st>>>(c->red, nblk, k, c->kst, c->d, c->dmark, c->dpos, c->pdn, c->pup, c->qup,
-                                           cnorm);
-  SKM_LAUNCHED(c);
-  SKM_PROF_BEGIN(c, "k_hsel_obj");
-  k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj, c->cnt);
-  SKM_LAUNCHED(c);
+  const int s64_was_valid = c->s64_valid;
+  c->s64_valid = 1;
+  const int fg = finish_fused_grid(c);
+  if (fg > 0) {
+    // ---- dirty list, norms, new centers, drift, J and Hamerly's summary: one cooperative launch
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)fg);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c->st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SKM_PROF_BEGIN(c, "k_finish_fused");
+    SKM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_finish_fused, k, (int64_t)c->kst, c->d, nblk, c->fx_inv, s64_was_valid,
+                                    c->n, c->dflag, c->dmark, c->dpos, c->dlist, (const long long*)c->S64, c->Ct,
+                                    c->nrm, c->red, c->pdn, c->pup, c->qup, cnorm, c->hsel, c->obj, c->cnt,
+                                    c->fbar));
+    SKM_LAUNCHED(c);
+  } else {
+    SKM_PROF_BEGIN(c, "k_dirty");
+    k_dirty<<<1, 1024, 0, c->st>>>(k, c->dflag, c->dmark, c->dpos, c->dlist, c->cnt, s64_was_valid, c->n);
+    SKM_LAUNCHED(c);
+    // ---- norms, new centers and drift of the dirty clusters
+    dim3 grid((unsigned)nblk, (unsigned)((k + 31) / 32));
+    SKM_PROF_BEGIN(c, "k_colnorm_part");
+    k_colnorm_part<<<grid, 256, 0, c->st>>>(c->S64, c->fx_inv, c->d, c->kst, c->dlist, c->cnt, c->red);
+    SKM_LAUNCHED(c);
+    SKM_PROF_BEGIN(c, "k_colnorm_final");
+    k_colnorm_final<<<k, 128, 0, c->st>>>(c->red, nblk, c->kst, c->dlist, c->cnt, c->nrm);
+    SKM_LAUNCHED(c);
+    SKM_PROF_BEGIN(c, "k_normalize_drift");
+    k_normalize_drift<<<grid, 256, 0, c->st>>>(c->S64, c->fx_inv, c->Ct, c->nrm, c->d, c->kst, c->dlist, c->cnt,
+                                               c->red);
+    SKM_LAUNCHED(c);
+    SKM_PROF_BEGIN(c, "k_drift_final");
+    k_drift_final<<<c->kst, 128, 0, c->st>>>(c->red, nblk, k, c->kst, c->d, c->dmark, c->dpos, c->pdn, c->pup,
+                                             c->qup, cnorm);
+    SKM_LAUNCHED(c);
+    SKM_PROF_BEGIN(c, "k_hsel_obj");
+    k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj, c->cnt);
+    SKM_LAUNCHED(c);
+  }
   const bool hamv = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
   const bool full = (c->variant == SKM_ELKAN || c->variant == SKM_HAMERLY);
   // |error| of an FP32 sum of 256 products <= gamma_256 |c_i||c_j|, plus

@@ -401,6 +401,7 @@ struct skm_ctx {
   int32_t* w2;
   // counters
   unsigned long long* cnt;   // device [C_NUM]
+  unsigned long long* fbar;  // device [2]: k_finish_fused's barrier and last-block counters (only grow)
   unsigned long long* hcnt;  // pinned host mirror [C_NUM]
   double* hobj;              // pinned host [1]
   // per-kernel CUDA-event timing (skm_profile)
@@ -457,6 +458,7 @@ int bf16_topk(skm_ctx* c, const void* Xb, const void* Cb, int use_thr, float* to
 int dense_lower(skm_ctx* c);
 int dense_recheck_cands(skm_ctx* c, bool hamerly);
 int wait_selftest(int64_t timeout_ns, cudaStream_t st);
+int barrier_selftest(int64_t timeout_ns, cudaStream_t st);
 // The first assignment kept by a seeding (seed_kmeanspp with first != NULL):
 // per row the best similarity, its center and the second best (device
 // buffers the seeding allocates and seed_finish frees); elkan: the seeding

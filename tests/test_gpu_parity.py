@@ -338,3 +338,40 @@ def test_long_rows_elkan(variant):
     assert survivors > 0  # the per-pair recompute ran
     km.close()
     std.close()
+
+
+@pytest.mark.parametrize("variant", ["standard", "hamerly", "elkan", "simp_elkan"])
+def test_fused_center_update_equals_separate_kernels(variant):
+    """The center update's phases after the sums run as one cooperative
+    launch (grid barriers between phases) or as separate kernels: labels,
+    objective and centers are bit-identical at every iteration, eagerly and
+    with the iteration replayed as a CUDA graph."""
+    X = synth.tfidf(synth.scaled(synth.CSR_RCV1_LIKE, n=8000, d=6000, seed=23))
+    k = 50
+    init = synth.init_rows(X.n, k, 23)
+    dev = [torch.from_numpy(a).cuda() for a in (X.row_ptr, X.col, X.val)]
+    seqs = {}
+    for sep in (False, True):
+        km = skm.KMeans(X.n, X.d, *dev, k, variant=variant, init_rows=init, fused_update=not sep)
+        seq = []
+        for _ in range(40):
+            ch = km.assign()
+            lab = km.labels()
+            if ch == 0:
+                seq.append((lab, None, None))
+                break
+            J = km.update_centers()
+            seq.append((lab, J, km.centers()))
+        seqs[sep] = seq
+        km.close()
+    assert len(seqs[False]) == len(seqs[True])
+    for (la, ja, ca), (lb, jb, cb) in zip(seqs[False], seqs[True]):
+        np.testing.assert_array_equal(la, lb)
+        assert ja == jb
+        if ca is not None:
+            np.testing.assert_array_equal(ca, cb)
+    g = skm.KMeans(X.n, X.d, *dev, k, variant=variant, init_rows=init, graph=True, fused_update=True)
+    it, J = g.run(40)
+    assert it == len(seqs[True])
+    np.testing.assert_array_equal(g.labels(), seqs[True][-1][0])
+    g.close()
