@@ -166,6 +166,12 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
+def screen_opt(args):
+    """--screen 1 / 0: FP16 screening of the Elkan whole-row recomputes on /
+    off; absent: the library's choice (on for k > 128)."""
+    return None if args.screen is None else bool(args.screen)
+
+
 def measured_peaks(skm, torch):
     """FP32 and FP64 FMA rates from the library's own microbenchmark
     (skm_measure_peak), and the FP8-E4M3 GEMM rate of cuBLAS through
@@ -248,7 +254,7 @@ def run_ours(args, rank, world, local):
         # every variant (the plain standard one included) replays its steady-state
         # iteration as a CUDA graph
         return skm.KMeans(n, d, rp, col, val, k, variant=variant, init_rows=init, stream=stream.cuda_stream,
-                          graph=not args.no_graph)
+                          graph=not args.no_graph, screen=screen_opt(args))
 
     def timed_runs(km, steps, warmup):
         for _ in range(warmup):
@@ -439,7 +445,7 @@ def run_ours(args, rank, world, local):
     e2e_iters = 0
     for _ in range(e2e_steps):
         kh = skm.KMeans(n, d, host[0], host[1], host[2], k, variant=variant, init_rows=init,
-                        stream=stream.cuda_stream, graph=not args.no_graph)
+                        stream=stream.cuda_stream, graph=not args.no_graph, screen=screen_opt(args))
         it, _ = kh.run(MAX_ITERS)
         lab_h = kh.labels()
         kh.close()
@@ -898,7 +904,8 @@ def run_large(args, rank, world, local):
     sampler = ClockSampler(local)
     sampler.start()
     for variant in ("elkan", "simp_elkan", "hamerly", "standard"):
-        km = skm.KMeans(csr.n, csr.d, *Xd, k, variant=variant, init_rows=init, stream=stream.cuda_stream)
+        km = skm.KMeans(csr.n, csr.d, *Xd, k, variant=variant, init_rows=init, stream=stream.cuda_stream,
+                        screen=screen_opt(args))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -1067,6 +1074,9 @@ def main():
     ap.add_argument("--embed-repeats", type=int, default=5)
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the precision form's per-result comparison with the FP64 oracle")
+    ap.add_argument("--screen", type=int, default=None, choices=[0, 1],
+                    help="Elkan variants: screen whole-row recomputes against FP16 centers (1) or not (0); "
+                         "default: the library's choice (on for k > 128)")
     ap.add_argument("--trace", action="store_true",
                     help="print a per-iteration table (labels changed, similarities, survivors, kernel ms) and exit")
     args = ap.parse_args()

@@ -131,7 +131,21 @@ typedef struct {
                               that gives up after 1 s makes the next
                               skm_assign return SKM_ETIMEOUT; destroy the
                               context then).  Results are bit-identical. */
-  int32_t reserved[4];
+  int32_t screen;          /* Elkan variants on CSR data (single runs, k <= 1024):
+                              the whole-row recomputes after the first
+                              assignment screened against an FP16 copy of the
+                              centers (half the bytes gathered; with k = 1000
+                              the FP32 center table outgrows L2).  The center
+                              update keeps E >= max_j |fp16(c_j) - c_j|; every
+                              FP16 similarity is then within eps_i =
+                              E + 1.001 delta_i of the exact one, so a row
+                              whose best two differ by more than
+                              2 (eps_i + delta_i) takes its label from them,
+                              and the other rows are recomputed exactly
+                              (labels identical either way; the Elkan bounds
+                              of screened rows are looser by eps_i).
+                              0 (default): on for k > 128; 1: on; 2: off. */
+  int32_t reserved[3];
 } skm_options;
 
 /* Counters of the last assignment and of the run so far. */

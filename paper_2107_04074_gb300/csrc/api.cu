@@ -132,8 +132,9 @@ int start_from_rows(skm_ctx* c, const std::vector<int64_t>& rows) {
   int64_t* drows = nullptr;
   TRY(dalloc(c, &drows, (size_t)c->k));
   SKM_CUDA_TRY(cudaMemcpyAsync(drows, rows.data(), sizeof(int64_t) * c->k, cudaMemcpyHostToDevice, c->st));
-  const int rc = init_centers(c, drows);
+  int rc = init_centers(c, drows);
   cudaFreeAsync(drows, c->st);
+  if (rc == SKM_OK) rc = ct16_all(c);
   // the host vector must outlive the copy
   SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
   if (rc) return rc;
@@ -199,7 +200,8 @@ void release(skm_ctx* c) {
                   c->ub,     c->w1,      c->w2,    c->cnt,    c->chg_i,  c->chg_old, c->dflag, c->dmark,
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
                   c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n,
-                  c->exr,    c->ebc,     c->ebw,   c->rsc,    c->gdbeg,  c->gdcnt,  c->gtask,  c->fbar};
+                  c->exr,    c->ebc,     c->ebw,   c->rsc,    c->gdbeg,  c->gdcnt,  c->gtask,  c->fbar,
+                  c->Ct16,   c->e2p,     c->e2c,   c->escr,   c->w4};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -390,6 +392,17 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
     TRY(dalloc(c, &c->ub, (size_t)ucount));
     TRY(dalloc(c, &c->w1, (size_t)n));
     TRY(dalloc(c, &c->w2, (size_t)n));
+  }
+  // ---- screened whole-row passes (Elkan variants, single runs, 128 < k <= 1024)
+  const int scr = c->opt.screen;  // 0 auto, 1 on, 2 off
+  if (elk && c->nruns == 0 && c->layout == SKM_CSR && k <= 1024 && (scr == 1 || (scr == 0 && k > 128))) {
+    TRY(dalloc(c, &c->Ct16, (size_t)(d * kst)));
+    TRY(dalloc(c, &c->e2p, (size_t)(reduction_blocks(d) * kst)));
+    TRY(dalloc(c, &c->e2c, (size_t)kst));
+    SKM_CUDA_TRY(cudaMemsetAsync(c->e2c, 0, sizeof(double) * kst, c->st));
+    TRY(dalloc(c, &c->escr, (size_t)1));
+    TRY(dalloc(c, &c->w3, (size_t)n));
+    TRY(dalloc(c, &c->w4, (size_t)n));
   }
   // fixed-point scale of the center sums: an entry |x| <= 1 maps below 2^40
   // (the 20 + 20 bit split of k_center_sum) and |sum| <= n must stay below
@@ -814,6 +827,7 @@ int skm_set_centers(skm_ctx* c, const float* C, int32_t space) {
     cudaFreeAsync(tmp, c->st);
     SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
   }
+  if (rc == SKM_OK) rc = ct16_all(c);
   c->have_bounds = 0;
   c->moved = 0;
   c->s64_valid = 0;

@@ -16,6 +16,13 @@
 //                    one pass over the row, reassignment under the tie rule.
 //   k_elk_recompute_long  the same for survivors with long rows, a warp per
 //                    point (32 row entries gathered per round trip).
+//   k_rows_top2 MODE 4  the screened whole-row pass of the Elkan variants for
+//                    k > 128: all k similarities against an FP16 copy of the
+//                    centers (half the bytes gathered: with k = 1000 the
+//                    center table is far larger than L2 and the FP32 pass
+//                    streams it from DRAM) with a proven error bound; rows
+//                    whose label the bound decides are done, the others go
+//                    to an exact pass (pairs or whole rows).
 #include <climits>
 #include <mutex>
 #include <unordered_map>
@@ -26,7 +33,15 @@ namespace skm {
 
 namespace {
 
+#define TRY_K(x)                   \
+  do {                             \
+    const int r__ = (x);           \
+    if (r__ != SKM_OK) return r__; \
+  } while (0)
+
 constexpr int kBlock = 256;
+constexpr int kTile = 8;       // points per warp tile of k_elk_bounds
+constexpr int kLongRow = 256;  // Elkan survivors with longer rows go to the warp-per-point recompute
 
 // Dynamic scheduling over `total` items by `nworkers` warps (or 8-lane
 // groups): worker w takes item w first, then items nworkers + c for
@@ -45,6 +60,46 @@ __device__ __forceinline__ int64_t grab_take(unsigned long long v, unsigned mask
   return (int64_t)__shfl_sync(mask, v, 0, width);
 }
 
+// Four consecutive center values of one term as FP32 (16 B of FP32 or 8 B
+// of FP16 centers).
+template <typename CT>
+__device__ __forceinline__ float4 ld_c4(const CT* p);
+template <>
+__device__ __forceinline__ float4 ld_c4<float>(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <>
+__device__ __forceinline__ float4 ld_c4<__half>(const __half* p) {
+  const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Raw loads of four center values, converted just before the FMAs: FP16
+// centers take half the registers, so twice as many row entries' gathers can
+// be in flight at once.
+template <typename CT>
+struct RawC4;
+template <>
+struct RawC4<float> {
+  using type = float4;
+  static __device__ __forceinline__ type load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+  static __device__ __forceinline__ type zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ float4 f4(type r) { return r; }
+};
+template <>
+struct RawC4<__half> {
+  using type = uint2;
+  static __device__ __forceinline__ type load(const __half* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
+  static __device__ __forceinline__ type zero() { return make_uint2(0u, 0u); }
+  static __device__ __forceinline__ float4 f4(type r) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+};
+
 // MODE 0: labels only (standard).  MODE 1: also l(i) and Hamerly's u(i).
 // MODE 2: also l(i) and every Elkan bound u(i,j).  MODE 3 (Yin-Yang): only
 // the centers of the live groups (a group of 8 consecutive centers is live
@@ -57,26 +112,46 @@ __device__ __forceinline__ int64_t grab_take(unsigned long long v, unsigned mask
 // sum runs over the row entries in CSR order (the canonical order).
 // For a batch (runs != nullptr) each row works on its run's slice of the
 // centers (global ids koff + j) and its run's bound row.
+// MODE 4 (screened Elkan whole rows, CT = __half, single runs, one pass):
+// the similarities s^ against the FP16 centers h_j satisfy |s^ - s| <= eps_i
+// for the exact cosine s, with eps_i = E + 1.001 delta_i (E = escr[0] bounds
+// |h_j - c_j| for every j, so |<x^, h_j - c_j>| <= E by Cauchy-Schwarz; the
+// FP32 chain over the products with h, |h_j| <= 1 + 6u + E, errs by at most
+// delta_i (1 + E), and E < 10^-3).  So |s^ - f| <= w_i = eps_i + delta_i for
+// the canonical FP32 similarity f.  Every u(i,j) becomes s^_ij + eps_i.  If
+// the best two differ by more than 2 w_i the best center is the one the
+// exact pass would pick: label and l(i) = s^_1 - eps_i.  Otherwise the
+// current label stays, l(i) = s^_cur - eps_i, and the row goes to the exact
+// pass: the pair recompute (w3) when at most 7 centers pass Elkan's test
+// against these bounds (counted from the bound row just written), else an
+// FP32 whole row (w4).
 // Resident blocks asked of the compiler: three (at most 80 registers, no
 // spills) up to 512 centers, two for the widest form.  Latency-bound as it is,
 // the kernel runs faster with more warps than with more registers.
 constexpr int rows_min_blocks(int G) { return G >= 8 ? 2 : 3; }
 
-template <typename VT, int G, int MODE, bool BATCH>
+template <typename VT, typename CT, int G, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
-    const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int32_t k,
+    const float* __restrict__ rinv, const float* __restrict__ dlt, const CT* __restrict__ Ct, int32_t k,
     int64_t kst, const int32_t* __restrict__ row_run, const RunDesc* __restrict__ runs,
     const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt, int64_t nrows,
     int64_t ustride, int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub,
-    int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt) {
+    int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old, unsigned long long* __restrict__ cnt,
+    unsigned long long* __restrict__ cursor, const float* __restrict__ escr, int32_t* __restrict__ w3,
+    int32_t* __restrict__ w4) {
   constexpr int KT = 128 * G;                     // centers per pass over the row
-  constexpr int NB = G >= 8 ? 1 : 8 / G;          // row entries batched per step
+  // row entries batched per step (their gathers in flight together): twice
+  // as many with FP16 centers, whose raw loads take half the registers
+  constexpr int NB = (sizeof(CT) == 2 ? 2 : 1) * (G >= 8 ? 1 : 8 / G);
+  using Raw = RawC4<CT>;
   const int lane = threadIdx.x & 31;
   const int64_t total = list ? (int64_t)(*list_cnt) : nrows;
   unsigned long long my_changed = 0, my_sims = 0;
   ChangedBuf chb;
-  unsigned long long* cursor = cnt + C_CURSOR;
+  // screened pass: E, and whether it is small enough for the bound (else every row goes to the exact pass)
+  const float Escr = MODE == 4 ? escr[0] : 0.f;
+  const bool scr_ok = MODE == 4 && Escr < 1e-3f;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nxt;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
@@ -93,6 +168,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
     int j1 = INT_MAX;
     float sv[MODE == 3 ? G : 1][4];  // Yin-Yang: this lane's similarities (-inf: not live)
     bool live[MODE == 3 ? G : 1];
+    const float eps = MODE == 4 ? __fadd_ru(Escr, __fmul_ru(dl, 1.001f)) : 0.f;
     unsigned live_cnt = 0;
     const float L3 = (MODE == 3 && cur >= 0) ? __fsub_rd(lb[i], 2.f * dl) : -INFINITY;
     for (int j0 = 0; j0 < kr; j0 += KT) {
@@ -108,7 +184,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           ok[g] = live[g];
         }
       }
-      const float* cbase = Ct + rg.koff + j0 + lane * 4;
+      const CT* cbase = Ct + rg.koff + j0 + lane * 4;
       // the row's entries 32 at a time, the next 32 loaded ahead
       int tt_n = 0;
       float vv_n = 0.f;
@@ -128,7 +204,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
         for (; q + NB <= nq; q += NB) {
           int t[NB];
           float v[NB];
-          float4 cv[NB][G];
+          typename Raw::type cv[NB][G];
 #pragma unroll
           for (int u = 0; u < NB; ++u) {
             t[u] = __shfl_sync(SKM_FULL_MASK, tt, q + u);
@@ -138,16 +214,16 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           for (int u = 0; u < NB; ++u)
 #pragma unroll
             for (int g = 0; g < G; ++g)
-              cv[u][g] = ok[g] ? __ldg(reinterpret_cast<const float4*>(cbase + (int64_t)t[u] * kst + g * 128))
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+              cv[u][g] = ok[g] ? Raw::load(cbase + (int64_t)t[u] * kst + g * 128) : Raw::zero();
 #pragma unroll
           for (int u = 0; u < NB; ++u)
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              acc[g].x = __fmaf_rn(v[u], cv[u][g].x, acc[g].x);
-              acc[g].y = __fmaf_rn(v[u], cv[u][g].y, acc[g].y);
-              acc[g].z = __fmaf_rn(v[u], cv[u][g].z, acc[g].z);
-              acc[g].w = __fmaf_rn(v[u], cv[u][g].w, acc[g].w);
+              const float4 c4 = Raw::f4(cv[u][g]);
+              acc[g].x = __fmaf_rn(v[u], c4.x, acc[g].x);
+              acc[g].y = __fmaf_rn(v[u], c4.y, acc[g].y);
+              acc[g].z = __fmaf_rn(v[u], c4.z, acc[g].z);
+              acc[g].w = __fmaf_rn(v[u], c4.w, acc[g].w);
             }
         }
         for (; q < nq; ++q) {
@@ -156,7 +232,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
 #pragma unroll
           for (int g = 0; g < G; ++g)
             if (ok[g]) {
-              const float4 c4 = __ldg(reinterpret_cast<const float4*>(cbase + (int64_t)t * kst + g * 128));
+              const float4 c4 = ld_c4<CT>(cbase + (int64_t)t * kst + g * 128);
               acc[g].x = __fmaf_rn(v, c4.x, acc[g].x);
               acc[g].y = __fmaf_rn(v, c4.y, acc[g].y);
               acc[g].z = __fmaf_rn(v, c4.z, acc[g].z);
@@ -178,6 +254,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
               ++live_cnt;
             }
             if (MODE == 2) ub[rg.ubase + j] = __fadd_ru(s, dl);
+            if (MODE == 4) ub[rg.ubase + j] = __fadd_ru(s, eps);
             if (j == cur) vcur = s;
             if (s > v1) {
               v2 = v1;
@@ -213,6 +290,38 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
       nb = j1;
       ssec = v2;
     }
+    // screened: decided (scr_dec 0), pair recompute (1) or exact whole row (2)
+    int scr_dec = 0;
+    float scr_l = 0.f;
+    if (MODE == 4) {
+      const float w2x = __fmul_ru(2.f, __fadd_ru(eps, dl));
+      if (scr_ok && __fsub_rd(v1, v2) > w2x) {
+        nb = j1;  // the exact standard pass picks j1: it beats every other center strictly
+        scr_l = __fsub_rd(v1, eps);
+      } else if (scr_ok && cur >= 0) {
+        // keep the label; count the centers Elkan's test (u(i,j) > l - 2 delta)
+        // lets through against the bound row written above, as the pair
+        // recompute will
+        nb = cur;
+        scr_l = __fsub_rd(vcur, eps);
+        const float L = __fsub_rd(scr_l, 2.f * dl);
+        __syncwarp();
+        int m = 0;
+        for (int jb = lane * 4; jb < kr; jb += 128) {
+          const float4 u4 = *reinterpret_cast<const float4*>(ub + rg.ubase + jb);
+          m += (jb + 0 < kr && jb + 0 != cur && u4.x > L) ? 1 : 0;
+          m += (jb + 1 < kr && jb + 1 != cur && u4.y > L) ? 1 : 0;
+          m += (jb + 2 < kr && jb + 2 != cur && u4.z > L) ? 1 : 0;
+          m += (jb + 3 < kr && jb + 3 != cur && u4.w > L) ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m += __shfl_xor_sync(SKM_FULL_MASK, m, o);
+        scr_dec = m <= 7 ? 1 : 2;
+      } else {
+        nb = cur;
+        scr_dec = 2;
+      }
+    }
     if (MODE == 3) {
       // the live groups' new bounds: the best of their other centers (two
       // lanes per group)
@@ -231,11 +340,21 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
       for (int o = 16; o; o >>= 1) live_cnt += __shfl_xor_sync(SKM_FULL_MASK, live_cnt, o);
     }
     if (lane == 0) {
-      a[i] = rg.koff + nb;
+      if (MODE != 4 || nb >= 0) a[i] = rg.koff + nb;
       my_changed += (nb != cur);
       my_sims += MODE == 3 ? (unsigned long long)live_cnt : (unsigned long long)kr;
-      if (MODE >= 1) lb[i] = __fsub_rd(v1, dl);
+      if (MODE >= 1 && MODE <= 3) lb[i] = __fsub_rd(v1, dl);
       if (MODE == 1) ub[i] = (kr > 1) ? __fadd_ru(ssec, dl) : -1.f;
+      if (MODE == 4) {
+        if (scr_dec < 2 || cur >= 0) lb[i] = scr_l;
+        if (scr_dec == 1) {
+          // long rows from the top of w3 down (ustride = n for this mode)
+          if (e - b > kLongRow) w3[(ustride - 1) - (int64_t)atomicAdd(cnt + C_W3L, 1ull)] = (int32_t)i;
+          else w3[atomicAdd(cnt + C_W3S, 1ull)] = (int32_t)i;
+        } else if (scr_dec == 2) {
+          w4[atomicAdd(cnt + C_W4, 1ull)] = (int32_t)i;
+        }
+      }
     }
     if (nb != cur) chb.push((int32_t)i, cur < 0 ? -1 : rg.koff + cur, chg_i, chg_old, cnt);
   }
@@ -406,9 +525,6 @@ __global__ void __launch_bounds__(kBlock) k_yy_bounds(int64_t n, int32_t ng, con
 // has at most kLongRow entries, else from the top down (w1[n - 1 - pos], for
 // the warp-per-point recompute) -- and one with more to w2 (recomputed as a
 // whole row); each list gets one atomic per tile.
-constexpr int kTile = 8;
-constexpr int kLongRow = 256;
-
 template <bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int64_t kst,
                                                        const int64_t* __restrict__ rp,
@@ -628,14 +744,14 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt,
     int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, const float* __restrict__ cc,
     int32_t* __restrict__ w2, int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
-    unsigned long long* __restrict__ cnt) {
+    unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ cursor,
+    unsigned long long* __restrict__ w2_cnt) {
   const int lane = threadIdx.x & 31, gid = lane >> 3, gl = lane & 7;
   const unsigned gmask = 0xFFu << (8 * gid);
   const int64_t total = (int64_t)(*w1_cnt);
   __shared__ int slot_j[kBlock / 8][8];  // per group: center of each compacted lane
   int* sj = slot_j[threadIdx.x >> 3];
   unsigned long long sims = 0, changed = 0;
-  unsigned long long* cursor = cnt + C_CURSOR_R;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
   unsigned long long nxt;
   for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; slot < total;
@@ -650,7 +766,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     const int m = elk_candidates<FULL>(urow, cc + rg.ccoff + (int64_t)ai * rg.kst, ai, L, rg.k, gmask, gl, sj);
     if (m > 7) {  // not expected (the bound kernel routes such points), handled anyway
       if (gl == 0) {
-        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
+        const unsigned long long pos = atomicAdd(w2_cnt, 1ull);
         w2[pos] = i;
       }
       continue;
@@ -689,7 +805,8 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
     const int32_t* __restrict__ w1_top, const unsigned long long* __restrict__ w1_cnt,
     int32_t* __restrict__ a, float* __restrict__ lb, float* __restrict__ ub, const float* __restrict__ cc,
     int32_t* __restrict__ w2, int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
-    unsigned long long* __restrict__ cnt) {
+    unsigned long long* __restrict__ cnt, unsigned long long* __restrict__ cursor,
+    unsigned long long* __restrict__ w2_cnt) {
   constexpr int NW = kBlock / 32, CH = kLongChunk;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t total = (int64_t)(*w1_cnt);
@@ -698,7 +815,6 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
   __shared__ float tvl[NW][2][CH];      // the chunk's values
   int* sj = slot_j[warp];
   unsigned long long sims = 0, changed = 0;
-  unsigned long long* cursor = cnt + C_CURSOR_L;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nxt;
   for (int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; slot < total;
@@ -716,7 +832,7 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
     __syncwarp();
     if (m > 7) {
       if (lane == 0) {
-        const unsigned long long pos = atomicAdd(cnt + C_W2, 1ull);
+        const unsigned long long pos = atomicAdd(w2_cnt, 1ull);
         w2[pos] = i;
       }
       continue;
@@ -821,27 +937,33 @@ inline int persistent_grid(const skm_ctx* c, const void* kernel) {
 }
 
 
+// One whole-row launch.  mode 0-3 as k_rows_top2 (FP32 centers); mode 4:
+// the screened Elkan pass (FP16 centers, single runs, one pass over k).
+// cursor: the work cursor of this launch (each launch of an assignment has
+// its own).
 template <typename VT, int G, bool BATCH>
-int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
-  const void* kern = mode == 0   ? (const void*)k_rows_top2<VT, G, 0, BATCH>
-                     : mode == 1 ? (const void*)k_rows_top2<VT, G, 1, BATCH>
-                     : mode == 2 ? (const void*)k_rows_top2<VT, G, 2, BATCH>
-                                 : (const void*)k_rows_top2<VT, G, 3, BATCH>;
+int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows,
+                  int cursor) {
+  const void* kern = mode == 0   ? (const void*)k_rows_top2<VT, float, G, 0, BATCH>
+                     : mode == 1 ? (const void*)k_rows_top2<VT, float, G, 1, BATCH>
+                     : mode == 2 ? (const void*)k_rows_top2<VT, float, G, 2, BATCH>
+                     : mode == 3 ? (const void*)k_rows_top2<VT, float, G, 3, BATCH>
+                                 : (const void*)k_rows_top2<VT, __half, G, 4, BATCH>;
   int64_t g = persistent_grid(c, kern);
   if (!list && g > (nrows * 32 + kBlock - 1) / kBlock) g = (nrows * 32 + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
   const VT* v = (const VT*)c->val;
-  SKM_PROF_BEGIN(c, list ? "k_rows_top2(list)" : "k_rows_top2");
-#define SKM_ROWS(M)                                                                                              \
-  k_rows_top2<VT, G, M, BATCH><<<(unsigned)g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, \
-                                                                  c->kst, c->row_run, c->runs, list, list_cnt,     \
-                                                                  nrows, c->n, c->a, c->lb, c->ub, c->chg_i,       \
-                                                                  c->chg_old, c->cnt)
+  SKM_PROF_BEGIN(c, mode == 4 ? "k_rows_top2(screen)" : list ? "k_rows_top2(list)" : "k_rows_top2");
+#define SKM_ROWS(CT, CP, M)                                                                                        \
+  k_rows_top2<VT, CT, G, M, BATCH><<<(unsigned)g, kBlock, 0, c->st>>>(                                            \
+      c->rp, c->col, v, c->rinv, c->dlt, CP, c->k, c->kst, c->row_run, c->runs, list, list_cnt, nrows, c->n, c->a, \
+      c->lb, c->ub, c->chg_i, c->chg_old, c->cnt, c->cnt + cursor, c->escr, c->w3, c->w4)
   switch (mode) {
-    case 0: SKM_ROWS(0); break;
-    case 1: SKM_ROWS(1); break;
-    case 2: SKM_ROWS(2); break;
-    default: SKM_ROWS(3);
+    case 0: SKM_ROWS(float, c->Ct, 0); break;
+    case 1: SKM_ROWS(float, c->Ct, 1); break;
+    case 2: SKM_ROWS(float, c->Ct, 2); break;
+    case 3: SKM_ROWS(float, c->Ct, 3); break;
+    default: SKM_ROWS(__half, c->Ct16, 4);
   }
 #undef SKM_ROWS
   SKM_LAUNCHED(c);
@@ -849,19 +971,21 @@ int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long
 }
 
 template <typename VT, int G>
-int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
-  return launch_rows_b<VT, G, false>(c, mode, list, list_cnt, nrows);
+int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows,
+                int cursor) {
+  return launch_rows_b<VT, G, false>(c, mode, list, list_cnt, nrows, cursor);
 }
 
 template <typename VT>
-int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows) {
+int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows,
+                  int cursor = C_CURSOR) {
   const int k = c->k;
   // a batch walks each row's own slice 128 centers at a time
-  if (c->nruns > 0) return launch_rows_b<VT, 1, true>(c, mode, list, list_cnt, nrows);
-  if (k <= 128) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows);
-  if (k <= 256) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows);
-  if (k <= 512) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows);
-  return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows);
+  if (c->nruns > 0) return launch_rows_b<VT, 1, true>(c, mode, list, list_cnt, nrows, cursor);
+  if (k <= 128) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows, cursor);
+  if (k <= 256) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows, cursor);
+  if (k <= 512) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows, cursor);
+  return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows, cursor);
 }
 
 // Hamerly's bound pass (k_ham_bounds for the context's variant and form).
@@ -925,7 +1049,8 @@ int elkan_step_t(skm_ctx* c) {
 #define SKM_ELKR(F, B)                                                                                           \
   k_elk_recompute<VT, F, B><<<persistent_grid(c, (const void*)k_elk_recompute<VT, F, B>), kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst,     \
                                                      c->row_run, c->runs, c->w1, c->cnt + C_W1, c->a, c->lb, c->ub, \
-                                                     c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
+                                                     c->cc, c->w2, c->chg_i, c->chg_old, c->cnt,               \
+                                                     c->cnt + C_CURSOR_R, c->cnt + C_W2)
   if (batch && full) SKM_ELKR(true, true);
   else if (batch) SKM_ELKR(false, true);
   else if (full) SKM_ELKR(true, false);
@@ -937,14 +1062,41 @@ int elkan_step_t(skm_ctx* c) {
   k_elk_recompute_long<VT, F, B><<<persistent_grid(c, (const void*)k_elk_recompute_long<VT, F, B>), kBlock, 0, \
                                    c->st>>>(                                                                   \
       c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->row_run, c->runs, c->w1 + (c->n - 1),         \
-      c->cnt + C_W1L, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i, c->chg_old, c->cnt)
+      c->cnt + C_W1L, c->a, c->lb, c->ub, c->cc, c->w2, c->chg_i, c->chg_old, c->cnt, c->cnt + C_CURSOR_L,    \
+      c->cnt + C_W2)
   if (batch && full) SKM_ELKL(true, true);
   else if (batch) SKM_ELKL(false, true);
   else if (full) SKM_ELKL(true, false);
   else SKM_ELKL(false, false);
 #undef SKM_ELKL
   SKM_LAUNCHED(c);
-  return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
+  if (!c->Ct16 || batch) return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
+  // screened whole rows (FP16 centers), then the exact pass for the rows the
+  // bound left open: pairs (w3, short rows from the bottom, long ones from
+  // the top) and FP32 whole rows (w4)
+  TRY_K(assign_full_t<VT>(c, 4, c->w2, c->cnt + C_W2, 0));
+  SKM_PROF_BEGIN(c, "k_elk_recompute(screen)");
+#define SKM_ELKR2(F)                                                                                           \
+  k_elk_recompute<VT, F, false><<<persistent_grid(c, (const void*)k_elk_recompute<VT, F, false>), kBlock, 0,  \
+                                  c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->row_run, \
+                                           c->runs, c->w3, c->cnt + C_W3S, c->a, c->lb, c->ub, c->cc, c->w4,   \
+                                           c->chg_i, c->chg_old, c->cnt, c->cnt + C_CURSOR_R2, c->cnt + C_W4)
+  if (full) SKM_ELKR2(true);
+  else SKM_ELKR2(false);
+#undef SKM_ELKR2
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_elk_recompute_long(screen)");
+#define SKM_ELKL2(F)                                                                                             \
+  k_elk_recompute_long<VT, F, false><<<persistent_grid(c, (const void*)k_elk_recompute_long<VT, F, false>),     \
+                                       kBlock, 0, c->st>>>(                                                      \
+      c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->row_run, c->runs, c->w3 + (c->n - 1),           \
+      c->cnt + C_W3L, c->a, c->lb, c->ub, c->cc, c->w4, c->chg_i, c->chg_old, c->cnt, c->cnt + C_CURSOR_L2,      \
+      c->cnt + C_W4)
+  if (full) SKM_ELKL2(true);
+  else SKM_ELKL2(false);
+#undef SKM_ELKL2
+  SKM_LAUNCHED(c);
+  return assign_full_t<VT>(c, 2, c->w4, c->cnt + C_W4, 0, C_CURSOR_2);
 }
 
 template <typename VT>

@@ -335,16 +335,21 @@ __global__ void __launch_bounds__(128) k_colnorm_final(const double* __restrict_
 // Tile (bx, by), threads as dev_colnorm_part.  The dirty centers are
 // overwritten in place; red2 receives per tile and slot sum c^2, sum c'^2 and
 // sum (c - c')^2 (FP32 per thread over 32 terms -- relative error <= 36u,
-// covered by the slack of dev_drift_final).  sh: shared double[3][8][33].
+// covered by the slack of dev_drift_final).  With Ct16 (screened contexts)
+// the new values are also written rounded to FP16, and e2p receives per tile
+// and slot the FP64 sum of the squared rounding errors (each difference is
+// exact in FP32, its square exact in FP64).  sh: shared double[4][8][33].
 __device__ __forceinline__ void dev_normalize_drift(const long long* __restrict__ S64, float inv,
                                                     float* __restrict__ Ct, const double* __restrict__ nrm,
                                                     int64_t d, int64_t kst, const int32_t* __restrict__ dlist,
                                                     int nd, double* __restrict__ red2, int bx, int by,
-                                                    double (*sh)[8][33]) {
+                                                    double (*sh)[8][33], __half* __restrict__ Ct16,
+                                                    double* __restrict__ e2p) {
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int slot = by * 32 + tx;
   const int64_t t0 = (int64_t)bx * kTB;
   float sn = 0.f, so = 0.f, sd = 0.f;
+  double se = 0.0;
   if (slot < nd) {
     const int j = __ldcg(dlist + slot);
     const double nr = __ldcg(nrm + j);
@@ -355,6 +360,12 @@ __device__ __forceinline__ void dev_normalize_drift(const long long* __restrict_
       const float co = *cp;
       const float cn = empty ? co : __fmul_rn(from_fixed(S64[t * kst + j], inv), rn);
       *cp = cn;
+      if (Ct16) {
+        const __half h = __float2half_rn(cn);
+        Ct16[t * kst + j] = h;
+        const double er = (double)__fsub_rn(cn, __half2float(h));  // exact
+        se += er * er;
+      }
       const float df = cn - co;
       sn = __fmaf_rn(cn, cn, sn);
       so = __fmaf_rn(co, co, so);
@@ -364,18 +375,21 @@ __device__ __forceinline__ void dev_normalize_drift(const long long* __restrict_
   sh[0][ty][tx] = sn;
   sh[1][ty][tx] = so;
   sh[2][ty][tx] = sd;
+  sh[3][ty][tx] = se;
   __syncthreads();
   if (ty == 0 && slot < nd) {
-    double r0 = 0.0, r1 = 0.0, r2 = 0.0;
+    double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
     for (int y = 0; y < 8; ++y) {
       r0 += sh[0][y][tx];
       r1 += sh[1][y][tx];
       r2 += sh[2][y][tx];
+      r3 += sh[3][y][tx];
     }
     double* o = red2 + ((int64_t)bx * kst + slot) * 3;
     o[0] = r0;
     o[1] = r1;
     o[2] = r2;
+    if (Ct16) e2p[(int64_t)bx * kst + slot] = r3;
   }
   __syncthreads();
 }
@@ -384,11 +398,12 @@ __global__ void __launch_bounds__(256) k_normalize_drift(const long long* __rest
                                                          float* __restrict__ Ct, const double* __restrict__ nrm,
                                                          int64_t d, int64_t kst, const int32_t* __restrict__ dlist,
                                                          const unsigned long long* __restrict__ cnt,
-                                                         double* __restrict__ red2) {
-  __shared__ double sh[3][8][33];
+                                                         double* __restrict__ red2, __half* __restrict__ Ct16,
+                                                         double* __restrict__ e2p) {
+  __shared__ double sh[4][8][33];
   const int nd = (int)cnt[C_NDIRTY];
   if ((int)(blockIdx.y * 32) >= nd) return;
-  dev_normalize_drift(S64, inv, Ct, nrm, d, kst, dlist, nd, red2, blockIdx.x, blockIdx.y, sh);
+  dev_normalize_drift(S64, inv, Ct, nrm, d, kst, dlist, nd, red2, blockIdx.x, blockIdx.y, sh, Ct16, e2p);
 }
 
 // Center j (the block's first 128 threads).  Clean centers did not move:
@@ -399,11 +414,15 @@ __global__ void __launch_bounds__(256) k_normalize_drift(const long long* __rest
 //   q_dn = (D (1-e) - (|N-N'| + e)^2) / (2 N N' (1+3e))  <= 1 - cos
 // pd = rd(1 - q_up), pu = ru(1 - q_dn), q = ru(max sin over [q_dn, q_up]).
 // sh: shared double[3][128].
+// With e2c (screened contexts) also e2c[j] = the sum of the FP16 error
+// partials of the moved center (fixed order); clean centers keep theirs.
+// sh: shared double[4][128].
 __device__ __forceinline__ void dev_drift_final(const double* __restrict__ red2, int64_t nblk, int32_t k,
                                                 int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
                                                 const int32_t* __restrict__ dpos, float* __restrict__ pdn,
                                                 float* __restrict__ pup, float* __restrict__ qup,
-                                                double* __restrict__ cnorm, int j, double (*sh)[128]) {
+                                                double* __restrict__ cnorm, int j, double (*sh)[128],
+                                                const double* __restrict__ e2p, double* __restrict__ e2c) {
   if (j >= k || !__ldcg(dmark + j)) {
     if (threadIdx.x == 0) {
       pdn[j] = 1.f;
@@ -414,18 +433,20 @@ __device__ __forceinline__ void dev_drift_final(const double* __restrict__ red2,
   }
   const bool on = threadIdx.x < 128;
   const int slot = __ldcg(dpos + j);
-  double sn = 0.0, so = 0.0, sd = 0.0;
+  double sn = 0.0, so = 0.0, sd = 0.0, se = 0.0;
   if (on)
     for (int64_t b = threadIdx.x; b < nblk; b += 128) {
       const double* r = red2 + (b * kst + slot) * 3;
       sn += __ldcg(r);
       so += __ldcg(r + 1);
       sd += __ldcg(r + 2);
+      if (e2c) se += __ldcg(e2p + b * kst + slot);
     }
   if (on) {
     sh[0][threadIdx.x] = sn;
     sh[1][threadIdx.x] = so;
     sh[2][threadIdx.x] = sd;
+    sh[3][threadIdx.x] = se;
   }
   __syncthreads();
   for (int o = 64; o; o >>= 1) {
@@ -433,10 +454,12 @@ __device__ __forceinline__ void dev_drift_final(const double* __restrict__ red2,
       sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
       sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
       sh[2][threadIdx.x] += sh[2][threadIdx.x + o];
+      sh[3][threadIdx.x] += sh[3][threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    if (e2c) e2c[j] = sh[3][0];
     sn = sh[0][0];
     so = sh[1][0];
     sd = sh[2][0];
@@ -477,9 +500,10 @@ __global__ void __launch_bounds__(128) k_drift_final(const double* __restrict__ 
                                                      int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
                                                      const int32_t* __restrict__ dpos, float* __restrict__ pdn,
                                                      float* __restrict__ pup, float* __restrict__ qup,
-                                                     double* __restrict__ cnorm) {
-  __shared__ double sh[3][128];
-  dev_drift_final(red2, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, blockIdx.x, sh);
+                                                     double* __restrict__ cnorm, const double* __restrict__ e2p,
+                                                     double* __restrict__ e2c) {
+  __shared__ double sh[4][128];
+  dev_drift_final(red2, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, blockIdx.x, sh, e2p, e2c);
 }
 
 // Shared memory of dev_hsel_obj: 1024 slots per quantity (a block of fewer
@@ -497,10 +521,27 @@ struct HselShared {
 // over the other centers, hence the second value for the argmin's members).
 // Also zeroes the assignment counters for the next assignment: the last
 // reader of them (the update) is done.
+// With e2c (screened contexts): escr = E >= max_j |fp16(c_j) - c_j| (the FP64
+// sums carry a relative error below 10^-9, covered by the slack).
+__device__ __forceinline__ void dev_fp16_err_max(const double* __restrict__ e2c, int32_t k, float* __restrict__ escr,
+                                                 double* sh /* >= blockDim.x doubles */) {
+  double m = 0.0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) m = fmax(m, __ldcg(e2c + j));
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) escr[0] = __double2float_ru(sqrt(sh[0] * (1.0 + 1e-9)) * (1.0 + 1e-15));
+  __syncthreads();
+}
+
 __device__ __forceinline__ void dev_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
                                              const float* __restrict__ qup, const double* __restrict__ nrm,
                                              int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
-                                             unsigned long long* __restrict__ cnt, HselShared& S) {
+                                             unsigned long long* __restrict__ cnt, HselShared& S,
+                                             const double* __restrict__ e2c, float* __restrict__ escr) {
   if (threadIdx.x < C_ERR) cnt[threadIdx.x] = 0ull;
   for (int v = threadIdx.x; v < 1024; v += blockDim.x) {
     float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
@@ -561,6 +602,8 @@ __device__ __forceinline__ void dev_hsel_obj(const float* __restrict__ pdn, cons
     hsel[8] = one ? 0.f : S.q2[0];
     obj[0] = S.J[0];
   }
+  __syncthreads();
+  if (e2c) dev_fp16_err_max(e2c, k, escr, S.J);
 }
 
 // The same results with 256 slots for the minima and maxima (which do not
@@ -574,7 +617,8 @@ struct HselSmall {
 __device__ __forceinline__ void dev_hsel_obj_256(const float* __restrict__ pdn, const float* __restrict__ pup,
                                                  const float* __restrict__ qup, const double* __restrict__ nrm,
                                                  int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
-                                                 unsigned long long* __restrict__ cnt, HselSmall& S) {
+                                                 unsigned long long* __restrict__ cnt, HselSmall& S,
+                                                 const double* __restrict__ e2c, float* __restrict__ escr) {
   if (threadIdx.x < C_ERR) cnt[threadIdx.x] = 0ull;
   const int tid = threadIdx.x;
   float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
@@ -635,14 +679,17 @@ __device__ __forceinline__ void dev_hsel_obj_256(const float* __restrict__ pdn, 
     hsel[8] = one ? 0.f : S.q2[0];
     obj[0] = S.J[0];
   }
+  __syncthreads();
+  if (e2c) dev_fp16_err_max(e2c, k, escr, S.J);
 }
 
 __global__ void __launch_bounds__(1024) k_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
                                                    const float* __restrict__ qup, const double* __restrict__ nrm,
                                                    int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
-                                                   unsigned long long* __restrict__ cnt) {
+                                                   unsigned long long* __restrict__ cnt,
+                                                   const double* __restrict__ e2c, float* __restrict__ escr) {
   __shared__ HselShared S;
-  dev_hsel_obj(pdn, pup, qup, nrm, k, hsel, obj, cnt, S);
+  dev_hsel_obj(pdn, pup, qup, nrm, k, hsel, obj, cnt, S, e2c, escr);
 }
 
 // ------------------------------------------------------------------
@@ -711,10 +758,12 @@ __global__ void __launch_bounds__(256) k_finish_fused(int32_t k, int64_t kst, in
                                                       float* __restrict__ pup, float* __restrict__ qup,
                                                       double* __restrict__ cnorm, float* __restrict__ hsel,
                                                       double* __restrict__ obj, unsigned long long* __restrict__ cnt,
-                                                      unsigned long long* __restrict__ bar) {
+                                                      unsigned long long* __restrict__ bar, __half* __restrict__ Ct16,
+                                                      double* __restrict__ e2p, double* __restrict__ e2c,
+                                                      float* __restrict__ escr) {
   __shared__ union {
-    double part[3][8][33];
-    double fin[3][128];
+    double part[4][8][33];
+    double fin[4][128];
     HselSmall hs;
   } sm;
   __shared__ int wsum[8];
@@ -739,10 +788,11 @@ __global__ void __launch_bounds__(256) k_finish_fused(int32_t k, int64_t kst, in
   for (int slot = blockIdx.x; slot < nd; slot += gridDim.x) dev_colnorm_final(red, nblk, kst, dlist, slot, nrm, sm.fin[0]);
   if (!grid_barrier(bar, b0, 3, cnt, &ok_sh)) return;
   for (int64_t w = blockIdx.x; w < ntile; w += gridDim.x)
-    dev_normalize_drift(S64, inv, Ct, nrm, d, kst, dlist, nd, red, (int)(w % nblk), (int)(w / nblk), sm.part);
+    dev_normalize_drift(S64, inv, Ct, nrm, d, kst, dlist, nd, red, (int)(w % nblk), (int)(w / nblk), sm.part, Ct16,
+                        e2p);
   if (!grid_barrier(bar, b0, 4, cnt, &ok_sh)) return;
   for (int64_t j = blockIdx.x; j < kst; j += gridDim.x)
-    dev_drift_final(red, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, (int)j, sm.fin);
+    dev_drift_final(red, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, (int)j, sm.fin, e2p, e2c);
   // the last block to get here writes J and Hamerly's summary
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -752,7 +802,7 @@ __global__ void __launch_bounds__(256) k_finish_fused(int32_t k, int64_t kst, in
     __threadfence();
   }
   __syncthreads();
-  if (last_sh) dev_hsel_obj_256(pdn, pup, qup, nrm, k, hsel, obj, cnt, sm.hs);
+  if (last_sh) dev_hsel_obj_256(pdn, pup, qup, nrm, k, hsel, obj, cnt, sm.hs, e2c, escr);
 }
 
 // The Gram by 64 x 64 tiles: grid (ceil(k/64), ceil(k/64), nsplit), block
@@ -1256,6 +1306,47 @@ int barrier_selftest(int64_t timeout_ns, cudaStream_t st) {
   return (h & E_TIMEOUT) ? SKM_ETIMEOUT : SKM_OK;
 }
 
+// Screened contexts, after Ct was set outside a center update (initial rows,
+// skm_set_centers): the FP16 copy of every center and its rounding error.
+// Tile (blockIdx.x: 256 terms, blockIdx.y: 32 centers), threads as
+// dev_colnorm_part; e2p gets the per-tile sums, then k_ct16_final sums them
+// per center in a fixed order and takes the maximum.
+__global__ void __launch_bounds__(256) k_ct16_part(const float* __restrict__ Ct, int64_t d, int64_t kst,
+                                                   __half* __restrict__ Ct16, double* __restrict__ e2p) {
+  __shared__ double sh[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.y * 32 + tx;
+  const int64_t t0 = (int64_t)blockIdx.x * kTB;
+  double se = 0.0;
+  if (j < kst)
+    for (int64_t t = t0 + ty; t < min(d, t0 + kTB); t += 8) {
+      const float c = Ct[t * kst + j];
+      const __half h = __float2half_rn(c);
+      Ct16[t * kst + j] = h;
+      const double er = (double)__fsub_rn(c, __half2float(h));  // exact
+      se += er * er;
+    }
+  sh[ty][tx] = se;
+  __syncthreads();
+  if (ty == 0 && j < kst) {
+    double r = 0.0;
+    for (int y = 0; y < 8; ++y) r += sh[y][tx];
+    e2p[(int64_t)blockIdx.x * kst + j] = r;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_ct16_final(const double* __restrict__ e2p, int64_t nblk, int32_t k,
+                                                     int64_t kst, double* __restrict__ e2c, float* __restrict__ escr) {
+  __shared__ double sh[1024];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int64_t b = 0; b < nblk; ++b) s += e2p[b * kst + j];
+    e2c[j] = s;
+  }
+  __syncthreads();
+  dev_fp16_err_max(e2c, k, escr, sh);
+}
+
 // Blocks of the fused finishing kernel: enough for its largest phase, at most
 // what is resident at once (its blocks wait on one another); 0 if it is not
 // asked for (opt.fused_update; on the RCV-1-like workload its four grid
@@ -1283,6 +1374,19 @@ int finish_fused_grid(const skm_ctx* c) {
   return (int)(g < 1 ? 1 : g);
 }
 
+int ct16_all(skm_ctx* c) {
+  if (!c->Ct16) return SKM_OK;
+  const int64_t nblk = reduction_blocks(c->d);
+  dim3 grid((unsigned)nblk, (unsigned)((c->kst + 31) / 32));
+  SKM_PROF_BEGIN(c, "k_ct16_part");
+  k_ct16_part<<<grid, 256, 0, c->st>>>(c->Ct, c->d, c->kst, c->Ct16, c->e2p);
+  SKM_LAUNCHED(c);
+  SKM_PROF_BEGIN(c, "k_ct16_final");
+  k_ct16_final<<<1, 1024, 0, c->st>>>(c->e2p, nblk, c->k, c->kst, c->e2c, c->escr);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
 // Dirty list, norms, new centers, drift and (full variants) the center-center
 // bounds, shared by the sparse and dense paths.
 int finish_update(skm_ctx* c) {
@@ -1308,7 +1412,7 @@ int finish_update(skm_ctx* c) {
     SKM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_finish_fused, k, (int64_t)c->kst, c->d, nblk, c->fx_inv, s64_was_valid,
                                     c->n, c->dflag, c->dmark, c->dpos, c->dlist, (const long long*)c->S64, c->Ct,
                                     c->nrm, c->red, c->pdn, c->pup, c->qup, cnorm, c->hsel, c->obj, c->cnt,
-                                    c->fbar));
+                                    c->fbar, c->Ct16, c->e2p, c->e2c, c->escr));
     SKM_LAUNCHED(c);
   } else {
     SKM_PROF_BEGIN(c, "k_dirty");
@@ -1324,14 +1428,14 @@ int finish_update(skm_ctx* c) {
     SKM_LAUNCHED(c);
     SKM_PROF_BEGIN(c, "k_normalize_drift");
     k_normalize_drift<<<grid, 256, 0, c->st>>>(c->S64, c->fx_inv, c->Ct, c->nrm, c->d, c->kst, c->dlist, c->cnt,
-                                               c->red);
+                                               c->red, c->Ct16, c->e2p);
     SKM_LAUNCHED(c);
     SKM_PROF_BEGIN(c, "k_drift_final");
     k_drift_final<<<c->kst, 128, 0, c->st>>>(c->red, nblk, k, c->kst, c->d, c->dmark, c->dpos, c->pdn, c->pup,
-                                             c->qup, cnorm);
+                                             c->qup, cnorm, c->e2p, c->e2c);
     SKM_LAUNCHED(c);
     SKM_PROF_BEGIN(c, "k_hsel_obj");
-    k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj, c->cnt);
+    k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj, c->cnt, c->e2c, c->escr);
     SKM_LAUNCHED(c);
   }
   const bool hamv = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);

@@ -26,9 +26,15 @@ enum Counter {
   C_CURSOR = 7,   // next work item of k_rows_top2 (dynamic scheduling)
   C_CURSOR_R = 8,  // ... of k_elk_recompute
   C_CURSOR_L = 9,  // ... of k_elk_recompute_long
-  C_ERR = 10,     // error flags (bit field)
-  C_NDIRTY = 11,  // clusters whose sum changed in the last center update
-  C_NUM = 12
+  C_W3S = 10,     // screened whole rows left open, short rows (pair recompute, from the bottom of w3)
+  C_W3L = 11,     // ... long rows (from the top of w3)
+  C_W4 = 12,      // rows for an exact FP32 whole-row pass after the screened one
+  C_CURSOR_2 = 13,   // cursors of the second launches of an assignment: k_rows_top2,
+  C_CURSOR_R2 = 14,  // k_elk_recompute,
+  C_CURSOR_L2 = 15,  // k_elk_recompute_long
+  C_ERR = 16,     // error flags (bit field)
+  C_NDIRTY = 17,  // clusters whose sum changed in the last center update
+  C_NUM = 18
 };
 
 // Data-preparation error bits (C_ERR).
@@ -344,6 +350,11 @@ struct skm_ctx {
   float fx_scale, fx_inv;
   // centers (term-major, d x kst)
   float* Ct;        // current centers
+  __half* Ct16;     // screened whole-row passes: FP16 copy of Ct (same layout), or NULL
+  double* e2p;      // per (256-term tile, dirty slot): sum of the squared FP16 rounding errors
+  double* e2c;      // [kst] per center: |fp16(c_j) - c_j|^2 (FP64 sum of exact squares)
+  float* escr;      // [1] E >= max_j |fp16(c_j) - c_j| (rounded up, with slack)
+  int32_t* w4;      // [n] rows for the exact whole-row pass after a screened one
   long long* S64;   // exact fixed-point cluster sums (d x kst)
   int s64_valid;    // S64 matches the current labels (else: full recompute)
   int chg_fresh;    // the changed-row list belongs to the last assignment
@@ -441,6 +452,7 @@ int elkan_step(skm_ctx* c);
 // update (k_update.cu)
 int update_centers(skm_ctx* c);
 int finish_update(skm_ctx* c);
+int ct16_all(skm_ctx* c);  // Ct16, e2c and escr from the whole of Ct (after Ct was set outside an update)
 
 // dense rows (k_dense.cu, k_mma.cu)
 int dense_prep_bf16(skm_ctx* c);

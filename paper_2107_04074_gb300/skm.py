@@ -48,7 +48,7 @@ class skm_options(ctypes.Structure):
     _fields_ = [("hamerly_tight", ctypes.c_int32), ("validate", ctypes.c_int32), ("row_threshold", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("graph", ctypes.c_int32), ("graph_check", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("fused_update", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("screen", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class skm_stats(ctypes.Structure):
@@ -215,7 +215,7 @@ class KMeans:
     def __init__(self, n: int, d: int, row_ptr, col_idx, values, k: int, variant="standard", init_rows=None,
                  seed: int = 0, hamerly_tight: bool = False, row_threshold: int = 0, stream=None,
                  precision: str = "fp32", graph: bool = False, graph_check: int = 0, blocks_per_sm: int = 0,
-                 fused_update: bool = False):
+                 fused_update: bool = False, screen: bool | None = None):
         lib = load()
         host = isinstance(values, np.ndarray)
         self._keep = (row_ptr, col_idx, values)
@@ -232,6 +232,8 @@ class KMeans:
         opt.graph_check = int(graph_check)
         opt.blocks_per_sm = int(blocks_per_sm)
         opt.fused_update = 1 if fused_update else 0
+        # screen: None = the library's choice (on for Elkan with k > 128), True / False = on / off
+        opt.screen = 0 if screen is None else (1 if screen else 2)
         self.n, self.d, self.k = int(n), int(d), int(k)
         self.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         rows = None

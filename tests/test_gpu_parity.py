@@ -375,3 +375,70 @@ def test_fused_center_update_equals_separate_kernels(variant):
     assert it == len(seqs[True])
     np.testing.assert_array_equal(g.labels(), seqs[True][-1][0])
     g.close()
+
+
+@pytest.mark.parametrize("k,screen", [(37, True), (300, None), (1000, None)])
+@pytest.mark.parametrize("variant", ["elkan", "simp_elkan"])
+def test_screened_whole_rows_keep_the_standard_labels(k, screen, variant):
+    """The Elkan variants screen their whole-row recomputes against FP16
+    centers (on by default for k > 128, forced on here for k = 37): a proven
+    per-row bound decides most rows and the rest are recomputed exactly, so
+    the label sequence over a whole run equals the standard variant's; the
+    screened pass runs in every iteration after the first, and the bounds it
+    leaves hold against exact similarities."""
+    X = synth.tfidf(synth.scaled(synth.CSR_RCV1_LIKE, n=12000, d=9000, seed=29))
+    init = synth.init_rows(X.n, k, 29)
+    dev = _dev(X)
+    seqs, prof = {}, {}
+    for v in ("standard", variant):
+        km = _km(X, k, v, init, dev, **({} if v == "standard" else {"screen": screen}))
+        labs = []
+        km.profile(True)
+        for t in range(25):
+            ch = km.assign()
+            labs.append(km.labels())
+            if ch == 0 or t == 24:  # stop right after an assignment: the bounds refer to these centers
+                break
+            km.update_centers()
+        prof[v] = km.profile_read()
+        km.profile(False)
+        seqs[v] = labs
+        if v == variant:
+            C = km.centers().astype(np.float64)
+            l, u = km.bounds()
+            lab = km.labels()
+            rows = np.random.default_rng(3).choice(X.n, 800, replace=False)
+            sub = X.rows(rows)
+            Xs = sub.dense() * oracle.rinv(oracle.Data.from_csr(sub))[:, None]
+            S = Xs @ (C / np.linalg.norm(C, axis=1, keepdims=True)).T
+            assert np.all(l[rows] <= S[np.arange(len(rows)), lab[rows]] + 1e-12)
+            mask = np.ones_like(S, dtype=bool)
+            mask[np.arange(len(rows)), lab[rows]] = False
+            assert np.all(u[rows][mask] >= S[mask] - 1e-12)
+        km.close()
+    assert len(seqs[variant]) == len(seqs["standard"])
+    for a_, b_ in zip(seqs[variant], seqs["standard"]):
+        np.testing.assert_array_equal(a_, b_)
+    assert prof[variant]["k_rows_top2(screen)"][1] == len(seqs[variant]) - 1
+
+
+def test_screened_teacher_forced():
+    X = synth.tfidf(synth.scaled(synth.CSR_RCV1_LIKE, n=5000, d=6000, seed=31))
+    init = synth.init_rows(X.n, 300, 31)
+    _teacher_forced(X, 300, "elkan", init, 10, sample=1500)
+
+
+def test_screening_off_gives_the_same_run():
+    """screen off (exact FP32 whole rows) and on: identical labels and centers
+    over a whole run at k = 300."""
+    X = synth.tfidf(synth.scaled(synth.CSR_RCV1_LIKE, n=8000, d=7000, seed=33))
+    init = synth.init_rows(X.n, 300, 33)
+    dev = _dev(X)
+    out = {}
+    for scr in (False, True):
+        km = _km(X, 300, "simp_elkan", init, dev, screen=scr)
+        out[scr] = (km.run(40), km.labels(), km.centers())
+        km.close()
+    assert out[False][0] == out[True][0]
+    np.testing.assert_array_equal(out[False][1], out[True][1])
+    np.testing.assert_array_equal(out[False][2], out[True][2])
