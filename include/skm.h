@@ -131,7 +131,8 @@ typedef struct {
                               that gives up after 1 s makes the next
                               skm_assign return SKM_ETIMEOUT; destroy the
                               context then).  Results are bit-identical. */
-  int32_t screen;          /* Elkan variants on CSR data (single runs, k <= 1024):
+  int32_t screen;          /* Elkan and Hamerly variants on CSR data (single
+                              runs, k <= 1024):
                               the whole-row recomputes after the first
                               assignment screened against an FP16 copy of the
                               centers (half the bytes gathered; with k = 1000
@@ -142,8 +143,8 @@ typedef struct {
                               whose best two differ by more than
                               2 (eps_i + delta_i) takes its label from them,
                               and the other rows are recomputed exactly
-                              (labels identical either way; the Elkan bounds
-                              of screened rows are looser by eps_i).
+                              (labels identical either way; the bounds of
+                              screened rows are looser by eps_i).
                               0 (default): on for k > 128; 1: on; 2: off. */
   int32_t reserved[3];
 } skm_options;

@@ -393,9 +393,11 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
     TRY(dalloc(c, &c->w1, (size_t)n));
     TRY(dalloc(c, &c->w2, (size_t)n));
   }
-  // ---- screened whole-row passes (Elkan variants, single runs, 128 < k <= 1024)
+  // ---- screened whole-row passes (Elkan and Hamerly variants, single runs, 128 < k <= 1024)
   const int scr = c->opt.screen;  // 0 auto, 1 on, 2 off
-  if (elk && c->nruns == 0 && c->layout == SKM_CSR && k <= 1024 && (scr == 1 || (scr == 0 && k > 128))) {
+  const bool hamv = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);
+  if ((elk || hamv) && c->nruns == 0 && c->layout == SKM_CSR && k <= 1024 &&
+      (scr == 1 || (scr == 0 && k > 128))) {
     TRY(dalloc(c, &c->Ct16, (size_t)(d * kst)));
     TRY(dalloc(c, &c->e2p, (size_t)(reduction_blocks(d) * kst)));
     TRY(dalloc(c, &c->e2c, (size_t)kst));

@@ -125,6 +125,10 @@ struct RawC4<__half> {
 // pass: the pair recompute (w3) when at most 7 centers pass Elkan's test
 // against these bounds (counted from the bound row just written), else an
 // FP32 whole row (w4).
+// MODE 5 (screened Hamerly whole rows, the same bound): a row whose best two
+// FP16 similarities differ by more than 2 w_i takes the best center as its
+// label, l(i) = s^_1 - eps_i and u(i) = s^_2 + eps_i (bounds on the exact
+// similarities); any other row goes to an FP32 whole row (w4).
 // Resident blocks asked of the compiler: three (at most 80 registers, no
 // spills) up to 512 centers, two for the widest form.  Latency-bound as it is,
 // the kernel runs faster with more warps than with more registers.
@@ -150,8 +154,9 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
   unsigned long long my_changed = 0, my_sims = 0;
   ChangedBuf chb;
   // screened pass: E, and whether it is small enough for the bound (else every row goes to the exact pass)
-  const float Escr = MODE == 4 ? escr[0] : 0.f;
-  const bool scr_ok = MODE == 4 && Escr < 1e-3f;
+  constexpr bool SCR = (MODE == 4 || MODE == 5);
+  const float Escr = SCR ? escr[0] : 0.f;
+  const bool scr_ok = SCR && Escr < 1e-3f;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long nxt;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total;
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
     int j1 = INT_MAX;
     float sv[MODE == 3 ? G : 1][4];  // Yin-Yang: this lane's similarities (-inf: not live)
     bool live[MODE == 3 ? G : 1];
-    const float eps = MODE == 4 ? __fadd_ru(Escr, __fmul_ru(dl, 1.001f)) : 0.f;
+    const float eps = SCR ? __fadd_ru(Escr, __fmul_ru(dl, 1.001f)) : 0.f;
     unsigned live_cnt = 0;
     const float L3 = (MODE == 3 && cur >= 0) ? __fsub_rd(lb[i], 2.f * dl) : -INFINITY;
     for (int j0 = 0; j0 < kr; j0 += KT) {
@@ -293,6 +298,16 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
     // screened: decided (scr_dec 0), pair recompute (1) or exact whole row (2)
     int scr_dec = 0;
     float scr_l = 0.f;
+    if (MODE == 5) {
+      const float w2x = __fmul_ru(2.f, __fadd_ru(eps, dl));
+      if (scr_ok && __fsub_rd(v1, v2) > w2x) {
+        nb = j1;
+        scr_l = __fsub_rd(v1, eps);
+      } else {
+        nb = cur;
+        scr_dec = 2;
+      }
+    }
     if (MODE == 4) {
       const float w2x = __fmul_ru(2.f, __fadd_ru(eps, dl));
       if (scr_ok && __fsub_rd(v1, v2) > w2x) {
@@ -340,11 +355,19 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
       for (int o = 16; o; o >>= 1) live_cnt += __shfl_xor_sync(SKM_FULL_MASK, live_cnt, o);
     }
     if (lane == 0) {
-      if (MODE != 4 || nb >= 0) a[i] = rg.koff + nb;
+      if (!SCR || nb >= 0) a[i] = rg.koff + nb;
       my_changed += (nb != cur);
       my_sims += MODE == 3 ? (unsigned long long)live_cnt : (unsigned long long)kr;
       if (MODE >= 1 && MODE <= 3) lb[i] = __fsub_rd(v1, dl);
       if (MODE == 1) ub[i] = (kr > 1) ? __fadd_ru(ssec, dl) : -1.f;
+      if (MODE == 5) {
+        if (scr_dec == 0) {
+          lb[i] = scr_l;
+          ub[i] = (kr > 1) ? __fadd_ru(v2, eps) : -1.f;
+        } else {
+          w4[atomicAdd(cnt + C_W4, 1ull)] = (int32_t)i;
+        }
+      }
       if (MODE == 4) {
         if (scr_dec < 2 || cur >= 0) lb[i] = scr_l;
         if (scr_dec == 1) {
@@ -937,8 +960,9 @@ inline int persistent_grid(const skm_ctx* c, const void* kernel) {
 }
 
 
-// One whole-row launch.  mode 0-3 as k_rows_top2 (FP32 centers); mode 4:
-// the screened Elkan pass (FP16 centers, single runs, one pass over k).
+// One whole-row launch.  mode 0-3 as k_rows_top2 (FP32 centers); modes 4, 5:
+// the screened Elkan / Hamerly passes (FP16 centers, single runs, one pass
+// over k).
 // cursor: the work cursor of this launch (each launch of an assignment has
 // its own).
 template <typename VT, int G, bool BATCH>
@@ -948,12 +972,13 @@ int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long
                      : mode == 1 ? (const void*)k_rows_top2<VT, float, G, 1, BATCH>
                      : mode == 2 ? (const void*)k_rows_top2<VT, float, G, 2, BATCH>
                      : mode == 3 ? (const void*)k_rows_top2<VT, float, G, 3, BATCH>
-                                 : (const void*)k_rows_top2<VT, __half, G, 4, BATCH>;
+                     : mode == 4 ? (const void*)k_rows_top2<VT, __half, G, 4, BATCH>
+                                 : (const void*)k_rows_top2<VT, __half, G, 5, BATCH>;
   int64_t g = persistent_grid(c, kern);
   if (!list && g > (nrows * 32 + kBlock - 1) / kBlock) g = (nrows * 32 + kBlock - 1) / kBlock;
   if (g < 1) g = 1;
   const VT* v = (const VT*)c->val;
-  SKM_PROF_BEGIN(c, mode == 4 ? "k_rows_top2(screen)" : list ? "k_rows_top2(list)" : "k_rows_top2");
+  SKM_PROF_BEGIN(c, mode >= 4 ? "k_rows_top2(screen)" : list ? "k_rows_top2(list)" : "k_rows_top2");
 #define SKM_ROWS(CT, CP, M)                                                                                        \
   k_rows_top2<VT, CT, G, M, BATCH><<<(unsigned)g, kBlock, 0, c->st>>>(                                            \
       c->rp, c->col, v, c->rinv, c->dlt, CP, c->k, c->kst, c->row_run, c->runs, list, list_cnt, nrows, c->n, c->a, \
@@ -963,7 +988,8 @@ int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long
     case 1: SKM_ROWS(float, c->Ct, 1); break;
     case 2: SKM_ROWS(float, c->Ct, 2); break;
     case 3: SKM_ROWS(float, c->Ct, 3); break;
-    default: SKM_ROWS(__half, c->Ct16, 4);
+    case 4: SKM_ROWS(__half, c->Ct16, 4); break;
+    default: SKM_ROWS(__half, c->Ct16, 5);
   }
 #undef SKM_ROWS
   SKM_LAUNCHED(c);
@@ -1021,7 +1047,10 @@ int hamerly_step_t(skm_ctx* c) {
                                                       c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt);
   }
   SKM_LAUNCHED(c);
-  return assign_full_t<VT>(c, 1, c->w2, c->cnt + C_W2, 0);
+  if (!c->Ct16 || c->nruns > 0) return assign_full_t<VT>(c, 1, c->w2, c->cnt + C_W2, 0);
+  // screened whole rows (FP16 centers), then FP32 whole rows for the rows the bound left open
+  TRY_K(assign_full_t<VT>(c, 5, c->w2, c->cnt + C_W2, 0));
+  return assign_full_t<VT>(c, 1, c->w4, c->cnt + C_W4, 0, C_CURSOR_2);
 }
 
 template <typename VT>
