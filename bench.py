@@ -204,6 +204,17 @@ def measured_peaks(skm, torch):
     return out
 
 
+def launch_traffic(name, avg_rows):
+    """ncu DRAM bytes per launch of `name` on the RCV-1-like workload: a
+    per-launch record, or a per-row record times the launch's average rows
+    (whole-row launches treat a different number of rows each iteration)."""
+    t = recorded_traffic(name, "rcv1-like-k100")
+    if t is not None:
+        return t
+    per_row = recorded_traffic(name, "rcv1-like-k100-per-row")
+    return int(per_row * avg_rows) if per_row is not None else None
+
+
 def kernel_bytes(name, it_rows, n, d, k, nnz, variant, full_sum=True, u_width=4):
     """Compulsory (algorithmic) bytes of one launch: what any implementation
     must move between HBM and the SMs for that step, given the rows it treats.
@@ -316,7 +327,7 @@ def run_ours(args, rank, world, local):
     # value), iteration by iteration so that each launch's rows are known
     flush.fill_(1.0)
     km.reset(init)
-    prof_ms, prof_n, prof_bytes, prof_gather, prof_flops = {}, {}, {}, {}, {}
+    prof_ms, prof_n, prof_bytes, prof_gather, prof_flops, prof_rows = {}, {}, {}, {}, {}, {}
     u_width = elk_u_width(skm, n, k)
     peaks_meas = measured_peaks(skm, torch)
     upd = {"full": [0.0, 0], "incremental": [0.0, 0]}  # center update: ms, count
@@ -339,6 +350,7 @@ def run_ours(args, rank, world, local):
         for nm, (ms_k, cnt_k) in list(pa.items()) + list(pu.items()):
             prof_ms[nm] = prof_ms.get(nm, 0.0) + ms_k
             prof_n[nm] = prof_n.get(nm, 0) + cnt_k
+            prof_rows[nm] = prof_rows.get(nm, 0) + rows_of.get(nm, n) * cnt_k
             b = kernel_bytes(nm, rows_of.get(nm, n), n, d, k, nnz, variant, full_sum, u_width)
             if b is not None:
                 prof_bytes[nm] = prof_bytes.get(nm, 0) + b * cnt_k
@@ -402,7 +414,7 @@ def run_ours(args, rank, world, local):
         ach = ab / avg_s / 1e9
         roof = {"kernel": top_name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(ach / hbm_peak, 4), "peak_source": peak_src,
-                "traffic": recorded_traffic(top_name, "rcv1-like-k100"),
+                "traffic": launch_traffic(top_name, prof_rows.get(top_name, 0) / prof_n[top_name]),
                 "avg_launch_us": round(avg_s * 1e6, 2), "launches": prof_n[top_name],
                 "algorithmic_bytes_per_launch": int(ab)}
         if top_name in prof_flops and peaks_meas.get("fp32_fma_tflops"):

@@ -56,3 +56,14 @@ def test_recorded_traffic_is_dropped_when_the_source_changes(monkeypatch):
 def test_hash_covers_the_kernel_file_and_the_shared_header(kernel):
     h = bench.source_hash(kernel)
     assert len(h) == 12 and h != bench.source_hash(None)
+
+
+def test_launch_traffic_scales_a_per_row_record(monkeypatch):
+    """Whole-row launches treat a different number of rows every iteration: a
+    per-row DRAM record is scaled by the launch's average rows, a per-launch
+    record is used as it is."""
+    recs = {("k_rows_top2(list)", "rcv1-like-k100-per-row"): 1468, ("k_elk_bounds", "rcv1-like-k100"): 43620000}
+    monkeypatch.setattr(bench, "recorded_traffic", lambda name, wl: recs.get((name, wl)))
+    assert bench.launch_traffic("k_rows_top2(list)", 37000.0) == 1468 * 37000
+    assert bench.launch_traffic("k_elk_bounds", 1.0) == 43620000
+    assert bench.launch_traffic("k_unknown", 10.0) is None
