@@ -139,6 +139,7 @@ int start_from_rows(skm_ctx* c, const std::vector<int64_t>& rows) {
   SKM_CUDA_TRY(cudaStreamSynchronize(c->st));
   if (rc) return rc;
   SKM_CUDA_TRY(cudaMemsetAsync(c->a, 0xff, sizeof(int32_t) * c->n, c->st));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->hst, 0, sizeof(int32_t) * 4, c->st));
   c->have_bounds = 0;
   c->moved = 0;
   c->s64_valid = 0;
@@ -201,7 +202,7 @@ void release(skm_ctx* c) {
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
                   c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n,
                   c->exr,    c->ebc,     c->ebw,   c->rsc,    c->gdbeg,  c->gdcnt,  c->gtask,  c->fbar,
-                  c->Ct16,   c->e2p,     c->e2c,   c->escr,   c->w4};
+                  c->Ct16,   c->e2p,     c->e2c,   c->escr,   c->w4,     c->hst};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -277,6 +278,8 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_NUM, c->st));
   TRY(dalloc(c, &c->fbar, 2));
   SKM_CUDA_TRY(cudaMemsetAsync(c->fbar, 0, sizeof(unsigned long long) * 2, c->st));
+  TRY(dalloc(c, &c->hst, 4));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->hst, 0, sizeof(int32_t) * 4, c->st));
   SKM_CUDA_TRY(cudaMallocHost((void**)&c->hcnt, sizeof(unsigned long long) * C_NUM));
   SKM_CUDA_TRY(cudaMallocHost((void**)&c->hobj, sizeof(double)));
   TRY(dalloc(c, &c->rinv, (size_t)n));

@@ -129,10 +129,12 @@ struct RawC4<__half> {
 // FP16 similarities differ by more than 2 w_i takes the best center as its
 // label, l(i) = s^_1 - eps_i and u(i) = s^_2 + eps_i (bounds on the exact
 // similarities); any other row goes to an FP32 whole row (w4).
-// Resident blocks asked of the compiler: three (at most 80 registers, no
-// spills) up to 512 centers, two for the widest form.  Latency-bound as it is,
-// the kernel runs faster with more warps than with more registers.
-constexpr int rows_min_blocks(int G) { return G >= 8 ? 2 : 3; }
+// Resident blocks asked of the compiler: two (128 registers, no spills).
+// Latency-bound as it is, the kernel runs faster with more gathers in flight
+// than with more warps: at 128 centers, 16 row entries per warp with 16 warps
+// per SM beat 8 entries with 24 warps (9 % per pass), and at 256 and 512
+// centers two blocks without spills beat three with them (2-4 % per run).
+constexpr int rows_min_blocks(int) { return 2; }
 
 template <typename VT, typename CT, int G, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
@@ -145,9 +147,10 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
     unsigned long long* __restrict__ cursor, const float* __restrict__ escr, int32_t* __restrict__ w3,
     int32_t* __restrict__ w4) {
   constexpr int KT = 128 * G;                     // centers per pass over the row
-  // row entries batched per step (their gathers in flight together): twice
-  // as many with FP16 centers, whose raw loads take half the registers
-  constexpr int NB = (sizeof(CT) == 2 ? 2 : 1) * (G >= 8 ? 1 : 8 / G);
+  // row entries batched per step (their gathers in flight together): 16 for
+  // one group of centers; for wider forms, twice as many with FP16 centers,
+  // whose raw loads take half the registers
+  constexpr int NB = G == 1 ? 16 : (sizeof(CT) == 2 ? 2 : 1) * (G >= 8 ? 1 : 8 / G);
   using Raw = RawC4<CT>;
   const int lane = threadIdx.x & 31;
   const int64_t total = list ? (int64_t)(*list_cnt) : nrows;
@@ -399,8 +402,12 @@ __global__ void __launch_bounds__(kBlock) k_ham_bounds(int64_t n, const int32_t*
                                                        const float* __restrict__ pup, const float* __restrict__ qup,
                                                        const float* __restrict__ hsel, const float* __restrict__ sc,
                                                        const int32_t* __restrict__ row_run, int tight, int moved,
-                                                       int32_t* __restrict__ w1, unsigned long long* __restrict__ cnt) {
+                                                       const int32_t* __restrict__ hst, int32_t* __restrict__ w1,
+                                                       int32_t* __restrict__ w2, unsigned long long* __restrict__ cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // tightening skipped this iteration: the survivors go to the whole-row list
+  // at once (and are still counted as survivors)
+  const bool skip_t = hst[0] != 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
     const int64_t i = base + threadIdx.x;
     bool take = false;
@@ -423,7 +430,13 @@ __global__ void __launch_bounds__(kBlock) k_ham_bounds(int64_t n, const int32_t*
       const bool prune = (L >= u) || (FULL && L >= 0.f && L >= sc[ai]);
       take = !prune;
     }
-    warp_push(take, (int32_t)i, w1, cnt + C_W1);
+    if (skip_t) {
+      warp_push(take, (int32_t)i, w2, cnt + C_W2);
+      const unsigned m = __ballot_sync(SKM_FULL_MASK, take);
+      if ((threadIdx.x & 31) == 0 && m) atomicAdd(cnt + C_W1, (unsigned long long)__popc(m));
+    } else {
+      warp_push(take, (int32_t)i, w1, cnt + C_W1);
+    }
   }
 }
 
@@ -431,16 +444,29 @@ __global__ void __launch_bounds__(kBlock) k_ham_bounds(int64_t n, const int32_t*
 // warp-cooperative canonical similarity, then the test again; the points still
 // failing go to `out`.  Each warp walks 8 consecutive survivors and pushes its
 // failures with one atomic.
+// Tightening costs a fraction of a whole row per survivor (about 0.4 of one
+// at 128 centers or fewer, less beyond) and pays only for the survivors it
+// prunes.  When Hamerly's single bound fails for nearly every point (one
+// center that moves far loosens every u), it prunes almost none, so the last
+// block to finish decides for the next iteration: if fewer than `thr` of at
+// least 1024 tightened survivors were pruned, the next iterations send their
+// survivors straight to the whole-row pass (hst[0] = 1), tightening again
+// every kTightProbe-th iteration to re-measure.  Labels do not depend on it
+// (the whole row computes <x, c_a> too); the similarity count does.
+// hst: [0] skip this iteration, [1] iterations skipped in a row, [2] blocks done.
+constexpr int kTightProbe = 8;
+
 template <typename VT, bool FULL>
 __global__ void __launch_bounds__(kBlock) k_ham_tighten(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const VT* __restrict__ val,
     const float* __restrict__ rinv, const float* __restrict__ dlt, const float* __restrict__ Ct, int64_t kst,
     const int32_t* __restrict__ w1, const unsigned long long* __restrict__ w1_cnt, const int32_t* __restrict__ a,
     float* __restrict__ lb, const float* __restrict__ ub, const float* __restrict__ sc, int32_t* __restrict__ out,
-    unsigned long long* __restrict__ cnt) {
+    unsigned long long* __restrict__ cnt, int32_t* __restrict__ hst, float thr) {
   constexpr int TP = 8;
   const int lane = threadIdx.x & 31;
-  const int64_t total = (int64_t)(*w1_cnt);
+  const bool skip_t = hst[0] != 0;
+  const int64_t total = skip_t ? 0 : (int64_t)(*w1_cnt);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long sims = 0;
   for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * TP < total; tile += nw) {
@@ -470,6 +496,23 @@ __global__ void __launch_bounds__(kBlock) k_ham_tighten(
     warp_push((keep >> lane) & 1u, my_i, out, cnt + C_W2);
   }
   if (lane == 0 && sims) atomicAdd(cnt + C_SIMS, sims);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(reinterpret_cast<unsigned*>(hst + 2), 1u);
+    if (done == gridDim.x - 1) {  // the last block: every push and count is in
+      __threadfence();
+      if (!skip_t) {
+        const unsigned long long t = *reinterpret_cast<volatile unsigned long long*>(cnt + C_W1);
+        const unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(cnt + C_W2);
+        hst[0] = (t >= 1024 && (double)(t - w) < (double)thr * (double)t) ? 1 : 0;
+        hst[1] = 0;
+      } else if (++hst[1] >= kTightProbe - 1) {
+        hst[0] = 0;
+      }
+      hst[2] = 0;
+    }
+  }
 }
 
 // --------------------------------------------------------------- Elkan
@@ -1020,7 +1063,7 @@ int ham_bounds_launch(skm_ctx* c) {
 #define SKM_HAMB(F, B)                                                                                            \
   k_ham_bounds<F, B><<<persistent_grid(c, (const void*)k_ham_bounds<F, B>), kBlock, 0, c->st>>>(                  \
       c->n, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->hsel, c->sc, c->row_run, c->opt.hamerly_tight, \
-      c->moved, c->w1, c->cnt)
+      c->moved, c->hst, c->w1, c->w2, c->cnt)
   SKM_PROF_BEGIN(c, "k_ham_bounds");
   if (full && batch) SKM_HAMB(true, true);
   else if (full) SKM_HAMB(true, false);
@@ -1038,13 +1081,16 @@ int hamerly_step_t(skm_ctx* c) {
   if (rc) return rc;
   const int g = persistent_grid(c, full ? (const void*)k_ham_tighten<VT, true> : (const void*)k_ham_tighten<VT, false>);
   const VT* v = (const VT*)c->val;
+  const float thr = (c->nruns > 0 ? c->kmax : c->k) <= 128 ? 0.4f : 0.15f;
   SKM_PROF_BEGIN(c, "k_ham_tighten");
   if (full) {
     k_ham_tighten<VT, true><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1,
-                                                     c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt);
+                                                     c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt,
+                                                     c->hst, thr);
   } else {
     k_ham_tighten<VT, false><<<g, kBlock, 0, c->st>>>(c->rp, c->col, v, c->rinv, c->dlt, c->Ct, c->kst, c->w1,
-                                                      c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt);
+                                                      c->cnt + C_W1, c->a, c->lb, c->ub, c->sc, c->w2, c->cnt,
+                                                      c->hst, thr);
   }
   SKM_LAUNCHED(c);
   if (!c->Ct16 || c->nruns > 0) return assign_full_t<VT>(c, 1, c->w2, c->cnt + C_W2, 0);

@@ -216,13 +216,20 @@ __global__ void k_dense_centers(const float* __restrict__ Ct, int64_t d, int32_t
 }
 
 // FP32 GEMM with fused top-2.  CTA: 128 rows x all centers (tiles of 128),
-// 256 threads (16 x 16), each thread 8 rows x 8 centers, K in chunks of 32
+// 256 threads (16 x 16), each thread 8 rows x 8 centers (trow: two runs of 4,
+// 64 apart, so that the 16 threads of a row group read consecutive 16-byte
+// words of a shared-memory tile row, free of bank conflicts), K in chunks of 32
 // through shared memory, double-buffered: the asynchronous copies of the next
 // chunk (4-byte cp.async into the transposed tiles, zero-filled outside the
 // data) are in flight while this one is multiplied.  Rows: all (list ==
 // nullptr) or list[0..*list_cnt).  MODE 0: labels only; MODE 1: also
-// Hamerly's l = s1 - delta, u = s2 + delta.
+// Hamerly's l = s1 - delta, u = s2 + delta.  Two blocks per SM (128
+// registers): the running top-2 of each thread's rows lives in shared memory.
 constexpr int kTR = 128, kTC = 128, kKC = 32;
+
+// The tile row (or center) of a thread's x-th row: 4 consecutive ones at
+// 4 g, then 4 more at 64 + 4 g.
+__device__ __forceinline__ int trow(int g, int x) { return (x < 4 ? 0 : 60) + g * 4 + x; }
 constexpr size_t kDenseSmem = sizeof(float) * 2 * kKC * (kTR + 4) * 2;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool in) {
@@ -232,18 +239,26 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool in)
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X, const float* __restrict__ rinv,
-                                                    const float* __restrict__ dlt, const float* __restrict__ Cr,
-                                                    int64_t n, int64_t d, int32_t k, const int32_t* __restrict__ list,
-                                                    const unsigned long long* __restrict__ list_cnt,
-                                                    int64_t few_limit, int32_t* __restrict__ a,
-                                                    float* __restrict__ lb, float* __restrict__ ub,
-                                                    int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
-                                                    unsigned long long* __restrict__ cnt) {
+__global__ void __launch_bounds__(256, 2) k_dense_top2(const float* __restrict__ X, const float* __restrict__ rinv,
+                                                       const float* __restrict__ dlt, const float* __restrict__ Cr,
+                                                       int64_t n, int64_t d, int32_t k,
+                                                       const int32_t* __restrict__ list,
+                                                       const unsigned long long* __restrict__ list_cnt,
+                                                       int64_t few_limit, int32_t* __restrict__ a,
+                                                       float* __restrict__ lb, float* __restrict__ ub,
+                                                       int32_t* __restrict__ chg_i, int32_t* __restrict__ chg_old,
+                                                       unsigned long long* __restrict__ cnt) {
   extern __shared__ __align__(16) float dense_smem[];
   float(*As)[kKC][kTR + 4] = reinterpret_cast<float(*)[kKC][kTR + 4]>(dense_smem);                      // [2]
   float(*Bs)[kKC][kTC + 4] = reinterpret_cast<float(*)[kKC][kTC + 4]>(dense_smem + 2 * kKC * (kTR + 4));  // [2]
-  __shared__ int rows_sh[kTR];
+  // per tile row: its index, current label and 1/|x|; per thread and row of
+  // its 8: the running top-2 over the center tiles done so far and the
+  // current label's similarity (kept here, not in registers, so that two
+  // blocks fit on an SM)
+  __shared__ int rows_sh[kTR], cur_sh[kTR];
+  __shared__ float ri_sh[kTR];
+  __shared__ float tv1[8][256], tv2[8][256], tvc[8][256];
+  __shared__ int tj1[8][256];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4, lane = tid & 31;
   const int64_t total = list ? (int64_t)(*list_cnt) : n;
   if (list && total <= few_limit) return;  // k_dense_rows_few takes short lists
@@ -253,19 +268,17 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
     __syncthreads();
     if (tid < kTR) {
       const int64_t q = tile * kTR + tid;
-      rows_sh[tid] = (q < total) ? (list ? list[q] : (int32_t)q) : -1;
+      const int32_t row = (q < total) ? (list ? list[q] : (int32_t)q) : -1;
+      rows_sh[tid] = row;
+      cur_sh[tid] = row >= 0 ? a[row] : -1;
+      ri_sh[tid] = row >= 0 ? rinv[row] : 0.f;
     }
-    __syncthreads();
-    int32_t myrow[8], cur[8];
-    float v1[8], v2[8], vc[8];
-    int j1[8];
 #pragma unroll
     for (int x = 0; x < 8; ++x) {
-      myrow[x] = rows_sh[ty * 8 + x];
-      cur[x] = myrow[x] >= 0 ? a[myrow[x]] : -1;
-      v1[x] = v2[x] = vc[x] = -INFINITY;
-      j1[x] = INT_MAX;
+      tv1[x][tid] = tv2[x][tid] = tvc[x][tid] = -INFINITY;
+      tj1[x][tid] = INT_MAX;
     }
+    __syncthreads();
     // chunks ci = (center tile, term chunk) in order; chunk ci + 1 is copied
     // while chunk ci is multiplied
     const int nkc = (int)((d + kKC - 1) / kKC), nct = (k + kTC - 1) / kTC, nch = nkc * nct;
@@ -299,10 +312,10 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
       }
 #pragma unroll 4
       for (int kk = 0; kk < kKC; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[sb][kk][ty * 8]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&As[sb][kk][ty * 8 + 4]);
-        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[sb][kk][tx * 8]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[sb][kk][tx * 8 + 4]);
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[sb][kk][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[sb][kk][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[sb][kk][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[sb][kk][64 + tx * 4]);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
         const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -316,64 +329,71 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
       // fold this center tile into the running top-2 of each row
 #pragma unroll
       for (int x = 0; x < 8; ++x) {
-        const float ri = myrow[x] >= 0 ? rinv[myrow[x]] : 0.f;
+        const float ri = ri_sh[trow(ty, x)];
+        const int cur = cur_sh[trow(ty, x)];
+        float v1 = tv1[x][tid], v2 = tv2[x][tid], vc = tvc[x][tid];
+        int j1 = tj1[x][tid];
 #pragma unroll
         for (int y = 0; y < 8; ++y) {
-          const int j = j0 + tx * 8 + y;
+          const int j = j0 + trow(tx, y);
           if (j < k) {
             const float s = __fmul_rn(acc[x][y], ri);
-            if (j == cur[x]) vc[x] = s;
-            if (s > v1[x]) {  // j ascends within a thread: ties keep the lowest index
-              v2[x] = v1[x];
-              v1[x] = s;
-              j1[x] = j;
-            } else if (s > v2[x]) {
-              v2[x] = s;
+            if (j == cur) vc = s;
+            if (s > v1) {  // j ascends within a thread: ties keep the lowest index
+              v2 = v1;
+              v1 = s;
+              j1 = j;
+            } else if (s > v2) {
+              v2 = s;
             }
           }
         }
+        tv1[x][tid] = v1;
+        tv2[x][tid] = v2;
+        tvc[x][tid] = vc;
+        tj1[x][tid] = j1;
       }
     }
     // merge across the 16 threads that share these rows (lanes of one half-warp)
-#pragma unroll
+#pragma unroll 1
     for (int x = 0; x < 8; ++x) {
+      float v1 = tv1[x][tid], v2 = tv2[x][tid], vc = tvc[x][tid];
+      int j1 = tj1[x][tid];
 #pragma unroll
       for (int o = 8; o; o >>= 1) {
-        const float ov1 = __shfl_xor_sync(SKM_FULL_MASK, v1[x], o);
-        const int oj1 = __shfl_xor_sync(SKM_FULL_MASK, j1[x], o);
-        const float ov2 = __shfl_xor_sync(SKM_FULL_MASK, v2[x], o);
-        if (ov1 > v1[x] || (ov1 == v1[x] && oj1 < j1[x])) {
-          v2[x] = fmaxf(ov2, v1[x]);
-          v1[x] = ov1;
-          j1[x] = oj1;
+        const float ov1 = __shfl_xor_sync(SKM_FULL_MASK, v1, o);
+        const int oj1 = __shfl_xor_sync(SKM_FULL_MASK, j1, o);
+        const float ov2 = __shfl_xor_sync(SKM_FULL_MASK, v2, o);
+        if (ov1 > v1 || (ov1 == v1 && oj1 < j1)) {
+          v2 = fmaxf(ov2, v1);
+          v1 = ov1;
+          j1 = oj1;
         } else {
-          v2[x] = fmaxf(v2[x], ov1);
+          v2 = fmaxf(v2, ov1);
         }
-        vc[x] = fmaxf(vc[x], __shfl_xor_sync(SKM_FULL_MASK, vc[x], o));
+        vc = fmaxf(vc, __shfl_xor_sync(SKM_FULL_MASK, vc, o));
       }
-    }
-#pragma unroll
-    for (int x = 0; x < 8; ++x) {
-      const int32_t row = myrow[x];
+      const int32_t row = rows_sh[trow(ty, x)];
+      const int32_t cur = cur_sh[trow(ty, x)];
       int32_t nb = -1;
       bool moved = false;
       if (row >= 0) {
         float ssec;
-        if (cur[x] >= 0 && vc[x] == v1[x]) {
-          nb = cur[x];
-          ssec = (j1[x] == cur[x]) ? v2[x] : v1[x];
+        if (cur >= 0 && vc == v1) {
+          nb = cur;
+          ssec = (j1 == cur) ? v2 : v1;
         } else {
-          nb = j1[x];
-          ssec = v2[x];
+          nb = j1;
+          ssec = v2;
         }
-        moved = (nb != cur[x]);
+        moved = (nb != cur);
         if (tx == 0) {
           a[row] = nb;
           changed += moved;
           sims += (unsigned long long)k;
           const float dl = dlt[row];
           if (MODE == 1) {
-            lb[row] = __fsub_rd(v1[x], dl);
+            lb[row] = __fsub_rd(v1, dl);
             ub[row] = (k > 1) ? __fadd_ru(ssec, dl) : -1.f;
           }
         }
@@ -389,7 +409,7 @@ __global__ void __launch_bounds__(256) k_dense_top2(const float* __restrict__ X,
         if (take) {
           const unsigned long long pos = base + __popc(m & ((1u << lane) - 1u));
           chg_i[pos] = row;
-          chg_old[pos] = cur[x];
+          chg_old[pos] = cur;
         }
       }
     }

@@ -336,6 +336,7 @@ struct skm_ctx {
   float* dlt;          // [n] delta_i: bound on the FP32 error of a similarity of row i
   int64_t* t_ptr;      // [d+1] term-major (CSC) offsets
   int32_t* t_row;      // [nnz]
+  int32_t* hst;        // [4] Hamerly: skip tightening this iteration, iterations skipped, blocks done
   void* t_val;         // [nnz] dtype
   int64_t nchunks;     // center-sum work items
   int32_t* ch_term;    // [nchunks]
