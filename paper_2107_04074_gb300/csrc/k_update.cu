@@ -272,15 +272,26 @@ __device__ __forceinline__ void dev_colnorm_part(const long long* __restrict__ S
   float s = 0.f, comp = 0.f;
   if (slot < nd) {
     const int j = __ldcg(dlist + slot);
-    for (int64_t t = t0 + ty; t < min(d, t0 + kTB); t += 8) {
-      const float v = from_fixed(S64[t * kst + j], inv);
+    const int64_t tend = min(d, t0 + kTB);
+    auto add = [&](long long raw) {
+      const float v = from_fixed(raw, inv);
       const float sq = __fmul_rn(v, v);
       const float err_sq = __fmaf_rn(v, v, -sq);  // exact low part of v*v
       const float ns = __fadd_rn(s, sq);
       comp += (fabsf(s) >= fabsf(sq)) ? ((s - ns) + sq) : ((sq - ns) + s);
       comp += err_sq;
       s = ns;
+    };
+    int64_t t = t0 + ty;
+    // eight loads in flight, then the sums in the same order
+    for (; t + 56 < tend; t += 64) {
+      long long raw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) raw[u] = S64[(t + 8 * u) * kst + j];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) add(raw[u]);
     }
+    for (; t < tend; t += 8) add(S64[t * kst + j]);
   }
   sh[ty][tx] = (double)s + (double)comp;
   __syncthreads();
@@ -355,11 +366,10 @@ __device__ __forceinline__ void dev_normalize_drift(const long long* __restrict_
     const double nr = __ldcg(nrm + j);
     const bool empty = !(nr > 0.0);
     const float rn = empty ? 0.f : (float)(1.0 / nr);
-    for (int64_t t = t0 + ty; t < min(d, t0 + kTB); t += 8) {
-      float* cp = Ct + t * kst + j;
-      const float co = *cp;
-      const float cn = empty ? co : __fmul_rn(from_fixed(S64[t * kst + j], inv), rn);
-      *cp = cn;
+    const int64_t tend = min(d, t0 + kTB);
+    auto step = [&](int64_t t, float co, long long raw) {
+      const float cn = empty ? co : __fmul_rn(from_fixed(raw, inv), rn);
+      Ct[t * kst + j] = cn;
       if (Ct16) {
         const __half h = __float2half_rn(cn);
         Ct16[t * kst + j] = h;
@@ -370,7 +380,21 @@ __device__ __forceinline__ void dev_normalize_drift(const long long* __restrict_
       sn = __fmaf_rn(cn, cn, sn);
       so = __fmaf_rn(co, co, so);
       sd = __fmaf_rn(df, df, sd);
+    };
+    int64_t t = t0 + ty;
+    // eight terms' loads in flight, then the updates in the same order
+    for (; t + 56 < tend; t += 64) {
+      float co[8];
+      long long raw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        co[u] = Ct[(t + 8 * u) * kst + j];
+        raw[u] = S64[(t + 8 * u) * kst + j];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) step(t + 8 * u, co[u], raw[u]);
     }
+    for (; t < tend; t += 8) step(t, Ct[t * kst + j], S64[t * kst + j]);
   }
   sh[0][ty][tx] = sn;
   sh[1][ty][tx] = so;
