@@ -340,6 +340,41 @@ def test_long_rows_elkan(variant):
     std.close()
 
 
+@pytest.mark.parametrize("variant", ["hamerly", "simp_hamerly"])
+def test_hamerly_tightening_schedule_keeps_labels(mid, variant):
+    """Where tightening prunes almost nothing, Hamerly's survivors go straight
+    to the whole-row pass, with tightening again every 8th iteration.  The
+    labels equal the standard variant's at every iteration, and the counters
+    show both kinds of iteration: with at least 1024 survivors, a skipped one
+    computes only whole rows (sims = rechecks k), a tightened one also one
+    similarity per survivor (sims = survivors + rechecks k)."""
+    k = 100
+    init = synth.init_rows(mid.n, k, 2)
+    dev = _dev(mid)
+    std = _km(mid, k, "standard", init, dev)
+    ham = _km(mid, k, variant, init, dev)
+    skipped = tightened = 0
+    for it in range(40):
+        cs = std.assign()
+        ch = ham.assign()
+        assert ch == cs
+        np.testing.assert_array_equal(ham.labels(), std.labels())
+        st = ham.stats()
+        if it > 0 and st.last_survivors >= 1024:
+            if st.last_sims == st.last_rechecks * k:
+                skipped += 1
+            else:
+                assert st.last_sims == st.last_survivors + st.last_rechecks * k
+                tightened += 1
+        if cs == 0:
+            break
+        std.update_centers()
+        ham.update_centers()
+    std.close()
+    ham.close()
+    assert skipped > 0 and tightened > 1
+
+
 @pytest.mark.parametrize("variant", ["standard", "hamerly", "elkan", "simp_elkan"])
 def test_fused_center_update_equals_separate_kernels(variant):
     """The center update's phases after the sums run as one cooperative
