@@ -146,7 +146,16 @@ typedef struct {
                               (labels identical either way; the bounds of
                               screened rows are looser by eps_i).
                               0 (default): on for k > 128; 1: on; 2: off. */
-  int32_t reserved[3];
+  int32_t k_tile;          /* centers per pass of the whole-row kernel (single
+                              CSR runs, every variant but Yin-Yang): 0
+                              (default) = the smallest of 128, 256, 512, 1024
+                              that holds k; else one of those four, and a
+                              row is walked once per tile of centers (fewer
+                              registers per pass).  Results do not depend on
+                              it; skm_autotune chooses it.  Other values, or
+                              a nonzero value for a batch or Yin-Yang:
+                              SKM_EINVAL / SKM_EUNSUPPORTED. */
+  int32_t reserved[2];
 } skm_options;
 
 /* Counters of the last assignment and of the run so far. */
@@ -262,14 +271,20 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
                    int32_t variant, const int64_t* init_rows, uint64_t seed, const skm_options* opt,
                    void* stream);
 
-/* Choose the launch configuration of the persistent bound and recompute
- * kernels (blocks per SM) and the Elkan whole-row threshold for this
- * context's shape by timing `iters` iterations per candidate from the
- * initial centers (results do not depend on the choice), then restore the
- * initial state.  The choice is kept in the text file cache_path (one line
- * per device and shape bucket) when cache_path is not NULL, and read from
- * it instead of timing when the bucket is already there.  *from_cache (may
- * be NULL) tells which happened. */
+/* Choose, for this context's shape, by timing `iters` iterations per
+ * candidate from the initial centers (results do not depend on the choice):
+ * the launch configuration of the persistent bound and recompute kernels
+ * (4, 8 or 16 blocks per SM) with the Elkan whole-row threshold (auto, 2,
+ * 7); then, for single CSR runs but Yin-Yang, the whole-row kernel's tile of
+ * centers (the default one or up to two smaller ones, opt.k_tile); then,
+ * where the context keeps FP16 centers (opt.screen), whether the screened
+ * whole-row pass is used.  A coordinate search: each stage keeps the best of
+ * the previous ones.  The initial state is restored afterwards.  The choice
+ * is kept in the text file cache_path (one line per device and shape bucket:
+ * key, blocks per SM, threshold, tile, screen off) when cache_path is not
+ * NULL, and read from it instead of timing when the bucket is already there
+ * (lines with only the first two values are read with the defaults for the
+ * others).  *from_cache (may be NULL) tells which happened. */
 int skm_autotune(skm_ctx* ctx, const char* cache_path, int32_t iters, int32_t* from_cache);
 
 /* Spherical k-means++ seeding (Section 5.6) of a context's centers: the

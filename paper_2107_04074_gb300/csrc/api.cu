@@ -457,6 +457,17 @@ int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const
   c->dtype = x->dtype;
   if (opt) c->opt = *opt;
   else skm_default_options(&c->opt);
+  {
+    const int kt = c->opt.k_tile;
+    if (kt != 0 && kt != 128 && kt != 256 && kt != 512 && kt != 1024) {
+      delete c;
+      return SKM_EINVAL;
+    }
+    if (kt != 0 && (variant == SKM_YINYANG || x->layout != SKM_CSR)) {
+      delete c;
+      return SKM_EUNSUPPORTED;
+    }
+  }
   if (x->layout == SKM_DENSE) {
     if (x->dtype != SKM_F32 || variant == SKM_ELKAN || variant == SKM_SIMP_ELKAN) {
       delete c;
@@ -491,6 +502,7 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
   if (!out) return SKM_EINVAL;
   *out = nullptr;
   if (!x || !run_rows || !ks || nruns < 1 || x->n < 1 || x->d < 1 || x->reserved != 0) return SKM_EINVAL;
+  if (opt && opt->k_tile != 0) return SKM_EUNSUPPORTED;  // a batch walks every run's slice 128 centers at a time
   if (x->layout != SKM_CSR) return SKM_EUNSUPPORTED;
   if (variant < SKM_STANDARD || variant > SKM_YINYANG) return SKM_EINVAL;
   if (variant == SKM_YINYANG) return SKM_EUNSUPPORTED;
@@ -981,9 +993,11 @@ int skm_autotune(skm_ctx* c, const char* cache_path, int32_t iters, int32_t* fro
   for (char* q = key; *q; ++q)
     if (*q == ' ') *q = '_';
   const bool elk = (c->variant == SKM_ELKAN || c->variant == SKM_SIMP_ELKAN);
-  auto apply = [&](int32_t bpsm, int32_t thr) -> int {
+  auto apply = [&](int32_t bpsm, int32_t thr, int32_t kt, int32_t so) -> int {
     c->opt.blocks_per_sm = bpsm;
     c->opt.row_threshold = thr;
+    c->opt.k_tile = kt;
+    c->scr_off = so;
     if (c->nruns > 0) {
       auto& R = *static_cast<std::vector<RunDesc>*>(c->hruns);
       for (auto& r : R) {
@@ -998,61 +1012,84 @@ int skm_autotune(skm_ctx* c, const char* cache_path, int32_t iters, int32_t* fro
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "r")) {
       char line[512];
-      int found = 0, bp = 0, th = 0;
+      int found = 0, bp = 0, th = 0, kt = 0, so = 0;
       while (std::fgets(line, sizeof(line), f)) {
         char k2[320];
-        int b2, t2;
-        if (std::sscanf(line, "%319s %d %d", k2, &b2, &t2) == 3 && std::strcmp(k2, key) == 0) {
+        int b2, t2, k3 = 0, s3 = 0;
+        const int nf = std::sscanf(line, "%319s %d %d %d %d", k2, &b2, &t2, &k3, &s3);
+        if (nf >= 3 && std::strcmp(k2, key) == 0) {
           found = 1;
           bp = b2;
           th = t2;
+          kt = nf >= 4 ? k3 : 0;
+          so = nf >= 5 ? s3 : 0;
         }
       }
       std::fclose(f);
       if (found) {
-        TRY(apply(bp, th));
+        TRY(apply(bp, th, kt, so));
         if (from_cache) *from_cache = 1;
         return SKM_OK;
       }
     }
   }
   const std::vector<int64_t> init = *static_cast<std::vector<int64_t>*>(c->hinit);
-  const int32_t bps[3] = {4, 8, 16};  // blocks per SM of the persistent kernels, capped at what is resident
-  const int32_t thrs[3] = {0, 2, 7};
-  const int nthr = elk ? 3 : 1;
   cudaEvent_t e0, e1;
   SKM_CUDA_TRY(cudaEventCreate(&e0));
   SKM_CUDA_TRY(cudaEventCreate(&e1));
-  float best = INFINITY;
-  int32_t bb = 8, bt = 0;
+  // time `iters` iterations from the initial centers under a setting
+  auto timed = [&](int32_t bpsm, int32_t thr, int32_t kt, int32_t so, float* ms) -> int {
+    TRY(apply(bpsm, thr, kt, so));
+    TRY(start_from_rows(c, init));
+    cudaEventRecord(e0, c->st);
+    int rc = SKM_OK;
+    for (int32_t it = 0; it < iters && rc == SKM_OK; ++it) {
+      rc = skm_assign(c, nullptr);
+      if (rc == SKM_OK) rc = skm_update_centers(c, nullptr);
+    }
+    cudaEventRecord(e1, c->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = SKM_ECUDA;
+    if (rc == SKM_OK) cudaEventElapsedTime(ms, e0, e1);
+    return rc;
+  };
+  // coordinate search: launch shape x Elkan whole-row threshold, then the
+  // whole-row kernel's tile of centers (single CSR runs but Yin-Yang: the
+  // default tile and up to two smaller ones), then the screened pass on or off
+  // (where the context keeps the FP16 centers)
+  const int32_t bps[3] = {4, 8, 16};  // blocks per SM of the persistent kernels, capped at what is resident
+  const int32_t thrs[3] = {0, 2, 7};
+  const int nthr = elk ? 3 : 1;
+  float best = INFINITY, ms = 0.f;
+  int32_t bb = 8, bt = 0, bk = 0, bs = 0;
   int rc = SKM_OK;
   for (int a = 0; a < 3 && rc == SKM_OK; ++a)
-    for (int b = 0; b < nthr && rc == SKM_OK; ++b) {
-      if ((rc = apply(bps[a], thrs[b])) != SKM_OK) break;
-      if ((rc = start_from_rows(c, init)) != SKM_OK) break;
-      cudaEventRecord(e0, c->st);
-      for (int32_t it = 0; it < iters && rc == SKM_OK; ++it) {
-        rc = skm_assign(c, nullptr);
-        if (rc == SKM_OK) rc = skm_update_centers(c, nullptr);
-      }
-      cudaEventRecord(e1, c->st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = SKM_ECUDA;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rc == SKM_OK && ms < best) {
+    for (int b = 0; b < nthr && rc == SKM_OK; ++b)
+      if ((rc = timed(bps[a], thrs[b], 0, 0, &ms)) == SKM_OK && ms < best) {
         best = ms;
         bb = bps[a];
         bt = thrs[b];
       }
-    }
+  if (rc == SKM_OK && c->nruns == 0 && c->layout == SKM_CSR && c->variant != SKM_YINYANG) {
+    const int32_t k = c->k;
+    const int32_t kt0 = k <= 128 ? 128 : k <= 256 ? 256 : k <= 512 ? 512 : 1024;
+    for (int32_t kt = kt0 / 2; kt >= 128 && kt >= kt0 / 4 && rc == SKM_OK; kt /= 2)
+      if ((rc = timed(bb, bt, kt, 0, &ms)) == SKM_OK && ms < best) {
+        best = ms;
+        bk = kt;
+      }
+  }
+  if (rc == SKM_OK && c->Ct16 && (rc = timed(bb, bt, bk, 1, &ms)) == SKM_OK && ms < best) {
+    best = ms;
+    bs = 1;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != SKM_OK) return rc;
-  TRY(apply(bb, bt));
+  TRY(apply(bb, bt, bk, bs));
   TRY(start_from_rows(c, init));
   if (cache_path) {
     if (FILE* f = std::fopen(cache_path, "a")) {
-      std::fprintf(f, "%s %d %d\n", key, bb, bt);
+      std::fprintf(f, "%s %d %d %d %d\n", key, bb, bt, bk, bs);
       std::fclose(f);
     }
   }

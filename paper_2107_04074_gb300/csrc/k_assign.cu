@@ -1051,9 +1051,11 @@ int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long
   const int k = c->k;
   // a batch walks each row's own slice 128 centers at a time
   if (c->nruns > 0) return launch_rows_b<VT, 1, true>(c, mode, list, list_cnt, nrows, cursor);
-  if (k <= 128) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows, cursor);
-  if (k <= 256) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows, cursor);
-  if (k <= 512) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows, cursor);
+  // centers per pass over a row: the chosen tile, else the smallest that holds k
+  const int kt = c->opt.k_tile > 0 ? c->opt.k_tile : k <= 128 ? 128 : k <= 256 ? 256 : k <= 512 ? 512 : 1024;
+  if (kt == 128) return launch_rows<VT, 1>(c, mode, list, list_cnt, nrows, cursor);
+  if (kt == 256) return launch_rows<VT, 2>(c, mode, list, list_cnt, nrows, cursor);
+  if (kt == 512) return launch_rows<VT, 4>(c, mode, list, list_cnt, nrows, cursor);
   return launch_rows<VT, 8>(c, mode, list, list_cnt, nrows, cursor);
 }
 
@@ -1093,7 +1095,7 @@ int hamerly_step_t(skm_ctx* c) {
                                                       c->hst, thr);
   }
   SKM_LAUNCHED(c);
-  if (!c->Ct16 || c->nruns > 0) return assign_full_t<VT>(c, 1, c->w2, c->cnt + C_W2, 0);
+  if (!c->Ct16 || c->scr_off || c->nruns > 0) return assign_full_t<VT>(c, 1, c->w2, c->cnt + C_W2, 0);
   // screened whole rows (FP16 centers), then FP32 whole rows for the rows the bound left open
   TRY_K(assign_full_t<VT>(c, 5, c->w2, c->cnt + C_W2, 0));
   return assign_full_t<VT>(c, 1, c->w4, c->cnt + C_W4, 0, C_CURSOR_2);
@@ -1145,7 +1147,7 @@ int elkan_step_t(skm_ctx* c) {
   else SKM_ELKL(false, false);
 #undef SKM_ELKL
   SKM_LAUNCHED(c);
-  if (!c->Ct16 || batch) return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
+  if (!c->Ct16 || c->scr_off || batch) return assign_full_t<VT>(c, 2, c->w2, c->cnt + C_W2, 0);
   // screened whole rows (FP16 centers), then the exact pass for the rows the
   // bound left open: pairs (w3, short rows from the bottom, long ones from
   // the top) and FP32 whole rows (w4)

@@ -337,6 +337,7 @@ struct skm_ctx {
   int64_t* t_ptr;      // [d+1] term-major (CSC) offsets
   int32_t* t_row;      // [nnz]
   int32_t* hst;        // [4] Hamerly: skip tightening this iteration, iterations skipped, blocks done
+  int32_t scr_off;     // 1: the screened whole-row pass is not used although Ct16 is kept (skm_autotune)
   void* t_val;         // [nnz] dtype
   int64_t nchunks;     // center-sum work items
   int32_t* ch_term;    // [nchunks]

@@ -48,7 +48,7 @@ class skm_options(ctypes.Structure):
     _fields_ = [("hamerly_tight", ctypes.c_int32), ("validate", ctypes.c_int32), ("row_threshold", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("graph", ctypes.c_int32), ("graph_check", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("fused_update", ctypes.c_int32),
-                ("screen", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("screen", ctypes.c_int32), ("k_tile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class skm_stats(ctypes.Structure):
@@ -215,7 +215,7 @@ class KMeans:
     def __init__(self, n: int, d: int, row_ptr, col_idx, values, k: int, variant="standard", init_rows=None,
                  seed: int = 0, hamerly_tight: bool = False, row_threshold: int = 0, stream=None,
                  precision: str = "fp32", graph: bool = False, graph_check: int = 0, blocks_per_sm: int = 0,
-                 fused_update: bool = False, screen: bool | None = None):
+                 fused_update: bool = False, screen: bool | None = None, k_tile: int = 0):
         lib = load()
         host = isinstance(values, np.ndarray)
         self._keep = (row_ptr, col_idx, values)
@@ -234,6 +234,8 @@ class KMeans:
         opt.fused_update = 1 if fused_update else 0
         # screen: None = the library's choice (on for Elkan with k > 128), True / False = on / off
         opt.screen = 0 if screen is None else (1 if screen else 2)
+        # centers per pass of the whole-row kernel: 0 = the smallest tile that holds k
+        opt.k_tile = int(k_tile)
         self.n, self.d, self.k = int(n), int(d), int(k)
         self.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         rows = None
@@ -374,8 +376,10 @@ class KMeans:
         return rows, (out.value if sync else None)
 
     def autotune(self, cache_path=None, iters: int = 3) -> bool:
-        """Pick the persistent kernels' launch shape (and the Elkan whole-row
-        threshold) by timing; True when the choice came from cache_path."""
+        """Pick, by timing, the persistent kernels' launch shape and the Elkan
+        whole-row threshold, then the whole-row kernel's tile of centers and
+        whether the screened pass is used (see skm_autotune); True when the
+        choice came from cache_path."""
         fc = ctypes.c_int32(0)
         path = None if cache_path is None else str(cache_path).encode()
         _check(load().skm_autotune(self._h, path, int(iters), ctypes.byref(fc)), "skm_autotune")

@@ -86,6 +86,13 @@ def test_unsupported_combinations_rejected_without_the_gpu():
     opt.precision = 7
     assert init(data(skm.DENSE, d=32), 3, V["standard"], opt) == skm.EINVAL  # no such precision
     assert init(data(skm.CSR, n=5000), 4097, V["elkan"]) == skm.EUNSUPPORTED
+    topt = skm.skm_options()
+    lib.skm_default_options(ctypes.byref(topt))
+    topt.k_tile = 100  # not a tile size
+    assert init(data(skm.CSR), 3, V["elkan"], topt) == skm.EINVAL
+    topt.k_tile = 256
+    assert init(data(skm.CSR), 3, V["yinyang"], topt) == skm.EUNSUPPORTED  # Yin-Yang walks a row once
+    assert init(data(skm.DENSE), 3, V["standard"], topt) == skm.EUNSUPPORTED  # the tile is the CSR kernel's
 
     x = data(skm.CSR)
     ks = np.array([2, 3], np.int32)
@@ -98,6 +105,10 @@ def test_unsupported_combinations_rejected_without_the_gpu():
         return rc
 
     assert batch([0, 4, 10], ks, V["yinyang"]) == skm.EUNSUPPORTED
+    rr = np.asarray([0, 4, 10], np.int64)
+    assert lib.skm_batch_init(ctypes.byref(h), ctypes.byref(x), rr.ctypes.data, ks.ctypes.data, 2, V["standard"],
+                              None, 0, ctypes.byref(topt), None) == skm.EUNSUPPORTED  # no tile choice in a batch
+    assert h.value is None
     assert batch([0, 4, 9], ks, V["standard"]) == skm.EINVAL      # does not end at n
     assert batch([1, 4, 10], ks, V["standard"]) == skm.EINVAL     # does not start at 0
     assert batch([0, 2, 10], np.array([3, 3], np.int32), V["standard"]) == skm.EINVAL  # k > rows of the run

@@ -375,6 +375,66 @@ def test_hamerly_tightening_schedule_keeps_labels(mid, variant):
     assert skipped > 0 and tightened > 1
 
 
+@pytest.mark.parametrize("variant,k,tiles", [("standard", 300, (128, 256)), ("elkan", 300, (128, 256)),
+                                             ("simp_hamerly", 300, (256,)), ("simp_elkan", 1000, (512,))])
+def test_center_tiles_give_the_same_run(variant, k, tiles):
+    """The whole-row kernel walks a row once per tile of centers: with tiles
+    smaller than the default, every iteration's labels, changed counts and
+    objective are those of the default tile (FP16 screening on, as by default
+    for k > 128)."""
+    X = synth.tfidf(synth.scaled(synth.CSR_RCV1_LIKE, n=6000, d=8000, seed=41))
+    init = synth.init_rows(X.n, k, 41)
+    dev = _dev(X)
+    runs = {}
+    for kt in (0,) + tuple(tiles):
+        km = _km(X, k, variant, init, dev, k_tile=kt)
+        seq = []
+        for _ in range(25):
+            ch = km.assign()
+            lab = km.labels()
+            if ch == 0:
+                seq.append((ch, lab, None))
+                break
+            seq.append((ch, lab, km.update_centers()))
+        km.close()
+        runs[kt] = seq
+    for kt in tiles:
+        assert len(runs[kt]) == len(runs[0])
+        for (ca, la, ja), (cb, lb_, jb) in zip(runs[0], runs[kt]):
+            assert ca == cb
+            np.testing.assert_array_equal(la, lb_)
+            assert ja == jb
+
+
+def test_autotune_single_run_tiles_and_cache(tmp_path):
+    """skm_autotune on a single run with k = 300 (default tile 512, screening
+    on): it times the launch shapes, two smaller tiles and the screened pass
+    off, writes one five-field cache line, a second context reads it back,
+    and a run after either gives the labels of a default context."""
+    X = synth.tfidf(synth.scaled(synth.CSR_RCV1_LIKE, n=6000, d=8000, seed=43))
+    k = 300
+    init = synth.init_rows(X.n, k, 43)
+    dev = _dev(X)
+    ref = _km(X, k, "simp_elkan", init, dev)
+    it_ref, _ = ref.run(30)
+    lab_ref = ref.labels()
+    ref.close()
+    cache = tmp_path / "tune.txt"
+    a = _km(X, k, "simp_elkan", init, dev)
+    assert a.autotune(cache, iters=2) is False
+    f = cache.read_text().split()
+    assert len(f) == 5 and int(f[3]) in (0, 128, 256) and int(f[4]) in (0, 1)
+    it_a, _ = a.run(30)
+    np.testing.assert_array_equal(a.labels(), lab_ref)
+    assert it_a == it_ref
+    a.close()
+    b = _km(X, k, "simp_elkan", init, dev)
+    assert b.autotune(cache, iters=2) is True
+    it_b, _ = b.run(30)
+    np.testing.assert_array_equal(b.labels(), lab_ref)
+    b.close()
+
+
 @pytest.mark.parametrize("variant", ["standard", "hamerly", "elkan", "simp_elkan"])
 def test_fused_center_update_equals_separate_kernels(variant):
     """The center update's phases after the sums run as one cooperative
