@@ -208,6 +208,9 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           vv_n = to_f32(val[p0 + 32 + lane]);
         }
         const int nq = (int)min((int64_t)32, e - p0);
+        // full batches of NB entries (NB divides 32), then the row's ragged
+        // tail as one more batch whose missing entries load and add nothing,
+        // so that it costs one round trip, not one per entry
         int q = 0;
         for (; q + NB <= nq; q += NB) {
           int t[NB];
@@ -234,18 +237,32 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
               acc[g].w = __fmaf_rn(v[u], c4.w, acc[g].w);
             }
         }
-        for (; q < nq; ++q) {
-          const int t = __shfl_sync(SKM_FULL_MASK, tt, q);
-          const float v = __shfl_sync(SKM_FULL_MASK, vv, q);
+        if (q < nq) {
+          const int nb = nq - q;  // 1 .. NB - 1 entries left
+          int t[NB];
+          float v[NB];
+          typename Raw::type cv[NB][G];
 #pragma unroll
-          for (int g = 0; g < G; ++g)
-            if (ok[g]) {
-              const float4 c4 = ld_c4<CT>(cbase + (int64_t)t * kst + g * 128);
-              acc[g].x = __fmaf_rn(v, c4.x, acc[g].x);
-              acc[g].y = __fmaf_rn(v, c4.y, acc[g].y);
-              acc[g].z = __fmaf_rn(v, c4.z, acc[g].z);
-              acc[g].w = __fmaf_rn(v, c4.w, acc[g].w);
-            }
+          for (int u = 0; u < NB; ++u) {
+            t[u] = __shfl_sync(SKM_FULL_MASK, tt, q + u);
+            v[u] = __shfl_sync(SKM_FULL_MASK, vv, q + u);
+          }
+#pragma unroll
+          for (int u = 0; u < NB; ++u)
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+              cv[u][g] = (ok[g] && u < nb) ? Raw::load(cbase + (int64_t)t[u] * kst + g * 128) : Raw::zero();
+#pragma unroll
+          for (int u = 0; u < NB; ++u)
+            if (u < nb)
+#pragma unroll
+              for (int g = 0; g < G; ++g) {
+                const float4 c4 = Raw::f4(cv[u][g]);
+                acc[g].x = __fmaf_rn(v[u], c4.x, acc[g].x);
+                acc[g].y = __fmaf_rn(v[u], c4.y, acc[g].y);
+                acc[g].z = __fmaf_rn(v[u], c4.z, acc[g].z);
+                acc[g].w = __fmaf_rn(v[u], c4.w, acc[g].w);
+              }
         }
       }
 #pragma unroll
