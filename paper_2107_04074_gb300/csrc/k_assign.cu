@@ -706,7 +706,9 @@ __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t*
     t1 = __ldg(col + b + 8 + gl);
     v1 = to_f32(val[b + 8 + gl]);
   }
-  for (int64_t p0 = b; p0 < e; p0 += 16) {
+  int64_t p0 = b;
+  // full batches of 16 entries, without per-entry tests
+  for (; p0 + 16 <= e; p0 += 16) {
     const int ct0 = t0, ct1 = t1;
     const float cv0 = v0, cv1 = v1;
     if (p0 + 16 + gl < e) {
@@ -717,16 +719,27 @@ __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t*
       t1 = __ldg(col + p0 + 24 + gl);
       v1 = to_f32(val[p0 + 24 + gl]);
     }
-    const int nq = (int)min((int64_t)16, e - p0);
     float c[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int t = __shfl_sync(gmask, q < 8 ? ct0 : ct1, q & 7, 8);
+      c[q] = on ? __ldg(cbase + (int64_t)t * kst) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc = __fmaf_rn(__shfl_sync(gmask, q < 8 ? cv0 : cv1, q & 7, 8), c[q], acc);
+  }
+  // the ragged tail: one more batch whose missing entries load and add nothing
+  if (p0 < e) {
+    const int nq = (int)(e - p0);
+    float c[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int t = __shfl_sync(gmask, q < 8 ? t0 : t1, q & 7, 8);
       c[q] = (on && q < nq) ? __ldg(cbase + (int64_t)t * kst) : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const float v = __shfl_sync(gmask, q < 8 ? cv0 : cv1, q & 7, 8);
+      const float v = __shfl_sync(gmask, q < 8 ? v0 : v1, q & 7, 8);
       if (q < nq) acc = __fmaf_rn(v, c[q], acc);
     }
   }
