@@ -907,8 +907,11 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t total = (int64_t)(*w1_cnt);
   __shared__ int slot_j[NW][8];
-  __shared__ float tile[NW][2][CH][9];  // [buffer][entry of the chunk][candidate], padded
-  __shared__ float tvl[NW][2][CH];      // the chunk's values
+  // [buffer][candidate][entry of the chunk]: a candidate lane reads four
+  // consecutive entries with one 16-byte load (rows padded to 68 floats, so
+  // that the eight candidate lanes hit different banks)
+  __shared__ __align__(16) float tile[NW][2][8][CH + 4];
+  __shared__ __align__(16) float tvl[NW][2][CH];  // the chunk's values
   int* sj = slot_j[warp];
   unsigned long long sims = 0, changed = 0;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -958,8 +961,8 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
       tvl[warp][buf][32 + lane] = x1;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        tile[warp][buf][lane][q] = g0[q];
-        tile[warp][buf][32 + lane][q] = g1[q];
+        tile[warp][buf][q][lane] = g0[q];
+        tile[warp][buf][q][32 + lane] = g1[q];
       }
       __syncwarp();
       // the next chunk's gathers go out before this chunk's FMA chains
@@ -976,13 +979,20 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
       }
       if (lane <= m) {
         const float* tv = tvl[warp][buf];
-        const float(*tl)[9] = tile[warp][buf];
+        const float* tl = tile[warp][buf][lane];
         if (e - p0 >= CH) {
-#pragma unroll 16
-          for (int q = 0; q < CH; ++q) acc = __fmaf_rn(tv[q], tl[q][lane], acc);
+#pragma unroll 4
+          for (int q = 0; q < CH; q += 4) {
+            const float4 xv = *reinterpret_cast<const float4*>(tv + q);
+            const float4 cv = *reinterpret_cast<const float4*>(tl + q);
+            acc = __fmaf_rn(xv.x, cv.x, acc);
+            acc = __fmaf_rn(xv.y, cv.y, acc);
+            acc = __fmaf_rn(xv.z, cv.z, acc);
+            acc = __fmaf_rn(xv.w, cv.w, acc);
+          }
         } else {
           const int nq = (int)(e - p0);
-          for (int q = 0; q < nq; ++q) acc = __fmaf_rn(tv[q], tl[q][lane], acc);
+          for (int q = 0; q < nq; ++q) acc = __fmaf_rn(tv[q], tl[q], acc);
         }
       }
       __syncwarp();
