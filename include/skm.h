@@ -171,6 +171,10 @@ typedef struct {
   double objective;       /* J = sum_j |S_j| after the last center update */
   int64_t last_cand_rechecks; /* precision form: ambiguous rows rechecked in
                                  FP32 against their BF16 candidates only */
+  int64_t last_skipped;   /* 1 when the last assignment skipped Elkan's bound
+                             pass (nearly every point had gone to a whole row)
+                             or Hamerly's tightening (it had pruned almost
+                             nothing): the survivors went to whole rows */
 } skm_stats;
 
 typedef struct skm_ctx skm_ctx;

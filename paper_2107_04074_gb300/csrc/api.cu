@@ -220,6 +220,7 @@ int read_counters(skm_ctx* c) {
   c->stats.last_survivors = (int64_t)(c->hcnt[C_W1] + c->hcnt[C_W1L]);
   c->stats.last_rechecks = (int64_t)c->hcnt[C_W2];
   c->stats.last_cand_rechecks = (int64_t)c->hcnt[C_W3];
+  c->stats.last_skipped = (int64_t)c->hcnt[C_SKIP];
   return SKM_OK;
 }
 

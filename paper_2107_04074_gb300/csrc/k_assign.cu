@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(kBlock) k_ham_tighten(
   constexpr int TP = 8;
   const int lane = threadIdx.x & 31;
   const bool skip_t = hst[0] != 0;
+  if (skip_t && blockIdx.x == 0 && threadIdx.x == 0) cnt[C_SKIP] = 1ull;
   const int64_t total = skip_t ? 0 : (int64_t)(*w1_cnt);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long sims = 0;
@@ -608,6 +609,16 @@ __global__ void __launch_bounds__(kBlock) k_yy_bounds(int64_t n, int32_t ng, con
 // has at most kLongRow entries, else from the top down (w1[n - 1 - pos], for
 // the warp-per-point recompute) -- and one with more to w2 (recomputed as a
 // whole row); each list gets one atomic per tile.
+// While nearly every point goes to w2 (the bounds prune nothing in the early
+// iterations), the bound pass is skipped: the last block to finish decides
+// for the next iteration from this one's count (hst[0] = 1 when at least 98 %
+// of n >= 4096 points went to w2), and a skipped pass sends every point to
+// w2 without reading or writing a bound -- the whole-row pass rewrites l and
+// every u(i,j) of each row anyway -- and passes the bounds again every
+// kElkProbe-th iteration to re-measure.  Labels do not depend on it.
+// hst: [0] skip this iteration, [1] passes skipped in a row, [2] blocks done.
+constexpr int kElkProbe = 8;
+
 template <bool FULL, bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int64_t kst,
                                                        const int64_t* __restrict__ rp,
@@ -618,10 +629,19 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
                                                        const float* __restrict__ pup, const float* __restrict__ qup,
                                                        const float* __restrict__ cc, const float* __restrict__ sc,
                                                        int moved, int32_t cap, int32_t* __restrict__ w1,
-                                                       int32_t* __restrict__ w2, unsigned long long* __restrict__ cnt) {
+                                                       int32_t* __restrict__ w2, unsigned long long* __restrict__ cnt,
+                                                       int32_t* __restrict__ hst) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * kTile < n; tile += nw) {
+  const bool skip_b = hst[0] != 0;
+  if (skip_b) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[C_SKIP] = 1ull;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
+         base += (int64_t)gridDim.x * blockDim.x)
+      warp_push(base + lane < n, (int32_t)(base + lane), w2, cnt + C_W2);
+  }
+  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; !skip_b && tile * kTile < n;
+       tile += nw) {
     const int64_t i0 = tile * kTile;
     const int rows = (int)min((int64_t)kTile, n - i0);
     int32_t my_a = 0;
@@ -681,6 +701,22 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
     warp_push(is_few && !my_long, (int32_t)(i0 + lane), w1, cnt + C_W1);
     warp_push_down(is_few && my_long, (int32_t)(i0 + lane), w1 + (n - 1), cnt + C_W1L);
     warp_push((many >> lane) & 1u, (int32_t)(i0 + lane), w2, cnt + C_W2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned done = atomicAdd(reinterpret_cast<unsigned*>(hst + 2), 1u);
+    if (done == gridDim.x - 1) {  // the last block: every push is counted
+      __threadfence();
+      if (!skip_b) {
+        const unsigned long long whole = *reinterpret_cast<volatile unsigned long long*>(cnt + C_W2);
+        hst[0] = (n >= 4096 && (double)whole >= 0.98 * (double)n) ? 1 : 0;
+        hst[1] = 0;
+      } else if (++hst[1] >= kElkProbe - 1) {
+        hst[0] = 0;
+      }
+      hst[2] = 0;
+    }
   }
 }
 
@@ -1154,7 +1190,7 @@ int elkan_step_t(skm_ctx* c) {
   k_elk_bounds<F, B><<<persistent_grid(c, (const void*)k_elk_bounds<F, B>), kBlock, 0, c->st>>>(c->n, c->k, c->kst, c->rp, c->row_run, c->runs, c->a, c->lb, c->ub, \
                                               c->dlt,                                                              \
                                               c->pdn, c->pup, c->qup, c->cc, c->sc, c->moved, row_thresh, c->w1,   \
-                                              c->w2, c->cnt)
+                                              c->w2, c->cnt, c->hst)
   if (batch && full) SKM_ELKB(true, true);
   else if (batch) SKM_ELKB(false, true);
   else if (full) SKM_ELKB(true, false);

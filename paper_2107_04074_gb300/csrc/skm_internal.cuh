@@ -32,9 +32,10 @@ enum Counter {
   C_CURSOR_2 = 13,   // cursors of the second launches of an assignment: k_rows_top2,
   C_CURSOR_R2 = 14,  // k_elk_recompute,
   C_CURSOR_L2 = 15,  // k_elk_recompute_long
-  C_ERR = 16,     // error flags (bit field)
-  C_NDIRTY = 17,  // clusters whose sum changed in the last center update
-  C_NUM = 18
+  C_SKIP = 16,    // 1: this assignment skipped Elkan's bound pass or Hamerly's tightening
+  C_ERR = 17,     // error flags (bit field)
+  C_NDIRTY = 18,  // clusters whose sum changed in the last center update
+  C_NUM = 19
 };
 
 // Data-preparation error bits (C_ERR).

@@ -55,7 +55,7 @@ class skm_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("last_changed", ctypes.c_int64), ("last_sims", ctypes.c_int64),
                 ("total_sims", ctypes.c_int64), ("last_survivors", ctypes.c_int64),
                 ("last_rechecks", ctypes.c_int64), ("objective", ctypes.c_double),
-                ("last_cand_rechecks", ctypes.c_int64)]
+                ("last_cand_rechecks", ctypes.c_int64), ("last_skipped", ctypes.c_int64)]
 
 
 _LIB = None
@@ -203,6 +203,7 @@ class Stats:
     last_rechecks: int
     objective: float
     last_cand_rechecks: int = 0
+    last_skipped: int = 0
 
 
 class KMeans:
@@ -389,7 +390,7 @@ class KMeans:
         s = skm_stats()
         _check(load().skm_get_stats(self._h, ctypes.byref(s)), "skm_get_stats")
         return Stats(s.iterations, s.last_changed, s.last_sims, s.total_sims, s.last_survivors, s.last_rechecks,
-                     s.objective, s.last_cand_rechecks)
+                     s.objective, s.last_cand_rechecks, s.last_skipped)
 
 
 class Batch(KMeans):

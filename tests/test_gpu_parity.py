@@ -340,6 +340,40 @@ def test_long_rows_elkan(variant):
     std.close()
 
 
+@pytest.mark.parametrize("variant", ["elkan", "simp_elkan"])
+def test_elkan_bound_pass_schedule_keeps_labels(mid, variant):
+    """While nearly every point goes to a whole row, Elkan's bound pass is
+    skipped (every point goes straight to the whole-row pass, which rewrites
+    its bounds) and run again every 8th iteration.  Labels and changed counts
+    equal the standard variant's at every iteration; skipped iterations
+    report last_skipped = 1 with every point recomputed whole, and later
+    iterations pass the bounds again and prune."""
+    k = 100
+    init = synth.init_rows(mid.n, k, 2)
+    dev = _dev(mid)
+    std = _km(mid, k, "standard", init, dev)
+    elk = _km(mid, k, variant, init, dev)
+    skipped = pruned = 0
+    for it in range(60):
+        cs = std.assign()
+        ch = elk.assign()
+        assert ch == cs
+        np.testing.assert_array_equal(elk.labels(), std.labels())
+        st = elk.stats()
+        if st.last_skipped:
+            skipped += 1
+            assert st.last_rechecks == mid.n and st.last_survivors == 0
+        elif it > 0 and st.last_rechecks < mid.n // 2:
+            pruned += 1
+        if cs == 0:
+            break
+        std.update_centers()
+        elk.update_centers()
+    std.close()
+    elk.close()
+    assert skipped > 0 and pruned > 0
+
+
 @pytest.mark.parametrize("variant", ["hamerly", "simp_hamerly"])
 def test_hamerly_tightening_schedule_keeps_labels(mid, variant):
     """Where tightening prunes almost nothing, Hamerly's survivors go straight
