@@ -187,8 +187,9 @@ void skm_default_options(skm_options* opt);
  * them from seed.  Prepares everything the iterations need (row norms, the
  * term-major copy of the data, work buffers).  stream: a cudaStream_t.
  * Errors: SKM_EINVAL (k < 1, k > n, malformed CSR, zero or non-finite row,
- * duplicate init rows), SKM_EUNSUPPORTED (Elkan with k > 4096), SKM_ENOMEM,
- * SKM_ECUDA.  On error *out is NULL. */
+ * duplicate init rows), SKM_EUNSUPPORTED (Elkan with k > 4096; CSR data
+ * whose term-major center table, d x round_up(k, 8) FP32 values, reaches
+ * 64 GB), SKM_ENOMEM, SKM_ECUDA.  On error *out is NULL. */
 int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant,
              const int64_t* init_rows, uint64_t seed, const skm_options* opt,
              void* stream);

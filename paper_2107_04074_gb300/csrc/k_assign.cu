@@ -85,6 +85,7 @@ template <>
 struct RawC4<float> {
   using type = float4;
   static __device__ __forceinline__ type load(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+  static __device__ __forceinline__ type load_v(const type* p) { return __ldg(p); }
   static __device__ __forceinline__ type zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
   static __device__ __forceinline__ float4 f4(type r) { return r; }
 };
@@ -92,6 +93,7 @@ template <>
 struct RawC4<__half> {
   using type = uint2;
   static __device__ __forceinline__ type load(const __half* p) { return __ldg(reinterpret_cast<const uint2*>(p)); }
+  static __device__ __forceinline__ type load_v(const type* p) { return __ldg(p); }
   static __device__ __forceinline__ type zero() { return make_uint2(0u, 0u); }
   static __device__ __forceinline__ float4 f4(type r) {
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
@@ -192,19 +194,23 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           ok[g] = live[g];
         }
       }
-      const CT* cbase = Ct + rg.koff + j0 + lane * 4;
+      // this lane's four centers of group 0 as one vector; an entry's term t
+      // becomes the 32-bit offset t kst / 4 in vectors (d kst / 4 < 2^32 is
+      // checked at init), computed once by the lane that loads the entry
+      const typename Raw::type* cbase = reinterpret_cast<const typename Raw::type*>(Ct + rg.koff + j0 + lane * 4);
+      const uint32_t kv = (uint32_t)(kst >> 2);
       // the row's entries 32 at a time, the next 32 loaded ahead
-      int tt_n = 0;
+      uint32_t tt_n = 0;
       float vv_n = 0.f;
       if (b + lane < e) {
-        tt_n = __ldg(col + b + lane);
+        tt_n = (uint32_t)__ldg(col + b + lane) * kv;
         vv_n = to_f32(val[b + lane]);
       }
       for (int64_t p0 = b; p0 < e; p0 += 32) {
-        const int tt = tt_n;
+        const uint32_t tt = tt_n;
         const float vv = vv_n;
         if (p0 + 32 + lane < e) {
-          tt_n = __ldg(col + p0 + 32 + lane);
+          tt_n = (uint32_t)__ldg(col + p0 + 32 + lane) * kv;
           vv_n = to_f32(val[p0 + 32 + lane]);
         }
         const int nq = (int)min((int64_t)32, e - p0);
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
         // so that it costs one round trip, not one per entry
         int q = 0;
         for (; q + NB <= nq; q += NB) {
-          int t[NB];
+          uint32_t t[NB];
           float v[NB];
           typename Raw::type cv[NB][G];
 #pragma unroll
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           for (int u = 0; u < NB; ++u)
 #pragma unroll
             for (int g = 0; g < G; ++g)
-              cv[u][g] = ok[g] ? Raw::load(cbase + (int64_t)t[u] * kst + g * 128) : Raw::zero();
+              cv[u][g] = ok[g] ? Raw::load_v(cbase + t[u] + g * 32) : Raw::zero();
 #pragma unroll
           for (int u = 0; u < NB; ++u)
 #pragma unroll
@@ -239,7 +245,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
         }
         if (q < nq) {
           const int nb = nq - q;  // 1 .. NB - 1 entries left
-          int t[NB];
+          uint32_t t[NB];
           float v[NB];
           typename Raw::type cv[NB][G];
 #pragma unroll
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           for (int u = 0; u < NB; ++u)
 #pragma unroll
             for (int g = 0; g < G; ++g)
-              cv[u][g] = (ok[g] && u < nb) ? Raw::load(cbase + (int64_t)t[u] * kst + g * 128) : Raw::zero();
+              cv[u][g] = (ok[g] && u < nb) ? Raw::load_v(cbase + t[u] + g * 32) : Raw::zero();
 #pragma unroll
           for (int u = 0; u < NB; ++u)
             if (u < nb)

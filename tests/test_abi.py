@@ -86,6 +86,7 @@ def test_unsupported_combinations_rejected_without_the_gpu():
     opt.precision = 7
     assert init(data(skm.DENSE, d=32), 3, V["standard"], opt) == skm.EINVAL  # no such precision
     assert init(data(skm.CSR, n=5000), 4097, V["elkan"]) == skm.EUNSUPPORTED
+    assert init(data(skm.CSR, n=5000, d=2 ** 26), 4096, V["standard"]) == skm.EUNSUPPORTED  # Ct of 1 TB
     topt = skm.skm_options()
     lib.skm_default_options(ctypes.byref(topt))
     topt.k_tile = 100  # not a tile size
