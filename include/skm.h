@@ -189,7 +189,7 @@ void skm_default_options(skm_options* opt);
  * Errors: SKM_EINVAL (k < 1, k > n, malformed CSR, zero or non-finite row,
  * duplicate init rows), SKM_EUNSUPPORTED (Elkan with k > 4096; CSR data
  * whose term-major center table, d x round_up(k, 8) FP32 values, reaches
- * 64 GB), SKM_ENOMEM, SKM_ECUDA.  On error *out is NULL. */
+ * 16 GB), SKM_ENOMEM, SKM_ECUDA.  On error *out is NULL. */
 int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant,
              const int64_t* init_rows, uint64_t seed, const skm_options* opt,
              void* stream);

@@ -445,9 +445,9 @@ int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const
   if (!x->values || (x->layout == SKM_CSR && (!x->row_ptr || !x->col_idx))) return SKM_EINVAL;
   if (x->d > INT32_MAX || x->n > INT32_MAX) return SKM_EUNSUPPORTED;
   if ((variant == SKM_ELKAN || variant == SKM_SIMP_ELKAN) && k > 4096) return SKM_EUNSUPPORTED;
-  // the whole-row kernel addresses the term-major centers with 32-bit offsets
-  // in 16-byte vectors: d round8(k) / 4 < 2^32 (a center table below 64 GB)
-  if (x->layout == SKM_CSR && x->d * (((int64_t)k + 7) / 8 * 8) / 4 >= (int64_t(1) << 32)) return SKM_EUNSUPPORTED;
+  // the sparse kernels address the term-major centers with 32-bit offsets:
+  // d round8(k) < 2^32 (a center table below 16 GB)
+  if (x->layout == SKM_CSR && x->d * (((int64_t)k + 7) / 8 * 8) >= (int64_t(1) << 32)) return SKM_EUNSUPPORTED;
   skm_ctx* c = new (std::nothrow) skm_ctx();
   if (!c) return SKM_ENOMEM;
   std::memset(c, 0, sizeof(*c));
@@ -538,7 +538,7 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
     if (d.kst > kmax) kmax = d.kst;
   }
   if (koff > INT32_MAX / 2) return SKM_EUNSUPPORTED;
-  if (x->d * koff / 4 >= (int64_t(1) << 32)) return SKM_EUNSUPPORTED;  // 32-bit vector offsets into Ct
+  if (x->d * koff >= (int64_t(1) << 32)) return SKM_EUNSUPPORTED;  // 32-bit offsets into Ct
   skm_ctx* c = new (std::nothrow) skm_ctx();
   if (!c) return SKM_ENOMEM;
   std::memset(c, 0, sizeof(*c));

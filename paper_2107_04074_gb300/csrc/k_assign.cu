@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
         }
       }
       // this lane's four centers of group 0 as one vector; an entry's term t
-      // becomes the 32-bit offset t kst / 4 in vectors (d kst / 4 < 2^32 is
+      // becomes the 32-bit offset t kst / 4 in vectors (d kst < 2^32 is
       // checked at init), computed once by the lane that loads the entry
       const typename Raw::type* cbase = reinterpret_cast<const typename Raw::type*>(Ct + rg.koff + j0 + lane * 4);
       const uint32_t kv = (uint32_t)(kst >> 2);
@@ -737,35 +737,38 @@ __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t*
                                             int my_j, unsigned gmask, int gl) {
   const bool on = my_j >= 0;
   const float* cbase = Ct + (on ? my_j : 0);
+  // an entry's term t as the 32-bit offset t kst (d kst < 2^32, checked at
+  // init), computed by the lane that loads the entry
+  const uint32_t ku = (uint32_t)kst;
   float acc = 0.f;
-  int t0 = 0, t1 = 0;
+  uint32_t t0 = 0, t1 = 0;
   float v0 = 0.f, v1 = 0.f;
   if (b + gl < e) {
-    t0 = __ldg(col + b + gl);
+    t0 = (uint32_t)__ldg(col + b + gl) * ku;
     v0 = to_f32(val[b + gl]);
   }
   if (b + 8 + gl < e) {
-    t1 = __ldg(col + b + 8 + gl);
+    t1 = (uint32_t)__ldg(col + b + 8 + gl) * ku;
     v1 = to_f32(val[b + 8 + gl]);
   }
   int64_t p0 = b;
   // full batches of 16 entries, without per-entry tests
   for (; p0 + 16 <= e; p0 += 16) {
-    const int ct0 = t0, ct1 = t1;
+    const uint32_t ct0 = t0, ct1 = t1;
     const float cv0 = v0, cv1 = v1;
     if (p0 + 16 + gl < e) {
-      t0 = __ldg(col + p0 + 16 + gl);
+      t0 = (uint32_t)__ldg(col + p0 + 16 + gl) * ku;
       v0 = to_f32(val[p0 + 16 + gl]);
     }
     if (p0 + 24 + gl < e) {
-      t1 = __ldg(col + p0 + 24 + gl);
+      t1 = (uint32_t)__ldg(col + p0 + 24 + gl) * ku;
       v1 = to_f32(val[p0 + 24 + gl]);
     }
     float c[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int t = __shfl_sync(gmask, q < 8 ? ct0 : ct1, q & 7, 8);
-      c[q] = on ? __ldg(cbase + (int64_t)t * kst) : 0.f;
+      const uint32_t t = __shfl_sync(gmask, q < 8 ? ct0 : ct1, q & 7, 8);
+      c[q] = on ? __ldg(cbase + t) : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc = __fmaf_rn(__shfl_sync(gmask, q < 8 ? cv0 : cv1, q & 7, 8), c[q], acc);
@@ -776,8 +779,8 @@ __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t*
     float c[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      const int t = __shfl_sync(gmask, q < 8 ? t0 : t1, q & 7, 8);
-      c[q] = (on && q < nq) ? __ldg(cbase + (int64_t)t * kst) : 0.f;
+      const uint32_t t = __shfl_sync(gmask, q < 8 ? t0 : t1, q & 7, 8);
+      c[q] = (on && q < nq) ? __ldg(cbase + t) : 0.f;
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -984,15 +987,17 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
 #pragma unroll
     for (int q = 0; q < 8; ++q) jq[q] = q <= m ? sj[q] : 0;
     // entries p0 + lane and p0 + 32 + lane of chunk p0: columns, values, gathers
-    int t0 = b + lane < e ? __ldg(col + b + lane) : 0;
-    int t1 = b + 32 + lane < e ? __ldg(col + b + 32 + lane) : 0;
+    // an entry's term t as the 32-bit offset t kst (d kst < 2^32, checked at init)
+    const uint32_t ku = (uint32_t)kst;
+    uint32_t t0 = b + lane < e ? (uint32_t)__ldg(col + b + lane) * ku : 0u;
+    uint32_t t1 = b + 32 + lane < e ? (uint32_t)__ldg(col + b + 32 + lane) * ku : 0u;
     float x0 = b + lane < e ? to_f32(val[b + lane]) : 0.f;
     float x1 = b + 32 + lane < e ? to_f32(val[b + 32 + lane]) : 0.f;
     float g0[8], g1[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      g0[q] = (b + lane < e && q <= m) ? __ldg(cb + (int64_t)t0 * kst + jq[q]) : 0.f;
-      g1[q] = (b + 32 + lane < e && q <= m) ? __ldg(cb + (int64_t)t1 * kst + jq[q]) : 0.f;
+      g0[q] = (b + lane < e && q <= m) ? __ldg(cb + t0 + jq[q]) : 0.f;
+      g1[q] = (b + 32 + lane < e && q <= m) ? __ldg(cb + t1 + jq[q]) : 0.f;
     }
     float acc = 0.f;
     int buf = 0;
@@ -1010,14 +1015,14 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute_long(
       // the next chunk's gathers go out before this chunk's FMA chains
       const int64_t pn = p0 + CH;
       const bool in0 = pn + lane < e, in1 = pn + 32 + lane < e;
-      t0 = in0 ? __ldg(col + pn + lane) : 0;
-      t1 = in1 ? __ldg(col + pn + 32 + lane) : 0;
+      t0 = in0 ? (uint32_t)__ldg(col + pn + lane) * ku : 0u;
+      t1 = in1 ? (uint32_t)__ldg(col + pn + 32 + lane) * ku : 0u;
       x0 = in0 ? to_f32(val[pn + lane]) : 0.f;
       x1 = in1 ? to_f32(val[pn + 32 + lane]) : 0.f;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        g0[q] = (in0 && q <= m) ? __ldg(cb + (int64_t)t0 * kst + jq[q]) : 0.f;
-        g1[q] = (in1 && q <= m) ? __ldg(cb + (int64_t)t1 * kst + jq[q]) : 0.f;
+        g0[q] = (in0 && q <= m) ? __ldg(cb + t0 + jq[q]) : 0.f;
+        g1[q] = (in1 && q <= m) ? __ldg(cb + t1 + jq[q]) : 0.f;
       }
       if (lane <= m) {
         const float* tv = tvl[warp][buf];
