@@ -277,8 +277,8 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   // ---- counters and per-row data
   TRY(dalloc(c, &c->cnt, C_NUM));
   SKM_CUDA_TRY(cudaMemsetAsync(c->cnt, 0, sizeof(unsigned long long) * C_NUM, c->st));
-  TRY(dalloc(c, &c->fbar, 2));
-  SKM_CUDA_TRY(cudaMemsetAsync(c->fbar, 0, sizeof(unsigned long long) * 2, c->st));
+  TRY(dalloc(c, &c->fbar, 3));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->fbar, 0, sizeof(unsigned long long) * 3, c->st));
   TRY(dalloc(c, &c->hst, 4));
   SKM_CUDA_TRY(cudaMemsetAsync(c->hst, 0, sizeof(int32_t) * 4, c->st));
   SKM_CUDA_TRY(cudaMallocHost((void**)&c->hcnt, sizeof(unsigned long long) * C_NUM));

@@ -22,10 +22,11 @@
 //                       FP64 across threads and blocks, fixed order).
 //   k_normalize_drift   c(j) = S_j/|S_j| in place for dirty clusters (an empty
 //                       cluster keeps c'(j)), partial sums for the drift.
-//   k_drift_final       per center an interval [pd, pu] for cos(angle(c, c'))
-//                       and an upper bound q of its sine, rounded outward.
-//   k_hsel_obj          J = sum_j |S_j| and Hamerly's worst-drift summary; zeroes
-//                       the assignment counters for the next assignment.
+//   k_drift_hsel        per center an interval [pd, pu] for cos(angle(c, c'))
+//                       and an upper bound q of its sine, rounded outward;
+//                       then, by the last block, J = sum_j |S_j| and Hamerly's
+//                       worst-drift summary, and the assignment counters
+//                       zeroed for the next assignment.
 //   k_gram_*            <c_i, c_j> (FP32 products, FP64 across 256-term
 //                       chunks): all tiles when many clusters moved, else only
 //                       the rows of the (at most 64) dirty clusters; then cc
@@ -519,17 +520,6 @@ __device__ __forceinline__ void dev_drift_final(const double* __restrict__ red2,
   __syncthreads();
 }
 
-// Block per center (grid kst).
-__global__ void __launch_bounds__(128) k_drift_final(const double* __restrict__ red2, int64_t nblk, int32_t k,
-                                                     int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
-                                                     const int32_t* __restrict__ dpos, float* __restrict__ pdn,
-                                                     float* __restrict__ pup, float* __restrict__ qup,
-                                                     double* __restrict__ cnorm, const double* __restrict__ e2p,
-                                                     double* __restrict__ e2c) {
-  __shared__ double sh[4][128];
-  dev_drift_final(red2, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, blockIdx.x, sh, e2p, e2c);
-}
-
 // Shared memory of dev_hsel_obj: 1024 slots per quantity (a block of fewer
 // threads takes several slots per thread, so the sums run in the order of a
 // 1024-thread block whatever the block size).
@@ -707,13 +697,34 @@ __device__ __forceinline__ void dev_hsel_obj_256(const float* __restrict__ pdn, 
   if (e2c) dev_fp16_err_max(e2c, k, escr, S.J);
 }
 
-__global__ void __launch_bounds__(1024) k_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
-                                                   const float* __restrict__ qup, const double* __restrict__ nrm,
-                                                   int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
-                                                   unsigned long long* __restrict__ cnt,
-                                                   const double* __restrict__ e2c, float* __restrict__ escr) {
-  __shared__ HselShared S;
-  dev_hsel_obj(pdn, pup, qup, nrm, k, hsel, obj, cnt, S, e2c, escr);
+// The drift per center and the summary in one launch: block per center (grid
+// kst, 256 threads) for the drift, then the last block to finish writes J and
+// Hamerly's summary (dev_hsel_obj's results, bit for bit).  done: a counter
+// that only grows, so launches and graph replays need no reset.
+__global__ void __launch_bounds__(256) k_drift_hsel(const double* __restrict__ red2, int64_t nblk, int32_t k,
+                                                    int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
+                                                    const int32_t* __restrict__ dpos, float* __restrict__ pdn,
+                                                    float* __restrict__ pup, float* __restrict__ qup,
+                                                    double* __restrict__ cnorm, const double* __restrict__ e2p,
+                                                    double* __restrict__ e2c, const double* __restrict__ nrm,
+                                                    float* __restrict__ hsel, double* __restrict__ obj,
+                                                    unsigned long long* __restrict__ cnt, float* __restrict__ escr,
+                                                    unsigned long long* __restrict__ done) {
+  __shared__ union {
+    double fin[4][128];
+    HselSmall hs;
+  } sm;
+  __shared__ int last_sh;
+  dev_drift_final(red2, nblk, k, kst, d, dmark, dpos, pdn, pup, qup, cnorm, blockIdx.x, sm.fin, e2p, e2c);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long v = atomicAdd(done, 1ull);
+    last_sh = (v % gridDim.x) == gridDim.x - 1;
+    __threadfence();
+  }
+  __syncthreads();
+  if (last_sh) dev_hsel_obj_256(pdn, pup, qup, nrm, k, hsel, obj, cnt, sm.hs, e2c, escr);
 }
 
 // ------------------------------------------------------------------
@@ -994,7 +1005,7 @@ __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ G
 // ---------------------------------------------------------------- batches
 
 // Block per run: Hamerly's worst-drift summary over the run's own centers
-// koff .. koff + k - 1 (global ids), the rule of k_hsel_obj.
+// koff .. koff + k - 1 (global ids), the rule of dev_hsel_obj.
 __global__ void __launch_bounds__(256) k_hsel_runs(const float* __restrict__ pdn, const float* __restrict__ pup,
                                                    const float* __restrict__ qup, const RunDesc* __restrict__ runs,
                                                    float* __restrict__ hsel) {
@@ -1454,12 +1465,10 @@ int finish_update(skm_ctx* c) {
     k_normalize_drift<<<grid, 256, 0, c->st>>>(c->S64, c->fx_inv, c->Ct, c->nrm, c->d, c->kst, c->dlist, c->cnt,
                                                c->red, c->Ct16, c->e2p);
     SKM_LAUNCHED(c);
-    SKM_PROF_BEGIN(c, "k_drift_final");
-    k_drift_final<<<c->kst, 128, 0, c->st>>>(c->red, nblk, k, c->kst, c->d, c->dmark, c->dpos, c->pdn, c->pup,
-                                             c->qup, cnorm, c->e2p, c->e2c);
-    SKM_LAUNCHED(c);
-    SKM_PROF_BEGIN(c, "k_hsel_obj");
-    k_hsel_obj<<<1, 1024, 0, c->st>>>(c->pdn, c->pup, c->qup, c->nrm, k, c->hsel, c->obj, c->cnt, c->e2c, c->escr);
+    SKM_PROF_BEGIN(c, "k_drift_hsel");
+    k_drift_hsel<<<c->kst, 256, 0, c->st>>>(c->red, nblk, k, c->kst, c->d, c->dmark, c->dpos, c->pdn, c->pup,
+                                            c->qup, cnorm, c->e2p, c->e2c, c->nrm, c->hsel, c->obj, c->cnt, c->escr,
+                                            c->fbar + 2);
     SKM_LAUNCHED(c);
   }
   const bool hamv = (c->variant == SKM_HAMERLY || c->variant == SKM_SIMP_HAMERLY);

@@ -415,7 +415,8 @@ struct skm_ctx {
   int32_t* w2;
   // counters
   unsigned long long* cnt;   // device [C_NUM]
-  unsigned long long* fbar;  // device [2]: k_finish_fused's barrier and last-block counters (only grow)
+  unsigned long long* fbar;  // device [3]: k_finish_fused's barrier and last-block counters, k_drift_hsel's
+                             // last-block counter (all only grow)
   unsigned long long* hcnt;  // pinned host mirror [C_NUM]
   double* hobj;              // pinned host [1]
   // per-kernel CUDA-event timing (skm_profile)
