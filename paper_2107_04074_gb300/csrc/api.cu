@@ -202,7 +202,7 @@ void release(skm_ctx* c) {
                   c->dpos,   c->dlist,   c->G,     c->rpart,  c->Xb,     c->Cr,     c->Cb,    c->topv,
                   c->topi,   c->w3,      c->lcount, c->loff,  c->lcursor, c->lmembers, c->cand, c->cand_n,
                   c->exr,    c->ebc,     c->ebw,   c->rsc,    c->gdbeg,  c->gdcnt,  c->gtask,  c->fbar,
-                  c->Ct16,   c->e2p,     c->e2c,   c->escr,   c->w4,     c->hst};
+                  c->Ct16,   c->e2p,     c->e2c,   c->escr,   c->w4,     c->hst,    c->n2l};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -293,6 +293,8 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
   const int64_t kst = c->kst, k = c->k;
   TRY(dalloc(c, &c->Ct, (size_t)(d * kst)));
   TRY(dalloc(c, &c->S64, (size_t)(d * kst)));
+  TRY(dalloc(c, &c->n2l, (size_t)(3 * kst)));
+  SKM_CUDA_TRY(cudaMemsetAsync(c->n2l, 0, sizeof(long long) * 3 * kst, c->st));
   SKM_CUDA_TRY(cudaMemsetAsync(c->S64, 0, sizeof(long long) * d * kst, c->st));
   TRY(dalloc(c, &c->chg_i, (size_t)n));
   TRY(dalloc(c, &c->chg_old, (size_t)n));

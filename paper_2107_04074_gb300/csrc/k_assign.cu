@@ -60,22 +60,6 @@ __device__ __forceinline__ int64_t grab_take(unsigned long long v, unsigned mask
   return (int64_t)__shfl_sync(mask, v, 0, width);
 }
 
-// Four consecutive center values of one term as FP32 (16 B of FP32 or 8 B
-// of FP16 centers).
-template <typename CT>
-__device__ __forceinline__ float4 ld_c4(const CT* p);
-template <>
-__device__ __forceinline__ float4 ld_c4<float>(const float* p) {
-  return __ldg(reinterpret_cast<const float4*>(p));
-}
-template <>
-__device__ __forceinline__ float4 ld_c4<__half>(const __half* p) {
-  const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
-  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
-  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
-  return make_float4(a.x, a.y, b.x, b.y);
-}
-
 // Raw loads of four center values, converted just before the FMAs: FP16
 // centers take half the registers, so twice as many row entries' gathers can
 // be in flight at once.

@@ -958,13 +958,15 @@ __global__ void __launch_bounds__(128) k_dense_cluster_sum(const float* __restri
   S64[t * kst + j] = s;
 }
 
-// Incremental: warp per changed row, -x from the old and +x to the new sum.
+// Incremental: warp per changed row, -x from the old and +x to the new sum;
+// both clusters' exact squared norms take the change of the squares (n2_add).
 __global__ void __launch_bounds__(256) k_dense_delta(const float* __restrict__ X, const float* __restrict__ rinv,
                                                      int64_t d, int64_t kst, const int32_t* __restrict__ chg_i,
                                                      const int32_t* __restrict__ chg_old, const int32_t* __restrict__ a,
                                                      float scale, long long* __restrict__ S64,
                                                      int32_t* __restrict__ dflag, int s64_valid,
-                                                     const unsigned long long* __restrict__ cnt, int64_t n) {
+                                                     const unsigned long long* __restrict__ cnt, int64_t n,
+                                                     long long* __restrict__ n2l) {
   if (full_update(s64_valid, cnt, n)) return;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -976,10 +978,22 @@ __global__ void __launch_bounds__(256) k_dense_delta(const float* __restrict__ X
       dflag[nu] = 1;
     }
     const float ri = rinv[i];
+    __int128 co = 0, cn = 0;
     for (int64_t t = lane; t < d; t += 32) {
       const long long fx = __float2ll_rn(__fmul_rn(__fmul_rn(X[(int64_t)i * d + t], ri), scale));
-      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + old), (unsigned long long)(-fx));
-      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + nu), (unsigned long long)fx);
+      const long long po =
+          (long long)atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + old), (unsigned long long)(-fx));
+      const long long pn =
+          (long long)atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + nu), (unsigned long long)fx);
+      const __int128 sq = (__int128)fx * fx;
+      co += sq - 2 * (__int128)po * fx;
+      cn += sq + 2 * (__int128)pn * fx;
+    }
+    co = warp_sum128(co);
+    cn = warp_sum128(cn);
+    if (lane == 0) {
+      n2_add(n2l, kst, old, co);
+      n2_add(n2l, kst, nu, cn);
     }
   }
 }
@@ -1168,7 +1182,7 @@ int dense_center_sums(skm_ctx* c) {
   SKM_PROF_BEGIN(c, "k_dense_delta");
   k_dense_delta<<<grid_cap(n * 32, 256, c->nsm), 256, 0, c->st>>>((const float*)c->val, c->rinv, c->d, c->kst,
                                                                    c->chg_i, c->chg_old, c->a, c->fx_scale, c->S64,
-                                                                   c->dflag, c->s64_valid, c->cnt, n);
+                                                                   c->dflag, c->s64_valid, c->cnt, n, c->n2l);
   SKM_LAUNCHED(c);
   return SKM_OK;
 }

@@ -180,7 +180,9 @@ __global__ void k_center_sum_multi(int64_t nmulti, const int32_t* __restrict__ m
 
 // Incremental: warp per changed row i (old label -> a[i]); each entry's fixed
 // point value -- the same x = v / |x_i| as the term-major copy -- moves from
-// the old cluster's sum to the new one.  Both clusters become dirty.
+// the old cluster's sum to the new one, and both clusters' squared norms
+// take the change of the entries' squares (n2_add).  Both clusters become
+// dirty.
 template <typename VT>
 __global__ void __launch_bounds__(256) k_center_delta(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                       const VT* __restrict__ val, const float* __restrict__ rinv,
@@ -188,7 +190,8 @@ __global__ void __launch_bounds__(256) k_center_delta(const int64_t* __restrict_
                                                       const int32_t* __restrict__ chg_old, const int32_t* __restrict__ a,
                                                       int64_t kst, float scale, long long* __restrict__ S64,
                                                       int32_t* __restrict__ dflag, int s64_valid,
-                                                      const unsigned long long* __restrict__ cnt, int64_t n) {
+                                                      const unsigned long long* __restrict__ cnt, int64_t n,
+                                                      long long* __restrict__ n2l) {
   if (full_update(s64_valid, cnt, n)) return;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -200,11 +203,23 @@ __global__ void __launch_bounds__(256) k_center_delta(const int64_t* __restrict_
       dflag[nu] = 1;
     }
     const float ri = rinv[i];
+    __int128 co = 0, cn = 0;
     for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
       const int64_t t = col[p];
       const long long fx = to_fixed(__fmul_rn(to_f32(val[p]), ri), scale);
-      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + old), (unsigned long long)(-fx));
-      atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + nu), (unsigned long long)fx);
+      const long long po =
+          (long long)atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + old), (unsigned long long)(-fx));
+      const long long pn =
+          (long long)atomicAdd(reinterpret_cast<unsigned long long*>(S64 + t * kst + nu), (unsigned long long)fx);
+      const __int128 sq = (__int128)fx * fx;
+      co += sq - 2 * (__int128)po * fx;
+      cn += sq + 2 * (__int128)pn * fx;
+    }
+    co = warp_sum128(co);
+    cn = warp_sum128(cn);
+    if (lane == 0) {
+      n2_add(n2l, kst, old, co);
+      n2_add(n2l, kst, nu, cn);
     }
   }
 }
@@ -261,76 +276,93 @@ __global__ void __launch_bounds__(1024) k_dirty(int32_t k, int32_t* __restrict__
 
 // Tile (bx, by) of 256 terms x 32 dirty slots, threads (x, y) = (tid & 31,
 // tid >> 5) of 256: thread (x, y) handles dirty slot 32 by + x and terms
-// t = y, y+8, ... of the tile.  Squares summed in FP32 with a compensation
-// term (Neumaier), accurate to ~2u per thread; threads and tiles combine in
-// FP64.  sh: shared double[8][33].
-__device__ __forceinline__ void dev_colnorm_part(const long long* __restrict__ S64, float inv, int64_t d, int64_t kst,
+// t = y, y+8, ... of the tile.  After a full recomputation of the sums: the
+// exact sum of the squares of the tile's fixed-point values (an __int128,
+// see n2_add) into red as (low, high) words; after an incremental update the
+// squared norms were kept up to date by k_center_delta and there is nothing
+// to do.  sh: shared long long[2][8][33].
+__device__ __forceinline__ void dev_colnorm_part(const long long* __restrict__ S64, int64_t d, int64_t kst,
                                                  const int32_t* __restrict__ dlist, int nd, double* __restrict__ red,
-                                                 int bx, int by, double (*sh)[33]) {
+                                                 int bx, int by, long long (*sh)[8][33], bool full) {
+  if (!full) return;  // the same for the whole block
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int slot = by * 32 + tx;
   const int64_t t0 = (int64_t)bx * kTB;
-  float s = 0.f, comp = 0.f;
+  __int128 acc = 0;
   if (slot < nd) {
     const int j = __ldcg(dlist + slot);
     const int64_t tend = min(d, t0 + kTB);
-    auto add = [&](long long raw) {
-      const float v = from_fixed(raw, inv);
-      const float sq = __fmul_rn(v, v);
-      const float err_sq = __fmaf_rn(v, v, -sq);  // exact low part of v*v
-      const float ns = __fadd_rn(s, sq);
-      comp += (fabsf(s) >= fabsf(sq)) ? ((s - ns) + sq) : ((sq - ns) + s);
-      comp += err_sq;
-      s = ns;
-    };
     int64_t t = t0 + ty;
-    // eight loads in flight, then the sums in the same order
+    // eight loads in flight
     for (; t + 56 < tend; t += 64) {
       long long raw[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) raw[u] = S64[(t + 8 * u) * kst + j];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) add(raw[u]);
+      for (int u = 0; u < 8; ++u) acc += (__int128)raw[u] * raw[u];
     }
-    for (; t < tend; t += 8) add(S64[t * kst + j]);
+    for (; t < tend; t += 8) {
+      const long long v = S64[t * kst + j];
+      acc += (__int128)v * v;
+    }
   }
-  sh[ty][tx] = (double)s + (double)comp;
+  sh[0][ty][tx] = (long long)acc;
+  sh[1][ty][tx] = (long long)(acc >> 64);
   __syncthreads();
   if (ty == 0 && slot < nd) {
-    double r = 0.0;
-    for (int y = 0; y < 8; ++y) r += sh[y][tx];
-    red[(int64_t)bx * kst + slot] = r;
+    __int128 r = 0;
+    for (int y = 0; y < 8; ++y) r += (((__int128)sh[1][y][tx]) << 64) | (unsigned long long)sh[0][y][tx];
+    long long* red64 = reinterpret_cast<long long*>(red);
+    red64[((int64_t)bx * kst + slot) * 2] = (long long)r;
+    red64[((int64_t)bx * kst + slot) * 2 + 1] = (long long)(r >> 64);
   }
   __syncthreads();
 }
 
 // grid (ceil(d/kTB), ceil(k/32)), block 256.
-__global__ void __launch_bounds__(256) k_colnorm_part(const long long* __restrict__ S64, float inv, int64_t d,
-                                                      int64_t kst, const int32_t* __restrict__ dlist,
+__global__ void __launch_bounds__(256) k_colnorm_part(const long long* __restrict__ S64, int64_t d, int64_t kst,
+                                                      const int32_t* __restrict__ dlist,
                                                       const unsigned long long* __restrict__ cnt,
-                                                      double* __restrict__ red) {
-  __shared__ double sh[8][33];
+                                                      double* __restrict__ red, int s64_valid, int64_t n) {
+  __shared__ long long sh[2][8][33];
   const int nd = (int)cnt[C_NDIRTY];
   if ((int)(blockIdx.y * 32) >= nd) return;
-  dev_colnorm_part(S64, inv, d, kst, dlist, nd, red, blockIdx.x, blockIdx.y, sh);
+  dev_colnorm_part(S64, d, kst, dlist, nd, red, blockIdx.x, blockIdx.y, sh, full_update(s64_valid, cnt, n));
 }
 
-// Dirty slot `slot`: |S_j| from the per-tile partials in a fixed order, by
-// the block's first 128 threads.  sh: shared double[128].
+// Dirty slot `slot`: |S_j|^2 exactly -- after a full recomputation the sum
+// of the per-tile partials (by the block's first 128 threads; integer sums,
+// so their order does not matter), else the value the incremental update
+// kept in the limbs -- stored back as limbs in range, and |S_j| = sqrt of it
+// times the fixed-point scale inv.  sh: shared long long[256].
 __device__ __forceinline__ void dev_colnorm_final(const double* __restrict__ red, int64_t nblk, int64_t kst,
                                                   const int32_t* __restrict__ dlist, int slot,
-                                                  double* __restrict__ nrm, double* sh) {
-  const bool on = threadIdx.x < 128;
-  double s = 0.0;
-  if (on)
-    for (int64_t b = threadIdx.x; b < nblk; b += 128) s += __ldcg(red + b * kst + slot);
-  if (on) sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 64; o; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+                                                  double* __restrict__ nrm, long long* sh, long long* __restrict__ n2l,
+                                                  bool full, float inv) {
+  const int j = __ldcg(dlist + slot);
+  __int128 v = 0;
+  if (full) {
+    const long long* red64 = reinterpret_cast<const long long*>(red);
+    const bool on = threadIdx.x < 128;
+    __int128 s = 0;
+    if (on)
+      for (int64_t b = threadIdx.x; b < nblk; b += 128)
+        s += (((__int128)__ldcg(red64 + (b * kst + slot) * 2 + 1)) << 64) |
+             (unsigned long long)__ldcg(red64 + (b * kst + slot) * 2);
+    if (on) {
+      sh[threadIdx.x] = (long long)s;
+      sh[128 + threadIdx.x] = (long long)(s >> 64);
+    }
     __syncthreads();
+    if (threadIdx.x == 0)
+      for (int q = 0; q < 128; ++q) v += (((__int128)sh[128 + q]) << 64) | (unsigned long long)sh[q];
+  } else if (threadIdx.x == 0) {
+    v = n2_get(n2l, kst, j);
   }
-  if (threadIdx.x == 0) nrm[__ldcg(dlist + slot)] = sqrt(sh[0]);
+  if (threadIdx.x == 0) {
+    n2_set(n2l, kst, j, v);
+    nrm[j] = sqrt((double)v) * (double)inv;
+  }
   __syncthreads();
 }
 
@@ -338,10 +370,11 @@ __device__ __forceinline__ void dev_colnorm_final(const double* __restrict__ red
 __global__ void __launch_bounds__(128) k_colnorm_final(const double* __restrict__ red, int64_t nblk, int64_t kst,
                                                        const int32_t* __restrict__ dlist,
                                                        const unsigned long long* __restrict__ cnt,
-                                                       double* __restrict__ nrm) {
-  __shared__ double sh[128];
+                                                       double* __restrict__ nrm, long long* __restrict__ n2l,
+                                                       int s64_valid, int64_t n, float inv) {
+  __shared__ long long sh[256];
   if ((int)blockIdx.x >= (int)cnt[C_NDIRTY]) return;
-  dev_colnorm_final(red, nblk, kst, dlist, blockIdx.x, nrm, sh);
+  dev_colnorm_final(red, nblk, kst, dlist, blockIdx.x, nrm, sh, n2l, full_update(s64_valid, cnt, n), inv);
 }
 
 // Tile (bx, by), threads as dev_colnorm_part.  The dirty centers are
@@ -520,15 +553,6 @@ __device__ __forceinline__ void dev_drift_final(const double* __restrict__ red2,
   __syncthreads();
 }
 
-// Shared memory of dev_hsel_obj: 1024 slots per quantity (a block of fewer
-// threads takes several slots per thread, so the sums run in the order of a
-// 1024-thread block whatever the block size).
-struct HselShared {
-  float pd[1024], pu[1024], q[1024], pd2[1024], pu2[1024], q2[1024];
-  int jd[1024], ju[1024], jq[1024];
-  double J[1024];
-};
-
 // One block: the objective J = sum_j |S_j| (fixed order) and Hamerly's
 // worst-drift summary -- argmin / min / second min of pd and of pu, argmax /
 // max / second max of q, lowest index on ties (Section 5.3: p' is the minimum
@@ -551,78 +575,10 @@ __device__ __forceinline__ void dev_fp16_err_max(const double* __restrict__ e2c,
   __syncthreads();
 }
 
-__device__ __forceinline__ void dev_hsel_obj(const float* __restrict__ pdn, const float* __restrict__ pup,
-                                             const float* __restrict__ qup, const double* __restrict__ nrm,
-                                             int32_t k, float* __restrict__ hsel, double* __restrict__ obj,
-                                             unsigned long long* __restrict__ cnt, HselShared& S,
-                                             const double* __restrict__ e2c, float* __restrict__ escr) {
-  if (threadIdx.x < C_ERR) cnt[threadIdx.x] = 0ull;
-  for (int v = threadIdx.x; v < 1024; v += blockDim.x) {
-    float bd = FLT_MAX, bd2 = FLT_MAX, bu = FLT_MAX, bu2 = FLT_MAX, bq = -FLT_MAX, bq2 = -FLT_MAX;
-    int jd = INT_MAX, ju = INT_MAX, jq = INT_MAX;
-    double J = 0.0;
-    for (int j = v; j < k; j += 1024) {
-      const float x = __ldcg(pdn + j), y = __ldcg(pup + j), z = __ldcg(qup + j);
-      if (x < bd) { bd2 = bd; bd = x; jd = j; } else if (x < bd2) bd2 = x;
-      if (y < bu) { bu2 = bu; bu = y; ju = j; } else if (y < bu2) bu2 = y;
-      if (z > bq) { bq2 = bq; bq = z; jq = j; } else if (z > bq2) bq2 = z;
-      J += __ldcg(nrm + j);
-    }
-    S.pd[v] = bd; S.pd2[v] = bd2; S.jd[v] = jd;
-    S.pu[v] = bu; S.pu2[v] = bu2; S.ju[v] = ju;
-    S.q[v] = bq; S.q2[v] = bq2; S.jq[v] = jq;
-    S.J[v] = J;
-  }
-  __syncthreads();
-  for (int o = 512; o; o >>= 1) {
-    for (int a = threadIdx.x; a < o; a += blockDim.x) {
-      const int b = a + o;
-      if (S.pd[b] < S.pd[a] || (S.pd[b] == S.pd[a] && S.jd[b] < S.jd[a])) {
-        S.pd2[a] = fminf(S.pd2[b], S.pd[a]);
-        S.pd[a] = S.pd[b];
-        S.jd[a] = S.jd[b];
-      } else {
-        S.pd2[a] = fminf(S.pd2[a], S.pd[b]);
-      }
-      if (S.pu[b] < S.pu[a] || (S.pu[b] == S.pu[a] && S.ju[b] < S.ju[a])) {
-        S.pu2[a] = fminf(S.pu2[b], S.pu[a]);
-        S.pu[a] = S.pu[b];
-        S.ju[a] = S.ju[b];
-      } else {
-        S.pu2[a] = fminf(S.pu2[a], S.pu[b]);
-      }
-      if (S.q[b] > S.q[a] || (S.q[b] == S.q[a] && S.jq[b] < S.jq[a])) {
-        S.q2[a] = fmaxf(S.q2[b], S.q[a]);
-        S.q[a] = S.q[b];
-        S.jq[a] = S.jq[b];
-      } else {
-        S.q2[a] = fmaxf(S.q2[a], S.q[b]);
-      }
-      S.J[a] += S.J[b];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    // with a single center there is no "other" center: no drift to account for
-    const bool one = (k == 1);
-    hsel[0] = (float)S.jd[0];
-    hsel[1] = S.pd[0];
-    hsel[2] = one ? 1.f : S.pd2[0];
-    hsel[3] = (float)S.ju[0];
-    hsel[4] = S.pu[0];
-    hsel[5] = one ? 1.f : S.pu2[0];
-    hsel[6] = (float)S.jq[0];
-    hsel[7] = S.q[0];
-    hsel[8] = one ? 0.f : S.q2[0];
-    obj[0] = S.J[0];
-  }
-  __syncthreads();
-  if (e2c) dev_fp16_err_max(e2c, k, escr, S.J);
-}
-
-// The same results with 256 slots for the minima and maxima (which do not
-// depend on the order they are combined in: values, then the lowest index on
-// ties) and the 1024-slot order for J, for a 256-thread block.
+// dev_hsel_obj_256 (a 256-thread block) computes it: 256 slots for the minima
+// and maxima (which do not depend on the order they are combined in: values,
+// then the lowest index on ties) and 1024 slots for J (slot v sums centers
+// v, v + 1024, ...; then a fixed tree).
 struct HselSmall {
   float pd[256], pu[256], q[256], pd2[256], pu2[256], q2[256];
   int jd[256], ju[256], jq[256];
@@ -699,7 +655,7 @@ __device__ __forceinline__ void dev_hsel_obj_256(const float* __restrict__ pdn, 
 
 // The drift per center and the summary in one launch: block per center (grid
 // kst, 256 threads) for the drift, then the last block to finish writes J and
-// Hamerly's summary (dev_hsel_obj's results, bit for bit).  done: a counter
+// Hamerly's summary (dev_hsel_obj_256).  done: a counter
 // that only grows, so launches and graph replays need no reset.
 __global__ void __launch_bounds__(256) k_drift_hsel(const double* __restrict__ red2, int64_t nblk, int32_t k,
                                                     int64_t kst, int64_t d, const int32_t* __restrict__ dmark,
@@ -795,8 +751,10 @@ __global__ void __launch_bounds__(256) k_finish_fused(int32_t k, int64_t kst, in
                                                       double* __restrict__ obj, unsigned long long* __restrict__ cnt,
                                                       unsigned long long* __restrict__ bar, __half* __restrict__ Ct16,
                                                       double* __restrict__ e2p, double* __restrict__ e2c,
-                                                      float* __restrict__ escr) {
+                                                      float* __restrict__ escr, long long* __restrict__ n2l) {
   __shared__ union {
+    long long cn[2][8][33];
+    long long cf[256];
     double part[4][8][33];
     double fin[4][128];
     HselSmall hs;
@@ -818,9 +776,10 @@ __global__ void __launch_bounds__(256) k_finish_fused(int32_t k, int64_t kst, in
   const int ngroups = (nd + 31) / 32;
   const int64_t ntile = nblk * ngroups;
   for (int64_t w = blockIdx.x; w < ntile; w += gridDim.x)
-    dev_colnorm_part(S64, inv, d, kst, dlist, nd, red, (int)(w % nblk), (int)(w / nblk), sm.part[0]);
+    dev_colnorm_part(S64, d, kst, dlist, nd, red, (int)(w % nblk), (int)(w / nblk), sm.cn, full);
   if (!grid_barrier(bar, b0, 2, cnt, &ok_sh)) return;
-  for (int slot = blockIdx.x; slot < nd; slot += gridDim.x) dev_colnorm_final(red, nblk, kst, dlist, slot, nrm, sm.fin[0]);
+  for (int slot = blockIdx.x; slot < nd; slot += gridDim.x)
+    dev_colnorm_final(red, nblk, kst, dlist, slot, nrm, sm.cf, n2l, full, inv);
   if (!grid_barrier(bar, b0, 3, cnt, &ok_sh)) return;
   for (int64_t w = blockIdx.x; w < ntile; w += gridDim.x)
     dev_normalize_drift(S64, inv, Ct, nrm, d, kst, dlist, nd, red, (int)(w % nblk), (int)(w / nblk), sm.part, Ct16,
@@ -1005,7 +964,7 @@ __global__ void __launch_bounds__(256) k_gram_final(const double* __restrict__ G
 // ---------------------------------------------------------------- batches
 
 // Block per run: Hamerly's worst-drift summary over the run's own centers
-// koff .. koff + k - 1 (global ids), the rule of dev_hsel_obj.
+// koff .. koff + k - 1 (global ids), the rule of dev_hsel_obj_256.
 __global__ void __launch_bounds__(256) k_hsel_runs(const float* __restrict__ pdn, const float* __restrict__ pup,
                                                    const float* __restrict__ qup, const RunDesc* __restrict__ runs,
                                                    float* __restrict__ hsel) {
@@ -1272,7 +1231,7 @@ int center_delta_t(skm_ctx* c) {
   SKM_PROF_BEGIN(c, "k_center_delta");
   k_center_delta<VT><<<grid_cap(c->n * 32, 256, c->nsm), 256, 0, c->st>>>(
       c->rp, c->col, (const VT*)c->val, c->rinv, c->chg_i, c->chg_old, c->a, c->kst, c->fx_scale, c->S64, c->dflag,
-      c->s64_valid, c->cnt, c->n);
+      c->s64_valid, c->cnt, c->n, c->n2l);
   SKM_LAUNCHED(c);
   return SKM_OK;
 }
@@ -1447,7 +1406,7 @@ int finish_update(skm_ctx* c) {
     SKM_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_finish_fused, k, (int64_t)c->kst, c->d, nblk, c->fx_inv, s64_was_valid,
                                     c->n, c->dflag, c->dmark, c->dpos, c->dlist, (const long long*)c->S64, c->Ct,
                                     c->nrm, c->red, c->pdn, c->pup, c->qup, cnorm, c->hsel, c->obj, c->cnt,
-                                    c->fbar, c->Ct16, c->e2p, c->e2c, c->escr));
+                                    c->fbar, c->Ct16, c->e2p, c->e2c, c->escr, c->n2l));
     SKM_LAUNCHED(c);
   } else {
     SKM_PROF_BEGIN(c, "k_dirty");
@@ -1456,10 +1415,11 @@ int finish_update(skm_ctx* c) {
     // ---- norms, new centers and drift of the dirty clusters
     dim3 grid((unsigned)nblk, (unsigned)((k + 31) / 32));
     SKM_PROF_BEGIN(c, "k_colnorm_part");
-    k_colnorm_part<<<grid, 256, 0, c->st>>>(c->S64, c->fx_inv, c->d, c->kst, c->dlist, c->cnt, c->red);
+    k_colnorm_part<<<grid, 256, 0, c->st>>>(c->S64, c->d, c->kst, c->dlist, c->cnt, c->red, s64_was_valid, c->n);
     SKM_LAUNCHED(c);
     SKM_PROF_BEGIN(c, "k_colnorm_final");
-    k_colnorm_final<<<k, 128, 0, c->st>>>(c->red, nblk, c->kst, c->dlist, c->cnt, c->nrm);
+    k_colnorm_final<<<k, 128, 0, c->st>>>(c->red, nblk, c->kst, c->dlist, c->cnt, c->nrm, c->n2l, s64_was_valid,
+                                          c->n, c->fx_inv);
     SKM_LAUNCHED(c);
     SKM_PROF_BEGIN(c, "k_normalize_drift");
     k_normalize_drift<<<grid, 256, 0, c->st>>>(c->S64, c->fx_inv, c->Ct, c->nrm, c->d, c->kst, c->dlist, c->cnt,

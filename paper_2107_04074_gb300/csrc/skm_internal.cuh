@@ -198,6 +198,52 @@ __device__ __forceinline__ float bound_u_hamerly(float u, float pd_min, float pu
   return bound_u(u, pd_min, pu_min, q_max);
 }
 
+// ---- squared norms of the sums, exactly
+// S64 holds fixed-point values S = x 2^s with the scale chosen so that the
+// squared norm of a cluster's column, at most (n_j 2^s)^2 < 2^124, fits an
+// __int128, as does every partial sum of it: the squared norm is an integer
+// computed exactly, whatever the order of the additions.  The full
+// recomputation sums the squares of the dirty columns (the colnorm pass);
+// the incremental update adds, for every entry a moved row touches, the
+// change of its square, (S + x)^2 - S^2 = 2 S x + x^2 from the value S its
+// atomic add replaced (these changes telescope to the exact new value, in
+// any order of the atomics).  Both give the same bits.  A cluster's running
+// value is kept as three limbs, n2l[j] + n2l[kst + j] 2^42 + n2l[2 kst + j]
+// 2^84, so that 64-bit atomics can add to it (each added piece below 2^42
+// in magnitude); the norm pass carries them back into range once per
+// update.
+constexpr int kLimb = 42;
+
+__device__ __forceinline__ void n2_add(long long* __restrict__ n2l, int64_t kst, int32_t j, __int128 c) {
+  const long long mask = (1ll << kLimb) - 1;
+  const long long c0 = (long long)c & mask;
+  const long long c1 = (long long)(c >> kLimb) & mask;
+  const long long c2 = (long long)(c >> (2 * kLimb));
+  atomicAdd(reinterpret_cast<unsigned long long*>(n2l + j), (unsigned long long)c0);
+  atomicAdd(reinterpret_cast<unsigned long long*>(n2l + kst + j), (unsigned long long)c1);
+  atomicAdd(reinterpret_cast<unsigned long long*>(n2l + 2 * kst + j), (unsigned long long)c2);
+}
+__device__ __forceinline__ __int128 n2_get(const long long* __restrict__ n2l, int64_t kst, int32_t j) {
+  return (__int128)__ldcg(n2l + j) + ((__int128)__ldcg(n2l + kst + j) << kLimb) +
+         ((__int128)__ldcg(n2l + 2 * kst + j) << (2 * kLimb));
+}
+__device__ __forceinline__ void n2_set(long long* __restrict__ n2l, int64_t kst, int32_t j, __int128 v) {
+  const long long mask = (1ll << kLimb) - 1;
+  n2l[j] = (long long)v & mask;
+  n2l[kst + j] = (long long)(v >> kLimb) & mask;
+  n2l[2 * kst + j] = (long long)(v >> (2 * kLimb));
+}
+// A warp's sum of one __int128 per lane (every lane gets it).
+__device__ __forceinline__ __int128 warp_sum128(__int128 v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long lo = __shfl_xor_sync(SKM_FULL_MASK, (unsigned long long)v, o);
+    const long long hi = __shfl_xor_sync(SKM_FULL_MASK, (long long)(v >> 64), o);
+    v += (((__int128)hi) << 64) | lo;
+  }
+  return v;
+}
+
 // Append (i, old) to the changed-row list through a per-warp buffer: lane r
 // holds the r-th pending entry; the warp flushes 32 at a time with one atomic.
 // All arguments but the buffer are warp-uniform.
@@ -338,6 +384,7 @@ struct skm_ctx {
   int64_t* t_ptr;      // [d+1] term-major (CSC) offsets
   int32_t* t_row;      // [nnz]
   int32_t* hst;        // [4] Hamerly: skip tightening this iteration, iterations skipped, blocks done
+  long long* n2l;      // [3 kst] exact squared norms of the cluster sums as 42-bit limbs
   int32_t scr_off;     // 1: the screened whole-row pass is not used although Ct16 is kept (skm_autotune)
   void* t_val;         // [nnz] dtype
   int64_t nchunks;     // center-sum work items
