@@ -90,14 +90,18 @@ __device__ __forceinline__ float warp_dot_dense_col(const VT* __restrict__ x, in
 // row keeps its best similarity (m, the seeding's own maximum), the lowest
 // center index reaching it (best) and the second best (second, the largest
 // of the others: equal to m on a tie); Elkan's u(i,j) = s_ij + delta_i
-// rounded up goes to uelk (row stride ustride).
+// rounded up goes to uelk[i si + j sj]: a center-major staging array (si = 1,
+// sj = n: the pass over center j writes one contiguous row, coalesced), later
+// transposed into the row-major bounds, or the bounds themselves (si = their
+// row stride, sj = 1) when the staging array would exceed kSeedStageBytes.
 struct SeedTrack {
   int32_t* best;
   float* second;
   float* uelk;
-  int64_t ustride;
+  int64_t si, sj;
   const float* dlt;
 };
+constexpr int64_t kSeedStageBytes = int64_t(2) << 30;
 
 __device__ __forceinline__ void seed_track(const SeedTrack& tr, int64_t i, int j, float sim, float m_old) {
   if (!tr.best) return;
@@ -110,7 +114,7 @@ __device__ __forceinline__ void seed_track(const SeedTrack& tr, int64_t i, int j
   } else if (sim > tr.second[i]) {
     tr.second[i] = sim;
   }
-  if (tr.uelk) tr.uelk[i * tr.ustride + j] = __fadd_ru(sim, tr.dlt[i]);
+  if (tr.uelk) tr.uelk[i * tr.si + j * tr.sj] = __fadd_ru(sim, tr.dlt[i]);
 }
 
 template <typename VT>
@@ -272,6 +276,23 @@ __global__ void __launch_bounds__(1024) k_seed_pick(const long long* __restrict_
   }
 }
 
+// The staged bounds (center-major, k x n) into the row-major bound array
+// (n x kst): 32 x 32 tiles through shared memory, both sides coalesced.
+__global__ void k_seed_stage_out(const float* __restrict__ ucol, int64_t n, int32_t k, int64_t kst,
+                                 float* __restrict__ ub) {
+  __shared__ float tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t j = j0 + r, i = i0 + threadIdx.x;
+    if (j < k && i < n) tile[r][threadIdx.x] = ucol[j * n + i];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int64_t i = i0 + r, j = j0 + threadIdx.x;
+    if (i < n && j < k) ub[i * kst + j] = tile[threadIdx.x][r];
+  }
+}
+
 // Thread per row: the first assignment from the seeding's similarities, as
 // k_rows_top2 leaves it (no label was current, so every label changes):
 // a(i) = best, l(i) = s1 - delta rounded down, Hamerly's u(i) = s2 + delta
@@ -311,13 +332,24 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host, SeedFirst* first) {
   SKM_CUDA_TRY(cudaMallocAsync((void**)&q, sizeof(long long) * n, c->st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&bsum, sizeof(long long) * nblk, c->st));
   SKM_CUDA_TRY(cudaMallocAsync((void**)&rows, sizeof(int64_t) * k, c->st));
-  SeedTrack tr = {nullptr, nullptr, nullptr, 0, nullptr};
+  SeedTrack tr = {nullptr, nullptr, nullptr, 0, 0, nullptr};
+  float* ucol = nullptr;  // center-major staging of Elkan's bounds
   if (first) {
     SKM_CUDA_TRY(cudaMallocAsync((void**)&tr.best, sizeof(int32_t) * n, c->st));
     SKM_CUDA_TRY(cudaMallocAsync((void**)&tr.second, sizeof(float) * n, c->st));
     if (first->elkan) {
-      tr.uelk = c->ub;
-      tr.ustride = kst;
+      if ((int64_t)sizeof(float) * k * n <= kSeedStageBytes &&
+          cudaMallocAsync((void**)&ucol, sizeof(float) * k * n, c->st) == cudaSuccess) {
+        tr.uelk = ucol;
+        tr.si = 1;
+        tr.sj = n;
+      } else {
+        (void)cudaGetLastError();
+        ucol = nullptr;
+        tr.uelk = c->ub;
+        tr.si = kst;
+        tr.sj = 1;
+      }
     }
     tr.dlt = c->dlt;
   }
@@ -347,6 +379,12 @@ int seed_t(skm_ctx* c, const double* u, int64_t* rows_host, SeedFirst* first) {
     SKM_LAUNCH_CHECK();
   }
   SKM_CUDA_TRY(cudaMemcpyAsync(rows_host, rows, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, c->st));
+  if (ucol) {
+    k_seed_stage_out<<<dim3((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32)), dim3(32, 8), 0, c->st>>>(
+        ucol, n, k, kst, c->ub);
+    SKM_LAUNCH_CHECK();
+    cudaFreeAsync(ucol, c->st);
+  }
   if (first) {
     // handed to seed_finish, which frees them
     first->m = m;
