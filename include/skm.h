@@ -50,9 +50,9 @@ extern "C" {
 /* ---- enumerations ---- */
 /* Variants (Section 5): standard Lloyd; Hamerly (5.3 + center test 5.4);
  * Elkan (5.2); Simplified Hamerly (5.4, no center test); Simplified Elkan
- * (5.1, no center-center tests); Yin-Yang group bounds (5.5, CSR data only:
- * one upper bound per group of 8 consecutive centers, moved by the group's
- * worst drift). */
+ * (5.1, no center-center tests); Yin-Yang group bounds (5.5, CSR data only,
+ * k <= 1024: one upper bound per group of 8 consecutive centers, moved by the
+ * group's worst drift). */
 typedef enum {
   SKM_STANDARD = 0,
   SKM_HAMERLY = 1,

@@ -447,6 +447,8 @@ int skm_init(skm_ctx** out, const skm_data* x, int32_t k, int32_t variant, const
   if (!x->values || (x->layout == SKM_CSR && (!x->row_ptr || !x->col_idx))) return SKM_EINVAL;
   if (x->d > INT32_MAX || x->n > INT32_MAX) return SKM_EUNSUPPORTED;
   if ((variant == SKM_ELKAN || variant == SKM_SIMP_ELKAN) && k > 4096) return SKM_EUNSUPPORTED;
+  // Yin-Yang keeps a row's similarities of one pass over the row (up to 1024 centers) for its group bounds
+  if (variant == SKM_YINYANG && k > 1024) return SKM_EUNSUPPORTED;
   // the sparse kernels address the term-major centers with 32-bit offsets:
   // d round8(k) < 2^32 (a center table below 16 GB)
   if (x->layout == SKM_CSR && x->d * (((int64_t)k + 7) / 8 * 8) >= (int64_t(1) << 32)) return SKM_EUNSUPPORTED;

@@ -52,7 +52,7 @@ def test_unsupported_combinations_rejected_without_the_gpu():
     """Combinations the library does not offer are refused before any CUDA
     call: dense rows with Elkan or Yin-Yang or non-FP32 values, the BF16
     precision form with d not a multiple of 8 (FP8: 16) or an unknown
-    precision, Elkan with k > 4096, a CSR center table of 16 GB or more, a
+    precision, Elkan with k > 4096, Yin-Yang with k > 1024, a CSR center table of 16 GB or more, a
     tile of centers that is not 128, 256, 512 or 1024 (or any tile for
     Yin-Yang, dense rows or a batch), and the batched form with Yin-Yang
     bounds or with a malformed run table."""
@@ -88,6 +88,7 @@ def test_unsupported_combinations_rejected_without_the_gpu():
     opt.precision = 7
     assert init(data(skm.DENSE, d=32), 3, V["standard"], opt) == skm.EINVAL  # no such precision
     assert init(data(skm.CSR, n=5000), 4097, V["elkan"]) == skm.EUNSUPPORTED
+    assert init(data(skm.CSR, n=5000), 1025, V["yinyang"]) == skm.EUNSUPPORTED  # one pass over a row
     assert init(data(skm.CSR, n=5000, d=2 ** 22), 1024, V["standard"]) == skm.EUNSUPPORTED  # Ct of 16 GB
     topt = skm.skm_options()
     lib.skm_default_options(ctypes.byref(topt))
