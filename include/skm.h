@@ -261,7 +261,9 @@ int skm_get_bf16_topk(skm_ctx* ctx, float* vals, int32_t* idx, float* eps, int32
  * (host int32[nruns], 1 <= ks[r] <= rows of the run, <= 4096).  init_rows:
  * host int64[sum ks], for each run in order ks[r] distinct row indices local
  * to the run, or NULL to draw them from seed (run r uses seed + r).
- * Variants: all but SKM_YINYANG (SKM_EUNSUPPORTED).  Hamerly's worst drift
+ * Every variant; Yin-Yang only with ks[r] <= 512 for every run (its group
+ * bounds, one per 8 consecutive centers of a run, come from one pass over
+ * the run's centers; else SKM_EUNSUPPORTED).  Hamerly's worst drift
  * p' (Section 5.3) is taken per run over the run's own centers, and the full
  * variants keep each run's own center-center bounds cc and s (Section 5.2):
  * the Gram is block-diagonal, one k_r x k_r block per run, whose rows and

@@ -391,9 +391,9 @@ int build_ctx(skm_ctx* c, const skm_data* x, const int64_t* init_rows, uint64_t 
     TRY(dalloc(c, &c->lb, (size_t)n));
     int64_t ucount = elk ? n * kst : yy ? n * ((k + 7) / 8) : n;
     if (yy) TRY(dalloc(c, &c->gdrift, (size_t)(3 * ((k + 7) / 8))));
-    if (elk && c->nruns > 0) {
+    if ((elk || yy) && c->nruns > 0) {
       const auto& R = *static_cast<std::vector<RunDesc>*>(c->hruns);
-      ucount = R.back().uoff + R.back().n * R.back().kst;
+      ucount = R.back().uoff + R.back().n * (yy ? R.back().kst / 8 : R.back().kst);
     }
     TRY(dalloc(c, &c->ub, (size_t)ucount));
     TRY(dalloc(c, &c->w1, (size_t)n));
@@ -513,7 +513,6 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
   if (opt && opt->k_tile != 0) return SKM_EUNSUPPORTED;  // a batch walks every run's slice 128 centers at a time
   if (x->layout != SKM_CSR) return SKM_EUNSUPPORTED;
   if (variant < SKM_STANDARD || variant > SKM_YINYANG) return SKM_EINVAL;
-  if (variant == SKM_YINYANG) return SKM_EUNSUPPORTED;
   if (x->dtype < SKM_F32 || x->dtype > SKM_BF16) return SKM_EINVAL;
   if (x->memspace != SKM_DEVICE && x->memspace != SKM_HOST) return SKM_EINVAL;
   if (!x->values || !x->row_ptr || !x->col_idx) return SKM_EINVAL;
@@ -526,6 +525,7 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
     const int64_t nr = run_rows[r + 1] - run_rows[r];
     if (nr < 1 || ks[r] < 1 || ks[r] > nr) return SKM_EINVAL;
     if (ks[r] > 4096) return SKM_EUNSUPPORTED;
+    if (variant == SKM_YINYANG && ks[r] > 512) return SKM_EUNSUPPORTED;  // group bounds from one pass
     RunDesc& d = R[(size_t)r];
     d.row0 = run_rows[r];
     d.n = nr;
@@ -537,7 +537,7 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
     int32_t cap = opt && opt->row_threshold > 0 ? opt->row_threshold : (ks[r] + 7) / 8;
     d.cap = cap > 7 ? 7 : cap;
     koff += d.kst;
-    uoff += nr * d.kst;
+    uoff += nr * (variant == SKM_YINYANG ? d.kst / 8 : d.kst);  // Elkan: a bound per center; Yin-Yang: per group
     ccoff += (int64_t)d.k * d.kst;
     if (d.kst > kmax) kmax = d.kst;
   }

@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
         ok[g] = (j0 + g * 128 + lane * 4) < kr;
         if (MODE == 3) {
           const int grp = (j0 + g * 128 + lane * 4) >> 3;
-          live[g] = ok[g] && (cur < 0 || grp == (cur >> 3) || __ldg(ub + (int64_t)grp * ustride + i) > L3);
+          const int64_t ya = BATCH ? rg.ybase + (int64_t)grp * rg.ystride : (int64_t)grp * ustride + i;
+          live[g] = ok[g] && (cur < 0 || grp == (cur >> 3) || __ldg(ub + ya) > L3);
           ok[g] = live[g];
         }
       }
@@ -358,8 +359,8 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
         for (int c = 0; c < 4; ++c)
           if (jb + c != nb) m = fmaxf(m, sv[g][c]);
         m = fmaxf(m, __shfl_xor_sync(SKM_FULL_MASK, m, 1));
-        if (live[g] && (lane & 1) == 0)
-          ub[(int64_t)(jb >> 3) * ustride + i] = (m == -INFINITY) ? -1.f : __fadd_ru(m, dl);
+        const int64_t ya = BATCH ? rg.ybase + (int64_t)(jb >> 3) * rg.ystride : (int64_t)(jb >> 3) * ustride + i;
+        if (live[g] && (lane & 1) == 0) ub[ya] = (m == -INFINITY) ? -1.f : __fadd_ru(m, dl);
       }
 #pragma unroll
       for (int o = 16; o; o >>= 1) live_cnt += __shfl_xor_sync(SKM_FULL_MASK, live_cnt, o);
@@ -558,12 +559,17 @@ __global__ void k_yy_drift(int32_t k, int32_t ng, const float* __restrict__ pdn,
 // the clamped Eq. (eqn:u-elkan) for every group bound with the group's worst
 // drift (the update grows as the drift grows, so it bounds every center of
 // the group), then the global test l - 2 delta >= max_G u(i,G).  Group bounds
-// are group-major (ug[G * n + i]).  Survivors go to w1.
+// are group-major (ug[G * n + i]; in a batch each run has its own block,
+// ug[uoff + G n_r + (i - row0)], and its groups are the global groups
+// koff / 8 ...).  Survivors go to w1.
+template <bool BATCH>
 __global__ void __launch_bounds__(kBlock) k_yy_bounds(int64_t n, int32_t ng, const int32_t* __restrict__ a,
                                                       float* __restrict__ lb, float* __restrict__ ug,
                                                       const float* __restrict__ dlt, const float* __restrict__ pdn,
                                                       const float* __restrict__ pup, const float* __restrict__ qup,
                                                       const float* __restrict__ gd, int moved,
+                                                      const int32_t* __restrict__ row_run,
+                                                      const RunDesc* __restrict__ runs,
                                                       int32_t* __restrict__ w1, unsigned long long* __restrict__ cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -576,12 +582,23 @@ __global__ void __launch_bounds__(kBlock) k_yy_bounds(int64_t n, int32_t ng, con
         l = bound_l(l, pdn[ai], pup[ai], qup[ai]);
         lb[i] = l;
       }
+      // this row's groups: all ng of a single run, or its run's own
+      int32_t g0 = 0, ngr = ng;
+      int64_t yb = i, ys = n;
+      if (BATCH) {
+        const RunDesc& R = runs[row_run[i]];
+        g0 = R.koff >> 3;
+        ngr = (R.k + 7) >> 3;
+        yb = R.uoff + (i - R.row0);
+        ys = R.n;
+      }
       float umax = -INFINITY;
-      for (int g = 0; g < ng; ++g) {
-        float u = ug[(int64_t)g * n + i];
+      for (int g = 0; g < ngr; ++g) {
+        float u = ug[yb + (int64_t)g * ys];
         if (moved) {
-          u = bound_u(u, gd[g], gd[ng + g], gd[2 * ng + g]);
-          ug[(int64_t)g * n + i] = u;
+          const int gg = g0 + g;
+          u = bound_u(u, gd[gg], gd[ng + gg], gd[2 * ng + gg]);
+          ug[yb + (int64_t)g * ys] = u;
         }
         umax = fmaxf(umax, u);
       }
@@ -1110,6 +1127,23 @@ int launch_rows_b(skm_ctx* c, int mode, const int32_t* list, const unsigned long
   return SKM_OK;
 }
 
+// Yin-Yang in a batch: the whole-row kernel with four groups of 128 centers,
+// one pass over every run's row (runs of at most 512 centers).
+template <typename VT>
+int launch_rows_yy_batch(skm_ctx* c, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows,
+                         int cursor) {
+  const void* kern = (const void*)k_rows_top2<VT, float, 4, 3, true>;
+  int64_t g = persistent_grid(c, kern);
+  if (!list && g > (nrows * 32 + kBlock - 1) / kBlock) g = (nrows * 32 + kBlock - 1) / kBlock;
+  if (g < 1) g = 1;
+  SKM_PROF_BEGIN(c, list ? "k_rows_top2(list)" : "k_rows_top2");
+  k_rows_top2<VT, float, 4, 3, true><<<(unsigned)g, kBlock, 0, c->st>>>(
+      c->rp, c->col, (const VT*)c->val, c->rinv, c->dlt, c->Ct, c->k, c->kst, c->row_run, c->runs, list, list_cnt,
+      nrows, c->n, c->a, c->lb, c->ub, c->chg_i, c->chg_old, c->cnt, c->cnt + cursor, c->escr, c->w3, c->w4);
+  SKM_LAUNCHED(c);
+  return SKM_OK;
+}
+
 template <typename VT, int G>
 int launch_rows(skm_ctx* c, int mode, const int32_t* list, const unsigned long long* list_cnt, int64_t nrows,
                 int cursor) {
@@ -1121,6 +1155,9 @@ int assign_full_t(skm_ctx* c, int mode, const int32_t* list, const unsigned long
                   int cursor = C_CURSOR) {
   const int k = c->k;
   // a batch walks each row's own slice 128 centers at a time
+  // (Yin-Yang in a batch: every run has at most 512 centers, walked in one
+  // pass, which its group bounds need)
+  if (c->nruns > 0 && mode == 3) return launch_rows_yy_batch<VT>(c, list, list_cnt, nrows, cursor);
   if (c->nruns > 0) return launch_rows_b<VT, 1, true>(c, mode, list, list_cnt, nrows, cursor);
   // centers per pass over a row: the chosen tile, else the smallest that holds k
   const int kt = c->opt.k_tile > 0 ? c->opt.k_tile : k <= 128 ? 128 : k <= 256 ? 256 : k <= 512 ? 512 : 1024;
@@ -1249,16 +1286,21 @@ int elkan_step_t(skm_ctx* c) {
 
 template <typename VT>
 int yinyang_step_t(skm_ctx* c) {
-  const int g = persistent_grid(c, (const void*)k_yy_bounds);
-  const int32_t ng = (c->k + 7) / 8;
+  const bool batch = c->nruns > 0;
+  const int g = persistent_grid(c, batch ? (const void*)k_yy_bounds<true> : (const void*)k_yy_bounds<false>);
+  const int32_t ng = (c->k + 7) / 8;  // a batch: every run's slice, each a whole number of groups
   if (c->moved) {
     SKM_PROF_BEGIN(c, "k_yy_drift");
     k_yy_drift<<<(ng + 127) / 128, 128, 0, c->st>>>(c->k, ng, c->pdn, c->pup, c->qup, c->gdrift);
     SKM_LAUNCHED(c);
   }
   SKM_PROF_BEGIN(c, "k_yy_bounds");
-  k_yy_bounds<<<g, kBlock, 0, c->st>>>(c->n, ng, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup, c->gdrift,
-                                       c->moved, c->w1, c->cnt);
+  if (batch)
+    k_yy_bounds<true><<<g, kBlock, 0, c->st>>>(c->n, ng, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup,
+                                               c->gdrift, c->moved, c->row_run, c->runs, c->w1, c->cnt);
+  else
+    k_yy_bounds<false><<<g, kBlock, 0, c->st>>>(c->n, ng, c->a, c->lb, c->ub, c->dlt, c->pdn, c->pup, c->qup,
+                                                c->gdrift, c->moved, nullptr, nullptr, c->w1, c->cnt);
   SKM_LAUNCHED(c);
   // the survivors go straight to the group pass: its group test uses the
   // moved (not tightened) l, and a(i)'s own group is always recomputed

@@ -327,6 +327,7 @@ struct RunDesc {
 struct RowGeom {
   int64_t ubase, ccoff;
   int32_t koff, k, cap, kst;
+  int64_t ybase, ystride;  // Yin-Yang in a batch: u(i,G) at ybase + G ystride (the run's group-major block)
 };
 template <bool BATCH>
 __device__ __forceinline__ RowGeom row_geom(int64_t i, int32_t k, int64_t kst, int32_t cap,
@@ -340,6 +341,8 @@ __device__ __forceinline__ RowGeom row_geom(int64_t i, int32_t k, int64_t kst, i
     g.k = k;
     g.cap = cap;
     g.kst = (int32_t)kst;
+    g.ybase = 0;  // single runs address u(i,G) as G n + i
+    g.ystride = 0;
   } else {
     const RunDesc& R = runs[row_run[i]];
     g.ubase = R.uoff + (i - R.row0) * (int64_t)R.kst;
@@ -348,6 +351,8 @@ __device__ __forceinline__ RowGeom row_geom(int64_t i, int32_t k, int64_t kst, i
     g.k = R.k;
     g.cap = R.cap;
     g.kst = R.kst;
+    g.ybase = R.uoff + (i - R.row0);  // Yin-Yang batches lay uoff out per group block
+    g.ystride = R.n;
   }
   return g;
 }

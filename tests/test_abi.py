@@ -101,14 +101,16 @@ def test_unsupported_combinations_rejected_without_the_gpu():
     x = data(skm.CSR)
     ks = np.array([2, 3], np.int32)
 
-    def batch(run_rows, ks, variant):
+    def batch(run_rows, ks, variant, xb=x):
         run_rows = np.asarray(run_rows, np.int64)
-        rc = lib.skm_batch_init(ctypes.byref(h), ctypes.byref(x), run_rows.ctypes.data, ks.ctypes.data, len(ks),
+        rc = lib.skm_batch_init(ctypes.byref(h), ctypes.byref(xb), run_rows.ctypes.data, ks.ctypes.data, len(ks),
                                 variant, None, 0, None, None)
         assert h.value is None
         return rc
 
-    assert batch([0, 4, 10], ks, V["yinyang"]) == skm.EUNSUPPORTED
+    # Yin-Yang in a batch: runs of at most 512 centers (one pass over a row)
+    assert batch([0, 10, 600], np.array([3, 513], np.int32), V["yinyang"], data(skm.CSR, n=600)) == \
+        skm.EUNSUPPORTED
     rr = np.asarray([0, 4, 10], np.int64)
     assert lib.skm_batch_init(ctypes.byref(h), ctypes.byref(x), rr.ctypes.data, ks.ctypes.data, 2, V["standard"],
                               None, 0, ctypes.byref(topt), None) == skm.EUNSUPPORTED  # no tile choice in a batch

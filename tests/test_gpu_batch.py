@@ -43,7 +43,7 @@ def _single(part, k, init, variant, **kw):
     return skm.KMeans(part.n, part.d, dev[0], dev[1], dev[2], int(k), variant=variant, init_rows=init, **kw), dev
 
 
-BATCH_VARIANTS = ["standard", "hamerly", "simp_hamerly", "elkan", "simp_elkan"]
+BATCH_VARIANTS = ["standard", "hamerly", "simp_hamerly", "elkan", "simp_elkan", "yinyang"]
 
 
 @pytest.mark.parametrize("variant", BATCH_VARIANTS)
@@ -72,7 +72,7 @@ def test_batch_equals_single_runs(small_batch, variant):
     b.close()
 
 
-@pytest.mark.parametrize("variant", ["simp_elkan", "elkan", "hamerly"])
+@pytest.mark.parametrize("variant", ["simp_elkan", "elkan", "hamerly", "yinyang"])
 def test_batch_runs_match_oracle(small_batch, variant):
     """Teacher-forced: every run's assignment from the batch's centers equals
     the FP64 oracle's (up to near-ties), and its center update matches."""
@@ -96,6 +96,40 @@ def test_batch_runs_match_oracle(small_batch, variant):
             assert np.max(np.abs(C2[r] - Co)) < 1e-5
             prev[r] = labs[r].copy()
     b.close()
+
+
+def test_yinyang_batch_large_runs():
+    """Yin-Yang in a batch with runs of up to 512 centers (all four 128-center
+    slices of the row kernel, a ragged last group of 8): every run follows its
+    single-run trajectory bit for bit, labels and centers."""
+    cfgs, _ = synth.batch_runs(nruns=4, d=4000, seed=23, n_lo=1500, n_hi=4000, k_choices=(3,))
+    ks = np.array([512, 129, 300, 77], np.int32)
+    parts = [synth.tfidf(c) for c in cfgs]
+    X, run_rows = synth.concat(parts)
+    inits = [synth.init_rows(p.n, int(k), 200 + r) for r, (p, k) in enumerate(zip(parts, ks))]
+    b, keep = _batch(X, run_rows, ks, inits, "yinyang")
+    singles = [_single(p, k, ini, "yinyang") for p, k, ini in zip(parts, ks, inits)]
+    for it in range(15):
+        ch = b.assign()
+        assert ch == sum(s.assign() for s, _ in singles)
+        labs = b.run_labels()
+        for r, (s, _) in enumerate(singles):
+            np.testing.assert_array_equal(labs[r], s.labels(), err_msg=f"run {r} iteration {it}")
+        if ch == 0:
+            break
+        b.update_centers()
+        for s, _ in singles:
+            s.update_centers()
+        C = b.run_centers()
+        for r, (s, _) in enumerate(singles):
+            np.testing.assert_array_equal(C[r], s.centers(), err_msg=f"run {r} iteration {it}")
+    # and the same run as the standard algorithm's
+    st, k2 = _batch(X, run_rows, ks, inits, "standard")
+    yy, k3 = _batch(X, run_rows, ks, inits, "yinyang")
+    assert yy.run(25) == st.run(25)
+    np.testing.assert_array_equal(yy.labels(), st.labels())
+    for h in [b, st, yy] + [s for s, _ in singles]:
+        h.close()
 
 
 @pytest.mark.parametrize("variant", BATCH_VARIANTS)
@@ -155,8 +189,12 @@ def test_autotune_and_cache(small_batch, tmp_path):
 def test_batch_rejections(small_batch):
     parts, X, run_rows, ks, inits = small_batch
     dev = [torch.from_numpy(a).cuda() for a in (X.row_ptr, X.col, X.val)]
+    big = ks.copy()
+    r = int(np.argmax([p.n for p in parts]))
+    big[r] = 513  # Yin-Yang's group bounds come from one pass over at most 512 centers
+    assert parts[r].n >= 513
     with pytest.raises(skm.SkmError):
-        skm.Batch(X.n, X.d, *dev, run_rows, ks, variant="yinyang")
+        skm.Batch(X.n, X.d, *dev, run_rows, big, variant="yinyang")
     bad = ks.copy()
     bad[0] = parts[0].n + 1
     with pytest.raises(skm.SkmError):
