@@ -176,7 +176,10 @@ def measured_peaks(skm, torch):
     """FP32 and FP64 FMA rates from the library's own microbenchmark
     (skm_measure_peak), and the FP8-E4M3 GEMM rate of cuBLAS through
     torch._scaled_mm (8192^3, best of 10; None where this PyTorch lacks it)."""
-    out = {"fp32_fma_tflops": round(skm.measure_peak("fp32"), 1),
+    f32, f32x2 = skm.measure_peak("fp32"), skm.measure_peak("fp32x2")
+    # the FP32 roof: the higher of scalar and packed-pair FMA issue
+    out = {"fp32_fma_tflops": round(max(f32, f32x2), 1), "fp32_fma_scalar_tflops": round(f32, 1),
+           "fp32_fma_packed_tflops": round(f32x2, 1),
            "fp64_fma_tflops": round(skm.measure_peak("fp64"), 2)}
     try:
         N = 8192
@@ -199,7 +202,8 @@ def measured_peaks(skm, torch):
     except Exception as ex:  # noqa: BLE001
         out["fp8_gemm_tflops"] = None
         out["fp8_note"] = f"{type(ex).__name__}: {ex}"[:160]
-    out["how"] = ("fp32/fp64: skm_measure_peak (independent FMA chains on every SM, CUDA events); "
+    out["how"] = ("fp32/fp64: skm_measure_peak (independent FMA chains on every SM, CUDA events; FP32 the "
+                  "higher of scalar and packed fma.rn.f32x2 chains); "
                   "fp8: torch._scaled_mm E4M3 8192^3 -> BF16, best of 10")
     return out
 

@@ -382,13 +382,16 @@ int skm_assign_noalloc(const skm_data* x, int32_t k, const float* centers, int32
 /* Measured peak arithmetic rate of the current GPU (the paper has no
  * counterpart: measurement support for the roofline fractions this library's
  * benchmark reports).  kind SKM_PEAK_FP32_FMA: FP32 FMA, the roof of the SIMT
- * similarity kernels; SKM_PEAK_FP64_FMA: FP64 FMA.  Runs one warm-up and one
+ * similarity kernels; SKM_PEAK_FP64_FMA: FP64 FMA; SKM_PEAK_FP32_FMA2: FP32
+ * FMA issued as packed pairs (fma.rn.f32x2, two FMAs per instruction, each
+ * rounded as one FMA).  Runs one warm-up and one
  * timed launch of a kernel of independent FMA chains on every SM (a few to a
  * few tens of ms) on the given stream, synchronises it, and writes the rate
  * in TFLOP/s (2 FLOP per FMA) to *tflops (host).  SKM_EINVAL for another
  * kind or a NULL pointer. */
 #define SKM_PEAK_FP32_FMA 0
 #define SKM_PEAK_FP64_FMA 1
+#define SKM_PEAK_FP32_FMA2 2
 int skm_measure_peak(int32_t kind, double* tflops, void* stream);
 
 #ifdef __cplusplus

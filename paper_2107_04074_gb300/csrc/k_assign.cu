@@ -63,6 +63,16 @@ __device__ __forceinline__ int64_t grab_take(unsigned long long v, unsigned mask
 // Raw loads of four center values, converted just before the FMAs: FP16
 // centers take half the registers, so twice as many row entries' gathers can
 // be in flight at once.
+// acc += v * c for four center sums (scalar FMAs: packed fma.rn.f32x2 pairs
+// were measured 3 % slower in the whole-row pass, which is bound by its
+// gathers, not by issue).
+__device__ __forceinline__ void fma4(float4& acc, float v, const float4& c) {
+  acc.x = __fmaf_rn(v, c.x, acc.x);
+  acc.y = __fmaf_rn(v, c.y, acc.y);
+  acc.z = __fmaf_rn(v, c.z, acc.z);
+  acc.w = __fmaf_rn(v, c.w, acc.w);
+}
+
 template <typename CT>
 struct RawC4;
 template <>
@@ -220,13 +230,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
 #pragma unroll
           for (int u = 0; u < NB; ++u)
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-              const float4 c4 = Raw::f4(cv[u][g]);
-              acc[g].x = __fmaf_rn(v[u], c4.x, acc[g].x);
-              acc[g].y = __fmaf_rn(v[u], c4.y, acc[g].y);
-              acc[g].z = __fmaf_rn(v[u], c4.z, acc[g].z);
-              acc[g].w = __fmaf_rn(v[u], c4.w, acc[g].w);
-            }
+            for (int g = 0; g < G; ++g) fma4(acc[g], v[u], Raw::f4(cv[u][g]));
         }
         if (q < nq) {
           const int nb = nq - q;  // 1 .. NB - 1 entries left
@@ -247,13 +251,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           for (int u = 0; u < NB; ++u)
             if (u < nb)
 #pragma unroll
-              for (int g = 0; g < G; ++g) {
-                const float4 c4 = Raw::f4(cv[u][g]);
-                acc[g].x = __fmaf_rn(v[u], c4.x, acc[g].x);
-                acc[g].y = __fmaf_rn(v[u], c4.y, acc[g].y);
-                acc[g].z = __fmaf_rn(v[u], c4.z, acc[g].z);
-                acc[g].w = __fmaf_rn(v[u], c4.w, acc[g].w);
-              }
+              for (int g = 0; g < G; ++g) fma4(acc[g], v[u], Raw::f4(cv[u][g]));
         }
       }
 #pragma unroll

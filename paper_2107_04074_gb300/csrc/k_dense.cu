@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, 2) k_dense_top2(const float* __restrict__
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
     issue(0);
-    float acc[8][8];
+    float2 acc[8][4];  // [row][center pair]: packed FMAs, each lane rounded as one FMA
     for (int ci = 0; ci < nch; ++ci) {
       if (ci + 1 < nch) issue(ci + 1);
       else asm volatile("cp.async.commit_group;" ::: "memory");
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256, 2) k_dense_top2(const float* __restrict__
 #pragma unroll
         for (int x = 0; x < 8; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+          for (int y = 0; y < 4; ++y) acc[x][y] = make_float2(0.f, 0.f);
       }
 #pragma unroll 4
       for (int kk = 0; kk < kKC; ++kk) {
@@ -317,11 +317,12 @@ __global__ void __launch_bounds__(256, 2) k_dense_top2(const float* __restrict__
         const float4 b0 = *reinterpret_cast<const float4*>(&Bs[sb][kk][tx * 4]);
         const float4 b1 = *reinterpret_cast<const float4*>(&Bs[sb][kk][64 + tx * 4]);
         const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+        const float2 bv[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                              make_float2(b1.z, b1.w)};
 #pragma unroll
         for (int x = 0; x < 8; ++x)
 #pragma unroll
-          for (int y = 0; y < 8; ++y) acc[x][y] = __fmaf_rn(av[x], bv[y], acc[x][y]);
+          for (int y = 0; y < 4; ++y) acc[x][y] = __ffma2_rn(make_float2(av[x], av[x]), bv[y], acc[x][y]);
       }
       __syncthreads();  // this stage is refilled by the copies of chunk ci + 2
       if (kc != nkc - 1) continue;
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(256, 2) k_dense_top2(const float* __restrict__
         for (int y = 0; y < 8; ++y) {
           const int j = j0 + trow(tx, y);
           if (j < k) {
-            const float s = __fmul_rn(acc[x][y], ri);
+            const float s = __fmul_rn((y & 1) ? acc[x][y >> 1].y : acc[x][y >> 1].x, ri);
             if (j == cur) vc = s;
             if (s > v1) {  // j ascends within a thread: ties keep the lowest index
               v2 = v1;

@@ -14,8 +14,10 @@ def test_measured_peaks_are_plausible():
     fraction of it), and an unknown kind is refused."""
     f32 = skm.measure_peak("fp32")
     f64 = skm.measure_peak("fp64")
+    f32x2 = skm.measure_peak("fp32x2")  # packed pairs: at least the scalar rate's neighbourhood
     assert 20.0 < f32 < 120.0, f32
     assert 0.1 < f64 < f32, f64
+    assert 0.8 * f32 < f32x2 < 250.0, (f32, f32x2)
     import ctypes
     out = ctypes.c_double(0)
     assert skm.load().skm_measure_peak(7, ctypes.byref(out), None) == skm.EINVAL
