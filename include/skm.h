@@ -279,7 +279,9 @@ int skm_batch_init(skm_ctx** out, const skm_data* x, const int64_t* run_rows, co
                    void* stream);
 
 /* Choose, for this context's shape, by timing `iters` iterations per
- * candidate from the initial centers (results do not depend on the choice):
+ * candidate, after 4 * iters untimed ones from the initial centers (the
+ * first iterations recompute nearly every row whatever the setting; results
+ * do not depend on the choice):
  * the launch configuration of the persistent bound and recompute kernels
  * (4, 8 or 16 blocks per SM) with the Elkan whole-row threshold (auto, 2,
  * 7); then, for single CSR runs but Yin-Yang, the whole-row kernel's tile of

@@ -1046,13 +1046,16 @@ int skm_autotune(skm_ctx* c, const char* cache_path, int32_t iters, int32_t* fro
   cudaEvent_t e0, e1;
   SKM_CUDA_TRY(cudaEventCreate(&e0));
   SKM_CUDA_TRY(cudaEventCreate(&e1));
-  // time `iters` iterations from the initial centers under a setting
+  // time `iters` iterations under a setting, after 4 iters untimed ones
+  // from the initial centers: the first iterations send nearly every row to
+  // a whole-row recompute whatever the setting, so they do not tell the
+  // settings apart
   auto timed = [&](int32_t bpsm, int32_t thr, int32_t kt, int32_t so, float* ms) -> int {
     TRY(apply(bpsm, thr, kt, so));
     TRY(start_from_rows(c, init));
-    cudaEventRecord(e0, c->st);
     int rc = SKM_OK;
-    for (int32_t it = 0; it < iters && rc == SKM_OK; ++it) {
+    for (int32_t it = 0; it < 5 * iters && rc == SKM_OK; ++it) {
+      if (it == 4 * iters) cudaEventRecord(e0, c->st);
       rc = skm_assign(c, nullptr);
       if (rc == SKM_OK) rc = skm_update_centers(c, nullptr);
     }
