@@ -386,7 +386,10 @@ int skm_assign_noalloc(const skm_data* x, int32_t k, const float* centers, int32
  * benchmark reports).  kind SKM_PEAK_FP32_FMA: FP32 FMA, the roof of the SIMT
  * similarity kernels; SKM_PEAK_FP64_FMA: FP64 FMA; SKM_PEAK_FP32_FMA2: FP32
  * FMA issued as packed pairs (fma.rn.f32x2, two FMAs per instruction, each
- * rounded as one FMA).  Runs one warm-up and one
+ * rounded as one FMA); SKM_PEAK_L2_GATHER: the rate (TB/s of bytes
+ * gathered) of warps that gather 416-byte rows (26 lanes x 16 B, the
+ * whole-row kernel's center slice at k = 100) at pseudo-random rows of an
+ * L2-resident 20.8 MB table, 16 rows in flight per warp.  Runs one warm-up and one
  * timed launch of a kernel of independent FMA chains on every SM (a few to a
  * few tens of ms) on the given stream, synchronises it, and writes the rate
  * in TFLOP/s (2 FLOP per FMA) to *tflops (host).  SKM_EINVAL for another
@@ -394,6 +397,7 @@ int skm_assign_noalloc(const skm_data* x, int32_t k, const float* centers, int32
 #define SKM_PEAK_FP32_FMA 0
 #define SKM_PEAK_FP64_FMA 1
 #define SKM_PEAK_FP32_FMA2 2
+#define SKM_PEAK_L2_GATHER 3 /* TB/s, not TFLOP/s: see below */
 int skm_measure_peak(int32_t kind, double* tflops, void* stream);
 
 #ifdef __cplusplus

@@ -60,9 +60,6 @@ __device__ __forceinline__ int64_t grab_take(unsigned long long v, unsigned mask
   return (int64_t)__shfl_sync(mask, v, 0, width);
 }
 
-// Raw loads of four center values, converted just before the FMAs: FP16
-// centers take half the registers, so twice as many row entries' gathers can
-// be in flight at once.
 // acc += v * c for four center sums (scalar FMAs: packed fma.rn.f32x2 pairs
 // were measured 3 % slower in the whole-row pass, which is bound by its
 // gathers, not by issue).
@@ -73,6 +70,9 @@ __device__ __forceinline__ void fma4(float4& acc, float v, const float4& c) {
   acc.w = __fmaf_rn(v, c.w, acc.w);
 }
 
+// Raw loads of four center values, converted just before the FMAs: FP16
+// centers take half the registers, so twice as many row entries' gathers can
+// be in flight at once.
 template <typename CT>
 struct RawC4;
 template <>

@@ -130,14 +130,16 @@ def selftest_wait(timeout_ns: int, stream=None) -> int:
     return int(load().skm_selftest_wait(int(timeout_ns), ctypes.c_void_p(stream or 0)))
 
 
-PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_FP32_FMA2 = 0, 1, 2
+PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_FP32_FMA2, PEAK_L2_GATHER = 0, 1, 2, 3
 
 
 def measure_peak(kind: str, stream=None) -> float:
     """Measured FMA rate of the current GPU in TFLOP/s (skm_measure_peak):
-    kind "fp32", "fp64" or "fp32x2" (FP32 FMAs issued as packed pairs)."""
+    kind "fp32", "fp64" or "fp32x2" (FP32 FMAs issued as packed pairs); kind
+    "l2_gather": TB/s of 416-byte rows gathered from an L2-resident table."""
     out = ctypes.c_double(0)
-    code = {"fp32": PEAK_FP32_FMA, "fp64": PEAK_FP64_FMA, "fp32x2": PEAK_FP32_FMA2}[kind]
+    code = {"fp32": PEAK_FP32_FMA, "fp64": PEAK_FP64_FMA, "fp32x2": PEAK_FP32_FMA2,
+            "l2_gather": PEAK_L2_GATHER}[kind]
     _check(load().skm_measure_peak(code, ctypes.byref(out), ctypes.c_void_p(stream or 0)), "skm_measure_peak")
     return out.value
 

@@ -18,6 +18,8 @@ def test_measured_peaks_are_plausible():
     assert 20.0 < f32 < 120.0, f32
     assert 0.1 < f64 < f32, f64
     assert 0.8 * f32 < f32x2 < 250.0, (f32, f32x2)
+    g = skm.measure_peak("l2_gather")  # TB/s of gathered bytes, L2-resident table
+    assert 1.0 < g < 100.0, g
     import ctypes
     out = ctypes.c_double(0)
     assert skm.load().skm_measure_peak(7, ctypes.byref(out), None) == skm.EINVAL
