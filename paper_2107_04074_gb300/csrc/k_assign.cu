@@ -70,6 +70,43 @@ __device__ __forceinline__ void fma4(float4& acc, float v, const float4& c) {
   acc.w = __fmaf_rn(v, c.w, acc.w);
 }
 
+// NB consecutive entries (offsets and values) of a warp's 32-entry buffer in
+// shared memory, read by every lane with broadcast vector loads (one shared
+// wavefront per four entries, against one per entry and array for shuffles).
+// q is a multiple of NB, and NB divides 32.
+template <int NB>
+__device__ __forceinline__ void entries_from_smem(const uint32_t* st, const float* sv, int q, uint32_t (&t)[NB],
+                                                  float (&v)[NB]) {
+  if constexpr (NB % 4 == 0) {
+#pragma unroll
+    for (int x = 0; x < NB / 4; ++x) {
+      const uint4 a = *reinterpret_cast<const uint4*>(st + q + 4 * x);
+      const float4 c = *reinterpret_cast<const float4*>(sv + q + 4 * x);
+      t[4 * x] = a.x;
+      t[4 * x + 1] = a.y;
+      t[4 * x + 2] = a.z;
+      t[4 * x + 3] = a.w;
+      v[4 * x] = c.x;
+      v[4 * x + 1] = c.y;
+      v[4 * x + 2] = c.z;
+      v[4 * x + 3] = c.w;
+    }
+  } else if constexpr (NB == 2) {
+    const uint2 a = *reinterpret_cast<const uint2*>(st + q);
+    const float2 c = *reinterpret_cast<const float2*>(sv + q);
+    t[0] = a.x;
+    t[1] = a.y;
+    v[0] = c.x;
+    v[1] = c.y;
+  } else {
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      t[u] = st[q + u];
+      v[u] = sv[q + u];
+    }
+  }
+}
+
 // Raw loads of four center values, converted just before the FMAs: FP16
 // centers take half the registers, so twice as many row entries' gathers can
 // be in flight at once.
@@ -149,6 +186,12 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
   constexpr int NB = G == 1 ? 16 : (sizeof(CT) == 2 ? 2 : 1) * (G >= 8 ? 1 : 8 / G);
   using Raw = RawC4<CT>;
   const int lane = threadIdx.x & 31;
+  // each warp's current 32 row entries (vector offsets, values), read back by
+  // all lanes with broadcast loads
+  __shared__ __align__(16) uint32_t ent_t[kBlock / 32][32];
+  __shared__ __align__(16) float ent_v[kBlock / 32][32];
+  uint32_t* const et = ent_t[threadIdx.x >> 5];
+  float* const ev = ent_v[threadIdx.x >> 5];
   const int64_t total = list ? (int64_t)(*list_cnt) : nrows;
   unsigned long long my_changed = 0, my_sims = 0;
   ChangedBuf chb;
@@ -202,8 +245,10 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
         vv_n = to_f32(val[b + lane]);
       }
       for (int64_t p0 = b; p0 < e; p0 += 32) {
-        const uint32_t tt = tt_n;
-        const float vv = vv_n;
+        __syncwarp();  // the previous chunk's reads are done
+        et[lane] = tt_n;
+        ev[lane] = vv_n;
+        __syncwarp();
         if (p0 + 32 + lane < e) {
           tt_n = (uint32_t)__ldg(col + p0 + 32 + lane) * kv;
           vv_n = to_f32(val[p0 + 32 + lane]);
@@ -217,11 +262,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           uint32_t t[NB];
           float v[NB];
           typename Raw::type cv[NB][G];
-#pragma unroll
-          for (int u = 0; u < NB; ++u) {
-            t[u] = __shfl_sync(SKM_FULL_MASK, tt, q + u);
-            v[u] = __shfl_sync(SKM_FULL_MASK, vv, q + u);
-          }
+          entries_from_smem<NB>(et, ev, q, t, v);
 #pragma unroll
           for (int u = 0; u < NB; ++u)
 #pragma unroll
@@ -237,11 +278,7 @@ __global__ void __launch_bounds__(kBlock, rows_min_blocks(G)) k_rows_top2(
           uint32_t t[NB];
           float v[NB];
           typename Raw::type cv[NB][G];
-#pragma unroll
-          for (int u = 0; u < NB; ++u) {
-            t[u] = __shfl_sync(SKM_FULL_MASK, tt, q + u);
-            v[u] = __shfl_sync(SKM_FULL_MASK, vv, q + u);
-          }
+          entries_from_smem<NB>(et, ev, q, t, v);  // entries past the row's end are stale; not used
 #pragma unroll
           for (int u = 0; u < NB; ++u)
 #pragma unroll
