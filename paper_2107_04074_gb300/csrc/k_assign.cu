@@ -770,7 +770,8 @@ __global__ void __launch_bounds__(kBlock) k_elk_bounds(int64_t n, int32_t k, int
 template <typename VT>
 __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t* __restrict__ col,
                                             const VT* __restrict__ val, const float* __restrict__ Ct, int64_t kst,
-                                            int my_j, unsigned gmask, int gl) {
+                                            int my_j, unsigned gmask, int gl, uint32_t* __restrict__ gt,
+                                            float* __restrict__ gv) {
   const bool on = my_j >= 0;
   const float* cbase = Ct + (on ? my_j : 0);
   // an entry's term t as the 32-bit offset t kst (d kst < 2^32, checked at
@@ -800,28 +801,57 @@ __device__ __forceinline__ float group8_dot(int64_t b, int64_t e, const int32_t*
       t1 = (uint32_t)__ldg(col + p0 + 24 + gl) * ku;
       v1 = to_f32(val[p0 + 24 + gl]);
     }
+    // the batch's 16 entries through the group's shared buffer (broadcast
+    // vector reads cost less of the load/store path than 32 shuffles)
+    __syncwarp(gmask);
+    gt[gl] = ct0;
+    gt[8 + gl] = ct1;
+    gv[gl] = cv0;
+    gv[8 + gl] = cv1;
+    __syncwarp(gmask);
     float c[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const uint32_t t = __shfl_sync(gmask, q < 8 ? ct0 : ct1, q & 7, 8);
-      c[q] = on ? __ldg(cbase + t) : 0.f;
+    for (int x = 0; x < 4; ++x) {
+      const uint4 t4 = *reinterpret_cast<const uint4*>(gt + 4 * x);
+      c[4 * x] = on ? __ldg(cbase + t4.x) : 0.f;
+      c[4 * x + 1] = on ? __ldg(cbase + t4.y) : 0.f;
+      c[4 * x + 2] = on ? __ldg(cbase + t4.z) : 0.f;
+      c[4 * x + 3] = on ? __ldg(cbase + t4.w) : 0.f;
     }
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc = __fmaf_rn(__shfl_sync(gmask, q < 8 ? cv0 : cv1, q & 7, 8), c[q], acc);
+    for (int x = 0; x < 4; ++x) {
+      const float4 v4 = *reinterpret_cast<const float4*>(gv + 4 * x);
+      acc = __fmaf_rn(v4.x, c[4 * x], acc);
+      acc = __fmaf_rn(v4.y, c[4 * x + 1], acc);
+      acc = __fmaf_rn(v4.z, c[4 * x + 2], acc);
+      acc = __fmaf_rn(v4.w, c[4 * x + 3], acc);
+    }
   }
   // the ragged tail: one more batch whose missing entries load and add nothing
   if (p0 < e) {
     const int nq = (int)(e - p0);
+    __syncwarp(gmask);
+    gt[gl] = t0;  // past the row's end: an earlier entry's offset (or 0), never used
+    gt[8 + gl] = t1;
+    gv[gl] = v0;
+    gv[8 + gl] = v1;
+    __syncwarp(gmask);
     float c[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const uint32_t t = __shfl_sync(gmask, q < 8 ? t0 : t1, q & 7, 8);
-      c[q] = (on && q < nq) ? __ldg(cbase + t) : 0.f;
+    for (int x = 0; x < 4; ++x) {
+      const uint4 t4 = *reinterpret_cast<const uint4*>(gt + 4 * x);
+      c[4 * x] = (on && 4 * x < nq) ? __ldg(cbase + t4.x) : 0.f;
+      c[4 * x + 1] = (on && 4 * x + 1 < nq) ? __ldg(cbase + t4.y) : 0.f;
+      c[4 * x + 2] = (on && 4 * x + 2 < nq) ? __ldg(cbase + t4.z) : 0.f;
+      c[4 * x + 3] = (on && 4 * x + 3 < nq) ? __ldg(cbase + t4.w) : 0.f;
     }
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const float v = __shfl_sync(gmask, q < 8 ? v0 : v1, q & 7, 8);
-      if (q < nq) acc = __fmaf_rn(v, c[q], acc);
+    for (int x = 0; x < 4; ++x) {
+      const float4 v4 = *reinterpret_cast<const float4*>(gv + 4 * x);
+      if (4 * x < nq) acc = __fmaf_rn(v4.x, c[4 * x], acc);
+      if (4 * x + 1 < nq) acc = __fmaf_rn(v4.y, c[4 * x + 1], acc);
+      if (4 * x + 2 < nq) acc = __fmaf_rn(v4.z, c[4 * x + 2], acc);
+      if (4 * x + 3 < nq) acc = __fmaf_rn(v4.w, c[4 * x + 3], acc);
     }
   }
   return acc;
@@ -927,6 +957,8 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
   const unsigned gmask = 0xFFu << (8 * gid);
   const int64_t total = (int64_t)(*w1_cnt);
   __shared__ int slot_j[kBlock / 8][8];  // per group: center of each compacted lane
+  __shared__ __align__(16) uint32_t ent_t[kBlock / 8][16];  // per group: a batch of row entries
+  __shared__ __align__(16) float ent_v[kBlock / 8][16];
   int* sj = slot_j[threadIdx.x >> 3];
   unsigned long long sims = 0, changed = 0;
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
@@ -950,7 +982,9 @@ __global__ void __launch_bounds__(kBlock) k_elk_recompute(
     }
     const int my_j = (gl <= m) ? sj[gl] : -1;
     const float sim = __fmul_rn(
-        group8_dot<VT>(rp[i], rp[i + 1], col, val, Ct, kst, my_j >= 0 ? rg.koff + my_j : -1, gmask, gl), rinv[i]);
+        group8_dot<VT>(rp[i], rp[i + 1], col, val, Ct, kst, my_j >= 0 ? rg.koff + my_j : -1, gmask, gl,
+                       ent_t[threadIdx.x >> 3], ent_v[threadIdx.x >> 3]),
+        rinv[i]);
     elk_decide(i, rg.koff, ai, m, my_j, sim, dl, urow, a, lb, chg_i, chg_old, cnt, gmask, gl, sims, changed);
   }
   __syncwarp();
